@@ -1,0 +1,181 @@
+/*
+ * fsib.h - C ABI of the GB300 (sm_103a) Fourier spectral immersed boundary step.
+ *
+ * Method: Chen & Peskin, "A Fourier spectral immersed boundary method with exact
+ * translation invariance, improved boundary resolution, and a divergence-free
+ * velocity field" (arXiv 2302.08694). Section and equation names below refer to
+ * that paper.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions shared by every entry point
+ * ---------------------------------------------------------------------------
+ * Box.      Periodic box [0, L)^d with L = 1, d in {2, 3}.
+ * Modes.    N Fourier modes per axis, N even, N >= 4. Integer modes per axis are
+ *           m = -N/2 .. N/2-1 (Eq. kNh) and k = 2*pi*m/L. The unpaired mode
+ *           m = -N/2 is held at zero in every spectral array (inputs: ignored;
+ *           outputs: written as 0), so the kept set is symmetric and every field
+ *           is real.
+ * Spectral arrays ("half spectrum", as the spectrum of a real field):
+ *           component-major, then (m_z,) m_y in FFT order (index i holds
+ *           m = i for i < N/2, m = i - N otherwise), then m_x = 0 .. N/2-1.
+ *           d = 3: [d][N][N][N/2] complex; d = 2: [d][N][N/2] complex.
+ *           Complex numbers are interleaved (re, im). Element type: double in
+ *           FSIB_FP64 mode, float in FSIB_MIXED mode.
+ *           Represented field: u-hat(m) = H(m) for m_x > 0, conj(H(-m)) for
+ *           m_x < 0, and the Hermitian part (H(m) + conj(H(-m)))/2 on m_x = 0.
+ * Points.   X, F, U, omega are double, structure of arrays: [d][M] (row a is
+ *           coordinate a, a = 0 is x). X is kept unwrapped; transforms use
+ *           X mod L, force laws use plain differences.
+ * Pointers. Every array argument may be device memory or host memory (pageable
+ *           or pinned). Host arrays are copied through staging buffers owned by
+ *           the handle and the call returns after the results are back on the
+ *           host. With device arrays the call is asynchronous on the handle's
+ *           stream unless stated otherwise. The caller owns all array arguments.
+ * Errors.   0 on success, a negative FSIB_E* code otherwise; fsib_last_error()
+ *           gives the message. No entry point falls back to the CPU.
+ */
+#ifndef FSIB_H
+#define FSIB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSIB_OK            0
+#define FSIB_EINVAL       -1  /* bad size, parameter, key or pointer */
+#define FSIB_ENOMEM       -2  /* device allocation failed */
+#define FSIB_ECUDA        -3  /* a CUDA call or kernel launch failed */
+#define FSIB_ENONFINITE   -4  /* non-finite positions or velocities detected */
+#define FSIB_ETIMEOUT     -5  /* a bounded device wait ran out */
+#define FSIB_EUNSUPPORTED -6  /* valid request this build does not support */
+#define FSIB_ESTATE       -7  /* call out of order (e.g. no force model set) */
+
+#define FSIB_FP64  0          /* transforms and fluid solve in double */
+#define FSIB_MIXED 1          /* spread, FFT, fluid solve, interp in float;
+                                 forces, positions, invariants in double */
+
+typedef struct fsib_plan* fsib_t;
+
+/* Create a handle for one problem.
+ * N: modes per axis (even, 4..512). d: 2 or 3. M: number of boundary points (>= 1).
+ * mu: dynamic viscosity (> 0). rho: density; rho > 0 selects Navier-Stokes
+ * (Algorithm 1, Eqs. spatial_1-4), rho <= 0 the quasi-static Stokes stepper
+ * (Eq. stokeslet, same midpoint rule in time). dt: time step (> 0).
+ * tol: requested relative accuracy of each NUFFT (1e-14 .. 1e-2); it fixes the
+ * spreading-kernel width and shape (appendix A.3). Precision starts as
+ * FSIB_FP64. Allocates every device workspace on the current device. */
+int fsib_create(fsib_t* out, int N, int d, int M, double mu, double rho,
+                double dt, double tol);
+
+/* Release the handle and all its device memory. NULL is accepted. */
+int fsib_destroy(fsib_t h);
+
+/* Stream (a cudaStream_t) on which later calls enqueue their work; NULL means
+ * the legacy default stream. */
+int fsib_set_stream(fsib_t h, void* stream);
+
+/* Set a tuning or mode option; re-plans and re-allocates as needed. Keys:
+ *  "precision"  0 = FSIB_FP64, 1 = FSIB_MIXED
+ *  "sigma"      upsampling factor of the fine grid (1.5 .. 3, default 2)
+ *  "width"      spreading-kernel width in fine cells (2 .. 16; 0 = from tol)
+ *  "bin"        bin side in fine cells for the point sort (4 .. 32; 0 = auto)
+ *  "graph"      1 = fsib_step replays a captured CUDA graph (default), 0 = direct launches
+ *  "check_finite" 1 = fsib_step checks positions for NaN/Inf at the end
+ *               (adds a synchronisation), 0 = no check (default)
+ * Returns FSIB_EINVAL for an unknown key or out-of-range value. */
+int fsib_set_option(fsib_t h, const char* key, double value);
+
+/* Query a planned value. Keys: "nf" (fine grid per axis), "width", "beta",
+ * "Nt" (dealiasing grid per axis), "precision", "bin", "workspace_bytes",
+ * "launches_per_step" (kernels one fsib_step step enqueues). */
+int fsib_get_info(fsib_t h, const char* key, double* value);
+
+/* Closed-curve Hookean tension, d = 2 (Eq. elstic_force_2d):
+ * F_i = K (X_{i+1} + X_{i-1} - 2 X_i)/dtheta^2, dtheta = 2*pi/M, weight omega = dtheta.
+ * Points are ordered along the curve; the curve is closed. */
+int fsib_set_force_curve(fsib_t h, double K);
+
+/* Triangulated membrane with cot-weight springs, d = 3 (Sec. 6.2.3):
+ * K_AB = (sigma/2)(cot C1 + cot C2) from the reference configuration Xref
+ * ([3][M] double), F_i = sum_j K_ij (X_j - X_i), omega = 1 (nodal forces).
+ * tri: [ntri][3] int32 vertex indices, counter-clockwise seen from outside
+ * (used for the enclosed volume). Both arrays are copied; host or device. */
+int fsib_set_force_mesh(fsib_t h, const int* tri, int ntri, const double* Xref,
+                        double sigma);
+
+/* Weighted force c_j = omega_j F_j of the current force model at X ([d][M]),
+ * written to c ([d][M] double). */
+int fsib_force(fsib_t h, const double* X, double* c);
+
+/* Type-1 NUFFT spread (Eq. force_spreading_quad; appendix A.1):
+ * f-hat(k) = L^-d sum_j omega_j F_j exp(-i k . X_j), k in K_N.
+ * X, F: [d][M] double. omega: [M] double, or NULL for omega_j = 1.
+ * fhat: half-spectrum output. Accuracy: the plan's tol, relative in the 2-norm. */
+int fsib_spread(fsib_t h, const double* X, const double* F, const double* omega,
+                void* fhat);
+
+/* Type-2 NUFFT interpolation (Eq. velo_intp_fini; appendix A.2):
+ * U_j = sum_{k in K_N} u-hat(k) exp(i k . X_j). uhat: half spectrum;
+ * X, U: [d][M] double. */
+int fsib_interp(fsib_t h, const void* uhat, const double* X, double* U);
+
+/* Fluid update in Fourier space.
+ * Navier-Stokes (rho > 0): with f-hat = fhat and u-hat^m = uhat on input,
+ *   u-hat^{m+1/2} = (dt/2 V(f, u^m) + u^m)/(1 + mu dt |k|^2/(2 rho))        (Eq. spatial_2)
+ *   u-hat^{m+1}   = (dt V(f, u^{m+1/2}) + (1 - mu dt|k|^2/(2 rho)) u^m)/(1 + mu dt |k|^2/(2 rho))  (Eq. spatial_3)
+ *   with V(f, u) = P_k (f/rho - s-hat(u)) (Algorithm 2), s-hat the
+ *   three-halves dealiased nonlinear term (Eq. nonlinear_kspace).
+ *   uhat is overwritten with u-hat^{m+1}; uhat_half (may be NULL) receives u-hat^{m+1/2}.
+ * Stokes (rho <= 0): uhat = mu^-1 (I/|k|^2 - k k^T/|k|^4) fhat, uhat(0) = 0
+ *   (Eq. stokeslet); uhat_half is ignored. */
+int fsib_fluid_step(fsib_t h, const void* fhat, void* uhat, void* uhat_half);
+
+/* Advance nsteps time steps in place.
+ * Navier-Stokes: state (X^m, u-hat^m, U^m) -> (X^{m+n}, u-hat^{m+n}, U^{m+n}) by
+ *   Algorithm 1, where U^m must equal the interpolated velocity u^m(X^m)
+ *   (fsib_interp gives U^0). U^{m+1} is interpolated at X^{m+1} after the
+ *   position update.
+ * Stokes: X^{m+1} = X^m + dt U(X^{m+1/2}), X^{m+1/2} = X^m + dt/2 U(X^m),
+ *   U(X) = interp(Stokeslet(spread(F(X), X)), X); uhat and U may be NULL
+ *   (when given, U receives U(X^{m+1/2}) of the last step).
+ * Needs a force model. */
+int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps);
+
+/* Diagnostics in double, synchronous (Sec. 4). out[0] enclosed volume (d = 3,
+ * needs the mesh) or area (d = 2, curve order), out[1] elastic energy E_p,
+ * out[2] kinetic energy E_K = rho/2 L^d sum |u-hat|^2 (rho = 1 for Stokes),
+ * out[3] |u-hat(0)|, out[4] max_k |k . u-hat(k)|/|k| over max_k |u-hat(k)|,
+ * out[5] dissipation mu L^d sum |k|^2 |u-hat|^2. uhat may be NULL (out[2..5] = 0).
+ * Returns FSIB_ENONFINITE if X or uhat holds NaN/Inf. */
+int fsib_invariants(fsib_t h, const double* X, const void* uhat, double out[6]);
+
+/* Per-launch-site profiling. When enabled, every call enqueues CUDA events
+ * around each kernel launch site on the handle's stream and fsib_step launches
+ * its kernels directly instead of replaying the captured graph. Entries
+ * accumulate until fsib_profile_reset. For entry i (0 <= i < fsib_profile_count):
+ * name (NUL-terminated, truncated to name_len), total milliseconds, number of
+ * launches, and the algorithmic bytes and flops of one launch (each input read
+ * once, each output written once; flops counted as 5 n log2 n per length-n
+ * complex FFT line). fsib_profile_entry synchronises the handle's stream. */
+int fsib_profile_enable(fsib_t h, int on);
+int fsib_profile_reset(fsib_t h);
+int fsib_profile_count(fsib_t h);
+int fsib_profile_entry(fsib_t h, int i, char* name, int name_len, double* total_ms,
+                       int* launches, double* bytes_per_launch, double* flops_per_launch);
+
+/* Measured arithmetic peak of the current device for the roofline: kind 0 =
+ * FP64 FMA throughput, kind 1 = FP32 FMA throughput, in GFLOP/s (an FMA counts
+ * as 2 flops). Runs a short register-resident kernel; synchronous. */
+int fsib_measure_peak(int kind, double* gflops);
+
+/* Message of the last error on this handle ("" if none); h may be NULL for
+ * errors of fsib_create. */
+const char* fsib_last_error(fsib_t h);
+
+/* Library version string. */
+const char* fsib_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSIB_H */

@@ -365,3 +365,19 @@ def max_divergence(uhat: np.ndarray, N: int, L: float = 1.0) -> float:
     if top == 0.0 or not np.any(nz):
         return 0.0
     return float(np.max(ku[nz] / np.sqrt(k2[nz]))) / top
+
+
+def spread_at_modes(X: np.ndarray, c: np.ndarray, modes: np.ndarray, L: float = 1.0) -> np.ndarray:
+    """The type-1 sum of Eq. force_spreading_quad at a list of integer modes (nk, d), one by one.
+
+    Returns (ncomp, nk) complex. Used to check large transforms on sampled modes.
+    """
+    d, M = X.shape
+    out = np.zeros((c.shape[0], modes.shape[0]), dtype=np.complex128)
+    for q in range(modes.shape[0]):
+        ph = np.zeros(M)
+        for a in range(d):
+            ph += TWO_PI / L * float(modes[q, a]) * X[a]
+        e = np.exp(-1j * ph)
+        out[:, q] = (c @ e) / L ** d
+    return out

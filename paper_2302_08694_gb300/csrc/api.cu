@@ -1,0 +1,982 @@
+// C ABI of the FSIB library: planning, workspaces, staging of host arrays, and the
+// orchestration of the transforms into spread / interp / fluid update / time step.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <mutex>
+#include <unordered_set>
+#include <string>
+#include <vector>
+
+#include "fsib_internal.cuh"
+
+using namespace fsib;
+
+#define FSIB_VERSION "0.1.0"
+
+struct fsib_plan {
+  Plan p;
+  Workspace ws;
+  cudaStream_t user = nullptr;
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::string err;
+  bool ready = false;  // workspaces allocated for the current plan
+  // per-launch-site profiler
+  struct Site { std::string name; double total_ms = 0; int launches = 0; double bytes = 0, flops = 0; };
+  struct Pending { int site; cudaEvent_t a, b; };
+  bool prof_on = false;
+  std::vector<Site> sites;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  // captured step graph
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[3] = {nullptr, nullptr, nullptr};
+  int graph_kernels = 0;
+};
+
+static std::string g_create_err;
+
+namespace fsib {
+
+int check_last(const char* where) {
+  (void)where;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FSIB_OK : FSIB_ECUDA;
+}
+
+void raise_smem_limit(const void* kernel) {
+  static std::mutex mu;
+  static std::unordered_set<const void*> done;
+  static int optin = -1;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(kernel)) return;
+  if (optin < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 48 * 1024;
+  }
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  done.insert(kernel);
+}
+
+}  // namespace fsib
+
+// ---------------------------------------------------------------------------
+// Planning
+// ---------------------------------------------------------------------------
+static bool is_smooth(int n) {
+  for (int q : {2, 3})
+    while (n % q == 0) n /= q;
+  return n == 1;
+}
+static int smooth_even_at_least(int n) {
+  if (n < 2) n = 2;
+  while (!(n % 2 == 0 && is_smooth(n))) ++n;
+  return n;
+}
+
+static void make_fftlen(FftLen& f, int n, int tw_off) {
+  f.n = n;
+  f.tw_off = tw_off;
+  f.nstages = 0;
+  int m = n;
+  while (m % 4 == 0) { f.radix[f.nstages++] = 4; m /= 4; }
+  while (m % 2 == 0) { f.radix[f.nstages++] = 2; m /= 2; }
+  while (m % 3 == 0) { f.radix[f.nstages++] = 3; m /= 3; }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wq) {
+  x.assign(n, 0.0);
+  wq.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double pp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1; p1 = p2;
+      }
+      const double pn = (n == 1) ? z : p1;
+      const double pnm1 = (n == 1) ? 1.0 : p0;
+      pp = n * (z * pn - pnm1) / (z * z - 1.0);
+      const double dz = pn / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z; x[n - 1 - i] = z;
+    wq[i] = wq[n - 1 - i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+// Fourier transform of the spreading kernel along one axis, in physical units:
+// Psi(k) = int phi(2x/(w h)) exp(-i k x) dx = (w h/2) int_{-1}^{1} phi(z) cos(k w h z/2) dz.
+static double psi_hat(double k, int w, double beta, double hf, const std::vector<double>& zq,
+                      const std::vector<double>& wq) {
+  const double a = 0.5 * w * hf;
+  double s = 0;
+  for (size_t i = 0; i < zq.size(); ++i) {
+    const double z = zq[i];
+    const double ph = std::exp(beta * (std::sqrt(std::max(0.0, 1.0 - z * z)) - 1.0));
+    s += wq[i] * ph * std::cos(k * a * z);
+  }
+  return a * s;
+}
+
+static int plan_sizes(Plan& p, std::string& err) {
+  const double pi = 3.14159265358979323846;
+  int w = p.width_opt;
+  if (w <= 0) w = (int)std::ceil(-std::log(p.tol) / (pi * std::sqrt(1.0 - 1.0 / p.sigma)));
+  w = std::min(16, std::max(2, w));
+  p.w = w;
+  p.beta = 0.97 * pi * w * (1.0 - 1.0 / (2.0 * p.sigma));
+  p.nf = smooth_even_at_least(std::max((int)std::ceil(p.sigma * p.N - 1e-9), 2 * w));
+  p.Nt = smooth_even_at_least((3 * p.N + 1) / 2);
+  if (p.nf > kMaxFFT || p.Nt > kMaxFFT) {
+    err = "fine or dealiasing grid exceeds the supported FFT length 512";
+    return FSIB_EUNSUPPORTED;
+  }
+  int b = p.bin_opt;
+  if (b <= 0) {
+    if (p.d == 2) b = 32;
+    else b = (p.prec == FSIB_FP64 && w > 8) ? 4 : 8;
+  }
+  while (b > 1 && p.nf % b) b /= 2;
+  for (int a = 0; a < 3; ++a) { p.bins[a] = (a < p.d) ? b : 1; p.nbin[a] = (a < p.d) ? p.nf / b : 1; }
+  p.nbins = 1;
+  for (int a = 0; a < p.d; ++a) p.nbins *= p.nbin[a];
+  make_fftlen(p.fl_nf, p.nf, 0);
+  make_fftlen(p.fl_nt, p.Nt, p.nf);
+  return FSIB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Profiler: CUDA events around a launch site (only while profiling is enabled)
+// ---------------------------------------------------------------------------
+struct Prof {
+  fsib_plan* h;
+  int site = -1;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t st;
+  Prof(fsib_plan* hh, const char* name, double bytes, double flops, cudaStream_t s) : h(hh), st(s) {
+    if (!h->prof_on) return;
+    for (size_t i = 0; i < h->sites.size(); ++i)
+      if (h->sites[i].name == name) { site = (int)i; break; }
+    if (site < 0) {
+      fsib_plan::Site x;
+      x.name = name;
+      h->sites.push_back(x);
+      site = (int)h->sites.size() - 1;
+    }
+    h->sites[site].bytes = bytes;
+    h->sites[site].flops = flops;
+    for (cudaEvent_t* e : {&a, &b}) {
+      if (!h->pool.empty()) { *e = h->pool.back(); h->pool.pop_back(); }
+      else cudaEventCreate(e);
+    }
+    cudaEventRecord(a, st);
+  }
+  ~Prof() {
+    if (site < 0) return;
+    cudaEventRecord(b, st);
+    h->pending.push_back({site, a, b});
+  }
+};
+
+static void prof_flush(fsib_plan* h) {
+  if (h->pending.empty()) return;
+  cudaStreamSynchronize(h->own);
+  for (auto& q : h->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      h->sites[q.site].total_ms += ms;
+      h->sites[q.site].launches += 1;
+    }
+    h->pool.push_back(q.a);
+    h->pool.push_back(q.b);
+  }
+  h->pending.clear();
+  cudaGetLastError();
+}
+
+static double fft_flops(double lines, int n) { return lines * 5.0 * n * std::log2((double)n); }
+
+// ---------------------------------------------------------------------------
+// Workspaces
+// ---------------------------------------------------------------------------
+static void free_ws(Workspace& ws) {
+  void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.s1, ws.s2, ws.fhat, ws.uhalf, ws.bin_of,
+                  ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
+                  ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  ws.tw = ws.dline = ws.dplane = ws.grid = ws.s1 = ws.s2 = ws.fhat = ws.uhalf = nullptr;
+  ws.bin_of = ws.rank = ws.counts = ws.offsets = ws.occ = ws.nocc = ws.perm = ws.i0 = nullptr;
+  ws.delta = nullptr;
+  ws.Xh = ws.cw = ws.Uh = ws.omega_ones = ws.red = nullptr;
+  ws.flag = nullptr;
+  for (int i = 0; i < 4; ++i) {
+    if (ws.stage[i]) cudaFree(ws.stage[i]);
+    ws.stage[i] = nullptr; ws.stage_bytes[i] = 0;
+  }
+}
+
+static void free_mesh(Workspace& ws) {
+  if (ws.csr_ptr) cudaFree(ws.csr_ptr);
+  if (ws.csr_col) cudaFree(ws.csr_col);
+  if (ws.csr_k) cudaFree(ws.csr_k);
+  if (ws.tri) cudaFree(ws.tri);
+  ws.csr_ptr = ws.csr_col = nullptr; ws.csr_k = nullptr; ws.tri = nullptr; ws.nnz = ws.ntri = 0;
+}
+
+template <typename P>
+static int dmalloc(P** ptr, size_t bytes, size_t& total) {
+  void* q = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) { cudaGetLastError(); return FSIB_ENOMEM; }
+  *ptr = reinterpret_cast<P*>(q);
+  total += bytes;
+  return FSIB_OK;
+}
+
+static size_t g_ws_bytes = 0;
+
+static int alloc_ws(fsib_plan* h) {
+  Plan& p = h->p;
+  Workspace& ws = h->ws;
+  free_ws(ws);
+  h->ready = false;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  const bool f64 = p.prec == FSIB_FP64;
+  const size_t rs = f64 ? 8 : 4, cs = 2 * rs;
+  const long long N = p.N, hh = p.N / 2, n = p.nf, Nt = p.Nt, d = p.d;
+  const long long spec = d * hh * N * (d == 3 ? N : 1);
+  long long s = 0;
+  if (d == 3) {
+    s = std::max({d * n * n * hh, d * n * N * hh, 3 * Nt * N * hh, 6 * Nt * Nt * hh, 6 * N * N * hh,
+                  3 * Nt * Nt * hh, 6 * Nt * N * hh});
+  } else {
+    s = std::max({d * n * hh, 2 * Nt * hh, 3 * Nt * hh, 3 * N * hh});
+  }
+  const long long gcells = d * n * n * (d == 3 ? n : 1);
+  size_t tot = 0;
+  int rc = FSIB_OK;
+  ws.spec_bytes = (size_t)spec * cs;
+  ws.grid_bytes = (size_t)gcells * rs;
+  ws.s1_bytes = ws.s2_bytes = (size_t)s * cs;
+  const int ntw = p.nf + p.Nt;
+  rc |= dmalloc(&ws.tw, (size_t)ntw * cs, tot);
+  rc |= dmalloc(&ws.dline, (size_t)N * rs, tot);
+  rc |= dmalloc(&ws.dplane, (size_t)(d == 3 ? N * hh : hh) * rs, tot);
+  rc |= dmalloc(&ws.grid, ws.grid_bytes, tot);
+  rc |= dmalloc(&ws.s1, ws.s1_bytes, tot);
+  rc |= dmalloc(&ws.s2, ws.s2_bytes, tot);
+  rc |= dmalloc(&ws.fhat, ws.spec_bytes, tot);
+  rc |= dmalloc(&ws.uhalf, ws.spec_bytes, tot);
+  rc |= dmalloc(&ws.bin_of, sizeof(int) * p.M, tot);
+  rc |= dmalloc(&ws.rank, sizeof(int) * p.M, tot);
+  rc |= dmalloc(&ws.counts, sizeof(int) * (size_t)p.nbins, tot);
+  rc |= dmalloc(&ws.offsets, sizeof(int) * (size_t)(p.nbins + 1), tot);
+  rc |= dmalloc(&ws.occ, sizeof(int) * (size_t)p.nbins, tot);
+  rc |= dmalloc(&ws.nocc, sizeof(int), tot);
+  rc |= dmalloc(&ws.perm, sizeof(int) * p.M, tot);
+  rc |= dmalloc(&ws.i0, sizeof(int) * d * p.M, tot);
+  rc |= dmalloc(&ws.delta, rs * d * p.M, tot);
+  rc |= dmalloc(&ws.Xh, sizeof(double) * d * p.M, tot);
+  rc |= dmalloc(&ws.cw, sizeof(double) * d * p.M, tot);
+  rc |= dmalloc(&ws.Uh, sizeof(double) * d * p.M, tot);
+  ws.red_blocks = 2 * 152;
+  rc |= dmalloc(&ws.red, sizeof(double) * (size_t)(ws.red_blocks + 1) * 10, tot);
+  rc |= dmalloc(&ws.flag, sizeof(int) * 4, tot);
+  if (rc != FSIB_OK) { free_ws(ws); h->err = "device allocation failed"; return FSIB_ENOMEM; }
+  g_ws_bytes = tot;
+
+  // twiddles exp(-2 pi i j/n) for the fine and dealiasing lengths
+  const double pi = 3.14159265358979323846;
+  std::vector<double> twd(2 * (size_t)ntw);
+  auto fill = [&](int nn, int off) {
+    for (int j = 0; j < nn; ++j) {
+      const double ang = 2.0 * pi * (double)j / (double)nn;
+      twd[2 * (off + j)] = std::cos(ang);
+      twd[2 * (off + j) + 1] = -std::sin(ang);
+    }
+  };
+  fill(p.nf, 0);
+  fill(p.Nt, p.nf);
+  // deconvolution: D[i] = h_f / Psi(k_i) per axis, FFT order, the unpaired mode -N/2 -> 0
+  std::vector<double> zq, wq;
+  gauss_legendre(std::max(64, 4 * p.w + 64), zq, wq);
+  const double hf = p.L / p.nf;
+  std::vector<double> D(N), Dp(d == 3 ? N * hh : hh);
+  for (long long i = 0; i < N; ++i) {
+    const long long m = (i < N / 2) ? i : i - N;
+    D[i] = (i == N / 2) ? 0.0 : hf / psi_hat(2.0 * pi * m / p.L, p.w, p.beta, hf, zq, wq);
+  }
+  if (d == 3)
+    for (long long iy = 0; iy < N; ++iy)
+      for (long long ix = 0; ix < hh; ++ix) Dp[iy * hh + ix] = D[iy] * D[ix];
+  else
+    for (long long ix = 0; ix < hh; ++ix) Dp[ix] = D[ix];
+  cudaError_t e = cudaSuccess;
+  if (f64) {
+    e = cudaMemcpy(ws.tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.dline, D.data(), D.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.dplane, Dp.data(), Dp.size() * 8, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> a(twd.begin(), twd.end()), b(D.begin(), D.end()), c(Dp.begin(), Dp.end());
+    e = cudaMemcpy(ws.tw, a.data(), a.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.dline, b.data(), b.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.dplane, c.data(), c.size() * 4, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) { h->err = std::string("table upload: ") + cudaGetErrorString(e); return FSIB_ECUDA; }
+  h->ready = true;
+  return FSIB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Transform sequences
+// ---------------------------------------------------------------------------
+template <typename T>
+static void forward_fine(fsib_plan* h, const T* grid, C<T>* out, cudaStream_t st) {
+  const Plan& p = h->p;
+  Workspace& ws = h->ws;
+  const int N = p.N, hh = N / 2, n = p.nf, d = p.d;
+  const C<T>* tw = (const C<T>*)ws.tw;
+  C<T>* s1 = (C<T>*)ws.s1;
+  C<T>* s2 = (C<T>*)ws.s2;
+  Mult<T> none;
+  Mult<T> dec;
+  dec.scale = (T)std::pow(p.L, -d);
+  dec.dline = (const T*)ws.dline;
+  dec.dplane = (const T*)ws.dplane;
+  const double rs = sizeof(T), cs = 2.0 * sizeof(T);
+  if (d == 3) {
+    { Prof pr(h, "t1.fx_rows_r2c", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
+      launch_fft_rows_r2c<T>(grid, s1, (long long)d * n * n, N, p.fl_nf, tw, st); }
+    { Prof pr(h, "t1.fy_strided", (double)d * n * hh * (n + N) * cs, fft_flops((double)d * n * hh, n), st);
+      launch_fft_strided<T>(s1, s2, d, n, hh, N, p.fl_nf, false, none, tw, st); }
+    { Prof pr(h, "t1.fz_strided_deconv", (double)d * N * hh * (n + N) * cs, fft_flops((double)d * N * hh, n), st);
+      launch_fft_strided<T>(s2, out, d, 1, N * hh, N, p.fl_nf, false, dec, tw, st); }
+  } else {
+    { Prof pr(h, "t1.fx_rows_r2c", (double)d * n * n * rs + (double)d * n * hh * cs, fft_flops(0.5 * d * n, n), st);
+      launch_fft_rows_r2c<T>(grid, s1, (long long)d * n, N, p.fl_nf, tw, st); }
+    { Prof pr(h, "t1.fy_strided_deconv", (double)d * hh * (n + N) * cs, fft_flops((double)d * hh, n), st);
+      launch_fft_strided<T>(s1, out, d, 1, hh, N, p.fl_nf, false, dec, tw, st); }
+  }
+}
+
+template <typename T>
+static void inverse_fine(fsib_plan* h, const C<T>* in, T* grid, cudaStream_t st) {
+  const Plan& p = h->p;
+  Workspace& ws = h->ws;
+  const int N = p.N, hh = N / 2, n = p.nf, d = p.d;
+  const C<T>* tw = (const C<T>*)ws.tw;
+  C<T>* s1 = (C<T>*)ws.s1;
+  C<T>* s2 = (C<T>*)ws.s2;
+  Mult<T> none;
+  Mult<T> dec;
+  dec.dline = (const T*)ws.dline;
+  dec.dplane = (const T*)ws.dplane;
+  const double rs = sizeof(T), cs = 2.0 * sizeof(T);
+  if (d == 3) {
+    { Prof pr(h, "t2.iz_strided_deconv", (double)d * N * hh * (n + N) * cs, fft_flops((double)d * N * hh, n), st);
+      launch_fft_strided<T>(in, s1, d, 1, N * hh, N, p.fl_nf, true, dec, tw, st); }
+    { Prof pr(h, "t2.iy_strided", (double)d * n * hh * (n + N) * cs, fft_flops((double)d * n * hh, n), st);
+      launch_fft_strided<T>(s1, s2, d, n, hh, N, p.fl_nf, true, none, tw, st); }
+    { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
+      launch_fft_rows_c2r<T>(s2, grid, (long long)d * n * n, N, p.fl_nf, tw, st); }
+  } else {
+    { Prof pr(h, "t2.iy_strided_deconv", (double)d * hh * (n + N) * cs, fft_flops((double)d * hh, n), st);
+      launch_fft_strided<T>(in, s2, d, 1, hh, N, p.fl_nf, true, dec, tw, st); }
+    { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * rs + (double)d * n * hh * cs, fft_flops(0.5 * d * n, n), st);
+      launch_fft_rows_c2r<T>(s2, grid, (long long)d * n, N, p.fl_nf, tw, st); }
+  }
+}
+
+// Fourier coefficients on K_N of the products u_a u_b (three-halves rule); returns the buffer.
+template <typename T>
+static const C<T>* products(fsib_plan* h, const C<T>* u, cudaStream_t st) {
+  const Plan& p = h->p;
+  Workspace& ws = h->ws;
+  const int N = p.N, hh = N / 2, nt = p.Nt, d = p.d;
+  const C<T>* tw = (const C<T>*)ws.tw;
+  C<T>* s1 = (C<T>*)ws.s1;
+  C<T>* s2 = (C<T>*)ws.s2;
+  Mult<T> none;
+  Mult<T> sc;
+  const double cs = 2.0 * sizeof(T);
+  if (d == 3) {
+    sc.scale = (T)(1.0 / ((double)nt * nt * nt));
+    { Prof pr(h, "nl.iz_strided", 3.0 * N * hh * (N + nt) * cs, fft_flops(3.0 * N * hh, nt), st);
+      launch_fft_strided<T>(u, s1, 3, 1, N * hh, N, p.fl_nt, true, none, tw, st); }
+    { Prof pr(h, "nl.iy_strided", 3.0 * nt * hh * (N + nt) * cs, fft_flops(3.0 * nt * hh, nt), st);
+      launch_fft_strided<T>(s1, s2, 3, nt, hh, N, p.fl_nt, true, none, tw, st); }
+    { Prof pr(h, "nl.rows_product", 9.0 * nt * nt * hh * cs, fft_flops(0.5 * nt * nt * 9.0, nt), st);
+      launch_rows_product<T>(s2, s1, 3, (long long)nt * nt, N, p.fl_nt, tw, st); }
+    { Prof pr(h, "nl.fy_strided", 6.0 * nt * hh * (N + nt) * cs, fft_flops(6.0 * nt * hh, nt), st);
+      launch_fft_strided<T>(s1, s2, 6, nt, hh, N, p.fl_nt, false, none, tw, st); }
+    { Prof pr(h, "nl.fz_strided", 6.0 * N * hh * (N + nt) * cs, fft_flops(6.0 * N * hh, nt), st);
+      launch_fft_strided<T>(s2, s1, 6, 1, N * hh, N, p.fl_nt, false, sc, tw, st); }
+    return s1;
+  } else {
+    sc.scale = (T)(1.0 / ((double)nt * nt));
+    { Prof pr(h, "nl.iy_strided", 2.0 * hh * (N + nt) * cs, fft_flops(2.0 * hh, nt), st);
+      launch_fft_strided<T>(u, s2, 2, 1, hh, N, p.fl_nt, true, none, tw, st); }
+    { Prof pr(h, "nl.rows_product", 5.0 * nt * hh * cs, fft_flops(0.5 * nt * 5.0, nt), st);
+      launch_rows_product<T>(s2, s1, 2, (long long)nt, N, p.fl_nt, tw, st); }
+    { Prof pr(h, "nl.fy_strided", 3.0 * hh * (N + nt) * cs, fft_flops(3.0 * hh, nt), st);
+      launch_fft_strided<T>(s1, s2, 3, 1, hh, N, p.fl_nt, false, sc, tw, st); }
+    return s2;
+  }
+}
+
+static void do_bin(fsib_plan* h, const double* X, cudaStream_t st) {
+  const Plan& p = h->p;
+  const double rs = (p.prec == FSIB_FP64) ? 8.0 : 4.0;
+  Prof pr(h, "sort", 2.0 * p.d * p.M * 8.0 + 4.0 * p.M * 8.0 + p.d * p.M * (4.0 + rs) + 12.0 * p.nbins, 0.0, st);
+  launch_bin_points(p, h->ws, X, st);
+}
+
+template <typename T>
+static double point_bytes(const Plan& p) { return (double)p.M * (4.0 + p.d * (4.0 + sizeof(T) + 8.0)); }
+
+template <typename T>
+static void do_spread(fsib_plan* h, const double* X, const double* c, const double* omega, C<T>* fhat,
+                      cudaStream_t st) {
+  do_bin(h, X, st);
+  { Prof pr(h, "zero_grid", (double)h->ws.grid_bytes, 0.0, st);
+    cudaMemsetAsync(h->ws.grid, 0, h->ws.grid_bytes, st); }
+  { Prof pr(h, "spread", point_bytes<T>(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+    launch_spread<T>(h->p, h->ws, c, omega, (T*)h->ws.grid, st); }
+  forward_fine<T>(h, (const T*)h->ws.grid, fhat, st);
+}
+
+// interp at the points of the last binning
+template <typename T>
+static void do_interp_sorted(fsib_plan* h, const C<T>* uhat, double* U, cudaStream_t st) {
+  inverse_fine<T>(h, uhat, (T*)h->ws.grid, st);
+  Prof pr(h, "interp", point_bytes<T>(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  launch_interp<T>(h->p, h->ws, (const T*)h->ws.grid, U, st);
+}
+
+template <typename T>
+static void do_stokeslet(fsib_plan* h, const C<T>* fhat, C<T>* u, cudaStream_t st) {
+  Prof pr(h, "stokeslet", 2.0 * (double)h->ws.spec_bytes, 0.0, st);
+  launch_stokeslet<T>(h->p, fhat, u, st);
+}
+
+template <typename T>
+static void do_fluid(fsib_plan* h, const C<T>* fhat, C<T>* u, C<T>* uhalf, cudaStream_t st) {
+  if (h->p.stokes) {
+    do_stokeslet<T>(h, fhat, u, st);
+    return;
+  }
+  const int d = h->p.d, np = d * (d + 1) / 2;
+  const double ub = (double)h->ws.spec_bytes / d * (np + 3 * d);
+  const C<T>* P = products<T>(h, u, st);
+  { Prof pr(h, "ns_update", ub, 0.0, st);
+    launch_ns_update<T>(h->p, P, fhat, u, uhalf, true, st); }
+  P = products<T>(h, uhalf, st);
+  { Prof pr(h, "ns_update", ub, 0.0, st);
+    launch_ns_update<T>(h->p, P, fhat, u, u, false, st); }
+}
+
+static void do_axpy(fsib_plan* h, double* y, const double* x, const double* v, double a, cudaStream_t st) {
+  const long long dm = (long long)h->p.d * h->p.M;
+  Prof pr(h, "positions", 24.0 * dm, 0.0, st);
+  launch_axpy(y, x, v, a, dm, st);
+}
+
+static void do_force(fsib_plan* h, const double* X, double* c, cudaStream_t st) {
+  const Plan& p = h->p;
+  Prof pr(h, "force", 16.0 * p.d * p.M + 12.0 * h->ws.nnz + 4.0 * p.M, 0.0, st);
+  launch_force(p, h->ws, X, c, st);
+}
+
+// One time step on device arrays (Algorithm 1, or the quasi-static Stokes midpoint rule).
+template <typename T>
+static void do_step(fsib_plan* h, double* X, C<T>* uhat, double* U, cudaStream_t st) {
+  const Plan& p = h->p;
+  Workspace& ws = h->ws;
+  const long long dm = (long long)p.d * p.M;
+  (void)dm;
+  C<T>* fhat = (C<T>*)ws.fhat;
+  C<T>* uh = (C<T>*)ws.uhalf;
+  if (!p.stokes) {
+    do_axpy(h, ws.Xh, X, U, 0.5 * p.dt, st);                    // Eq. spatial_1
+    do_force(h, ws.Xh, ws.cw, st);                               // F^{m+1/2}
+    do_spread<T>(h, ws.Xh, ws.cw, nullptr, fhat, st);            // type-1 NUFFT
+    do_fluid<T>(h, fhat, uhat, uh, st);                          // Eqs. spatial_2, spatial_3
+    do_interp_sorted<T>(h, uh, ws.Uh, st);                       // U^{m+1/2} at X^{m+1/2}
+    do_axpy(h, X, X, ws.Uh, p.dt, st);                           // Eq. spatial_4
+    do_bin(h, X, st);
+    do_interp_sorted<T>(h, uhat, U, st);                         // U^{m+1} at X^{m+1}
+  } else {
+    // U(X^m)
+    do_force(h, X, ws.cw, st);
+    do_spread<T>(h, X, ws.cw, nullptr, fhat, st);
+    do_stokeslet<T>(h, fhat, uh, st);
+    do_interp_sorted<T>(h, uh, ws.Uh, st);
+    do_axpy(h, ws.Xh, X, ws.Uh, 0.5 * p.dt, st);
+    // U(X^{m+1/2})
+    do_force(h, ws.Xh, ws.cw, st);
+    do_spread<T>(h, ws.Xh, ws.cw, nullptr, fhat, st);
+    do_stokeslet<T>(h, fhat, uh, st);
+    do_interp_sorted<T>(h, uh, ws.Uh, st);
+    do_axpy(h, X, X, ws.Uh, p.dt, st);
+    if (U) cudaMemcpyAsync(U, ws.Uh, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
+    if (uhat) cudaMemcpyAsync(uhat, uh, ws.spec_bytes, cudaMemcpyDeviceToDevice, st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Entry helpers
+// ---------------------------------------------------------------------------
+static int fail(fsib_plan* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+static bool is_device_ptr(const void* q) {
+  if (!q) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, q) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Begin a call: order the own stream after the user's stream.
+static int begin(fsib_plan* h) {
+  if (!h) return FSIB_EINVAL;
+  if (!h->ready) return fail(h, FSIB_ESTATE, "workspaces not allocated");
+  h->err.clear();
+  if (cudaEventRecord(h->ev_in, h->user) != cudaSuccess) return fail(h, FSIB_ECUDA, "event record failed");
+  if (cudaStreamWaitEvent(h->own, h->ev_in, 0) != cudaSuccess) return fail(h, FSIB_ECUDA, "stream wait failed");
+  return FSIB_OK;
+}
+
+static int finish(fsib_plan* h, bool sync) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, FSIB_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+  if (cudaEventRecord(h->ev_out, h->own) != cudaSuccess) return fail(h, FSIB_ECUDA, "event record failed");
+  if (cudaStreamWaitEvent(h->user, h->ev_out, 0) != cudaSuccess) return fail(h, FSIB_ECUDA, "stream wait failed");
+  if (sync) {
+    e = cudaStreamSynchronize(h->own);
+    if (e != cudaSuccess) return fail(h, FSIB_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+  }
+  return FSIB_OK;
+}
+
+// Device view of an argument: the pointer itself, or a staging buffer (copied in if `in`).
+struct Arg {
+  void* dev = nullptr;
+  void* host = nullptr;
+  size_t bytes = 0;
+};
+
+static int stage(fsib_plan* h, int slot, const void* q, size_t bytes, bool in, Arg& a) {
+  a.bytes = bytes;
+  if (!q) { a.dev = nullptr; return FSIB_OK; }
+  if (is_device_ptr(q)) { a.dev = const_cast<void*>(q); return FSIB_OK; }
+  Workspace& ws = h->ws;
+  if (ws.stage_bytes[slot] < bytes) {
+    if (ws.stage[slot]) cudaFree(ws.stage[slot]);
+    ws.stage[slot] = nullptr;
+    ws.stage_bytes[slot] = 0;
+    if (cudaMalloc(&ws.stage[slot], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, FSIB_ENOMEM, "staging allocation failed");
+    }
+    ws.stage_bytes[slot] = bytes;
+  }
+  a.dev = ws.stage[slot];
+  a.host = const_cast<void*>(q);
+  if (in && cudaMemcpyAsync(a.dev, q, bytes, cudaMemcpyHostToDevice, h->own) != cudaSuccess)
+    return fail(h, FSIB_ECUDA, "host-to-device copy failed");
+  return FSIB_OK;
+}
+
+static int unstage(fsib_plan* h, const Arg& a) {
+  if (a.host && a.dev && cudaMemcpyAsync(a.host, a.dev, a.bytes, cudaMemcpyDeviceToHost, h->own) != cudaSuccess)
+    return fail(h, FSIB_ECUDA, "device-to-host copy failed");
+  return FSIB_OK;
+}
+
+static size_t spec_bytes(const fsib_plan* h) { return h->ws.spec_bytes; }
+static size_t pts_bytes(const fsib_plan* h) { return sizeof(double) * (size_t)h->p.d * h->p.M; }
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* fsib_version(void) { return FSIB_VERSION; }
+
+const char* fsib_last_error(fsib_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int fsib_create(fsib_t* out, int N, int d, int M, double mu, double rho, double dt, double tol) {
+  g_create_err.clear();
+  if (!out) { g_create_err = "out is NULL"; return FSIB_EINVAL; }
+  *out = nullptr;
+  if (d != 2 && d != 3) { g_create_err = "d must be 2 or 3"; return FSIB_EINVAL; }
+  if (N < 4 || N > 512 || (N % 2)) { g_create_err = "N must be even, 4 <= N <= 512"; return FSIB_EINVAL; }
+  if (M < 1) { g_create_err = "M must be >= 1"; return FSIB_EINVAL; }
+  if (!(mu > 0) || !(dt > 0) || !std::isfinite(mu) || !std::isfinite(dt) || !std::isfinite(rho)) {
+    g_create_err = "mu and dt must be positive and finite";
+    return FSIB_EINVAL;
+  }
+  if (!(tol >= 1e-14 && tol <= 1e-2)) { g_create_err = "tol must be in [1e-14, 1e-2]"; return FSIB_EINVAL; }
+  fsib_plan* h = new fsib_plan();
+  Plan& p = h->p;
+  p.d = d; p.N = N; p.M = M; p.mu = mu; p.rho = rho; p.dt = dt; p.tol = tol;
+  p.stokes = !(rho > 0);
+  int rc = plan_sizes(p, h->err);
+  if (rc != FSIB_OK) { g_create_err = h->err; delete h; return rc; }
+  if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "CUDA stream/event creation failed (no device?)";
+    delete h;
+    return FSIB_ECUDA;
+  }
+  rc = alloc_ws(h);
+  if (rc != FSIB_OK) {
+    g_create_err = h->err;
+    fsib_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return FSIB_OK;
+}
+
+int fsib_destroy(fsib_t h) {
+  if (!h) return FSIB_OK;
+  if (h->own) cudaStreamSynchronize(h->own);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  prof_flush(h);
+  for (auto e : h->pool) cudaEventDestroy(e);
+  free_ws(h->ws);
+  free_mesh(h->ws);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+  return FSIB_OK;
+}
+
+int fsib_set_stream(fsib_t h, void* stream) {
+  if (!h) return FSIB_EINVAL;
+  h->user = (cudaStream_t)stream;
+  return FSIB_OK;
+}
+
+int fsib_set_option(fsib_t h, const char* key, double v) {
+  if (!h || !key) return FSIB_EINVAL;
+  Plan q = h->p;
+  std::string k(key);
+  if (k == "precision") {
+    if (v != 0 && v != 1) return fail(h, FSIB_EINVAL, "precision must be 0 or 1");
+    q.prec = (int)v;
+  } else if (k == "sigma") {
+    if (!(v >= 1.5 && v <= 3.0)) return fail(h, FSIB_EINVAL, "sigma must be in [1.5, 3]");
+    q.sigma = v;
+  } else if (k == "width") {
+    if (!(v == 0 || (v >= 2 && v <= 16))) return fail(h, FSIB_EINVAL, "width must be 0 or in [2, 16]");
+    q.width_opt = (int)v;
+  } else if (k == "bin") {
+    if (!(v == 0 || (v >= 4 && v <= 64))) return fail(h, FSIB_EINVAL, "bin must be 0 or in [4, 64]");
+    q.bin_opt = (int)v;
+  } else if (k == "graph") {
+    h->p.use_graph = (v != 0);
+    return FSIB_OK;
+  } else if (k == "check_finite") {
+    h->p.check_finite = (v != 0);
+    return FSIB_OK;
+  } else {
+    return fail(h, FSIB_EINVAL, "unknown option key: " + k);
+  }
+  std::string err;
+  int rc = plan_sizes(q, err);
+  if (rc != FSIB_OK) return fail(h, rc, err);
+  cudaStreamSynchronize(h->own);
+  h->p = q;
+  return alloc_ws(h);
+}
+
+int fsib_get_info(fsib_t h, const char* key, double* value) {
+  if (!h || !key || !value) return FSIB_EINVAL;
+  std::string k(key);
+  const Plan& p = h->p;
+  if (k == "nf") *value = p.nf;
+  else if (k == "width") *value = p.w;
+  else if (k == "beta") *value = p.beta;
+  else if (k == "Nt") *value = p.Nt;
+  else if (k == "precision") *value = p.prec;
+  else if (k == "bin") *value = p.bins[0];
+  else if (k == "sigma") *value = p.sigma;
+  else if (k == "workspace_bytes") *value = (double)g_ws_bytes;
+  else if (k == "launches_per_step") *value = h->graph_kernels;
+  else return fail(h, FSIB_EINVAL, "unknown info key: " + k);
+  return FSIB_OK;
+}
+
+int fsib_set_force_curve(fsib_t h, double K) {
+  if (!h) return FSIB_EINVAL;
+  if (h->p.d != 2) return fail(h, FSIB_EINVAL, "curve force needs d = 2");
+  if (!std::isfinite(K)) return fail(h, FSIB_EINVAL, "K must be finite");
+  h->ws.force_kind = 1;
+  h->ws.curve_K = K;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return FSIB_OK;
+}
+
+int fsib_set_force_mesh(fsib_t h, const int* tri, int ntri, const double* Xref, double sigma) {
+  if (!h || !tri || !Xref || ntri < 1) return FSIB_EINVAL;
+  if (h->p.d != 3) return fail(h, FSIB_EINVAL, "mesh force needs d = 3");
+  const int M = h->p.M;
+  // connectivity on the host (integer work): undirected edges -> CSR adjacency
+  std::vector<int> t(3 * (size_t)ntri);
+  if (is_device_ptr(tri)) {
+    if (cudaMemcpy(t.data(), tri, t.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(h, FSIB_ECUDA, "copy of tri failed");
+  } else {
+    std::memcpy(t.data(), tri, t.size() * sizeof(int));
+  }
+  std::vector<std::vector<int>> adj(M);
+  for (int q = 0; q < ntri; ++q) {
+    for (int e = 0; e < 3; ++e) {
+      const int a = t[3 * q + e], b = t[3 * q + (e + 1) % 3];
+      if (a < 0 || a >= M || b < 0 || b >= M || a == b) return fail(h, FSIB_EINVAL, "bad triangle index");
+      adj[a].push_back(b);
+      adj[b].push_back(a);
+    }
+  }
+  std::vector<int> ptr(M + 1, 0), col;
+  for (int i = 0; i < M; ++i) {
+    auto& v = adj[i];
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    ptr[i + 1] = ptr[i] + (int)v.size();
+    col.insert(col.end(), v.begin(), v.end());
+  }
+  Workspace& ws = h->ws;
+  free_mesh(ws);
+  size_t tot = 0;
+  int rc = FSIB_OK;
+  ws.nnz = (int)col.size();
+  ws.ntri = ntri;
+  rc |= dmalloc(&ws.csr_ptr, sizeof(int) * (M + 1), tot);
+  rc |= dmalloc(&ws.csr_col, sizeof(int) * std::max<size_t>(1, col.size()), tot);
+  rc |= dmalloc(&ws.csr_k, sizeof(double) * std::max<size_t>(1, col.size()), tot);
+  rc |= dmalloc(&ws.tri, sizeof(int) * t.size(), tot);
+  if (rc != FSIB_OK) { free_mesh(ws); return fail(h, FSIB_ENOMEM, "mesh allocation failed"); }
+  cudaMemcpy(ws.csr_ptr, ptr.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
+  cudaMemcpy(ws.csr_col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(ws.tri, t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice);
+  if ((rc = begin(h)) != FSIB_OK) return rc;
+  Arg xr;
+  if ((rc = stage(h, 0, Xref, sizeof(double) * 3 * (size_t)M, true, xr)) != FSIB_OK) return rc;
+  launch_mesh_stiffness((const double*)xr.dev, ws.tri, ntri, M, sigma, ws.csr_ptr, ws.csr_col, ws.csr_k,
+                        ws.nnz, h->own);
+  ws.force_kind = 2;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return finish(h, true);
+}
+
+int fsib_force(fsib_t h, const double* X, double* c) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!X || !c) return fail(h, FSIB_EINVAL, "NULL array");
+  if (!h->ws.force_kind) return fail(h, FSIB_ESTATE, "no force model set");
+  Arg ax, ac;
+  if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, c, pts_bytes(h), false, ac)) != FSIB_OK) return rc;
+  do_force(h, (const double*)ax.dev, (double*)ac.dev, h->own);
+  if ((rc = unstage(h, ac)) != FSIB_OK) return rc;
+  return finish(h, ac.host != nullptr);
+}
+
+int fsib_spread(fsib_t h, const double* X, const double* F, const double* omega, void* fhat) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!X || !F || !fhat) return fail(h, FSIB_EINVAL, "NULL array");
+  Arg ax, af, ao, ah;
+  if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, F, pts_bytes(h), true, af)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 2, omega, sizeof(double) * h->p.M, true, ao)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 3, fhat, spec_bytes(h), false, ah)) != FSIB_OK) return rc;
+  if (h->p.prec == FSIB_FP64)
+    do_spread<double>(h, (const double*)ax.dev, (const double*)af.dev, (const double*)ao.dev,
+                      (C<double>*)ah.dev, h->own);
+  else
+    do_spread<float>(h, (const double*)ax.dev, (const double*)af.dev, (const double*)ao.dev,
+                     (C<float>*)ah.dev, h->own);
+  if ((rc = unstage(h, ah)) != FSIB_OK) return rc;
+  return finish(h, ah.host != nullptr);
+}
+
+int fsib_interp(fsib_t h, const void* uhat, const double* X, double* U) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!X || !U || !uhat) return fail(h, FSIB_EINVAL, "NULL array");
+  Arg ax, au, ah;
+  if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 3, uhat, spec_bytes(h), true, ah)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, U, pts_bytes(h), false, au)) != FSIB_OK) return rc;
+  do_bin(h, (const double*)ax.dev, h->own);
+  if (h->p.prec == FSIB_FP64)
+    do_interp_sorted<double>(h, (const C<double>*)ah.dev, (double*)au.dev, h->own);
+  else
+    do_interp_sorted<float>(h, (const C<float>*)ah.dev, (double*)au.dev, h->own);
+  if ((rc = unstage(h, au)) != FSIB_OK) return rc;
+  return finish(h, au.host != nullptr);
+}
+
+int fsib_fluid_step(fsib_t h, const void* fhat, void* uhat, void* uhat_half) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!fhat || !uhat) return fail(h, FSIB_EINVAL, "NULL array");
+  Arg af, au, ah;
+  if ((rc = stage(h, 0, fhat, spec_bytes(h), true, af)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, uhat, spec_bytes(h), !h->p.stokes, au)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 2, uhat_half, spec_bytes(h), false, ah)) != FSIB_OK) return rc;
+  void* half = ah.dev ? ah.dev : h->ws.uhalf;
+  if (h->p.prec == FSIB_FP64)
+    do_fluid<double>(h, (const C<double>*)af.dev, (C<double>*)au.dev, (C<double>*)half, h->own);
+  else
+    do_fluid<float>(h, (const C<float>*)af.dev, (C<float>*)au.dev, (C<float>*)half, h->own);
+  if ((rc = unstage(h, au)) != FSIB_OK) return rc;
+  if (!h->p.stokes && (rc = unstage(h, ah)) != FSIB_OK) return rc;
+  return finish(h, au.host != nullptr || ah.host != nullptr);
+}
+
+static int count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  int k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!X) return fail(h, FSIB_EINVAL, "X is NULL");
+  if (nsteps < 0) return fail(h, FSIB_EINVAL, "nsteps < 0");
+  if (!h->ws.force_kind) return fail(h, FSIB_ESTATE, "no force model set");
+  const bool ns = !h->p.stokes;
+  if (ns && (!uhat || !U)) return fail(h, FSIB_EINVAL, "Navier-Stokes step needs uhat and U");
+  Arg ax, au, aU;
+  if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 3, uhat, spec_bytes(h), ns, au)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, U, pts_bytes(h), ns, aU)) != FSIB_OK) return rc;
+  const bool f64 = h->p.prec == FSIB_FP64;
+  auto enqueue = [&](cudaStream_t st) {
+    if (f64) do_step<double>(h, (double*)ax.dev, (C<double>*)au.dev, (double*)aU.dev, st);
+    else do_step<float>(h, (double*)ax.dev, (C<float>*)au.dev, (double*)aU.dev, st);
+  };
+  if (nsteps > 0) {
+    if (h->p.use_graph && !h->prof_on) {
+      const void* key[3] = {ax.dev, au.dev, aU.dev};
+      if (!h->gexec || std::memcmp(key, h->gkey, sizeof(key)) != 0) {
+        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+          return fail(h, FSIB_ECUDA, "stream capture failed to start");
+        enqueue(h->own);
+        cudaError_t e = cudaStreamEndCapture(h->own, &g);
+        if (e != cudaSuccess || !g) return fail(h, FSIB_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+        h->graph_kernels = count_kernel_nodes(g);
+        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { h->gexec = nullptr; return fail(h, FSIB_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+        std::memcpy(h->gkey, key, sizeof(key));
+      }
+      for (int s = 0; s < nsteps; ++s)
+        if (cudaGraphLaunch(h->gexec, h->own) != cudaSuccess) return fail(h, FSIB_ECUDA, "graph launch failed");
+    } else {
+      for (int s = 0; s < nsteps; ++s) enqueue(h->own);
+    }
+  }
+  if ((rc = unstage(h, ax)) != FSIB_OK) return rc;
+  if ((rc = unstage(h, au)) != FSIB_OK) return rc;
+  if ((rc = unstage(h, aU)) != FSIB_OK) return rc;
+  const bool host = ax.host || au.host || aU.host;
+  rc = finish(h, host || h->p.check_finite);
+  if (rc != FSIB_OK) return rc;
+  if (h->p.check_finite) {
+    double inv[6];
+    const int r2 = f64 ? run_invariants<double>(h->p, h->ws, (const double*)ax.dev, nullptr, inv, h->own)
+                       : run_invariants<float>(h->p, h->ws, (const double*)ax.dev, nullptr, inv, h->own);
+    if (r2 == FSIB_ENONFINITE) return fail(h, FSIB_ENONFINITE, "non-finite positions after the step");
+    if (r2 != FSIB_OK) return fail(h, r2, "finite check failed");
+  }
+  return FSIB_OK;
+}
+
+int fsib_invariants(fsib_t h, const double* X, const void* uhat, double out[6]) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!X || !out) return fail(h, FSIB_EINVAL, "NULL array");
+  if (h->p.d == 3 && !h->ws.tri) return fail(h, FSIB_ESTATE, "3D invariants need the mesh (fsib_set_force_mesh)");
+  Arg ax, au;
+  if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 3, uhat, spec_bytes(h), true, au)) != FSIB_OK) return rc;
+  if (h->p.prec == FSIB_FP64)
+    rc = run_invariants<double>(h->p, h->ws, (const double*)ax.dev, (const C<double>*)au.dev, out, h->own);
+  else
+    rc = run_invariants<float>(h->p, h->ws, (const double*)ax.dev, (const C<float>*)au.dev, out, h->own);
+  const int rc2 = finish(h, true);
+  if (rc == FSIB_ENONFINITE) return fail(h, rc, "non-finite values in X or uhat");
+  if (rc != FSIB_OK) return fail(h, rc, "invariant reduction failed");
+  return rc2;
+}
+
+int fsib_profile_enable(fsib_t h, int on) {
+  if (!h) return FSIB_EINVAL;
+  prof_flush(h);
+  h->prof_on = (on != 0);
+  return FSIB_OK;
+}
+
+int fsib_profile_reset(fsib_t h) {
+  if (!h) return FSIB_EINVAL;
+  prof_flush(h);
+  h->sites.clear();
+  return FSIB_OK;
+}
+
+int fsib_profile_count(fsib_t h) {
+  if (!h) return FSIB_EINVAL;
+  prof_flush(h);
+  return (int)h->sites.size();
+}
+
+int fsib_profile_entry(fsib_t h, int i, char* name, int name_len, double* total_ms, int* launches,
+                       double* bytes_per_launch, double* flops_per_launch) {
+  if (!h) return FSIB_EINVAL;
+  prof_flush(h);
+  if (i < 0 || i >= (int)h->sites.size()) return fail(h, FSIB_EINVAL, "profile index out of range");
+  const auto& s = h->sites[i];
+  if (name && name_len > 0) {
+    std::strncpy(name, s.name.c_str(), (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (total_ms) *total_ms = s.total_ms;
+  if (launches) *launches = s.launches;
+  if (bytes_per_launch) *bytes_per_launch = s.bytes;
+  if (flops_per_launch) *flops_per_launch = s.flops;
+  return FSIB_OK;
+}
+
+}  // extern "C"

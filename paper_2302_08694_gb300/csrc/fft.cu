@@ -1,0 +1,300 @@
+// Transform passes between real grids and half spectra.
+//
+// A d-dimensional real transform is split into passes, one per axis:
+//  * rows (x axis, contiguous): real rows of length n <-> the N/2 kept modes
+//    m_x = 0..N/2-1. Two real rows are packed into one complex line.
+//  * strided (y or z axis): complex lines along an axis of stride `inner`,
+//    processed P adjacent lines at a time so that every global access is a run
+//    of P consecutive complex values.
+// Forward passes keep the modes of K_N (pruned output, the unpaired mode -N/2
+// written as zero); inverse passes read K_N and zero-pad to n. The deconvolution
+// of appendix A (division by the kernel's Fourier transform) or a plain scale is
+// applied where all mode indices are known: on the output of the last forward
+// pass and on the input of the first inverse pass.
+#include "fft_device.cuh"
+
+namespace fsib {
+
+constexpr int kP = 8;        // adjacent lines per strided tile
+constexpr int kQrows = 4;    // row pairs per CTA in the row passes
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Strided pass
+// ---------------------------------------------------------------------------
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kThreads)
+k_fft_strided(const C<T>* __restrict__ in, C<T>* __restrict__ out, int inner, int Nk,
+              FftLen fl, Mult<T> mult, const C<T>* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = fl.n;
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* a = tw + n;
+  C<T>* b = a + n * kP;
+  const int ntile = (inner + kP - 1) / kP;
+  const long long co = blockIdx.x / ntile;       // component * outer + outer index
+  const int q0 = (blockIdx.x % ntile) * kP;
+  const int Lin = INV ? Nk : n, Lout = INV ? n : Nk;
+  const int h = Nk / 2;
+  const C<T>* src = in + co * (long long)Lin * inner;
+  C<T>* dst = out + co * (long long)Lout * inner;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
+  for (int t = threadIdx.x; t < n * kP; t += blockDim.x) {
+    const int p = t % kP, i = t / kP, q = q0 + p;
+    C<T> v = mk<T>(T(0), T(0));
+    if (q < inner) {
+      if (!INV) {
+        v = src[(long long)i * inner + q];
+      } else {
+        // FFT position i holds mode i (i < N/2) or i - n (i > n - N/2); the rest is padding
+        const int si = (i < h) ? i : ((i > n - h) ? i - (n - Nk) : -1);
+        if (si >= 0) {
+          v = src[(long long)si * inner + q];
+          T s = mult.scale;
+          if (mult.dline) s *= mult.dline[si];
+          if (mult.dplane) s *= mult.dplane[q];
+          v = cscale<T>(v, s);
+        }
+      }
+    }
+    a[i * kP + p] = v;
+  }
+  __syncthreads();
+  C<T>* r = smem_fft<T, INV>(a, b, kP, 1, kP, true, fl, tw);
+  if (!INV) {
+    for (int t = threadIdx.x; t < Nk * kP; t += blockDim.x) {
+      const int p = t % kP, io = t / kP, q = q0 + p;
+      if (q >= inner) continue;
+      C<T> v = mk<T>(T(0), T(0));
+      if (io != h) {
+        const int fi = (io < h) ? io : io + (n - Nk);
+        v = r[fi * kP + p];
+        T s = mult.scale;
+        if (mult.dline) s *= mult.dline[io];
+        if (mult.dplane) s *= mult.dplane[q];
+        v = cscale<T>(v, s);
+      }
+      dst[(long long)io * inner + q] = v;
+    }
+  } else {
+    for (int t = threadIdx.x; t < n * kP; t += blockDim.x) {
+      const int p = t % kP, i = t / kP, q = q0 + p;
+      if (q < inner) dst[(long long)i * inner + q] = r[i * kP + p];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row passes: real rows (length n) <-> half spectra (N/2 modes)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
+           FftLen fl, const C<T>* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = fl.n, ls = n + 1, h = Nk / 2;
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* a = tw + n;
+  C<T>* b = a + kQrows * ls;
+  const long long pr0 = (long long)blockIdx.x * kQrows;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
+  for (int t = threadIdx.x; t < kQrows * n; t += blockDim.x) {
+    const int p = t / n, x = t % n;
+    const long long pr = pr0 + p;
+    C<T> v = mk<T>(T(0), T(0));
+    if (pr < npairs) v = mk<T>(in[(2 * pr) * n + x], in[(2 * pr + 1) * n + x]);
+    a[p * ls + x] = v;
+  }
+  __syncthreads();
+  C<T>* r = smem_fft<T, false>(a, b, kQrows, ls, 1, false, fl, tw);
+  for (int t = threadIdx.x; t < kQrows * h; t += blockDim.x) {
+    const int p = t / h, k = t % h;
+    const long long pr = pr0 + p;
+    if (pr >= npairs) continue;
+    const C<T> Z = r[p * ls + k];
+    const C<T> Zc = cconj<T>(r[p * ls + ((n - k) % n)]);
+    const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
+    out[(2 * pr) * h + k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
+    out[(2 * pr + 1) * h + k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
+  }
+}
+
+// Build the packed complex spectrum Z = A + iB of two real rows from their half spectra.
+template <typename T>
+__device__ __forceinline__ C<T> pack_rows(const C<T>* __restrict__ A, const C<T>* __restrict__ B,
+                                          int k, int n, int h) {
+  if (k == 0) return mk<T>(A[0].x, B[0].x);  // Hermitian part of the m_x = 0 column
+  if (k < h) {
+    const C<T> a = A[k], bb = B[k];
+    return mk<T>(a.x - bb.y, a.y + bb.x);
+  }
+  if (k > n - h) {
+    const C<T> a = A[n - k], bb = B[n - k];  // conj(A) + i conj(B)
+    return mk<T>(a.x + bb.y, -a.y + bb.x);
+  }
+  return mk<T>(T(0), T(0));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
+           FftLen fl, const C<T>* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = fl.n, ls = n + 1, h = Nk / 2;
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* a = tw + n;
+  C<T>* b = a + kQrows * ls;
+  const long long pr0 = (long long)blockIdx.x * kQrows;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
+  for (int t = threadIdx.x; t < kQrows * n; t += blockDim.x) {
+    const int p = t / n, k = t % n;
+    const long long pr = pr0 + p;
+    C<T> v = mk<T>(T(0), T(0));
+    if (pr < npairs) v = pack_rows<T>(in + (2 * pr) * h, in + (2 * pr + 1) * h, k, n, h);
+    a[p * ls + k] = v;
+  }
+  __syncthreads();
+  C<T>* r = smem_fft<T, true>(a, b, kQrows, ls, 1, false, fl, tw);
+  for (int t = threadIdx.x; t < kQrows * n; t += blockDim.x) {
+    const int p = t / n, x = t % n;
+    const long long pr = pr0 + p;
+    if (pr >= npairs) continue;
+    const C<T> z = r[p * ls + x];
+    out[(2 * pr) * n + x] = z.x;
+    out[(2 * pr + 1) * n + x] = z.y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Products of the velocity components on the dealiasing grid (three-halves rule):
+// half spectra of u_a along x -> real rows u_a(x) -> u_a u_b -> half spectra of
+// the d(d+1)/2 products. Input [d][nrows][N/2], output [d(d+1)/2][nrows][N/2],
+// products ordered (xx, xy, xz, yy, yz, zz) in 3D and (xx, xy, yy) in 2D.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows,
+               int Nk, FftLen fl, const C<T>* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = fl.n, ls = n + 1, h = Nk / 2;
+  const int np = d * (d + 1) / 2;
+  const long long npairs = nrows / 2;
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* a = tw + n;
+  C<T>* b = a + kQrows * 6 * ls;
+  const long long pr0 = (long long)blockIdx.x * kQrows;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
+  for (int t = threadIdx.x; t < kQrows * d * n; t += blockDim.x) {
+    const int k = t % n, line = t / n, p = line / d, c = line % d;
+    const long long pr = pr0 + p;
+    C<T> v = mk<T>(T(0), T(0));
+    if (pr < npairs) {
+      const C<T>* base = in + ((long long)c * nrows + 2 * pr) * h;
+      v = pack_rows<T>(base, base + h, k, n, h);
+    }
+    a[line * ls + k] = v;
+  }
+  __syncthreads();
+  C<T>* r = smem_fft<T, true>(a, b, kQrows * d, ls, 1, false, fl, tw);
+  C<T>* o = (r == a) ? b : a;
+  // products: re holds row 2p, im holds row 2p+1
+  for (int t = threadIdx.x; t < kQrows * np * n; t += blockDim.x) {
+    const int x = t % n, line = t / n, p = line / np, ab = line % np;
+    int ca = 0, cb = ab;
+    if (d == 3) {
+      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+      ca = ia[ab]; cb = ib[ab];
+    } else {
+      const int ia[3] = {0, 0, 1}, ib[3] = {0, 1, 1};
+      ca = ia[ab]; cb = ib[ab];
+    }
+    const C<T> ua = r[(p * d + ca) * ls + x], ub = r[(p * d + cb) * ls + x];
+    o[line * ls + x] = mk<T>(ua.x * ub.x, ua.y * ub.y);
+  }
+  __syncthreads();
+  C<T>* f = smem_fft<T, false>(o, r, kQrows * np, ls, 1, false, fl, tw);
+  for (int t = threadIdx.x; t < kQrows * np * h; t += blockDim.x) {
+    const int k = t % h, line = t / h, p = line / np, ab = line % np;
+    const long long pr = pr0 + p;
+    if (pr >= npairs) continue;
+    const C<T> Z = f[line * ls + k];
+    const C<T> Zc = cconj<T>(f[line * ls + ((n - k) % n)]);
+    const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
+    C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
+    ob[k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
+    ob[h + k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+// Raise the dynamic shared-memory limit of a kernel to the device's opt-in maximum,
+// once per kernel (this is not a stream operation, so it is also safe while a
+// stream is being captured).
+template <typename K>
+static void set_smem(K kern, size_t bytes) {
+  raise_smem_limit(reinterpret_cast<const void*>(kern));
+  (void)bytes;
+}
+
+template <typename T>
+void launch_fft_strided(const C<T>* in, C<T>* out, int ncomp, int outer, int inner, int Nk,
+                        const FftLen& fl, bool inverse, Mult<T> mult, const C<T>* tw,
+                        cudaStream_t st) {
+  const int ntile = (inner + kP - 1) / kP;
+  const long long blocks = (long long)ncomp * outer * ntile;
+  const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * fl.n * kP);
+  if (inverse) {
+    set_smem(k_fft_strided<T, true>, smem);
+    k_fft_strided<T, true><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
+  } else {
+    set_smem(k_fft_strided<T, false>, smem);
+    k_fft_strided<T, false><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
+  }
+}
+
+template <typename T>
+void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const FftLen& fl,
+                         const C<T>* tw, cudaStream_t st) {
+  const long long npairs = nrows / 2;
+  const long long blocks = (npairs + kQrows - 1) / kQrows;
+  const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
+  set_smem(k_rows_r2c<T>, smem);
+  k_rows_r2c<T><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
+}
+
+template <typename T>
+void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
+                         const C<T>* tw, cudaStream_t st) {
+  const long long npairs = nrows / 2;
+  const long long blocks = (npairs + kQrows - 1) / kQrows;
+  const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
+  set_smem(k_rows_c2r<T>, smem);
+  k_rows_c2r<T><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
+}
+
+template <typename T>
+void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int Nk,
+                         const FftLen& fl, const C<T>* tw, cudaStream_t st) {
+  const long long npairs = nrows / 2;
+  const long long blocks = (npairs + kQrows - 1) / kQrows;
+  const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * 6 * (fl.n + 1));
+  set_smem(k_rows_product<T>, smem);
+  k_rows_product<T><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, d, nrows, Nk, fl, tw);
+}
+
+#define INST(T)                                                                                  \
+  template void launch_fft_strided<T>(const C<T>*, C<T>*, int, int, int, int, const FftLen&,     \
+                                      bool, Mult<T>, const C<T>*, cudaStream_t);                 \
+  template void launch_fft_rows_r2c<T>(const T*, C<T>*, long long, int, const FftLen&,           \
+                                       const C<T>*, cudaStream_t);                               \
+  template void launch_fft_rows_c2r<T>(const C<T>*, T*, long long, int, const FftLen&,           \
+                                       const C<T>*, cudaStream_t);                               \
+  template void launch_rows_product<T>(const C<T>*, C<T>*, int, long long, int, const FftLen&,   \
+                                       const C<T>*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace fsib

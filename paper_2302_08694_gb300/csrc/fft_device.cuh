@@ -1,0 +1,105 @@
+// Shared-memory mixed-radix FFT used by every transform pass.
+//
+// Self-sorting (Stockham) formulation: stage s with radix R reads element
+// j + r*n/R (r = 0..R-1) of each line, multiplies by twiddles
+// w^{(j mod Ns) r n/(Ns R)}, does an R-point DFT and writes to
+// (j div Ns) Ns R + (j mod Ns) + r Ns, where Ns is the product of the radices
+// of the earlier stages. The output is in natural order after the last stage.
+// Lines live in shared memory; element i of line l is at base[l*ls + i*es].
+// Two buffers alternate between stages.
+#pragma once
+#include "fsib_internal.cuh"
+
+namespace fsib {
+
+template <typename T> struct Consts;
+template <> struct Consts<float>  { static constexpr float  s3 = 0.866025403784438646763723170752936183f; };
+template <> struct Consts<double> { static constexpr double s3 = 0.866025403784438646763723170752936183; };
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft2(C<T>* v) {
+  C<T> a = v[0], b = v[1];
+  v[0] = cadd<T>(a, b);
+  v[1] = csub<T>(a, b);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft3(C<T>* v) {
+  // forward: y1 = v0 - (v1+v2)/2 - i s3 (v1 - v2), y2 = v0 - (v1+v2)/2 + i s3 (v1 - v2)
+  C<T> s = cadd<T>(v[1], v[2]);
+  C<T> d = csub<T>(v[1], v[2]);
+  C<T> m = mk<T>(v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y);
+  C<T> t = cscale<T>(d, Consts<T>::s3);
+  C<T> it = INV ? cmul_i<T>(t) : cmul_mi<T>(t);
+  v[0] = cadd<T>(v[0], s);
+  v[1] = cadd<T>(m, it);
+  v[2] = csub<T>(m, it);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(C<T>* v) {
+  C<T> s02 = cadd<T>(v[0], v[2]), d02 = csub<T>(v[0], v[2]);
+  C<T> s13 = cadd<T>(v[1], v[3]), d13 = csub<T>(v[1], v[3]);
+  C<T> id = INV ? cmul_i<T>(d13) : cmul_mi<T>(d13);
+  v[0] = cadd<T>(s02, s13);
+  v[2] = csub<T>(s02, s13);
+  v[1] = cadd<T>(d02, id);
+  v[3] = csub<T>(d02, id);
+}
+
+template <typename T, bool INV, int R>
+__device__ __forceinline__ void stage_item(const C<T>* __restrict__ src, C<T>* __restrict__ dst,
+                                           int l, int j, int n, int Ns, int ls, int es,
+                                           const C<T>* __restrict__ tw) {
+  const int nb = n / R;
+  C<T> v[R];
+  const C<T>* s = src + l * ls;
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * es];
+  const int k = j % Ns;
+  if (Ns > 1) {
+    const int step = n / (Ns * R);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      C<T> w = tw[k * r * step];  // k r step < n since k < Ns, r < R
+      if (INV) w = cconj<T>(w);
+      v[r] = cmul<T>(v[r], w);
+    }
+  }
+  if (R == 2) dft2<T, INV>(v);
+  if (R == 3) dft3<T, INV>(v);
+  if (R == 4) dft4<T, INV>(v);
+  C<T>* d = dst + l * ls;
+  const int o = (j / Ns) * Ns * R + k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) d[(o + r * Ns) * es] = v[r];
+}
+
+// Transform nl lines; returns the buffer that holds the result (a or b).
+// lines_fast: consecutive threads take consecutive lines (strided layouts) rather
+// than consecutive butterflies of one line (contiguous rows).
+// Must be called by all threads of the block; ends with a barrier.
+template <typename T, bool INV>
+__device__ C<T>* smem_fft(C<T>* a, C<T>* b, int nl, int ls, int es, bool lines_fast,
+                          const FftLen& fl, const C<T>* __restrict__ tw) {
+  const int n = fl.n;
+  int Ns = 1;
+  for (int s = 0; s < fl.nstages; ++s) {
+    const int R = fl.radix[s];
+    const int nb = n / R;
+    const int total = nl * nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      int l, j;
+      if (lines_fast) { l = t % nl; j = t / nl; } else { j = t % nb; l = t / nb; }
+      if (R == 4) stage_item<T, INV, 4>(a, b, l, j, n, Ns, ls, es, tw);
+      else if (R == 2) stage_item<T, INV, 2>(a, b, l, j, n, Ns, ls, es, tw);
+      else stage_item<T, INV, 3>(a, b, l, j, n, Ns, ls, es, tw);
+    }
+    __syncthreads();
+    C<T>* t = a; a = b; b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+}  // namespace fsib

@@ -1,0 +1,159 @@
+// Internal declarations of the FSIB library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/fsib.h"
+
+namespace fsib {
+
+// ---------------------------------------------------------------------------
+// Complex numbers: plain two-component structs so that loads are 8/16-byte vectors.
+// ---------------------------------------------------------------------------
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float>  { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <typename T> using C = typename cplx_t<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> mk(T x, T y) { C<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> cconj(C<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// multiply by +i (or -i)
+template <typename T> __host__ __device__ __forceinline__ C<T> cmul_i(C<T> a) { return mk<T>(-a.y, a.x); }
+template <typename T> __host__ __device__ __forceinline__ C<T> cmul_mi(C<T> a) { return mk<T>(a.y, -a.x); }
+
+// ---------------------------------------------------------------------------
+// 1-D FFT plan of one length n = 2^a 3^b (radix stages of 4, 2 and 3).
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 12;
+constexpr int kMaxFFT = 512;
+
+struct FftLen {
+  int n = 0;
+  int nstages = 0;
+  int radix[kMaxStages] = {0};
+  int tw_off = 0;  // offset of exp(-2 pi i j/n), j = 0..n-1, in the twiddle table
+};
+
+// Multiplier applied at the mode end of a strided pass:
+//   value *= scale * dline[m_line] * (dplane ? dplane[q] : 1)
+// where m_line indexes the pass axis (length-N FFT order) and q the inner index.
+template <typename T> struct Mult {
+  T scale = T(1);
+  const T* dline = nullptr;
+  const T* dplane = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// Plan and workspaces of one problem (owned by fsib_plan).
+// ---------------------------------------------------------------------------
+struct Plan {
+  int d = 3, N = 0, M = 0;
+  double L = 1.0, mu = 1.0, rho = 1.0, dt = 1e-3, tol = 1e-12;
+  bool stokes = false;
+  int prec = FSIB_FP64;
+  double sigma = 2.0;
+  int width_opt = 0, bin_opt = 0;
+  int use_graph = 1, check_finite = 0;
+
+  // derived
+  int nf = 0;        // fine grid per axis
+  int w = 0;         // kernel width (cells)
+  double beta = 0;   // ES shape
+  int Nt = 0;        // dealias grid per axis
+  int bins[3] = {1, 1, 1}, nbin[3] = {1, 1, 1};
+  long long nbins = 1;
+  FftLen fl_nf, fl_nt;
+};
+
+struct Workspace {
+  // twiddles (double and float copies), deconvolution tables
+  void* tw = nullptr;        // C<T> table, T per precision
+  void* dline = nullptr;     // T[N]
+  void* dplane = nullptr;    // T[N*N/2] (3D) or T[N/2] (2D)
+  // fine grid (real, d components) and two complex scratch buffers
+  void* grid = nullptr;  size_t grid_bytes = 0;
+  void* s1 = nullptr;    size_t s1_bytes = 0;
+  void* s2 = nullptr;    size_t s2_bytes = 0;
+  void* fhat = nullptr;  size_t spec_bytes = 0;  // d * N^{d-1} * N/2 complex
+  void* uhalf = nullptr;
+  // sort
+  int* bin_of = nullptr;      // [M]
+  int* rank = nullptr;        // [M]
+  int* counts = nullptr;      // [nbins]
+  int* offsets = nullptr;     // [nbins + 1]
+  int* occ = nullptr;         // [nbins] occupied bins; occ count at offsets[nbins]? (see nocc)
+  int* nocc = nullptr;        // [1]
+  int* perm = nullptr;        // [M] sorted -> original
+  int* i0 = nullptr;          // [d][M] window start per axis (sorted order)
+  void* delta = nullptr;      // T[d][M] i0 - t (sorted order)
+  // Lagrangian scratch (double)
+  double* Xh = nullptr;       // [d][M]
+  double* cw = nullptr;       // [d][M] omega * F
+  double* Uh = nullptr;       // [d][M]
+  double* omega_ones = nullptr;
+  // force models
+  int force_kind = 0;         // 0 none, 1 curve, 2 mesh
+  double curve_K = 0.0;
+  int* csr_ptr = nullptr; int* csr_col = nullptr; double* csr_k = nullptr; int nnz = 0;
+  int* tri = nullptr; int ntri = 0;
+  // reductions
+  double* red = nullptr;      // partial sums
+  int red_blocks = 0;
+  int* flag = nullptr;
+  // staging for host pointers
+  void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t stage_bytes[4] = {0, 0, 0, 0};
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (implemented in the .cu files). All enqueue on `st`.
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_fft_strided(const C<T>* in, C<T>* out, int ncomp, int outer, int inner,
+                        int Nk, const FftLen& fl, bool inverse, Mult<T> mult,
+                        const C<T>* tw, cudaStream_t st);
+template <typename T>
+void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const FftLen& fl,
+                         const C<T>* tw, cudaStream_t st);
+template <typename T>
+void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
+                         const C<T>* tw, cudaStream_t st);
+template <typename T>
+void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int Nk,
+                         const FftLen& fl, const C<T>* tw, cudaStream_t st);
+
+void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st);
+template <typename T>
+void launch_spread(const Plan& p, Workspace& ws, const double* cw, const double* omega,
+                   T* grid, cudaStream_t st);
+template <typename T>
+void launch_interp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st);
+
+template <typename T>
+void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t st);
+template <typename T>
+void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
+                      C<T>* out, bool half, cudaStream_t st);
+
+void launch_axpy(double* y, const double* x, const double* v, double a, long long n, cudaStream_t st);
+void launch_force(const Plan& p, const Workspace& ws, const double* X, double* c, cudaStream_t st);
+void launch_mesh_stiffness(const double* Xref, const int* tri, int ntri, int M, double sigma,
+                           int* csr_ptr, int* csr_col, double* csr_k, int nnz, cudaStream_t st);
+template <typename T>
+int run_invariants(const Plan& p, Workspace& ws, const double* X, const C<T>* uhat,
+                   double* out, cudaStream_t st);
+
+int check_last(const char* where);
+void raise_smem_limit(const void* kernel);
+
+}  // namespace fsib

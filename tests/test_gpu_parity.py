@@ -1,0 +1,277 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Tolerances: FP64 mode must match the oracle to 1e-10 relative (2-norm and
+element-wise against the largest entry); FP32-mixed mode to 1e-5 relative.
+Sizes span several bins and FFT tiles with ragged tails; points include
+coordinates outside [0, L) (the library wraps them periodically).
+"""
+import numpy as np
+import pytest
+
+from oracle import spectral as sp
+from oracle import stepper as st
+from oracle import lagrangian as lg
+from paper_2302_08694_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+NTOL = {"fp64": 1e-12, "mixed": 1e-6}
+
+
+def rel2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def cuda(a, torch):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def half_random(rng, d, N):
+    shape = (d,) + (N,) * (d - 1) + (N // 2,)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def make(lib, N, d, M, prec, mu=1.0, rho=0.0, dt=1e-3, **kw):
+    return lib.Problem(N, d, M, mu, rho, dt, NTOL[prec], precision=prec, **kw)
+
+
+# --- type-1 / type-2 against the direct sums --------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1)])
+def test_spread_matches_oracle(lib, torch_mod, prec, d, N, M):
+    torch = torch_mod
+    rng = np.random.default_rng(100 + d * N + M)
+    X = rng.uniform(-0.7, 1.9, (d, M))
+    F = rng.standard_normal((d, M))
+    om = rng.uniform(0.5, 1.5, M)
+    pb = make(lib, N, d, M, prec)
+    fh = pb.spread(cuda(X, torch), cuda(F, torch), cuda(om, torch))
+    torch.cuda.synchronize()
+    ref = sp.full_to_half(sp.spread_direct(X, F * om[None, :], N), N)
+    got = to_np(fh)
+    assert rel2(got, ref) <= TOL[prec]
+    assert relmax(got, ref) <= 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1)])
+def test_interp_matches_oracle(lib, torch_mod, prec, d, N, M):
+    torch = torch_mod
+    rng = np.random.default_rng(200 + d * N + M)
+    X = rng.uniform(-0.5, 1.5, (d, M))
+    H = half_random(rng, d, N)
+    pb = make(lib, N, d, M, prec)
+    Ht = cuda(H if prec == "fp64" else H.astype(np.complex64), torch)
+    U = pb.interp(Ht, cuda(X, torch))
+    torch.cuda.synchronize()
+    ref = sp.interp_direct(sp.half_to_full(H, N, d), X, N)
+    assert rel2(to_np(U), ref) <= TOL[prec]
+
+
+def test_spread_interp_host_pointers_match_device(lib, torch_mod):
+    torch = torch_mod
+    rng = np.random.default_rng(7)
+    d, N, M = 3, 12, 333
+    X = rng.uniform(0, 1, (d, M))
+    F = rng.standard_normal((d, M))
+    pb = make(lib, N, d, M, "fp64")
+    dev = to_np(pb.spread(cuda(X, torch), cuda(F, torch)))
+    host = np.zeros(pb.spec_shape, dtype=np.complex128)
+    pb.spread(X, F, None, out=host)
+    assert np.array_equal(dev, host) or rel2(host, dev) < 1e-14
+    U = np.zeros((d, M))
+    pb.interp(host, X, out=U)
+    ref = sp.interp_direct(sp.half_to_full(host, N, d), X, N)
+    assert rel2(U, ref) <= 1e-10
+
+
+def test_spread_interp_adjoint(lib, torch_mod):
+    """Duality (Sec. 4.4): L^d <f-hat, u-hat> = <c, U> holds for the GPU pair to NUFFT tolerance."""
+    torch = torch_mod
+    rng = np.random.default_rng(8)
+    d, N, M = 3, 16, 400
+    X = rng.uniform(0, 1, (d, M))
+    c = rng.standard_normal((d, M))
+    H = half_random(rng, d, N)
+    pb = make(lib, N, d, M, "fp64")
+    fh = to_np(pb.spread(cuda(X, torch), cuda(c, torch)))
+    U = to_np(pb.interp(cuda(H, torch), cuda(X, torch)))
+    lhs = np.sum(sp.half_to_full(fh, N, d) * np.conj(sp.half_to_full(H, N, d))).real
+    rhs = np.sum(c * U)
+    assert abs(lhs - rhs) <= 1e-10 * np.sum(np.abs(c) * np.abs(U))
+
+
+# --- fluid updates --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("d,N", [(2, 16), (3, 12)])
+def test_stokeslet_matches_oracle(lib, torch_mod, prec, d, N):
+    torch = torch_mod
+    rng = np.random.default_rng(300 + d + N)
+    H = half_random(rng, d, N)
+    pb = make(lib, N, d, 4, prec, mu=0.7, rho=0.0)
+    dt = np.complex128 if prec == "fp64" else np.complex64
+    f = cuda(H.astype(dt), torch)
+    u = pb.new_spec()
+    pb.fluid_step(f, u)
+    torch.cuda.synchronize()
+    ref = sp.full_to_half(sp.stokeslet(sp.half_to_full(H, N, d), N, 0.7), N)
+    got = sp.full_to_half(sp.half_to_full(to_np(u).astype(np.complex128), N, d), N)
+    assert rel2(got, ref) <= (1e-14 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("d,N", [(2, 16), (2, 10), (3, 8), (3, 12)])
+def test_ns_substeps_match_oracle(lib, torch_mod, prec, d, N):
+    torch = torch_mod
+    rng = np.random.default_rng(400 + d + N)
+    mu, rho, dt = 0.05, 1.3, 0.02
+    u0 = sp.leray(sp.half_to_full(half_random(rng, d, N), N, d), N)
+    f = sp.half_to_full(half_random(rng, d, N), N, d)
+    pb = make(lib, N, d, 4, prec, mu=mu, rho=rho, dt=dt)
+    cd = np.complex128 if prec == "fp64" else np.complex64
+    ft = cuda(sp.full_to_half(f, N).astype(cd), torch)
+    ut = cuda(sp.full_to_half(u0, N).astype(cd), torch)
+    uh = pb.new_spec()
+    pb.fluid_step(ft, ut, uh)
+    torch.cuda.synchronize()
+    rh, r1 = sp.ns_substeps(f, u0, N, mu, rho, dt)
+    gh = sp.half_to_full(to_np(uh).astype(np.complex128), N, d)
+    g1 = sp.half_to_full(to_np(ut).astype(np.complex128), N, d)
+    assert rel2(gh, rh) <= TOL[prec]
+    assert rel2(g1, r1) <= TOL[prec]
+    assert sp.max_divergence(g1, N) <= (1e-13 if prec == "fp64" else 1e-6)
+
+
+# --- whole steps ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_stokes2d_steps_match_oracle(lib, torch_mod, prec):
+    """Quasi-static Stokes stepper on a closed elastic curve (the 2D Stokes workload, reduced)."""
+    torch = torch_mod
+    N, M, dt, nsteps = 32, 128, 1e-3, 5
+    rng = np.random.default_rng(1)
+    X0 = wl.ellipse(M, 0.3, 0.2, rng.uniform(0, 1, 2))
+    pb = make(lib, N, 2, M, prec, mu=1.0, rho=0.0, dt=dt)
+    pb.set_force_curve(1.0)
+    Xt = cuda(X0, torch)
+    pb.step(Xt, nsteps=nsteps)
+    torch.cuda.synchronize()
+    force = st.curve_model(1.0)
+    X = X0.copy()
+    for _ in range(nsteps):
+        X = st.stokes_step(X, force, N, 1.0, dt)
+    disp = X - X0
+    assert rel2(to_np(Xt) - X0, disp) <= TOL[prec] * (10 if prec == "mixed" else 1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ns3d_steps_match_oracle(lib, torch_mod, prec):
+    torch = torch_mod
+    N, dt, nsteps, mu, rho = 12, 2e-3, 2, 0.01, 1.0
+    Xref, tri = wl.latlong_sphere(6, 12, 0.25, (0.52, 0.47, 0.5))
+    X0 = 0.5 + (Xref - 0.5) * np.array([[1.15], [0.9], [1.0]])
+    M = X0.shape[1]
+    rng = np.random.default_rng(5)
+    u0 = 0.1 * sp.leray(sp.half_to_full(half_random(rng, 3, N), N, 3), N)
+    pb = make(lib, N, 3, M, prec, mu=mu, rho=rho, dt=dt)
+    pb.set_force_mesh(tri, cuda(Xref, torch), 1.0)
+    cd = np.complex128 if prec == "fp64" else np.complex64
+    Xt = cuda(X0, torch)
+    ut = cuda(sp.full_to_half(u0, N).astype(cd), torch)
+    Ut = pb.interp(ut, Xt)
+    pb.step(Xt, ut, Ut, nsteps=nsteps)
+    torch.cuda.synchronize()
+    force = st.mesh_model(Xref, tri, 1.0)
+    X, u = X0.copy(), u0.copy()
+    U = sp.interp_direct(u, X, N)
+    for _ in range(nsteps):
+        X, u, U = st.ns_step(X, u, U, force, N, mu, rho, dt)
+    assert rel2(to_np(Xt) - X0, X - X0) <= TOL[prec] * (10 if prec == "mixed" else 1)
+    assert rel2(sp.half_to_full(to_np(ut).astype(np.complex128), N, 3), u) <= TOL[prec]
+    assert rel2(to_np(Ut), U) <= TOL[prec]
+
+
+def test_step_graph_and_direct_agree(lib, torch_mod):
+    torch = torch_mod
+    N, M = 16, 64
+    X0 = wl.ellipse(M, 0.25, 0.2, (0.4, 0.6))
+    res = []
+    for graph in (True, False):
+        pb = make(lib, N, 2, M, "fp64", mu=0.02, rho=1.0, dt=1e-3, graph=graph)
+        pb.set_force_curve(1.0)
+        X = cuda(X0, torch)
+        u = pb.new_spec()
+        U = torch.zeros_like(X)
+        pb.step(X, u, U, nsteps=3)
+        torch.cuda.synchronize()
+        res.append(to_np(X))
+    assert rel2(res[0] - X0, res[1] - X0) <= 1e-12
+
+
+# --- invariants -------------------------------------------------------------------------------
+
+def test_invariants_match_oracle(lib, torch_mod):
+    torch = torch_mod
+    N = 12
+    Xref, tri = wl.latlong_sphere(5, 10, 0.25, (0.5, 0.5, 0.5))
+    X = 0.5 + (Xref - 0.5) * np.array([[1.1], [0.95], [1.0]])
+    M = X.shape[1]
+    rng = np.random.default_rng(11)
+    H = half_random(rng, 3, N)
+    pb = make(lib, N, 3, M, "fp64", mu=0.3, rho=1.7)
+    pb.set_force_mesh(tri, Xref, 1.0)
+    inv = pb.invariants(cuda(X, torch), cuda(H, torch))
+    u = sp.half_to_full(H, N, 3)
+    edges, K = lg.spring_stiffness(Xref, tri, 1.0)
+    assert abs(inv["volume"] - lg.enclosed_volume(X, tri)) <= 1e-14
+    assert abs(inv["Ep"] - lg.spring_energy(X, edges, K)) <= 1e-12 * abs(inv["Ep"])
+    assert abs(inv["Ek"] - sp.kinetic_energy(u, N, 1.7)) <= 1e-12 * inv["Ek"]
+    assert abs(inv["dissipation"] - sp.dissipation(u, N, 0.3)) <= 1e-12 * inv["dissipation"]
+    assert abs(inv["u0"] - np.linalg.norm(u[:, 0, 0, 0])) <= 1e-14
+    assert abs(inv["max_div"] - sp.max_divergence(u, N)) <= 1e-12
+    # force of the model equals the oracle's spring force
+    c = to_np(pb.force(cuda(X, torch)))
+    assert rel2(c, lg.spring_force(X, edges, K)) <= 1e-14
+
+
+def test_nonfinite_is_reported(lib, torch_mod):
+    torch = torch_mod
+    X = wl.ellipse(32, 0.2, 0.2, (0.5, 0.5))
+    X[0, 3] = np.nan
+    pb = make(lib, 8, 2, 32, "fp64")
+    pb.set_force_curve(1.0)
+    with pytest.raises(lib.FsibError) as ei:
+        pb.invariants(cuda(X, torch))
+    assert ei.value.code == -4
+
+
+def test_bad_arguments_rejected(lib, torch_mod):
+    with pytest.raises(lib.FsibError):
+        lib.Problem(7, 3, 10, 1.0, 1.0, 1e-3, 1e-6)      # odd N
+    with pytest.raises(lib.FsibError):
+        lib.Problem(16, 4, 10, 1.0, 1.0, 1e-3, 1e-6)     # d = 4
+    pb = lib.Problem(16, 2, 10, 1.0, 1.0, 1e-3, 1e-6)
+    with pytest.raises(lib.FsibError):
+        pb.set_option("no_such_key", 1)
+    with pytest.raises(lib.FsibError) as ei:
+        pb.step(np.zeros((2, 10)), pb.new_spec(), np.zeros((2, 10)))  # no force model
+    assert ei.value.code == -7

@@ -271,3 +271,19 @@ def test_trapezoid_spread_converges_exponentially():
     errs = [np.max(np.abs(fh(M) - ref)) for M in (8, 16, 32)]
     assert errs[1] < 1e-2 * errs[0]
     assert errs[2] < 1e-12
+
+
+def test_spread_at_modes_matches_full_sum():
+    rng = np.random.default_rng(41)
+    X = rng.uniform(0, 1, (3, 17))
+    c = rng.standard_normal((3, 17))
+    N = 6
+    F = sp.spread_direct(X, c, N)
+    m = sp.mode_ints(N)
+    idx = rng.integers(0, N, (9, 3))
+    modes = np.stack([m[idx[:, 0]], m[idx[:, 1]], m[idx[:, 2]]], axis=1)  # (mx, my, mz)
+    S = sp.spread_at_modes(X, c, modes)
+    for q in range(9):
+        if any(v == -N // 2 for v in modes[q]):
+            continue
+        assert np.allclose(S[:, q], F[:, idx[q, 2], idx[q, 1], idx[q, 0]], atol=1e-14)
