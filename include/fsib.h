@@ -168,6 +168,34 @@ int fsib_profile_entry(fsib_t h, int i, char* name, int name_len, double* total_
  * as 2 flops). Runs a short register-resident kernel; synchronous. */
 int fsib_measure_peak(int kind, double* gflops);
 
+/* Type-1 spread that allocates no device memory.
+ * The paper has no counterpart: this is a library service. Some callers cannot
+ * call cudaMalloc at all - code living inside a host framework whose caching
+ * allocator owns all device memory, or latency-critical loops that cannot take
+ * cudaMalloc's implicit device-wide synchronisation - and fsib_create allocates
+ * its workspaces. This entry point computes the same transform as fsib_spread
+ * (f-hat(k) = L^-d sum_j omega_j F_j exp(-i k . X_j), k in K_N, same layouts and
+ * accuracy) with every scratch buffer (fine grid, FFT intermediates, point sort,
+ * tables) carved from one file-scope device array of FSIB_STATIC_SCRATCH_BYTES
+ * = 64 MiB, which every GPU that loads the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ * X, F ([d][M] double), omega ([M] double or NULL) and fhat (half spectrum,
+ * double or float complex per precision) must be device arrays; the work is
+ * enqueued on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * Returns FSIB_EINVAL, with a message in fsib_static_last_error(), when the
+ * problem needs more scratch than the array holds (e.g. 3D FP64 N > 40, or 3D
+ * mixed N > 64 at moderate M) or an argument is invalid.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. All calls share the one array, which keeps the previous
+ * call's contents (the call clears what must start at zero): calls that overlap
+ * on the GPU, from several streams or host threads, race on it. */
+int fsib_spread_static(int N, int d, int M, double tol, int precision, const double* X,
+                       const double* F, const double* omega, void* fhat, void* stream);
+
+/* Message of the last fsib_spread_static error on the calling host thread. */
+const char* fsib_static_last_error(void);
+
 /* Message of the last error on this handle ("" if none); h may be NULL for
  * errors of fsib_create. */
 const char* fsib_last_error(fsib_t h);

@@ -980,3 +980,193 @@ int fsib_profile_entry(fsib_t h, int i, char* name, int name_len, double* total_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Type-1 spread that allocates nothing (fsib_spread_static).
+//
+// Some callers cannot call cudaMalloc: code that runs inside a host framework
+// whose caching allocator owns all device memory and forbids raw allocations,
+// and latency-critical loops where cudaMalloc's implicit device-wide
+// synchronisation is not acceptable. For them the whole scratch of one type-1
+// transform (fine grid, FFT intermediates, point sort, twiddle and
+// deconvolution tables) lives in the file-scope array below, which every GPU
+// that loads the library holds until the process exits. The caller passes only
+// its inputs and output. All calls share this array: two calls that overlap on
+// the GPU (different streams, or different host threads) race on it.
+// ---------------------------------------------------------------------------
+#define FSIB_STATIC_SCRATCH_BYTES (64ull << 20)
+
+static __device__ __align__(256) unsigned char g_static_scratch[FSIB_STATIC_SCRATCH_BYTES];
+
+// Device address of g_static_scratch per device. In host code the symbol name is
+// only a host-side stand-in, so the address must come from cudaGetSymbolAddress
+// with the device current.
+static std::mutex g_static_mu;
+static void* g_static_addr[64] = {nullptr};
+
+static int static_scratch_base(void** out, std::string& err) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    err = "no current CUDA device";
+    return FSIB_ECUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      err = std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e);
+      return FSIB_ECUDA;
+    }
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return FSIB_OK;
+}
+
+static thread_local std::string g_static_err;
+
+// Carve 256-byte aligned pieces out of [base, base + cap).
+struct Carver {
+  unsigned char* base;
+  size_t used = 0;
+  template <typename P>
+  P* take(size_t bytes) {
+    used = (used + 255) & ~size_t(255);
+    P* q = reinterpret_cast<P*>(base ? base + used : nullptr);
+    used += bytes ? bytes : 16;
+    return q;
+  }
+};
+
+template <typename T>
+static int spread_static_impl(const Plan& p, const double* X, const double* F, const double* omega,
+                              void* fhat, cudaStream_t st) {
+  const long long N = p.N, hh = p.N / 2, n = p.nf, d = p.d;
+  const size_t rs = sizeof(T), cs = 2 * sizeof(T);
+  const long long gcells = d * n * n * (d == 3 ? n : 1);
+  const long long s1n = (d == 3) ? d * n * n * hh : d * n * hh;
+  const long long s2n = (d == 3) ? d * n * N * hh : 1;
+  const long long dpn = (d == 3) ? N * hh : hh;
+
+  // Layout pass (base = null) to size the request, then the real carve.
+  Workspace ws;
+  size_t need = 0;
+  unsigned char* base = nullptr;
+  for (int pass = 0; pass < 2; ++pass) {
+    Carver c{base};
+    ws.tw = c.take<void>((size_t)n * cs);
+    ws.dline = c.take<void>((size_t)N * rs);
+    ws.dplane = c.take<void>((size_t)dpn * rs);
+    ws.grid = c.take<void>((size_t)gcells * rs);
+    ws.grid_bytes = (size_t)gcells * rs;
+    ws.s1 = c.take<void>((size_t)s1n * cs);
+    ws.s2 = c.take<void>((size_t)s2n * cs);
+    ws.bin_of = c.take<int>(sizeof(int) * p.M);
+    ws.rank = c.take<int>(sizeof(int) * p.M);
+    ws.perm = c.take<int>(sizeof(int) * p.M);
+    ws.i0 = c.take<int>(sizeof(int) * d * p.M);
+    ws.delta = c.take<void>(rs * d * p.M);
+    ws.counts = c.take<int>(sizeof(int) * (size_t)p.nbins);
+    ws.offsets = c.take<int>(sizeof(int) * (size_t)(p.nbins + 1));
+    ws.occ = c.take<int>(sizeof(int) * (size_t)p.nbins);
+    ws.nocc = c.take<int>(sizeof(int));
+    need = c.used;
+    if (pass == 0) {
+      if (need > FSIB_STATIC_SCRATCH_BYTES) {
+        g_static_err = "problem needs " + std::to_string(need) + " bytes of scratch; the static scratch holds " +
+                       std::to_string((unsigned long long)FSIB_STATIC_SCRATCH_BYTES) + " bytes";
+        return FSIB_EINVAL;
+      }
+      void* b = nullptr;
+      const int rc = static_scratch_base(&b, g_static_err);
+      if (rc != FSIB_OK) return rc;
+      base = static_cast<unsigned char*>(b);
+    }
+  }
+
+  // Host tables (twiddles of the fine grid, per-axis deconvolution), copied into the scratch.
+  const double pi = 3.14159265358979323846;
+  std::vector<T> tw(2 * (size_t)n), D(N), Dp(dpn);
+  for (long long j = 0; j < n; ++j) {
+    const double ang = 2.0 * pi * (double)j / (double)n;
+    tw[2 * j] = (T)std::cos(ang);
+    tw[2 * j + 1] = (T)(-std::sin(ang));
+  }
+  std::vector<double> zq, wq, Dd(N);
+  gauss_legendre(std::max(64, 4 * p.w + 64), zq, wq);
+  const double hf = p.L / p.nf;
+  for (long long i = 0; i < N; ++i) {
+    const long long m = (i < N / 2) ? i : i - N;
+    Dd[i] = (i == N / 2) ? 0.0 : hf / psi_hat(2.0 * pi * m / p.L, p.w, p.beta, hf, zq, wq);
+    D[i] = (T)Dd[i];
+  }
+  for (long long q = 0; q < dpn; ++q) Dp[q] = (T)((d == 3) ? Dd[q / hh] * Dd[q % hh] : Dd[q]);
+  cudaError_t e = cudaMemcpyAsync(ws.tw, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws.dline, D.data(), D.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws.dplane, Dp.data(), Dp.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+  // The scratch keeps the previous call's contents: zero what must start at zero
+  // (the grid accumulates spread contributions; launch_bin_points clears the bin counts).
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.grid, 0, ws.grid_bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g_static_err = std::string("table upload: ") + cudaGetErrorString(e);
+    return FSIB_ECUDA;
+  }
+
+  launch_bin_points(p, ws, X, st);
+  launch_spread<T>(p, ws, F, omega, (T*)ws.grid, st);
+  const C<T>* twc = (const C<T>*)ws.tw;
+  C<T>* s1 = (C<T>*)ws.s1;
+  C<T>* s2 = (C<T>*)ws.s2;
+  Mult<T> none, dec;
+  dec.scale = (T)std::pow(p.L, -(double)d);
+  dec.dline = (const T*)ws.dline;
+  dec.dplane = (const T*)ws.dplane;
+  if (d == 3) {
+    launch_fft_rows_r2c<T>((const T*)ws.grid, s1, d * n * n, p.N, p.fl_nf, twc, st);
+    launch_fft_strided<T>(s1, s2, (int)d, (int)n, (int)hh, p.N, p.fl_nf, false, none, twc, st);
+    launch_fft_strided<T>(s2, (C<T>*)fhat, (int)d, 1, (int)(N * hh), p.N, p.fl_nf, false, dec, twc, st);
+  } else {
+    launch_fft_rows_r2c<T>((const T*)ws.grid, s1, d * n, p.N, p.fl_nf, twc, st);
+    launch_fft_strided<T>(s1, (C<T>*)fhat, (int)d, 1, (int)hh, p.N, p.fl_nf, false, dec, twc, st);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_static_err = std::string("CUDA: ") + cudaGetErrorString(e);
+    return FSIB_ECUDA;
+  }
+  return FSIB_OK;
+}
+
+extern "C" {
+
+int fsib_spread_static(int N, int d, int M, double tol, int precision, const double* X, const double* F,
+                       const double* omega, void* fhat, void* stream) {
+  g_static_err.clear();
+  if ((d != 2 && d != 3) || N < 4 || N > 512 || (N % 2) || M < 1 || !(tol >= 1e-14 && tol <= 1e-2) ||
+      (precision != FSIB_FP64 && precision != FSIB_MIXED)) {
+    g_static_err = "bad N, d, M, tol or precision";
+    return FSIB_EINVAL;
+  }
+  if (!X || !F || !fhat) { g_static_err = "NULL array"; return FSIB_EINVAL; }
+  if (!is_device_ptr(X) || !is_device_ptr(F) || !is_device_ptr(fhat) || (omega && !is_device_ptr(omega))) {
+    g_static_err = "fsib_spread_static takes device arrays only";
+    return FSIB_EINVAL;
+  }
+  Plan p;
+  p.d = d; p.N = N; p.M = M; p.tol = tol; p.prec = precision;
+  std::string err;
+  int rc = plan_sizes(p, err);
+  if (rc != FSIB_OK) { g_static_err = err; return rc; }
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = (precision == FSIB_FP64) ? spread_static_impl<double>(p, X, F, omega, fhat, st)
+                                : spread_static_impl<float>(p, X, F, omega, fhat, st);
+  return rc;
+}
+
+const char* fsib_static_last_error(void) { return g_static_err.c_str(); }
+
+}  // extern "C"

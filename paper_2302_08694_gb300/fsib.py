@@ -26,7 +26,7 @@ EXPORTS = ["fsib_create", "fsib_destroy", "fsib_set_stream", "fsib_set_option", 
            "fsib_set_force_curve", "fsib_set_force_mesh", "fsib_force", "fsib_spread", "fsib_interp",
            "fsib_fluid_step", "fsib_step", "fsib_invariants", "fsib_last_error", "fsib_version",
            "fsib_profile_enable", "fsib_profile_reset", "fsib_profile_count", "fsib_profile_entry",
-           "fsib_measure_peak"]
+           "fsib_measure_peak", "fsib_spread_static", "fsib_static_last_error"]
 
 _lib = None
 
@@ -70,6 +70,8 @@ def load(path: str | None = None):
         "fsib_profile_count": ([vp], i_),
         "fsib_profile_entry": ([vp, i_, ctypes.c_char_p, i_, dp, ip, dp, dp], i_),
         "fsib_measure_peak": ([i_, dp], i_),
+        "fsib_spread_static": ([i_, i_, i_, d_, i_, vp, vp, vp, vp, vp], i_),
+        "fsib_static_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -244,6 +246,16 @@ def measure_peak(kind):
     if rc != FSIB_OK:
         raise FsibError(rc, "peak measurement failed")
     return v.value
+
+
+def spread_static(N, d, M, tol, precision, X, F, omega, fhat, stream=None):
+    """fsib_spread_static: the type-1 spread with no device allocation (device arrays only)."""
+    lib = load()
+    rc = lib.fsib_spread_static(int(N), int(d), int(M), float(tol), FSIB_MIXED if precision == "mixed" else FSIB_FP64,
+                                _ptr(X), _ptr(F), _ptr(omega), _ptr(fhat), stream)
+    if rc != FSIB_OK:
+        raise FsibError(rc, lib.fsib_static_last_error().decode())
+    return fhat
 
 
 def version():
