@@ -79,6 +79,9 @@ int fsib_set_stream(fsib_t h, void* stream);
  *  "sigma"      upsampling factor of the fine grid (1.5 .. 3, default 2)
  *  "width"      spreading-kernel width in fine cells (2 .. 16; 0 = from tol)
  *  "bin"        bin side in fine cells for the point sort (4 .. 32; 0 = auto)
+ *  "native_fp64" FSIB_FP64 mode only: 0 = transforms in double-float arithmetic
+ *               (pairs of floats, about 48 bits; default, fast on GB300's FP32
+ *               pipes), 1 = transforms in FP64 arithmetic
  *  "graph"      1 = fsib_step replays a captured CUDA graph (default), 0 = direct launches
  *  "check_finite" 1 = fsib_step checks positions for NaN/Inf at the end
  *               (adds a synchronisation), 0 = no check (default)

@@ -136,16 +136,22 @@ static int plan_sizes(Plan& p, std::string& err) {
   p.w = w;
   p.beta = 0.97 * pi * w * (1.0 - 1.0 / (2.0 * p.sigma));
   p.nf = smooth_even_at_least(std::max((int)std::ceil(p.sigma * p.N - 1e-9), 2 * w));
+  while (p.nf % 8) p.nf = smooth_even_at_least(p.nf + 1);  // boxes of 8 cells tile the grid
   p.Nt = smooth_even_at_least((3 * p.N + 1) / 2);
   if (p.nf > kMaxFFT || p.Nt > kMaxFFT) {
     err = "fine or dealiasing grid exceeds the supported FFT length 512";
     return FSIB_EUNSUPPORTED;
   }
   int b = p.bin_opt;
-  if (b <= 0) {
+  const bool gather = !(p.prec == FSIB_FP64 && p.native_fp64);
+  if (gather) {
+    b = (p.d == 2) ? (b > 0 ? b : 32) : 8;  // 3D gather boxes are 8^3 (one run of 8 cells per task)
+    if (p.d == 2) { b = std::max(8, std::min(32, b)); b = (b / 8) * 8; }
+  } else if (b <= 0) {
     if (p.d == 2) b = 32;
     else b = (p.prec == FSIB_FP64 && w > 8) ? 4 : 8;
   }
+  while (b > 8 && p.nf % b) b -= 8;
   while (b > 1 && p.nf % b) b /= 2;
   for (int a = 0; a < 3; ++a) { p.bins[a] = (a < p.d) ? b : 1; p.nbin[a] = (a < p.d) ? p.nf / b : 1; }
   p.nbins = 1;
@@ -212,7 +218,8 @@ static double fft_flops(double lines, int n) { return lines * 5.0 * n * std::log
 static void free_ws(Workspace& ws) {
   void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.s1, ws.s2, ws.fhat, ws.uhalf, ws.bin_of,
                   ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
-                  ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag};
+                  ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.fx, ws.wts, ws.cwp,
+                  ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   ws.tw = ws.dline = ws.dplane = ws.grid = ws.s1 = ws.s2 = ws.fhat = ws.uhalf = nullptr;
@@ -220,6 +227,10 @@ static void free_ws(Workspace& ws) {
   ws.delta = nullptr;
   ws.Xh = ws.cw = ws.Uh = ws.omega_ones = ws.red = nullptr;
   ws.flag = nullptr;
+  ws.fx = nullptr;
+  ws.wts = ws.cwp = nullptr;
+  ws.box_ns = ws.box_np = ws.box_so = ws.box_po = nullptr;
+  ws.part = nullptr;
   for (int i = 0; i < 4; ++i) {
     if (ws.stage[i]) cudaFree(ws.stage[i]);
     ws.stage[i] = nullptr; ws.stage_bytes[i] = 0;
@@ -293,6 +304,16 @@ static int alloc_ws(fsib_plan* h) {
   ws.red_blocks = 2 * 152;
   rc |= dmalloc(&ws.red, sizeof(double) * (size_t)(ws.red_blocks + 1) * 10, tot);
   rc |= dmalloc(&ws.flag, sizeof(int) * 4, tot);
+  rc |= dmalloc(&ws.fx, sizeof(unsigned long long) * 2, tot);
+  rc |= dmalloc(&ws.wts, sizeof(double) * (size_t)p.M * d * p.w, tot);
+  rc |= dmalloc(&ws.cwp, sizeof(double) * (size_t)p.M * d, tot);
+  rc |= dmalloc(&ws.box_ns, sizeof(int) * (size_t)p.nbins, tot);
+  rc |= dmalloc(&ws.box_np, sizeof(int) * (size_t)p.nbins, tot);
+  rc |= dmalloc(&ws.box_so, sizeof(int) * (size_t)(p.nbins + 1), tot);
+  rc |= dmalloc(&ws.box_po, sizeof(int) * (size_t)(p.nbins + 1), tot);
+  // partial slots: boxes with K > 1 hold K slots, K <= 2 cand/256; sum cand <= 27 M
+  ws.part_slots = (d == 3) ? (size_t)(2 * 27 * (long long)p.M / 256 + 64) : 1;
+  rc |= dmalloc(&ws.part, sizeof(double) * 3 * 512 * ws.part_slots, tot);
   if (rc != FSIB_OK) { free_ws(ws); h->err = "device allocation failed"; return FSIB_ENOMEM; }
   g_ws_bytes = tot;
 
@@ -323,7 +344,12 @@ static int alloc_ws(fsib_plan* h) {
   else
     for (long long ix = 0; ix < hh; ++ix) Dp[ix] = D[ix];
   cudaError_t e = cudaSuccess;
-  if (f64) {
+  if (f64 && !p.native_fp64) {
+    std::vector<dd> a(twd.begin(), twd.end()), b(D.begin(), D.end()), c(Dp.begin(), Dp.end());
+    e = cudaMemcpy(ws.tw, a.data(), a.size() * sizeof(dd), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.dline, b.data(), b.size() * sizeof(dd), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ws.dplane, c.data(), c.size() * sizeof(dd), cudaMemcpyHostToDevice);
+  } else if (f64) {
     e = cudaMemcpy(ws.tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ws.dline, D.data(), D.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ws.dplane, Dp.data(), Dp.size() * 8, cudaMemcpyHostToDevice);
@@ -338,152 +364,198 @@ static int alloc_ws(fsib_plan* h) {
   return FSIB_OK;
 }
 
+// Point side per arithmetic: gather spread / warp interp with per-point weight tables for
+// the float and dd transforms; FP64 atomics kernels for native FP64.
+template <typename TI>
+static void spread_points(fsib_plan* h, const double* c, const double* omega, TI* grid, cudaStream_t st);
+template <typename TI>
+static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st);
+template <typename TI>
+static void rows_r2c_first(const Plan& p, Workspace& ws, const TI* grid, C<TI>* out, long long nrows,
+                           const C<TI>* tw, cudaStream_t st) {
+  launch_fft_rows_r2c<TI>(grid, out, nrows, p.N, p.fl_nf, tw, st);
+}
+
 // ---------------------------------------------------------------------------
-// Transform sequences
+// Transform sequences. TI is the transform arithmetic (float in mixed mode; dd,
+// or double with the "native_fp64" option, in FP64 mode); TA is the element type
+// of the spectral arrays at the API (float or double).
 // ---------------------------------------------------------------------------
-template <typename T>
-static void forward_fine(fsib_plan* h, const T* grid, C<T>* out, cudaStream_t st) {
+template <typename TI, typename TA>
+static void forward_fine(fsib_plan* h, const TI* grid, C<TA>* out, cudaStream_t st) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const int N = p.N, hh = N / 2, n = p.nf, d = p.d;
-  const C<T>* tw = (const C<T>*)ws.tw;
-  C<T>* s1 = (C<T>*)ws.s1;
-  C<T>* s2 = (C<T>*)ws.s2;
-  Mult<T> none;
-  Mult<T> dec;
-  dec.scale = (T)std::pow(p.L, -d);
-  dec.dline = (const T*)ws.dline;
-  dec.dplane = (const T*)ws.dplane;
-  const double rs = sizeof(T), cs = 2.0 * sizeof(T);
+  const C<TI>* tw = (const C<TI>*)ws.tw;
+  C<TI>* s1 = (C<TI>*)ws.s1;
+  C<TI>* s2 = (C<TI>*)ws.s2;
+  Mult<TI> none;
+  Mult<TI> dec;
+  dec.scale = (TI)std::pow(p.L, -d);
+  dec.dline = (const TI*)ws.dline;
+  dec.dplane = (const TI*)ws.dplane;
+  const double rs = sizeof(TI), cs = 2.0 * sizeof(TI);
   if (d == 3) {
     { Prof pr(h, "t1.fx_rows_r2c", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
-      launch_fft_rows_r2c<T>(grid, s1, (long long)d * n * n, N, p.fl_nf, tw, st); }
+      rows_r2c_first<TI>(p, ws, grid, s1, (long long)d * n * n, tw, st); }
     { Prof pr(h, "t1.fy_strided", (double)d * n * hh * (n + N) * cs, fft_flops((double)d * n * hh, n), st);
-      launch_fft_strided<T>(s1, s2, d, n, hh, N, p.fl_nf, false, none, tw, st); }
+      launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, false, none, tw, st); }
     { Prof pr(h, "t1.fz_strided_deconv", (double)d * N * hh * (n + N) * cs, fft_flops((double)d * N * hh, n), st);
-      launch_fft_strided<T>(s2, out, d, 1, N * hh, N, p.fl_nf, false, dec, tw, st); }
+      launch_fft_strided<TI, TI, TA>(s2, out, d, 1, N * hh, N, p.fl_nf, false, dec, tw, st); }
   } else {
     { Prof pr(h, "t1.fx_rows_r2c", (double)d * n * n * rs + (double)d * n * hh * cs, fft_flops(0.5 * d * n, n), st);
-      launch_fft_rows_r2c<T>(grid, s1, (long long)d * n, N, p.fl_nf, tw, st); }
+      rows_r2c_first<TI>(p, ws, grid, s1, (long long)d * n, tw, st); }
     { Prof pr(h, "t1.fy_strided_deconv", (double)d * hh * (n + N) * cs, fft_flops((double)d * hh, n), st);
-      launch_fft_strided<T>(s1, out, d, 1, hh, N, p.fl_nf, false, dec, tw, st); }
+      launch_fft_strided<TI, TI, TA>(s1, out, d, 1, hh, N, p.fl_nf, false, dec, tw, st); }
   }
 }
 
-template <typename T>
-static void inverse_fine(fsib_plan* h, const C<T>* in, T* grid, cudaStream_t st) {
+template <typename TI, typename TA>
+static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t st) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const int N = p.N, hh = N / 2, n = p.nf, d = p.d;
-  const C<T>* tw = (const C<T>*)ws.tw;
-  C<T>* s1 = (C<T>*)ws.s1;
-  C<T>* s2 = (C<T>*)ws.s2;
-  Mult<T> none;
-  Mult<T> dec;
-  dec.dline = (const T*)ws.dline;
-  dec.dplane = (const T*)ws.dplane;
-  const double rs = sizeof(T), cs = 2.0 * sizeof(T);
+  const C<TI>* tw = (const C<TI>*)ws.tw;
+  C<TI>* s1 = (C<TI>*)ws.s1;
+  C<TI>* s2 = (C<TI>*)ws.s2;
+  Mult<TI> none;
+  Mult<TI> dec;
+  dec.dline = (const TI*)ws.dline;
+  dec.dplane = (const TI*)ws.dplane;
+  const double rs = sizeof(TI), cs = 2.0 * sizeof(TI);
   if (d == 3) {
     { Prof pr(h, "t2.iz_strided_deconv", (double)d * N * hh * (n + N) * cs, fft_flops((double)d * N * hh, n), st);
-      launch_fft_strided<T>(in, s1, d, 1, N * hh, N, p.fl_nf, true, dec, tw, st); }
+      launch_fft_strided<TI, TA, TI>(in, s1, d, 1, N * hh, N, p.fl_nf, true, dec, tw, st); }
     { Prof pr(h, "t2.iy_strided", (double)d * n * hh * (n + N) * cs, fft_flops((double)d * n * hh, n), st);
-      launch_fft_strided<T>(s1, s2, d, n, hh, N, p.fl_nf, true, none, tw, st); }
+      launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, true, none, tw, st); }
     { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
-      launch_fft_rows_c2r<T>(s2, grid, (long long)d * n * n, N, p.fl_nf, tw, st); }
+      launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n * n, N, p.fl_nf, tw, st); }
   } else {
     { Prof pr(h, "t2.iy_strided_deconv", (double)d * hh * (n + N) * cs, fft_flops((double)d * hh, n), st);
-      launch_fft_strided<T>(in, s2, d, 1, hh, N, p.fl_nf, true, dec, tw, st); }
+      launch_fft_strided<TI, TA, TI>(in, s2, d, 1, hh, N, p.fl_nf, true, dec, tw, st); }
     { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * rs + (double)d * n * hh * cs, fft_flops(0.5 * d * n, n), st);
-      launch_fft_rows_c2r<T>(s2, grid, (long long)d * n, N, p.fl_nf, tw, st); }
+      launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n, N, p.fl_nf, tw, st); }
   }
 }
 
-// Fourier coefficients on K_N of the products u_a u_b (three-halves rule); returns the buffer.
-template <typename T>
-static const C<T>* products(fsib_plan* h, const C<T>* u, cudaStream_t st) {
+// Fourier coefficients on K_N of the products u_a u_b (three-halves rule), as TA; returns the buffer.
+template <typename TI, typename TA>
+static const C<TA>* products(fsib_plan* h, const C<TA>* u, cudaStream_t st) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const int N = p.N, hh = N / 2, nt = p.Nt, d = p.d;
-  const C<T>* tw = (const C<T>*)ws.tw;
-  C<T>* s1 = (C<T>*)ws.s1;
-  C<T>* s2 = (C<T>*)ws.s2;
-  Mult<T> none;
-  Mult<T> sc;
-  const double cs = 2.0 * sizeof(T);
+  const C<TI>* tw = (const C<TI>*)ws.tw;
+  C<TI>* s1 = (C<TI>*)ws.s1;
+  C<TI>* s2 = (C<TI>*)ws.s2;
+  Mult<TI> none;
+  Mult<TI> sc;
+  const double cs = 2.0 * sizeof(TI);
   if (d == 3) {
-    sc.scale = (T)(1.0 / ((double)nt * nt * nt));
+    sc.scale = (TI)(1.0 / ((double)nt * nt * nt));
     { Prof pr(h, "nl.iz_strided", 3.0 * N * hh * (N + nt) * cs, fft_flops(3.0 * N * hh, nt), st);
-      launch_fft_strided<T>(u, s1, 3, 1, N * hh, N, p.fl_nt, true, none, tw, st); }
+      launch_fft_strided<TI, TA, TI>(u, s1, 3, 1, N * hh, N, p.fl_nt, true, none, tw, st); }
     { Prof pr(h, "nl.iy_strided", 3.0 * nt * hh * (N + nt) * cs, fft_flops(3.0 * nt * hh, nt), st);
-      launch_fft_strided<T>(s1, s2, 3, nt, hh, N, p.fl_nt, true, none, tw, st); }
+      launch_fft_strided<TI>(s1, s2, 3, nt, hh, N, p.fl_nt, true, none, tw, st); }
     { Prof pr(h, "nl.rows_product", 9.0 * nt * nt * hh * cs, fft_flops(0.5 * nt * nt * 9.0, nt), st);
-      launch_rows_product<T>(s2, s1, 3, (long long)nt * nt, N, p.fl_nt, tw, st); }
+      launch_rows_product<TI>(s2, s1, 3, (long long)nt * nt, N, p.fl_nt, tw, st); }
     { Prof pr(h, "nl.fy_strided", 6.0 * nt * hh * (N + nt) * cs, fft_flops(6.0 * nt * hh, nt), st);
-      launch_fft_strided<T>(s1, s2, 6, nt, hh, N, p.fl_nt, false, none, tw, st); }
+      launch_fft_strided<TI>(s1, s2, 6, nt, hh, N, p.fl_nt, false, none, tw, st); }
     { Prof pr(h, "nl.fz_strided", 6.0 * N * hh * (N + nt) * cs, fft_flops(6.0 * N * hh, nt), st);
-      launch_fft_strided<T>(s2, s1, 6, 1, N * hh, N, p.fl_nt, false, sc, tw, st); }
-    return s1;
+      launch_fft_strided<TI, TI, TA>(s2, (C<TA>*)s1, 6, 1, N * hh, N, p.fl_nt, false, sc, tw, st); }
+    return (const C<TA>*)s1;
   } else {
-    sc.scale = (T)(1.0 / ((double)nt * nt));
+    sc.scale = (TI)(1.0 / ((double)nt * nt));
     { Prof pr(h, "nl.iy_strided", 2.0 * hh * (N + nt) * cs, fft_flops(2.0 * hh, nt), st);
-      launch_fft_strided<T>(u, s2, 2, 1, hh, N, p.fl_nt, true, none, tw, st); }
+      launch_fft_strided<TI, TA, TI>(u, s2, 2, 1, hh, N, p.fl_nt, true, none, tw, st); }
     { Prof pr(h, "nl.rows_product", 5.0 * nt * hh * cs, fft_flops(0.5 * nt * 5.0, nt), st);
-      launch_rows_product<T>(s2, s1, 2, (long long)nt, N, p.fl_nt, tw, st); }
+      launch_rows_product<TI>(s2, s1, 2, (long long)nt, N, p.fl_nt, tw, st); }
     { Prof pr(h, "nl.fy_strided", 3.0 * hh * (N + nt) * cs, fft_flops(3.0 * hh, nt), st);
-      launch_fft_strided<T>(s1, s2, 3, 1, hh, N, p.fl_nt, false, sc, tw, st); }
-    return s2;
+      launch_fft_strided<TI, TI, TA>(s1, (C<TA>*)s2, 3, 1, hh, N, p.fl_nt, false, sc, tw, st); }
+    return (const C<TA>*)s2;
   }
 }
 
-static void do_bin(fsib_plan* h, const double* X, cudaStream_t st) {
+static bool uses_prep(const Plan& p) { return !(p.prec == FSIB_FP64 && p.native_fp64); }
+
+// Sort the points into bins; for the gather kernels also evaluate their kernel weights
+// (and, when c is given, their weighted forces) once per sort.
+static void do_bin(fsib_plan* h, const double* X, cudaStream_t st, const double* c = nullptr,
+                   const double* omega = nullptr) {
   const Plan& p = h->p;
   const double rs = (p.prec == FSIB_FP64) ? 8.0 : 4.0;
-  Prof pr(h, "sort", 2.0 * p.d * p.M * 8.0 + 4.0 * p.M * 8.0 + p.d * p.M * (4.0 + rs) + 12.0 * p.nbins, 0.0, st);
-  launch_bin_points(p, h->ws, X, st);
+  {
+    Prof pr(h, "sort", 2.0 * p.d * p.M * 8.0 + 4.0 * p.M * 8.0 + p.d * p.M * (4.0 + rs) + 12.0 * p.nbins, 0.0, st);
+    launch_bin_points(p, h->ws, X, st);
+  }
+  if (!uses_prep(p)) return;
+  const double ts = (p.prec == FSIB_FP64) ? 8.0 : 4.0;
+  Prof pr(h, "point_weights", (double)p.M * p.d * (p.w * ts + rs + (c ? 8.0 + ts : 0.0)), 0.0, st);
+  if (p.prec == FSIB_FP64) launch_point_prep<dd>(p, h->ws, c, omega, st);
+  else launch_point_prep<float>(p, h->ws, c, omega, st);
 }
 
-template <typename T>
-static double point_bytes(const Plan& p) { return (double)p.M * (4.0 + p.d * (4.0 + sizeof(T) + 8.0)); }
+static double point_bytes(const Plan& p) {
+  return (double)p.M * (4.0 + p.d * (4.0 + (p.prec == FSIB_FP64 ? 8.0 : 4.0) + 8.0));
+}
 
-template <typename T>
-static void do_spread(fsib_plan* h, const double* X, const double* c, const double* omega, C<T>* fhat,
-                      cudaStream_t st) {
-  do_bin(h, X, st);
+template <typename TI>
+static void spread_points(fsib_plan* h, const double* c, const double* omega, TI* grid, cudaStream_t st) {
+  Prof pr(h, "spread", point_bytes(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  launch_spread_gather<TI>(h->p, h->ws, grid, st);
+}
+template <>
+void spread_points<double>(fsib_plan* h, const double* c, const double* omega, double* grid, cudaStream_t st) {
   { Prof pr(h, "zero_grid", (double)h->ws.grid_bytes, 0.0, st);
     cudaMemsetAsync(h->ws.grid, 0, h->ws.grid_bytes, st); }
-  { Prof pr(h, "spread", point_bytes<T>(h->p) + (double)h->ws.grid_bytes, 0.0, st);
-    launch_spread<T>(h->p, h->ws, c, omega, (T*)h->ws.grid, st); }
-  forward_fine<T>(h, (const T*)h->ws.grid, fhat, st);
+  Prof pr(h, "spread", point_bytes(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  launch_spread<double>(h->p, h->ws, c, omega, grid, st);
+}
+template <typename TI>
+static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st) {
+  Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  launch_interp_warp<TI>(h->p, h->ws, grid, U, st);
+}
+template <>
+void interp_points<double>(fsib_plan* h, const double* grid, double* U, cudaStream_t st) {
+  Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  launch_interp<double>(h->p, h->ws, grid, U, st);
+}
+
+template <typename TI, typename TA>
+static void do_spread(fsib_plan* h, const double* X, const double* c, const double* omega, C<TA>* fhat,
+                      cudaStream_t st) {
+  do_bin(h, X, st, c, omega);
+  spread_points<TI>(h, c, omega, (TI*)h->ws.grid, st);
+  forward_fine<TI, TA>(h, (const TI*)h->ws.grid, fhat, st);
 }
 
 // interp at the points of the last binning
-template <typename T>
-static void do_interp_sorted(fsib_plan* h, const C<T>* uhat, double* U, cudaStream_t st) {
-  inverse_fine<T>(h, uhat, (T*)h->ws.grid, st);
-  Prof pr(h, "interp", point_bytes<T>(h->p) + (double)h->ws.grid_bytes, 0.0, st);
-  launch_interp<T>(h->p, h->ws, (const T*)h->ws.grid, U, st);
+template <typename TI, typename TA>
+static void do_interp_sorted(fsib_plan* h, const C<TA>* uhat, double* U, cudaStream_t st) {
+  inverse_fine<TI, TA>(h, uhat, (TI*)h->ws.grid, st);
+  interp_points<TI>(h, (const TI*)h->ws.grid, U, st);
 }
 
-template <typename T>
-static void do_stokeslet(fsib_plan* h, const C<T>* fhat, C<T>* u, cudaStream_t st) {
+template <typename TA>
+static void do_stokeslet(fsib_plan* h, const C<TA>* fhat, C<TA>* u, cudaStream_t st) {
   Prof pr(h, "stokeslet", 2.0 * (double)h->ws.spec_bytes, 0.0, st);
-  launch_stokeslet<T>(h->p, fhat, u, st);
+  launch_stokeslet<TA>(h->p, fhat, u, st);
 }
 
-template <typename T>
-static void do_fluid(fsib_plan* h, const C<T>* fhat, C<T>* u, C<T>* uhalf, cudaStream_t st) {
+template <typename TI, typename TA>
+static void do_fluid(fsib_plan* h, const C<TA>* fhat, C<TA>* u, C<TA>* uhalf, cudaStream_t st) {
   if (h->p.stokes) {
-    do_stokeslet<T>(h, fhat, u, st);
+    do_stokeslet<TA>(h, fhat, u, st);
     return;
   }
   const int d = h->p.d, np = d * (d + 1) / 2;
   const double ub = (double)h->ws.spec_bytes / d * (np + 3 * d);
-  const C<T>* P = products<T>(h, u, st);
+  const C<TA>* P = products<TI, TA>(h, u, st);
   { Prof pr(h, "ns_update", ub, 0.0, st);
-    launch_ns_update<T>(h->p, P, fhat, u, uhalf, true, st); }
-  P = products<T>(h, uhalf, st);
+    launch_ns_update<TA>(h->p, P, fhat, u, uhalf, true, st); }
+  P = products<TI, TA>(h, uhalf, st);
   { Prof pr(h, "ns_update", ub, 0.0, st);
-    launch_ns_update<T>(h->p, P, fhat, u, u, false, st); }
+    launch_ns_update<TA>(h->p, P, fhat, u, u, false, st); }
 }
 
 static void do_axpy(fsib_plan* h, double* y, const double* x, const double* v, double a, cudaStream_t st) {
@@ -499,40 +571,47 @@ static void do_force(fsib_plan* h, const double* X, double* c, cudaStream_t st) 
 }
 
 // One time step on device arrays (Algorithm 1, or the quasi-static Stokes midpoint rule).
-template <typename T>
-static void do_step(fsib_plan* h, double* X, C<T>* uhat, double* U, cudaStream_t st) {
+template <typename TI, typename TA>
+static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_t st) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const long long dm = (long long)p.d * p.M;
-  (void)dm;
-  C<T>* fhat = (C<T>*)ws.fhat;
-  C<T>* uh = (C<T>*)ws.uhalf;
+  C<TA>* fhat = (C<TA>*)ws.fhat;
+  C<TA>* uh = (C<TA>*)ws.uhalf;
   if (!p.stokes) {
     do_axpy(h, ws.Xh, X, U, 0.5 * p.dt, st);                    // Eq. spatial_1
     do_force(h, ws.Xh, ws.cw, st);                               // F^{m+1/2}
-    do_spread<T>(h, ws.Xh, ws.cw, nullptr, fhat, st);            // type-1 NUFFT
-    do_fluid<T>(h, fhat, uhat, uh, st);                          // Eqs. spatial_2, spatial_3
-    do_interp_sorted<T>(h, uh, ws.Uh, st);                       // U^{m+1/2} at X^{m+1/2}
+    do_spread<TI, TA>(h, ws.Xh, ws.cw, nullptr, fhat, st);       // type-1 NUFFT
+    do_fluid<TI, TA>(h, fhat, uhat, uh, st);                     // Eqs. spatial_2, spatial_3
+    do_interp_sorted<TI, TA>(h, uh, ws.Uh, st);                  // U^{m+1/2} at X^{m+1/2}
     do_axpy(h, X, X, ws.Uh, p.dt, st);                           // Eq. spatial_4
     do_bin(h, X, st);
-    do_interp_sorted<T>(h, uhat, U, st);                         // U^{m+1} at X^{m+1}
+    do_interp_sorted<TI, TA>(h, uhat, U, st);                    // U^{m+1} at X^{m+1}
   } else {
     // U(X^m)
     do_force(h, X, ws.cw, st);
-    do_spread<T>(h, X, ws.cw, nullptr, fhat, st);
-    do_stokeslet<T>(h, fhat, uh, st);
-    do_interp_sorted<T>(h, uh, ws.Uh, st);
+    do_spread<TI, TA>(h, X, ws.cw, nullptr, fhat, st);
+    do_stokeslet<TA>(h, fhat, uh, st);
+    do_interp_sorted<TI, TA>(h, uh, ws.Uh, st);
     do_axpy(h, ws.Xh, X, ws.Uh, 0.5 * p.dt, st);
     // U(X^{m+1/2})
     do_force(h, ws.Xh, ws.cw, st);
-    do_spread<T>(h, ws.Xh, ws.cw, nullptr, fhat, st);
-    do_stokeslet<T>(h, fhat, uh, st);
-    do_interp_sorted<T>(h, uh, ws.Uh, st);
+    do_spread<TI, TA>(h, ws.Xh, ws.cw, nullptr, fhat, st);
+    do_stokeslet<TA>(h, fhat, uh, st);
+    do_interp_sorted<TI, TA>(h, uh, ws.Uh, st);
     do_axpy(h, X, X, ws.Uh, p.dt, st);
     if (U) cudaMemcpyAsync(U, ws.Uh, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
     if (uhat) cudaMemcpyAsync(uhat, uh, ws.spec_bytes, cudaMemcpyDeviceToDevice, st);
   }
 }
+
+// Run f<TI, TA> for the handle's arithmetic.
+#define FSIB_DISPATCH(h, CALL_F, CALL_DD, CALL_D) \
+  do {                                            \
+    if ((h)->p.prec == FSIB_MIXED) { CALL_F; }    \
+    else if ((h)->p.native_fp64) { CALL_D; }      \
+    else { CALL_DD; }                             \
+  } while (0)
 
 // ---------------------------------------------------------------------------
 // Entry helpers
@@ -691,6 +770,8 @@ int fsib_set_option(fsib_t h, const char* key, double v) {
   } else if (k == "bin") {
     if (!(v == 0 || (v >= 4 && v <= 64))) return fail(h, FSIB_EINVAL, "bin must be 0 or in [4, 64]");
     q.bin_opt = (int)v;
+  } else if (k == "native_fp64") {
+    q.native_fp64 = (v != 0);
   } else if (k == "graph") {
     h->p.use_graph = (v != 0);
     return FSIB_OK;
@@ -719,6 +800,7 @@ int fsib_get_info(fsib_t h, const char* key, double* value) {
   else if (k == "precision") *value = p.prec;
   else if (k == "bin") *value = p.bins[0];
   else if (k == "sigma") *value = p.sigma;
+  else if (k == "native_fp64") *value = p.native_fp64;
   else if (k == "workspace_bytes") *value = (double)g_ws_bytes;
   else if (k == "launches_per_step") *value = h->graph_kernels;
   else return fail(h, FSIB_EINVAL, "unknown info key: " + k);
@@ -810,12 +892,10 @@ int fsib_spread(fsib_t h, const double* X, const double* F, const double* omega,
   if ((rc = stage(h, 1, F, pts_bytes(h), true, af)) != FSIB_OK) return rc;
   if ((rc = stage(h, 2, omega, sizeof(double) * h->p.M, true, ao)) != FSIB_OK) return rc;
   if ((rc = stage(h, 3, fhat, spec_bytes(h), false, ah)) != FSIB_OK) return rc;
-  if (h->p.prec == FSIB_FP64)
-    do_spread<double>(h, (const double*)ax.dev, (const double*)af.dev, (const double*)ao.dev,
-                      (C<double>*)ah.dev, h->own);
-  else
-    do_spread<float>(h, (const double*)ax.dev, (const double*)af.dev, (const double*)ao.dev,
-                     (C<float>*)ah.dev, h->own);
+  const double *xd = (const double*)ax.dev, *fd = (const double*)af.dev, *od = (const double*)ao.dev;
+  FSIB_DISPATCH(h, (do_spread<float, float>(h, xd, fd, od, (C<float>*)ah.dev, h->own)),
+                (do_spread<dd, double>(h, xd, fd, od, (C<double>*)ah.dev, h->own)),
+                (do_spread<double, double>(h, xd, fd, od, (C<double>*)ah.dev, h->own)));
   if ((rc = unstage(h, ah)) != FSIB_OK) return rc;
   return finish(h, ah.host != nullptr);
 }
@@ -829,10 +909,9 @@ int fsib_interp(fsib_t h, const void* uhat, const double* X, double* U) {
   if ((rc = stage(h, 3, uhat, spec_bytes(h), true, ah)) != FSIB_OK) return rc;
   if ((rc = stage(h, 1, U, pts_bytes(h), false, au)) != FSIB_OK) return rc;
   do_bin(h, (const double*)ax.dev, h->own);
-  if (h->p.prec == FSIB_FP64)
-    do_interp_sorted<double>(h, (const C<double>*)ah.dev, (double*)au.dev, h->own);
-  else
-    do_interp_sorted<float>(h, (const C<float>*)ah.dev, (double*)au.dev, h->own);
+  FSIB_DISPATCH(h, (do_interp_sorted<float, float>(h, (const C<float>*)ah.dev, (double*)au.dev, h->own)),
+                (do_interp_sorted<dd, double>(h, (const C<double>*)ah.dev, (double*)au.dev, h->own)),
+                (do_interp_sorted<double, double>(h, (const C<double>*)ah.dev, (double*)au.dev, h->own)));
   if ((rc = unstage(h, au)) != FSIB_OK) return rc;
   return finish(h, au.host != nullptr);
 }
@@ -846,10 +925,9 @@ int fsib_fluid_step(fsib_t h, const void* fhat, void* uhat, void* uhat_half) {
   if ((rc = stage(h, 1, uhat, spec_bytes(h), !h->p.stokes, au)) != FSIB_OK) return rc;
   if ((rc = stage(h, 2, uhat_half, spec_bytes(h), false, ah)) != FSIB_OK) return rc;
   void* half = ah.dev ? ah.dev : h->ws.uhalf;
-  if (h->p.prec == FSIB_FP64)
-    do_fluid<double>(h, (const C<double>*)af.dev, (C<double>*)au.dev, (C<double>*)half, h->own);
-  else
-    do_fluid<float>(h, (const C<float>*)af.dev, (C<float>*)au.dev, (C<float>*)half, h->own);
+  FSIB_DISPATCH(h, (do_fluid<float, float>(h, (const C<float>*)af.dev, (C<float>*)au.dev, (C<float>*)half, h->own)),
+                (do_fluid<dd, double>(h, (const C<double>*)af.dev, (C<double>*)au.dev, (C<double>*)half, h->own)),
+                (do_fluid<double, double>(h, (const C<double>*)af.dev, (C<double>*)au.dev, (C<double>*)half, h->own)));
   if ((rc = unstage(h, au)) != FSIB_OK) return rc;
   if (!h->p.stokes && (rc = unstage(h, ah)) != FSIB_OK) return rc;
   return finish(h, au.host != nullptr || ah.host != nullptr);
@@ -882,8 +960,9 @@ int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps) {
   if ((rc = stage(h, 1, U, pts_bytes(h), ns, aU)) != FSIB_OK) return rc;
   const bool f64 = h->p.prec == FSIB_FP64;
   auto enqueue = [&](cudaStream_t st) {
-    if (f64) do_step<double>(h, (double*)ax.dev, (C<double>*)au.dev, (double*)aU.dev, st);
-    else do_step<float>(h, (double*)ax.dev, (C<float>*)au.dev, (double*)aU.dev, st);
+    FSIB_DISPATCH(h, (do_step<float, float>(h, (double*)ax.dev, (C<float>*)au.dev, (double*)aU.dev, st)),
+                  (do_step<dd, double>(h, (double*)ax.dev, (C<double>*)au.dev, (double*)aU.dev, st)),
+                  (do_step<double, double>(h, (double*)ax.dev, (C<double>*)au.dev, (double*)aU.dev, st)));
   };
   if (nsteps > 0) {
     if (h->p.use_graph && !h->prof_on) {

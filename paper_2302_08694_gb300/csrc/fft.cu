@@ -22,9 +22,9 @@ constexpr int kThreads = 256;
 // ---------------------------------------------------------------------------
 // Strided pass
 // ---------------------------------------------------------------------------
-template <typename T, bool INV>
+template <typename T, bool INV, typename Tin, typename Tout>
 __global__ void __launch_bounds__(kThreads)
-k_fft_strided(const C<T>* __restrict__ in, C<T>* __restrict__ out, int inner, int Nk,
+k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk,
               FftLen fl, Mult<T> mult, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = fl.n;
@@ -36,20 +36,20 @@ k_fft_strided(const C<T>* __restrict__ in, C<T>* __restrict__ out, int inner, in
   const int q0 = (blockIdx.x % ntile) * kP;
   const int Lin = INV ? Nk : n, Lout = INV ? n : Nk;
   const int h = Nk / 2;
-  const C<T>* src = in + co * (long long)Lin * inner;
-  C<T>* dst = out + co * (long long)Lout * inner;
+  const C<Tin>* src = in + co * (long long)Lin * inner;
+  C<Tout>* dst = out + co * (long long)Lout * inner;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
   for (int t = threadIdx.x; t < n * kP; t += blockDim.x) {
     const int p = t % kP, i = t / kP, q = q0 + p;
     C<T> v = mk<T>(T(0), T(0));
     if (q < inner) {
       if (!INV) {
-        v = src[(long long)i * inner + q];
+        v = ccvt<T, Tin>(src[(long long)i * inner + q]);
       } else {
         // FFT position i holds mode i (i < N/2) or i - n (i > n - N/2); the rest is padding
         const int si = (i < h) ? i : ((i > n - h) ? i - (n - Nk) : -1);
         if (si >= 0) {
-          v = src[(long long)si * inner + q];
+          v = ccvt<T, Tin>(src[(long long)si * inner + q]);
           T s = mult.scale;
           if (mult.dline) s *= mult.dline[si];
           if (mult.dplane) s *= mult.dplane[q];
@@ -74,12 +74,12 @@ k_fft_strided(const C<T>* __restrict__ in, C<T>* __restrict__ out, int inner, in
         if (mult.dplane) s *= mult.dplane[q];
         v = cscale<T>(v, s);
       }
-      dst[(long long)io * inner + q] = v;
+      dst[(long long)io * inner + q] = ccvt<Tout, T>(v);
     }
   } else {
     for (int t = threadIdx.x; t < n * kP; t += blockDim.x) {
       const int p = t % kP, i = t / kP, q = q0 + p;
-      if (q < inner) dst[(long long)i * inner + q] = r[i * kP + p];
+      if (q < inner) dst[(long long)i * inner + q] = ccvt<Tout, T>(r[i * kP + p]);
     }
   }
 }
@@ -87,22 +87,36 @@ k_fft_strided(const C<T>* __restrict__ in, C<T>* __restrict__ out, int inner, in
 // ---------------------------------------------------------------------------
 // Row passes: real rows (length n) <-> half spectra (N/2 modes)
 // ---------------------------------------------------------------------------
-template <typename T>
+// FX: the input rows hold fixed-point integers (value = integer * 2^-k) written by the spread.
+template <typename T, bool FX>
 __global__ void __launch_bounds__(kThreads)
-k_rows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
-           FftLen fl, const C<T>* __restrict__ twg) {
+k_rows_r2c(const void* __restrict__ in_, const unsigned long long* __restrict__ fxmax, int M,
+           C<T>* __restrict__ out, long long npairs, int Nk, FftLen fl, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = fl.n, ls = n + 1, h = Nk / 2;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* a = tw + n;
   C<T>* b = a + kQrows * ls;
   const long long pr0 = (long long)blockIdx.x * kQrows;
+  float isc = 1.0f;
+  if (FX) isc = pow2f(-fx_exponent(*fxmax, M));
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
   for (int t = threadIdx.x; t < kQrows * n; t += blockDim.x) {
     const int p = t / n, x = t % n;
     const long long pr = pr0 + p;
     C<T> v = mk<T>(T(0), T(0));
-    if (pr < npairs) v = mk<T>(in[(2 * pr) * n + x], in[(2 * pr + 1) * n + x]);
+    if (pr < npairs) {
+      if (FX) {
+        const long long* in = reinterpret_cast<const long long*>(in_);
+        T r0, r1;
+        fx_to(in[(2 * pr) * n + x], isc, r0);
+        fx_to(in[(2 * pr + 1) * n + x], isc, r1);
+        v = mk<T>(r0, r1);
+      } else {
+        const T* in = reinterpret_cast<const T*>(in_);
+        v = mk<T>(in[(2 * pr) * n + x], in[(2 * pr + 1) * n + x]);
+      }
+    }
     a[p * ls + x] = v;
   }
   __syncthreads();
@@ -238,19 +252,19 @@ static void set_smem(K kern, size_t bytes) {
   (void)bytes;
 }
 
-template <typename T>
-void launch_fft_strided(const C<T>* in, C<T>* out, int ncomp, int outer, int inner, int Nk,
+template <typename T, typename Tin, typename Tout>
+void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, int inner, int Nk,
                         const FftLen& fl, bool inverse, Mult<T> mult, const C<T>* tw,
                         cudaStream_t st) {
   const int ntile = (inner + kP - 1) / kP;
   const long long blocks = (long long)ncomp * outer * ntile;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * fl.n * kP);
   if (inverse) {
-    set_smem(k_fft_strided<T, true>, smem);
-    k_fft_strided<T, true><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
+    set_smem(k_fft_strided<T, true, Tin, Tout>, smem);
+    k_fft_strided<T, true, Tin, Tout><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
   } else {
-    set_smem(k_fft_strided<T, false>, smem);
-    k_fft_strided<T, false><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
+    set_smem(k_fft_strided<T, false, Tin, Tout>, smem);
+    k_fft_strided<T, false, Tin, Tout><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
   }
 }
 
@@ -260,9 +274,23 @@ void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const 
   const long long npairs = nrows / 2;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
-  set_smem(k_rows_r2c<T>, smem);
-  k_rows_r2c<T><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
+  set_smem(k_rows_r2c<T, false>, smem);
+  k_rows_r2c<T, false><<<(unsigned)blocks, kThreads, smem, st>>>(in, nullptr, 0, out, npairs, Nk, fl, tw);
 }
+
+template <typename T>
+void launch_fft_rows_r2c_fx(const long long* in, const unsigned long long* fxmax, int M, C<T>* out,
+                            long long nrows, int Nk, const FftLen& fl, const C<T>* tw, cudaStream_t st) {
+  const long long npairs = nrows / 2;
+  const long long blocks = (npairs + kQrows - 1) / kQrows;
+  const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
+  set_smem(k_rows_r2c<T, true>, smem);
+  k_rows_r2c<T, true><<<(unsigned)blocks, kThreads, smem, st>>>(in, fxmax, M, out, npairs, Nk, fl, tw);
+}
+template void launch_fft_rows_r2c_fx<dd>(const long long*, const unsigned long long*, int, C<dd>*, long long, int,
+                                         const FftLen&, const C<dd>*, cudaStream_t);
+template void launch_fft_rows_r2c_fx<float>(const long long*, const unsigned long long*, int, C<float>*, long long,
+                                            int, const FftLen&, const C<float>*, cudaStream_t);
 
 template <typename T>
 void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
@@ -285,8 +313,6 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
 }
 
 #define INST(T)                                                                                  \
-  template void launch_fft_strided<T>(const C<T>*, C<T>*, int, int, int, int, const FftLen&,     \
-                                      bool, Mult<T>, const C<T>*, cudaStream_t);                 \
   template void launch_fft_rows_r2c<T>(const T*, C<T>*, long long, int, const FftLen&,           \
                                        const C<T>*, cudaStream_t);                               \
   template void launch_fft_rows_c2r<T>(const C<T>*, T*, long long, int, const FftLen&,           \
@@ -295,6 +321,17 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
                                        const C<T>*, cudaStream_t);
 INST(float)
 INST(double)
+INST(dd)
+#define INST_S(T, Ti, To)                                                                        \
+  template void launch_fft_strided<T, Ti, To>(const C<Ti>*, C<To>*, int, int, int, int,          \
+                                              const FftLen&, bool, Mult<T>, const C<T>*,         \
+                                              cudaStream_t);
+INST_S(float, float, float)
+INST_S(double, double, double)
+INST_S(dd, dd, dd)
+INST_S(dd, double, dd)
+INST_S(dd, dd, double)
+#undef INST_S
 #undef INST
 
 }  // namespace fsib

@@ -12,9 +12,14 @@
 
 namespace fsib {
 
-template <typename T> struct Consts;
-template <> struct Consts<float>  { static constexpr float  s3 = 0.866025403784438646763723170752936183f; };
-template <> struct Consts<double> { static constexpr double s3 = 0.866025403784438646763723170752936183; };
+// sqrt(3)/2 in each arithmetic type
+template <typename T> __device__ __forceinline__ T sqrt3_2();
+template <> __device__ __forceinline__ float sqrt3_2<float>() { return 0.866025403784438646763723170752936183f; }
+template <> __device__ __forceinline__ double sqrt3_2<double>() { return 0.866025403784438646763723170752936183; }
+template <> __device__ __forceinline__ dd sqrt3_2<dd>() {
+  constexpr dd v(0.866025403784438646763723170752936183);
+  return v;
+}
 
 template <typename T, bool INV>
 __device__ __forceinline__ void dft2(C<T>* v) {
@@ -29,7 +34,7 @@ __device__ __forceinline__ void dft3(C<T>* v) {
   C<T> s = cadd<T>(v[1], v[2]);
   C<T> d = csub<T>(v[1], v[2]);
   C<T> m = mk<T>(v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y);
-  C<T> t = cscale<T>(d, Consts<T>::s3);
+  C<T> t = cscale<T>(d, sqrt3_2<T>());
   C<T> it = INV ? cmul_i<T>(t) : cmul_mi<T>(t);
   v[0] = cadd<T>(v[0], s);
   v[1] = cadd<T>(m, it);

@@ -8,28 +8,69 @@
 #include <vector>
 
 #include "../../include/fsib.h"
+#include "dd.cuh"
 
 namespace fsib {
 
 // ---------------------------------------------------------------------------
 // Complex numbers: plain two-component structs so that loads are 8/16-byte vectors.
+// Element types: float (mixed mode), double (API arrays in FP64 mode, native
+// FP64 kernels) and dd (double-float, the FP64-mode transform arithmetic).
 // ---------------------------------------------------------------------------
 template <typename T> struct cplx_t;
 template <> struct cplx_t<float>  { using type = float2; };
 template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<dd>     { using type = dd2; };
 template <typename T> using C = typename cplx_t<T>::type;
 
-template <typename T> __host__ __device__ __forceinline__ C<T> mk(T x, T y) { C<T> r; r.x = x; r.y = y; return r; }
-template <typename T> __host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
-template <typename T> __host__ __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
-template <typename T> __host__ __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+template <typename T> __device__ __forceinline__ C<T> mk(T x, T y) { C<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
   return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-template <typename T> __host__ __device__ __forceinline__ C<T> cconj(C<T> a) { return mk<T>(a.x, -a.y); }
-template <typename T> __host__ __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ C<T> cconj(C<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
 // multiply by +i (or -i)
-template <typename T> __host__ __device__ __forceinline__ C<T> cmul_i(C<T> a) { return mk<T>(-a.y, a.x); }
-template <typename T> __host__ __device__ __forceinline__ C<T> cmul_mi(C<T> a) { return mk<T>(a.y, -a.x); }
+template <typename T> __device__ __forceinline__ C<T> cmul_i(C<T> a) { return mk<T>(-a.y, a.x); }
+template <typename T> __device__ __forceinline__ C<T> cmul_mi(C<T> a) { return mk<T>(a.y, -a.x); }
+
+// Element conversions at the boundary between API arrays and the transform type.
+__device__ __forceinline__ void cvt(float& o, float i) { o = i; }
+__device__ __forceinline__ void cvt(double& o, double i) { o = i; }
+__device__ __forceinline__ void cvt(dd& o, dd i) { o = i; }
+__device__ __forceinline__ void cvt(dd& o, double i) { o = dd(i); }
+__device__ __forceinline__ void cvt(double& o, dd i) { o = i.to_double(); }
+template <typename To, typename From>
+__device__ __forceinline__ C<To> ccvt(const C<From>& i) {
+  C<To> o;
+  cvt(o.x, i.x);
+  cvt(o.y, i.y);
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point grid values of the spread: value = integer * 2^-k.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }  // exact, |k| <= 126
+
+// k such that M * max|omega c| * 2^k < 2^61 (max passed as its IEEE bit pattern).
+__device__ __forceinline__ int fx_exponent(unsigned long long mbits, int M) {
+  const double m = __longlong_as_double((long long)mbits);
+  if (!(m > 0.0)) return 0;
+  int e = 0;
+  frexp(m * (double)M, &e);  // M max < 2^e
+  const int k = 61 - e;
+  return k > 100 ? 100 : (k < -100 ? -100 : k);
+}
+
+__device__ __forceinline__ void fx_to(long long x, float isc, float& o) { o = __ll2float_rn(x) * isc; }
+__device__ __forceinline__ void fx_to(long long x, float isc, double& o) { o = (double)x * (double)isc; }
+__device__ __forceinline__ void fx_to(long long x, float isc, dd& o) {
+  const float hi = __ll2float_rn(x);
+  const float lo = __ll2float_rn(x - __float2ll_rn(hi));
+  o = dd(hi * isc, lo * isc);
+}
 
 // ---------------------------------------------------------------------------
 // 1-D FFT plan of one length n = 2^a 3^b (radix stages of 4, 2 and 3).
@@ -64,6 +105,7 @@ struct Plan {
   double sigma = 2.0;
   int width_opt = 0, bin_opt = 0;
   int use_graph = 1, check_finite = 0;
+  int native_fp64 = 0;  // FP64 mode: 0 = double-float transforms, 1 = native FP64 arithmetic
 
   // derived
   int nf = 0;        // fine grid per axis
@@ -110,6 +152,15 @@ struct Workspace {
   double* red = nullptr;      // partial sums
   int red_blocks = 0;
   int* flag = nullptr;
+  unsigned long long* fx = nullptr;  // bit pattern of max |omega c| for the fixed-point spread
+  void* wts = nullptr;               // T[M][d][w] kernel weights per sorted point
+  void* cwp = nullptr;               // T[M][d] weighted forces per sorted point
+  int* box_ns = nullptr;             // [nbins] slices per gather box (3D)
+  int* box_np = nullptr;             // [nbins] partial slots per box
+  int* box_so = nullptr;             // [nbins + 1] slice offsets
+  int* box_po = nullptr;             // [nbins + 1] partial-slot offsets
+  void* part = nullptr;              // T[slots][3][512] partial boxes
+  size_t part_slots = 0;
   // staging for host pointers
   void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t stage_bytes[4] = {0, 0, 0, 0};
@@ -118,8 +169,8 @@ struct Workspace {
 // ---------------------------------------------------------------------------
 // Launchers (implemented in the .cu files). All enqueue on `st`.
 // ---------------------------------------------------------------------------
-template <typename T>
-void launch_fft_strided(const C<T>* in, C<T>* out, int ncomp, int outer, int inner,
+template <typename T, typename Tin = T, typename Tout = T>
+void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, int inner,
                         int Nk, const FftLen& fl, bool inverse, Mult<T> mult,
                         const C<T>* tw, cudaStream_t st);
 template <typename T>
@@ -138,6 +189,25 @@ void launch_spread(const Plan& p, Workspace& ws, const double* cw, const double*
                    T* grid, cudaStream_t st);
 template <typename T>
 void launch_interp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st);
+
+void launch_spread_dd(const Plan& p, Workspace& ws, const double* cw, const double* omega, dd* grid,
+                      cudaStream_t st);
+void launch_interp_dd(const Plan& p, Workspace& ws, const dd* grid, double* U, cudaStream_t st);
+// Fixed-point spread (grid: int64 when T = dd, float when T = float) and staged interp.
+template <typename T>
+void launch_spread_fx(const Plan& p, Workspace& ws, const double* cw, const double* omega, void* grid,
+                      cudaStream_t st);
+template <typename T>
+void launch_interp_staged(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st);
+template <typename T>
+void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const double* omega, cudaStream_t st);
+template <typename T>
+void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st);
+template <typename T>
+void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st);
+template <typename T>
+void launch_fft_rows_r2c_fx(const long long* in, const unsigned long long* fxmax, int M, C<T>* out,
+                            long long nrows, int Nk, const FftLen& fl, const C<T>* tw, cudaStream_t st);
 
 template <typename T>
 void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t st);

@@ -5,6 +5,9 @@
 // for |z| <= 1, z = 2 (x - X_j)/(w h_f), w cells wide (the kernel of the NUFFT
 // library the paper uses; the paper's appendix presents the Kaiser-Bessel member
 // of the same family). Its Fourier transform is divided out in the transform passes.
+#include <algorithm>
+#include <type_traits>
+
 #include "fsib_internal.cuh"
 
 namespace fsib {
@@ -57,38 +60,104 @@ __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __re
   }
 }
 
-// Exclusive scan of the bin counts and list of occupied bins, in one block.
+// Exclusive scan of the bin counts and the list of occupied bins, in one block.
+// The bins are processed in tiles of kScanThreads * 8; each thread owns 8
+// consecutive bins of a tile (one 32-byte load), warps scan with shuffles, and
+// a running carry links the tiles.
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
 __global__ void __launch_bounds__(kScanThreads)
 k_bin_scan(const int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
            int* __restrict__ occ, int* __restrict__ nocc) {
-  __shared__ long long s_sum[kScanThreads];
-  __shared__ int s_cnt[kScanThreads];
-  const long long chunk = (nbins + kScanThreads - 1) / kScanThreads;
-  const long long lo = threadIdx.x * chunk, hi = min(nbins, lo + chunk);
-  long long sum = 0;
-  int cnt = 0;
-  for (long long i = lo; i < hi; ++i) { const int c = counts[i]; sum += c; cnt += (c > 0); }
-  s_sum[threadIdx.x] = sum;
-  s_cnt[threadIdx.x] = cnt;
+  __shared__ int w_sum[32], w_occ[32];
+  __shared__ int carry[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) { carry[0] = 0; carry[1] = 0; }
   __syncthreads();
-  // Hillis-Steele inclusive scan over the block
-  for (int off = 1; off < kScanThreads; off <<= 1) {
-    long long vs = 0; int vc = 0;
-    if (threadIdx.x >= off) { vs = s_sum[threadIdx.x - off]; vc = s_cnt[threadIdx.x - off]; }
+  for (long long base = 0; base < nbins; base += (long long)kScanThreads * kScanPer) {
+    const long long i0 = base + (long long)tid * kScanPer;
+    int c[kScanPer];
+    int s = 0, o = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      c[k] = (i0 + k < nbins) ? counts[i0 + k] : 0;
+      s += c[k];
+      o += (c[k] > 0);
+    }
+    int is = s, io = o;  // warp inclusive scan
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int ts = __shfl_up_sync(0xffffffffu, is, off), to = __shfl_up_sync(0xffffffffu, io, off);
+      if (lane >= off) { is += ts; io += to; }
+    }
+    if (lane == 31) { w_sum[warp] = is; w_occ[warp] = io; }
     __syncthreads();
-    s_sum[threadIdx.x] += vs; s_cnt[threadIdx.x] += vc;
+    if (warp == 0) {
+      int ws = w_sum[lane], wo = w_occ[lane];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int ts = __shfl_up_sync(0xffffffffu, ws, off), to = __shfl_up_sync(0xffffffffu, wo, off);
+        if (lane >= off) { ws += ts; wo += to; }
+      }
+      w_sum[lane] = ws;  // inclusive over warps
+      w_occ[lane] = wo;
+    }
+    __syncthreads();
+    int run = carry[0] + (warp ? w_sum[warp - 1] : 0) + is - s;
+    int runo = carry[1] + (warp ? w_occ[warp - 1] : 0) + io - o;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      if (i0 + k < nbins) {
+        offsets[i0 + k] = run;
+        if (c[k] > 0) occ[runo++] = (int)(i0 + k);
+      }
+      run += c[k];
+    }
+    __syncthreads();
+    if (tid == 0) { carry[0] += w_sum[31]; carry[1] += w_occ[31]; }
     __syncthreads();
   }
-  long long run = s_sum[threadIdx.x] - sum;
-  int runc = s_cnt[threadIdx.x] - cnt;
-  for (long long i = lo; i < hi; ++i) {
-    const int c = counts[i];
-    offsets[i] = (int)run;
-    if (c > 0) occ[runc++] = (int)i;
-    run += c;
+  if (tid == 0) { offsets[nbins] = carry[0]; *nocc = carry[1]; }
+}
+
+// Exclusive scans of two int arrays of length n in one block; out arrays hold n + 1 entries.
+__global__ void __launch_bounds__(1024)
+k_scan2(const int* __restrict__ a, const int* __restrict__ b, int n, int* __restrict__ oa, int* __restrict__ ob) {
+  __shared__ int wa[32], wb[32];
+  __shared__ int carry[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) { carry[0] = 0; carry[1] = 0; }
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + tid;
+    const int va = (i < n) ? a[i] : 0, vb = (i < n) ? b[i] : 0;
+    int sa = va, sb = vb;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int ta = __shfl_up_sync(0xffffffffu, sa, off), tb = __shfl_up_sync(0xffffffffu, sb, off);
+      if (lane >= off) { sa += ta; sb += tb; }
+    }
+    if (lane == 31) { wa[warp] = sa; wb[warp] = sb; }
+    __syncthreads();
+    if (warp == 0) {
+      int xa = wa[lane], xb = wb[lane];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int ta = __shfl_up_sync(0xffffffffu, xa, off), tb = __shfl_up_sync(0xffffffffu, xb, off);
+        if (lane >= off) { xa += ta; xb += tb; }
+      }
+      wa[lane] = xa; wb[lane] = xb;
+    }
+    __syncthreads();
+    if (i < n) {
+      oa[i] = carry[0] + (warp ? wa[warp - 1] : 0) + sa - va;
+      ob[i] = carry[1] + (warp ? wb[warp - 1] : 0) + sb - vb;
+    }
+    __syncthreads();
+    if (tid == 0) { carry[0] += wa[31]; carry[1] += wb[31]; }
+    __syncthreads();
   }
-  if (threadIdx.x == kScanThreads - 1) { offsets[nbins] = (int)s_sum[kScanThreads - 1]; *nocc = s_cnt[kScanThreads - 1]; }
+  if (tid == 0) { oa[n] = carry[0]; ob[n] = carry[1]; }
 }
 
 template <typename T>
@@ -129,6 +198,18 @@ __device__ __forceinline__ T es_kernel(T z, T beta) {
   const T s = T(1) - z * z;
   return s > T(0) ? exp(beta * (sqrt(s) - T(1))) : T(0);
 }
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ dd warp_sum(dd v) {
+  for (int off = 16; off > 0; off >>= 1)
+    v = v + dd(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+  return v;
+}
+__device__ __forceinline__ double to_double_val(float v) { return (double)v; }
+__device__ __forceinline__ double to_double_val(dd v) { return v.to_double(); }
 
 template <typename T, int D>
 __device__ __forceinline__ void point_weights(T* wts /*[D][kMaxW]*/, const T* __restrict__ delta,
@@ -276,6 +357,734 @@ k_interp(PointGeom g, T beta, const int* __restrict__ perm, const int* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64-mode point kernels in double-float arithmetic. The kernel weights are
+// evaluated in FP64 (3w values per point) and split into dd; every per-cell
+// product and sum runs on the FP32 pipes. The grid holds dd values.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void point_weights_dd(dd* wts, const double* __restrict__ delta, long long s, int M,
+                                                 int w, double beta, int lane) {
+  if (lane < w) {
+    const double two_w = 2.0 / w;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double z = two_w * ((double)lane + delta[(long long)a * M + s]);
+      wts[a * kMaxW + lane] = dd(es_kernel<double>(z, beta));
+    }
+  }
+  __syncwarp();
+}
+
+// Accumulate v into the float pair (hi, lo) of shared or global memory: the rounding
+// error of the atomic addition on hi is recovered exactly (TwoSum on the returned
+// old value) and added to lo together with v.lo.
+__device__ __forceinline__ void atomic_add_dd(float* hi, float* lo, dd v) {
+  const float old = atomicAdd(hi, v.hi);
+  float s, e;
+  two_sum(old, v.hi, s, e);
+  const float r = __fadd_rn(e, v.lo);
+  if (r != 0.0f) atomicAdd(lo, r);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kSpreadThreads)
+k_spread_dd(PointGeom g, double beta, const double* __restrict__ cw, const double* __restrict__ omega,
+            const int* __restrict__ perm, const int* __restrict__ offsets, const int* __restrict__ occ,
+            const int* __restrict__ nocc, const int* __restrict__ i0s, const double* __restrict__ delta,
+            dd* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = g.w, nf = g.nf, M = g.M;
+  const int Tx = g.b[0] + w, Ty = g.b[1] + w, Tz = (D == 3) ? g.b[2] + w : 1;
+  const int tcells = Tx * Ty * Tz;
+  const int nwarp = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  dd* wts_all = reinterpret_cast<dd*>(smem_raw);          // [nwarp][D][kMaxW]
+  float* thi = reinterpret_cast<float*>(wts_all + nwarp * D * kMaxW);  // [D][tcells]
+  float* tlo = thi + D * tcells;                          // [D][tcells]
+  dd* wts = wts_all + warp * D * kMaxW;
+  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
+  const int nrow = (D == 3) ? w * w : w;
+  const int nb_occ = *nocc;
+  for (int k = blockIdx.x; k < nb_occ; k += gridDim.x) {
+    const int bin = occ[k];
+    const int Bx = bin % g.nb[0];
+    const int By = (bin / g.nb[0]) % g.nb[1];
+    const int Bz = (D == 3) ? bin / (g.nb[0] * g.nb[1]) : 0;
+    const int half = w / 2;
+    const int ox = Bx * g.b[0] - half, oy = By * g.b[1] - half, oz = (D == 3) ? Bz * g.b[2] - half : 0;
+    for (int i = threadIdx.x; i < D * tcells; i += blockDim.x) { thi[i] = 0.0f; tlo[i] = 0.0f; }
+    __syncthreads();
+    const int s0 = offsets[bin], s1 = offsets[bin + 1];
+    for (int s = s0 + warp; s < s1; s += nwarp) {
+      const int j = perm[s];
+      point_weights_dd<D>(wts, delta, s, M, w, beta, lane);
+      const double om = omega ? omega[j] : 1.0;
+      dd cv[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) cv[a] = dd(om * cw[(long long)a * M + j]);
+      const int bx = i0s[s] - ox, by = i0s[(long long)M + s] - oy;
+      const int bz = (D == 3) ? i0s[2LL * M + s] - oz : 0;
+      for (int r = lane; r < nrow; r += 32) {  // one (y, z) row of the window per lane
+        const int qy = r % w, qz = (D == 3) ? r / w : 0;
+        dd wyz = wts[kMaxW + qy];
+        if (D == 3) wyz = wyz * wts[2 * kMaxW + qz];
+        dd t[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) t[a] = cv[a] * wyz;
+        const int rowc = ((bz + qz) * Ty + (by + qy)) * Tx + bx;
+        for (int qx = 0; qx < w; ++qx) {
+          const dd wx = wts[qx];
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+            atomic_add_dd(&thi[a * tcells + rowc + qx], &tlo[a * tcells + rowc + qx], t[a] * wx);
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tcells; i += blockDim.x) {
+      const int cx = i % Tx, cy = (i / Tx) % Ty, cz = i / (Tx * Ty);
+      int gx = ox + cx, gy = oy + cy, gz = oz + cz;
+      gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
+      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
+      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
+      const long long gi = ((long long)gz * nf + gy) * nf + gx;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float h, l;
+        quick_two_sum(thi[a * tcells + i], tlo[a * tcells + i], h, l);
+        if (h != 0.0f) {
+          dd* gp = &grid[a * gcells + gi];
+          atomic_add_dd(&gp->hi, &gp->lo, dd(h, l));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kSpreadThreads)
+k_interp_dd(PointGeom g, double beta, const int* __restrict__ perm, const int* __restrict__ i0s,
+            const double* __restrict__ delta, const dd* __restrict__ grid, double* __restrict__ U) {
+  __shared__ dd wts_all[(kSpreadThreads / 32) * 3 * kMaxW];
+  const int w = g.w, nf = g.nf, M = g.M;
+  const int nwarp = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  dd* wts = wts_all + warp * D * kMaxW;
+  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
+  const int nrow = (D == 3) ? w * w : w;
+  for (long long s = (long long)blockIdx.x * nwarp + warp; s < M; s += (long long)gridDim.x * nwarp) {
+    point_weights_dd<D>(wts, delta, s, M, w, beta, lane);
+    const int bx = i0s[s], by = i0s[(long long)M + s], bz = (D == 3) ? i0s[2LL * M + s] : 0;
+    dd acc[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] = dd(0.0f, 0.0f);
+    for (int r = lane; r < nrow; r += 32) {
+      const int qy = r % w, qz = (D == 3) ? r / w : 0;
+      int gy = by + qy, gz = bz + qz;
+      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
+      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
+      const long long row = ((long long)gz * nf + gy) * nf;
+      dd srow[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) srow[a] = dd(0.0f, 0.0f);
+      for (int qx = 0; qx < w; ++qx) {
+        int gx = bx + qx;
+        gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
+        const dd wx = wts[qx];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const dd gv = grid[a * gcells + row + gx];
+          srow[a] = srow[a] + gv * wx;
+        }
+      }
+      dd wyz = wts[kMaxW + qy];
+      if (D == 3) wyz = wyz * wts[2 * kMaxW + qz];
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] = acc[a] + srow[a] * wyz;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      dd v = acc[a];
+      for (int off = 16; off > 0; off >>= 1) {
+        const dd o(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+        v = v + o;
+      }
+      acc[a] = v;
+    }
+    if (lane == 0) {
+      const int j = perm[s];
+#pragma unroll
+      for (int a = 0; a < D; ++a) U[(long long)a * M + j] = acc[a].to_double();
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Spread by exact fixed-point accumulation (transform modes: float and dd).
+//
+// Each contribution c_j phi_x phi_y phi_z is computed in the transform arithmetic
+// T, rounded to an integer multiple of 2^-k and added as a 64-bit integer, so the
+// accumulated grid value does not depend on the order of the additions
+// (deterministic) and carries no accumulation error beyond that rounding. The
+// scale 2^k is chosen on the device from B = M max_j |omega_j c_j|, a bound on
+// any grid value (phi <= 1), so that B 2^k < 2^61.
+// One block owns one occupied bin and its (b + w)^D tile in shared memory; the
+// points of the bin are taken one at a time by all threads of the block (the
+// cells of one window are distinct, so the tile needs no atomics), with the
+// kernel weights of the next point computed during the current one.
+// ---------------------------------------------------------------------------
+template <typename T> struct DeltaT;
+template <> struct DeltaT<float> { using type = float; };
+template <> struct DeltaT<dd> { using type = double; };
+
+__device__ __forceinline__ float es_weight(float z, double beta) { return es_kernel<float>(z, (float)beta); }
+
+template <typename T>
+__device__ __forceinline__ T weight_of(typename DeltaT<T>::type delta, int q, int w, double beta);
+template <>
+__device__ __forceinline__ float weight_of<float>(float delta, int q, int w, double beta) {
+  const float z = (2.0f / (float)w) * ((float)q + delta);
+  return es_kernel<float>(z, (float)beta);
+}
+template <>
+__device__ __forceinline__ dd weight_of<dd>(double delta, int q, int w, double beta) {
+  const double z = (2.0 / (double)w) * ((double)q + delta);
+  return dd(es_kernel<double>(z, beta));
+}
+
+
+__device__ __forceinline__ long long to_fixed(float v, float s) { return __float2ll_rn(v * s); }
+__device__ __forceinline__ long long to_fixed(dd v, float s) {
+  return __float2ll_rn(v.hi * s) + __float2ll_rn(v.lo * s);
+}
+
+
+__global__ void k_fx_max(const double* __restrict__ cw, const double* __restrict__ omega, int d, int M,
+                         unsigned long long* __restrict__ mx) {
+  double m = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    const double om = omega ? fabs(omega[j]) : 1.0;
+    for (int a = 0; a < d; ++a) m = fmax(m, fabs(cw[(long long)a * M + j]) * om);
+  }
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+template <typename T, int D, bool FXGRID>
+__global__ void __launch_bounds__(kSpreadThreads)
+k_spread_fx(PointGeom g, double beta, const double* __restrict__ cw, const double* __restrict__ omega,
+            const int* __restrict__ perm, const int* __restrict__ offsets, const int* __restrict__ occ,
+            const int* __restrict__ nocc, const int* __restrict__ i0s,
+            const typename DeltaT<T>::type* __restrict__ delta, const unsigned long long* __restrict__ fxmax,
+            void* __restrict__ grid_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = g.w, nf = g.nf, M = g.M;
+  const int Tx = g.b[0] + w, Ty = g.b[1] + w, Tz = (D == 3) ? g.b[2] + w : 1;
+  const int tcells = Tx * Ty * Tz;
+  long long* tile = reinterpret_cast<long long*>(smem_raw);                // [D][tcells]
+  T* wbuf = reinterpret_cast<T*>(tile + (size_t)D * tcells);              // [2][D][kMaxW]
+  T* cbuf = wbuf + 2 * D * kMaxW;                                          // [2][D]
+  int* obuf = reinterpret_cast<int*>(cbuf + 2 * D);                        // [2][3] window offsets in the tile
+  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
+  const int wd = (D == 3) ? w * w * w : w * w;
+  const int k = fx_exponent(*fxmax, M);
+  const float sc = pow2f(k), isc = pow2f(-k);
+  const int nb_occ = *nocc;
+  for (int kb = blockIdx.x; kb < nb_occ; kb += gridDim.x) {
+    const int bin = occ[kb];
+    const int Bx = bin % g.nb[0];
+    const int By = (bin / g.nb[0]) % g.nb[1];
+    const int Bz = (D == 3) ? bin / (g.nb[0] * g.nb[1]) : 0;
+    const int half = w / 2;
+    const int ox = Bx * g.b[0] - half, oy = By * g.b[1] - half, oz = (D == 3) ? Bz * g.b[2] - half : 0;
+    const int s0 = offsets[bin], s1 = offsets[bin + 1];
+    for (int i = threadIdx.x; i < D * tcells; i += blockDim.x) tile[i] = 0;
+    // weights, weighted force and window offsets of point s into buffer b
+    auto prepare = [&](int s, int b) {
+      const int t = threadIdx.x;
+      if (t < D * w) {
+        const int a = t / w, q = t % w;
+        wbuf[(b * D + a) * kMaxW + q] = weight_of<T>(delta[(long long)a * M + s], q, w, beta);
+      } else if (t < D * w + D) {
+        const int a = t - D * w;
+        const int j = perm[s];
+        const double om = omega ? omega[j] : 1.0;
+        cbuf[b * D + a] = T(om * cw[(long long)a * M + j]);
+      } else if (t == D * w + D) {
+        obuf[b * 3 + 0] = i0s[s] - ox;
+        obuf[b * 3 + 1] = i0s[(long long)M + s] - oy;
+        obuf[b * 3 + 2] = (D == 3) ? i0s[2LL * M + s] - oz : 0;
+      }
+    };
+    if (s0 < s1) prepare(s0, 0);
+    __syncthreads();
+    for (int s = s0; s < s1; ++s) {
+      const int b = (s - s0) & 1;
+      if (s + 1 < s1) prepare(s + 1, b ^ 1);
+      const T* wx = wbuf + (b * D + 0) * kMaxW;
+      const T* wy = wbuf + (b * D + 1) * kMaxW;
+      const T* wz = wbuf + (b * D + 2 % D) * kMaxW;
+      const int bx = obuf[b * 3], by = obuf[b * 3 + 1], bz = obuf[b * 3 + 2];
+      T cv[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) cv[a] = cbuf[b * D + a];
+      for (int i = threadIdx.x; i < wd; i += blockDim.x) {
+        const int qx = i % w, qy = (i / w) % w, qz = (D == 3) ? i / (w * w) : 0;
+        T wt = wx[qx] * wy[qy];
+        if (D == 3) wt = wt * wz[qz];
+        const int cell = ((bz + qz) * Ty + (by + qy)) * Tx + (bx + qx);
+#pragma unroll
+        for (int a = 0; a < D; ++a) tile[a * tcells + cell] += to_fixed(cv[a] * wt, sc);
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < tcells; i += blockDim.x) {
+      const int cx = i % Tx, cy = (i / Tx) % Ty, cz = i / (Tx * Ty);
+      int gx = ox + cx, gy = oy + cy, gz = oz + cz;
+      gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
+      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
+      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
+      const long long gi = ((long long)gz * nf + gy) * nf + gx;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const long long v = tile[a * tcells + i];
+        if (v != 0) {
+          if (FXGRID)
+            atomicAdd(reinterpret_cast<unsigned long long*>(grid_out) + a * gcells + gi, (unsigned long long)v);
+          else
+            atomicAdd(reinterpret_cast<float*>(grid_out) + a * gcells + gi, (float)v * isc);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Interp with the bin's tile staged in shared memory (transform modes: float and dd).
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__global__ void __launch_bounds__(kSpreadThreads)
+k_interp_staged(PointGeom g, double beta, const int* __restrict__ perm, const int* __restrict__ offsets,
+                const int* __restrict__ occ, const int* __restrict__ nocc, const int* __restrict__ i0s,
+                const typename DeltaT<T>::type* __restrict__ delta, const T* __restrict__ grid,
+                double* __restrict__ U) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = g.w, nf = g.nf, M = g.M;
+  const int Tx = g.b[0] + w, Ty = g.b[1] + w, Tz = (D == 3) ? g.b[2] + w : 1;
+  const int tcells = Tx * Ty * Tz;
+  const int nwarp = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  T* tile = reinterpret_cast<T*>(smem_raw);                  // [D][tcells]
+  T* wts = tile + (size_t)D * tcells + warp * D * kMaxW;     // per warp [D][kMaxW]
+  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
+  const int nrow = (D == 3) ? w * w : w;
+  const int nb_occ = *nocc;
+  for (int kb = blockIdx.x; kb < nb_occ; kb += gridDim.x) {
+    const int bin = occ[kb];
+    const int Bx = bin % g.nb[0];
+    const int By = (bin / g.nb[0]) % g.nb[1];
+    const int Bz = (D == 3) ? bin / (g.nb[0] * g.nb[1]) : 0;
+    const int half = w / 2;
+    const int ox = Bx * g.b[0] - half, oy = By * g.b[1] - half, oz = (D == 3) ? Bz * g.b[2] - half : 0;
+    for (int i = threadIdx.x; i < tcells; i += blockDim.x) {
+      const int cx = i % Tx, cy = (i / Tx) % Ty, cz = i / (Tx * Ty);
+      int gx = ox + cx, gy = oy + cy, gz = oz + cz;
+      gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
+      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
+      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
+      const long long gi = ((long long)gz * nf + gy) * nf + gx;
+#pragma unroll
+      for (int a = 0; a < D; ++a) tile[a * tcells + i] = grid[a * gcells + gi];
+    }
+    __syncthreads();
+    const int s0 = offsets[bin], s1 = offsets[bin + 1];
+    for (int s = s0 + warp; s < s1; s += nwarp) {
+      if (lane < w) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) wts[a * kMaxW + lane] = weight_of<T>(delta[(long long)a * M + s], lane, w, beta);
+      }
+      __syncwarp();
+      const int bx = i0s[s] - ox, by = i0s[(long long)M + s] - oy, bz = (D == 3) ? i0s[2LL * M + s] - oz : 0;
+      T acc[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] = T(0);
+      for (int r = lane; r < nrow; r += 32) {
+        const int qy = r % w, qz = (D == 3) ? r / w : 0;
+        const int rowc = ((bz + qz) * Ty + (by + qy)) * Tx + bx;
+        T srow[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) srow[a] = T(0);
+        for (int qx = 0; qx < w; ++qx) {
+          const T wxq = wts[qx];
+#pragma unroll
+          for (int a = 0; a < D; ++a) srow[a] = srow[a] + tile[a * tcells + rowc + qx] * wxq;
+        }
+        T wyz = wts[kMaxW + qy];
+        if (D == 3) wyz = wyz * wts[2 * kMaxW + qz];
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[a] = acc[a] + srow[a] * wyz;
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] = warp_sum(acc[a]);
+      if (lane == 0) {
+        const int j = perm[s];
+#pragma unroll
+        for (int a = 0; a < D; ++a) U[(long long)a * M + j] = to_double_val(acc[a]);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transform modes float / dd, gather formulation.
+//
+// k_point_prep: for every sorted point s, the kernel weights W[s][a][q] =
+//   phi(2 (i0_a + q - t_a)/w) (evaluated in FP64 for dd, in float for float) and, for
+//   a spread, the weighted force C[s][a] = omega_j c_a,j.
+// k_spread_gather: one block per output box of bx * by (* bz) grid cells. Every point
+//   whose window meets the box lies in one of the neighbouring bins, so the block
+//   walks those bins' point ranges, stages the candidates in shared memory, and each
+//   thread adds the contributions to its own run of 8 cells of one component in
+//   registers. Each grid cell is written once, by plain stores (no atomics, no
+//   separate zero fill); boxes with no candidate write zeros.
+// k_interp_warp: one warp per point; lane = qx + w k reads row segments of the window
+//   (coalesced along x) and accumulates g * (w_y w_z), then multiplies by w_x.
+// ---------------------------------------------------------------------------
+constexpr int kSeg = 8;  // cells per thread run along x in the gather
+
+template <typename T, int D>
+__global__ void k_point_prep(PointGeom g, double beta, const typename DeltaT<T>::type* __restrict__ delta,
+                             const int* __restrict__ perm, const double* __restrict__ cw,
+                             const double* __restrict__ omega, T* __restrict__ W, T* __restrict__ Cw) {
+  const int w = g.w, M = g.M;
+  const long long nw = (long long)M * D * w;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nw; t += (long long)gridDim.x * blockDim.x) {
+    const long long s = t / (D * w);
+    const int r = (int)(t % (D * w)), a = r / w, q = r % w;
+    W[t] = weight_of<T>(delta[(long long)a * M + s], q, w, beta);
+    if (Cw && q == 0) {
+      const int j = perm[s];
+      const double om = omega ? omega[j] : 1.0;
+      Cw[s * D + a] = T(om * cw[(long long)a * M + j]);
+    }
+  }
+}
+
+constexpr int kChunk = 32;  // candidates staged per round
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256)
+k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
+                const T* __restrict__ W, const T* __restrict__ Cw, T* __restrict__ grid) {
+  __shared__ T sW[kChunk * D * kMaxW];
+  __shared__ T sC[kChunk * D];
+  __shared__ int sI[kChunk * 3];
+  const int w = g.w, nf = g.nf, M = g.M;
+  const int bxs = g.b[0], bys = g.b[1], bzs = (D == 3) ? g.b[2] : 1;
+  const int nseg = bxs / kSeg;
+  const int box = blockIdx.x;
+  const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = (D == 3) ? box / (g.nb[0] * g.nb[1]) : 0;
+  const int ox = Bx * bxs, oy = By * bys, oz = Bz * bzs;
+  // task: (component, z, y, segment) -> a run of kSeg cells along x
+  const int ntask = D * bzs * bys * nseg;
+  const int task = threadIdx.x;
+  const bool active = task < ntask;
+  const int seg = task % nseg, ty = (task / nseg) % bys, tz = (task / (nseg * bys)) % bzs;
+  const int comp = task / (nseg * bys * bzs);
+  const int cx0 = ox + seg * kSeg, cy = oy + ty, cz = oz + tz;
+  T acc[kSeg];
+#pragma unroll
+  for (int i = 0; i < kSeg; ++i) acc[i] = T(0);
+  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
+  // neighbour bins per axis: B + dlo .. B + dhi (mod nb), or every bin once if that span covers the axis
+  const int span = dhi - dlo + 1;
+  const int sx = min(span, g.nb[0]), sy = min(span, g.nb[1]), sz = (D == 3) ? min(span, g.nb[2]) : 1;
+  const int bx0 = (span >= g.nb[0]) ? 0 : Bx + dlo, by0 = (span >= g.nb[1]) ? 0 : By + dlo;
+  const int bz0 = (D == 3) ? ((span >= g.nb[2]) ? 0 : Bz + dlo) : 0;
+  const int nnb = sx * sy * sz;
+  for (int nb = 0; nb < nnb; ++nb) {
+    int nbx = bx0 + nb % sx, nby = by0 + (nb / sx) % sy, nbz = (D == 3) ? bz0 + nb / (sx * sy) : 0;
+    nbx = (nbx % g.nb[0] + g.nb[0]) % g.nb[0];
+    nby = (nby % g.nb[1] + g.nb[1]) % g.nb[1];
+    if (D == 3) nbz = (nbz % g.nb[2] + g.nb[2]) % g.nb[2];
+    const int bin = (nbz * g.nb[1] + nby) * g.nb[0] + nbx;
+    const int p0 = offsets[bin], p1 = offsets[bin + 1];
+    for (int c0 = p0; c0 < p1; c0 += kChunk) {
+      const int nc = min(kChunk, p1 - c0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < nc * D * w; i += blockDim.x) {
+        const int c = i / (D * w), r = i % (D * w);
+        sW[c * D * kMaxW + r] = W[(long long)(c0 + c) * D * w + r];
+      }
+      for (int i = threadIdx.x; i < nc * D; i += blockDim.x) sC[i] = Cw[(long long)c0 * D + i];
+      for (int i = threadIdx.x; i < nc * D; i += blockDim.x) {
+        const int c = i / D, a = i % D;
+        sI[c * 3 + a] = i0s[(long long)a * M + c0 + c];
+      }
+      __syncthreads();
+      if (!active) continue;
+      for (int c = 0; c < nc; ++c) {
+        // window index of this thread's cells: (cell - i0) mod nf must lie in [0, w). With
+        // cell in [0, nf) and i0 in [-w/2, nf - w/2] one wrap suffices; since w + b <= nf a
+        // window meets the box through one periodic image only.
+        int qy = cy - sI[c * 3 + 1];
+        qy += (qy < 0) ? nf : 0; qy -= (qy >= nf) ? nf : 0;
+        if (qy >= w) continue;
+        int qz = 0;
+        if (D == 3) {
+          qz = cz - sI[c * 3 + 2];
+          qz += (qz < 0) ? nf : 0; qz -= (qz >= nf) ? nf : 0;
+          if (qz >= w) continue;
+        }
+        int qx0 = cx0 - sI[c * 3 + 0];
+        qx0 += (qx0 < 0) ? nf : 0; qx0 -= (qx0 >= nf) ? nf : 0;
+        if (qx0 > nf - kSeg) qx0 -= nf;  // run starts just before the window start
+        if (qx0 >= w) continue;
+        const T* wc = sW + c * D * kMaxW;  // axis a at offset a * w (layout of W)
+        T t = sC[c * D + comp] * wc[w + qy];
+        if (D == 3) t = t * wc[2 * w + qz];
+#pragma unroll
+        for (int i = 0; i < kSeg; ++i) {
+          const int qx = qx0 + i;
+          if (qx >= 0 && qx < w) acc[i] = acc[i] + t * wc[qx];
+        }
+      }
+    }
+  }
+  if (active) {
+    T* out = grid + comp * gcells + ((long long)cz * nf + cy) * nf + cx0;
+#pragma unroll
+    for (int i = 0; i < kSeg; ++i) out[i] = acc[i];
+  }
+}
+
+__device__ __forceinline__ void fma_acc(float& acc, float a, float b) { acc = __fmaf_rn(a, b, acc); }
+__device__ __forceinline__ void fma_acc(dd& acc, dd a, dd b) { dd_fma_acc(acc, a, b); }
+__device__ __forceinline__ float acc_norm(float a) { return a; }
+__device__ __forceinline__ dd acc_norm(dd a) { return dd_norm(a); }
+
+// Work list of the 3D gather: box b is split into K_b = max(1, ceil(cand_b / kSliceCand))
+// slices of at most kSliceCand candidates (cand_b = points in its neighbouring bins).
+constexpr int kSliceCand = 256;
+
+__device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int Bx, int By, int Bz, int lane,
+                                       int* bin) {
+  const int span = dhi - dlo + 1;
+  const int sx = min(span, g.nb[0]), sy = min(span, g.nb[1]), sz = min(span, g.nb[2]);
+  const int bx0 = (span >= g.nb[0]) ? 0 : Bx + dlo, by0 = (span >= g.nb[1]) ? 0 : By + dlo;
+  const int bz0 = (span >= g.nb[2]) ? 0 : Bz + dlo;
+  const int nnb = sx * sy * sz;
+  if (lane < nnb) {
+    int nbx = bx0 + lane % sx, nby = by0 + (lane / sx) % sy, nbz = bz0 + lane / (sx * sy);
+    nbx = (nbx % g.nb[0] + g.nb[0]) % g.nb[0];
+    nby = (nby % g.nb[1] + g.nb[1]) % g.nb[1];
+    nbz = (nbz % g.nb[2] + g.nb[2]) % g.nb[2];
+    *bin = (nbz * g.nb[1] + nby) * g.nb[0] + nbx;
+  }
+  return nnb;
+}
+
+// One warp per box: number of slices of the box.
+__global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
+                             int* __restrict__ nslice, int* __restrict__ npart) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
+  if (warp >= nbox) return;
+  const int Bx = warp % g.nb[0], By = (warp / g.nb[0]) % g.nb[1], Bz = warp / (g.nb[0] * g.nb[1]);
+  int bin = 0;
+  const int nnb = nb_list(g, dlo, dhi, Bx, By, Bz, lane, &bin);
+  int c = (lane < nnb) ? offsets[bin + 1] - offsets[bin] : 0;
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if (lane == 0) {
+    const int K = max(1, (c + kSliceCand - 1) / kSliceCand);
+    nslice[warp] = K;
+    npart[warp] = (K > 1) ? K : 0;
+  }
+}
+
+// 3D gather with an 8^3 box: warp z owns the box plane oz + z, lane l owns the cells
+// (x, y) = (l % 8, l / 8) and (l % 8, l / 8 + 4) of that plane for all three
+// components, in registers. The candidates (points of the 27 neighbouring bins) are
+// staged in shared memory; a candidate whose window misses a warp's plane is skipped
+// by the whole warp.
+constexpr int kBoxChunk = 64;
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
+              const T* __restrict__ W, const T* __restrict__ Cw, const int* __restrict__ slice_off,
+              const int* __restrict__ part_off, T* __restrict__ part, T* __restrict__ grid) {
+  __shared__ T sW[kBoxChunk * 3 * kMaxW];
+  __shared__ T sC[kBoxChunk * 3];
+  __shared__ int sI[kBoxChunk * 3];
+  __shared__ int sRange[2 * 32];
+  __shared__ int sNr;
+  const int w = g.w, nf = g.nf, M = g.M;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
+  const int nslices = slice_off[nbox];
+  for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+    // box of this slice: last b with slice_off[b] <= sl
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (slice_off[mid] <= sl) lo = mid; else hi = mid - 1;
+    }
+    const int box = lo, ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
+    const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
+    const int ox = Bx * 8, oy = By * 8, oz = Bz * 8;
+    const int cx = ox + (lane & 7), cy0 = oy + (lane >> 3), cz = oz + warp;
+    __syncthreads();
+    if (warp == 0) {  // candidate ranges of the neighbouring bins, in one round trip
+      int bin = 0;
+      const int nnb = nb_list(g, dlo, dhi, Bx, By, Bz, lane, &bin);
+      int p0 = 0, p1 = 0;
+      if (lane < nnb) { p0 = offsets[bin]; p1 = offsets[bin + 1]; }
+      const unsigned nonempty = __ballot_sync(0xffffffffu, p1 > p0);
+      if (p1 > p0) {
+        const int slot = __popc(nonempty & ((1u << lane) - 1u));
+        sRange[2 * slot] = p0;
+        sRange[2 * slot + 1] = p1;
+      }
+      if (lane == 0) sNr = __popc(nonempty);
+    }
+    T acc[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) acc[k][a] = T(0);
+    __syncthreads();
+    const int nr = sNr;
+    // this slice takes candidates [ks * kSliceCand, (ks + 1) * kSliceCand) of the concatenated ranges
+    int skip = ks * kSliceCand, take = kSliceCand;
+    for (int ri = 0; ri < nr && take > 0; ++ri) {
+      int r0 = sRange[2 * ri], r1 = sRange[2 * ri + 1];
+      const int len = r1 - r0;
+      if (skip >= len) { skip -= len; continue; }
+      r0 += skip;
+      skip = 0;
+      r1 = min(r1, r0 + take);
+      take -= r1 - r0;
+      for (int c0 = r0; c0 < r1; c0 += kBoxChunk) {
+        const int nc = min(kBoxChunk, r1 - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nc * 3 * w; i += blockDim.x) {
+          const int c = i / (3 * w), r = i - c * (3 * w);
+          sW[c * 3 * kMaxW + r] = W[(long long)(c0 + c) * 3 * w + r];
+        }
+        for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
+          sC[i] = Cw[(long long)c0 * 3 + i];
+          const int c = i / 3, a = i - 3 * c;
+          sI[c * 3 + a] = i0s[(long long)a * M + c0 + c];
+        }
+        __syncthreads();
+        for (int c = 0; c < nc; ++c) {
+          int qz = cz - sI[c * 3 + 2];
+          qz += (qz < 0) ? nf : 0; qz -= (qz >= nf) ? nf : 0;
+          if (qz >= w) continue;  // uniform across the warp
+          int qx = cx - sI[c * 3 + 0];
+          qx += (qx < 0) ? nf : 0; qx -= (qx >= nf) ? nf : 0;
+          if (qx >= w) continue;
+          const T* wc = sW + c * 3 * kMaxW;  // axis a at offset a * w
+          const T wxz = wc[qx] * wc[2 * w + qz];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            int qy = cy0 + 4 * k - sI[c * 3 + 1];
+            qy += (qy < 0) ? nf : 0; qy -= (qy >= nf) ? nf : 0;
+            if (qy < w) {
+              const T wt = wxz * wc[w + qy];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) fma_acc(acc[k][a], sC[c * 3 + a], wt);
+            }
+          }
+        }
+      }
+    }
+    const long long gcells = (long long)nf * nf * nf;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int ly = (lane >> 3) + 4 * k;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T v = acc_norm(acc[k][a]);
+        if (K == 1) {
+          grid[a * gcells + ((long long)cz * nf + (cy0 + 4 * k)) * nf + cx] = v;
+        } else {
+          // partial box, layout [slot][a][z][y][x]
+          part[((long long)(part_off[box] + ks) * 3 + a) * 512 + (warp * 8 + ly) * 8 + (lane & 7)] = v;
+        }
+      }
+    }
+  }
+}
+
+// Boxes split into several slices: add their partials in slice order and store the box.
+template <typename T>
+__global__ void k_box_reduce(PointGeom g, const int* __restrict__ slice_off, const int* __restrict__ part_off,
+                             const T* __restrict__ part, T* __restrict__ grid) {
+  const int box = blockIdx.x;
+  const int K = slice_off[box + 1] - slice_off[box];
+  if (K <= 1) return;
+  const int nf = g.nf;
+  const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
+  const long long gcells = (long long)nf * nf * nf;
+  for (int i = threadIdx.x; i < 3 * 512; i += blockDim.x) {
+    const int a = i / 512, c = i % 512;
+    T v = T(0);
+    for (int k = 0; k < K; ++k) v = v + part[((long long)(part_off[box] + k) * 3 + a) * 512 + c];
+    const int x = c % 8, y = (c / 8) % 8, z = c / 64;
+    grid[a * gcells + ((long long)(Bz * 8 + z) * nf + (By * 8 + y)) * nf + (Bx * 8 + x)] = v;
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256)
+k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__ i0s, const T* __restrict__ W,
+              const T* __restrict__ grid, double* __restrict__ U) {
+  const int w = g.w, nf = g.nf, M = g.M;
+  const int nwarp = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int K = 32 / w;                 // lane groups
+  const int qx = lane % w, kg = lane / w;
+  const bool on = kg < K;
+  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
+  const int nrow = (D == 3) ? w * w : w;
+  for (long long s = (long long)blockIdx.x * nwarp + warp; s < M; s += (long long)gridDim.x * nwarp) {
+    const T* ws = W + s * D * w;
+    const int bx = i0s[s], by = i0s[(long long)M + s], bz = (D == 3) ? i0s[2LL * M + s] : 0;
+    int gx = bx + qx;
+    gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
+    T acc[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] = T(0);
+    if (on) {
+      for (int r = kg; r < nrow; r += K) {
+        const int qy = r % w, qz = (D == 3) ? r / w : 0;
+        int gy = by + qy, gz = bz + qz;
+        gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
+        if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
+        T wyz = ws[w + qy];
+        if (D == 3) wyz = wyz * ws[2 * w + qz];
+        const long long cell = ((long long)gz * nf + gy) * nf + gx;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[a] = acc[a] + grid[a * gcells + cell] * wyz;
+      }
+      const T wxq = ws[qx];
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] = acc[a] * wxq;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] = warp_sum(acc[a]);
+    if (lane == 0) {
+      const int j = perm[s];
+#pragma unroll
+      for (int a = 0; a < D; ++a) U[(long long)a * M + j] = to_double_val(acc[a]);
+    }
+  }
+}
+
 static int num_sms() {
   static int n = 0;
   if (!n) {
@@ -323,6 +1132,126 @@ void launch_interp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaS
   else
     k_interp<T, 2><<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, beta, ws.perm, ws.i0, (const T*)ws.delta, grid, U);
 }
+
+void launch_spread_dd(const Plan& p, Workspace& ws, const double* cw, const double* omega, dd* grid,
+                      cudaStream_t st) {
+  const PointGeom g = geom(p);
+  const int D = p.d;
+  const int tcells = (g.b[0] + g.w) * (g.b[1] + g.w) * (D == 3 ? g.b[2] + g.w : 1);
+  const size_t smem = sizeof(dd) * (size_t)((kSpreadThreads / 32) * D * kMaxW) + 2 * sizeof(float) * (size_t)D * tcells;
+  const int blocks = 4 * num_sms();
+  auto kern = (D == 3) ? k_spread_dd<3> : k_spread_dd<2>;
+  raise_smem_limit(reinterpret_cast<const void*>(kern));
+  kern<<<blocks, kSpreadThreads, smem, st>>>(g, p.beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
+                                             (const double*)ws.delta, grid);
+}
+
+void launch_interp_dd(const Plan& p, Workspace& ws, const dd* grid, double* U, cudaStream_t st) {
+  const PointGeom g = geom(p);
+  const int nwarp = kSpreadThreads / 32;
+  long long blocks = (p.M + nwarp - 1) / nwarp;
+  if (blocks > 16LL * num_sms()) blocks = 16LL * num_sms();
+  if (p.d == 3)
+    k_interp_dd<3><<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, p.beta, ws.perm, ws.i0, (const double*)ws.delta, grid, U);
+  else
+    k_interp_dd<2><<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, p.beta, ws.perm, ws.i0, (const double*)ws.delta, grid, U);
+}
+
+template <typename T>
+void launch_spread_fx(const Plan& p, Workspace& ws, const double* cw, const double* omega, void* grid,
+                      cudaStream_t st) {
+  const PointGeom g = geom(p);
+  const int D = p.d;
+  cudaMemsetAsync(ws.fx, 0, sizeof(unsigned long long), st);
+  k_fx_max<<<std::min(64, (p.M + 255) / 256), 256, 0, st>>>(cw, omega, D, p.M, ws.fx);
+  const int tcells = (g.b[0] + g.w) * (g.b[1] + g.w) * (D == 3 ? g.b[2] + g.w : 1);
+  const size_t smem = sizeof(long long) * (size_t)D * tcells + sizeof(T) * (size_t)(2 * D * kMaxW + 2 * D) +
+                      sizeof(int) * 8;
+  const int blocks = 2 * num_sms();
+  using Td = typename DeltaT<T>::type;
+  const bool fxgrid = std::is_same<T, dd>::value;
+  if (D == 3) {
+    auto kern = fxgrid ? k_spread_fx<T, 3, true> : k_spread_fx<T, 3, false>;
+    raise_smem_limit(reinterpret_cast<const void*>(kern));
+    kern<<<blocks, kSpreadThreads, smem, st>>>(g, p.beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
+                                               (const Td*)ws.delta, ws.fx, grid);
+  } else {
+    auto kern = fxgrid ? k_spread_fx<T, 2, true> : k_spread_fx<T, 2, false>;
+    raise_smem_limit(reinterpret_cast<const void*>(kern));
+    kern<<<blocks, kSpreadThreads, smem, st>>>(g, p.beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
+                                               (const Td*)ws.delta, ws.fx, grid);
+  }
+}
+
+template <typename T>
+void launch_interp_staged(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st) {
+  const PointGeom g = geom(p);
+  const int D = p.d;
+  const int tcells = (g.b[0] + g.w) * (g.b[1] + g.w) * (D == 3 ? g.b[2] + g.w : 1);
+  const size_t smem = sizeof(T) * ((size_t)D * tcells + (size_t)(kSpreadThreads / 32) * D * kMaxW);
+  const int blocks = 2 * num_sms();
+  using Td = typename DeltaT<T>::type;
+  auto kern = (D == 3) ? k_interp_staged<T, 3> : k_interp_staged<T, 2>;
+  raise_smem_limit(reinterpret_cast<const void*>(kern));
+  kern<<<blocks, kSpreadThreads, smem, st>>>(g, p.beta, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
+                                             (const Td*)ws.delta, grid, U);
+}
+
+template <typename T>
+void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const double* omega, cudaStream_t st) {
+  const PointGeom g = geom(p);
+  using Td = typename DeltaT<T>::type;
+  const long long nw = (long long)p.M * p.d * p.w;
+  long long blocks = (nw + 255) / 256;
+  if (blocks > 64LL * num_sms()) blocks = 64LL * num_sms();
+  T* Cw = cw ? (T*)ws.cwp : nullptr;
+  if (p.d == 3)
+    k_point_prep<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw);
+  else
+    k_point_prep<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw);
+}
+
+template <typename T>
+void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st) {
+  const PointGeom g = geom(p);
+  const int h = p.w / 2, b = p.bins[0];
+  // neighbour bins holding window starts that reach the box: floor((-w + 1 + h)/b) .. floor((b - 1 + h)/b)
+  auto fl = [](int a, int bb) { return (a >= 0) ? a / bb : -((-a + bb - 1) / bb); };
+  const int dlo = fl(-p.w + 1 + h, b), dhi = fl(b - 1 + h, b);
+  const int nbox = (int)p.nbins;
+  if (p.d == 3) {
+    // slices per box, their prefix sums, then the sliced gather and the partial reduction
+    k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np);
+    k_scan2<<<1, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
+    k_spread_box3<T><<<6 * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
+                                                    (const T*)ws.cwp, ws.box_so, ws.box_po, (T*)ws.part, grid);
+    k_box_reduce<T><<<nbox, 256, 0, st>>>(g, ws.box_so, ws.box_po, (const T*)ws.part, grid);
+  } else
+    k_spread_gather<T, 2><<<nbox, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
+}
+
+template <typename T>
+void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st) {
+  const PointGeom g = geom(p);
+  long long blocks = (p.M + 7) / 8;
+  if (blocks > 32LL * num_sms()) blocks = 32LL * num_sms();
+  if (p.d == 3)
+    k_interp_warp<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U);
+  else
+    k_interp_warp<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U);
+}
+
+template void launch_point_prep<float>(const Plan&, Workspace&, const double*, const double*, cudaStream_t);
+template void launch_point_prep<dd>(const Plan&, Workspace&, const double*, const double*, cudaStream_t);
+template void launch_spread_gather<float>(const Plan&, Workspace&, float*, cudaStream_t);
+template void launch_spread_gather<dd>(const Plan&, Workspace&, dd*, cudaStream_t);
+template void launch_interp_warp<float>(const Plan&, Workspace&, const float*, double*, cudaStream_t);
+template void launch_interp_warp<dd>(const Plan&, Workspace&, const dd*, double*, cudaStream_t);
+
+template void launch_spread_fx<float>(const Plan&, Workspace&, const double*, const double*, void*, cudaStream_t);
+template void launch_spread_fx<dd>(const Plan&, Workspace&, const double*, const double*, void*, cudaStream_t);
+template void launch_interp_staged<float>(const Plan&, Workspace&, const float*, double*, cudaStream_t);
+template void launch_interp_staged<dd>(const Plan&, Workspace&, const dd*, double*, cudaStream_t);
 
 template void launch_spread<float>(const Plan&, Workspace&, const double*, const double*, float*, cudaStream_t);
 template void launch_spread<double>(const Plan&, Workspace&, const double*, const double*, double*, cudaStream_t);

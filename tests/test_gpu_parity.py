@@ -15,8 +15,9 @@ from paper_2302_08694_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "mixed": 1e-5}
-NTOL = {"fp64": 1e-12, "mixed": 1e-6}
+TOL = {"fp64": 1e-10, "fp64native": 1e-10, "mixed": 1e-5}
+NTOL = {"fp64": 1e-12, "fp64native": 1e-12, "mixed": 1e-6}
+CDT = {"fp64": np.complex128, "fp64native": np.complex128, "mixed": np.complex64}
 
 
 def rel2(a, b):
@@ -49,12 +50,16 @@ def torch_mod():
 
 
 def make(lib, N, d, M, prec, mu=1.0, rho=0.0, dt=1e-3, **kw):
-    return lib.Problem(N, d, M, mu, rho, dt, NTOL[prec], precision=prec, **kw)
+    """fp64: double-float transforms (default FP64 mode); fp64native: FP64 arithmetic."""
+    pb = lib.Problem(N, d, M, mu, rho, dt, NTOL[prec], precision="mixed" if prec == "mixed" else "fp64", **kw)
+    if prec == "fp64native":
+        pb.set_option("native_fp64", 1)
+    return pb
 
 
 # --- type-1 / type-2 against the direct sums --------------------------------------------------
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
 @pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1)])
 def test_spread_matches_oracle(lib, torch_mod, prec, d, N, M):
     torch = torch_mod
@@ -71,7 +76,7 @@ def test_spread_matches_oracle(lib, torch_mod, prec, d, N, M):
     assert relmax(got, ref) <= 10 * TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
 @pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1)])
 def test_interp_matches_oracle(lib, torch_mod, prec, d, N, M):
     torch = torch_mod
@@ -79,7 +84,7 @@ def test_interp_matches_oracle(lib, torch_mod, prec, d, N, M):
     X = rng.uniform(-0.5, 1.5, (d, M))
     H = half_random(rng, d, N)
     pb = make(lib, N, d, M, prec)
-    Ht = cuda(H if prec == "fp64" else H.astype(np.complex64), torch)
+    Ht = cuda(H.astype(CDT[prec]), torch)
     U = pb.interp(Ht, cuda(X, torch))
     torch.cuda.synchronize()
     ref = sp.interp_direct(sp.half_to_full(H, N, d), X, N)
@@ -128,17 +133,16 @@ def test_stokeslet_matches_oracle(lib, torch_mod, prec, d, N):
     rng = np.random.default_rng(300 + d + N)
     H = half_random(rng, d, N)
     pb = make(lib, N, d, 4, prec, mu=0.7, rho=0.0)
-    dt = np.complex128 if prec == "fp64" else np.complex64
-    f = cuda(H.astype(dt), torch)
+    f = cuda(H.astype(CDT[prec]), torch)
     u = pb.new_spec()
     pb.fluid_step(f, u)
     torch.cuda.synchronize()
     ref = sp.full_to_half(sp.stokeslet(sp.half_to_full(H, N, d), N, 0.7), N)
     got = sp.full_to_half(sp.half_to_full(to_np(u).astype(np.complex128), N, d), N)
-    assert rel2(got, ref) <= (1e-14 if prec == "fp64" else 1e-6)
+    assert rel2(got, ref) <= (1e-6 if prec == "mixed" else 1e-14)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
 @pytest.mark.parametrize("d,N", [(2, 16), (2, 10), (3, 8), (3, 12)])
 def test_ns_substeps_match_oracle(lib, torch_mod, prec, d, N):
     torch = torch_mod
@@ -147,7 +151,7 @@ def test_ns_substeps_match_oracle(lib, torch_mod, prec, d, N):
     u0 = sp.leray(sp.half_to_full(half_random(rng, d, N), N, d), N)
     f = sp.half_to_full(half_random(rng, d, N), N, d)
     pb = make(lib, N, d, 4, prec, mu=mu, rho=rho, dt=dt)
-    cd = np.complex128 if prec == "fp64" else np.complex64
+    cd = CDT[prec]
     ft = cuda(sp.full_to_half(f, N).astype(cd), torch)
     ut = cuda(sp.full_to_half(u0, N).astype(cd), torch)
     uh = pb.new_spec()
@@ -158,12 +162,12 @@ def test_ns_substeps_match_oracle(lib, torch_mod, prec, d, N):
     g1 = sp.half_to_full(to_np(ut).astype(np.complex128), N, d)
     assert rel2(gh, rh) <= TOL[prec]
     assert rel2(g1, r1) <= TOL[prec]
-    assert sp.max_divergence(g1, N) <= (1e-13 if prec == "fp64" else 1e-6)
+    assert sp.max_divergence(g1, N) <= (1e-6 if prec == "mixed" else 1e-13)
 
 
 # --- whole steps ------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
 def test_stokes2d_steps_match_oracle(lib, torch_mod, prec):
     """Quasi-static Stokes stepper on a closed elastic curve (the 2D Stokes workload, reduced)."""
     torch = torch_mod
@@ -183,7 +187,7 @@ def test_stokes2d_steps_match_oracle(lib, torch_mod, prec):
     assert rel2(to_np(Xt) - X0, disp) <= TOL[prec] * (10 if prec == "mixed" else 1)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
 def test_ns3d_steps_match_oracle(lib, torch_mod, prec):
     torch = torch_mod
     N, dt, nsteps, mu, rho = 12, 2e-3, 2, 0.01, 1.0
@@ -194,7 +198,7 @@ def test_ns3d_steps_match_oracle(lib, torch_mod, prec):
     u0 = 0.1 * sp.leray(sp.half_to_full(half_random(rng, 3, N), N, 3), N)
     pb = make(lib, N, 3, M, prec, mu=mu, rho=rho, dt=dt)
     pb.set_force_mesh(tri, cuda(Xref, torch), 1.0)
-    cd = np.complex128 if prec == "fp64" else np.complex64
+    cd = CDT[prec]
     Xt = cuda(X0, torch)
     ut = cuda(sp.full_to_half(u0, N).astype(cd), torch)
     Ut = pb.interp(ut, Xt)
