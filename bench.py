@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--native-fp64", action="store_true", help="FP64 arithmetic instead of double-float")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-mixed workload block")
     return ap.parse_args()
 
 
@@ -102,8 +103,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+NATIVE_FP64 = False
+
+
 def make_problem(fsib, prob, precision):
-    pb = fsib.Problem(prob.N, prob.d, prob.M, prob.mu, prob.rho, prob.dt, prob.tol, precision=precision)
+    pb = fsib.Problem(prob.N, prob.d, prob.M, prob.mu, prob.rho, prob.dt,
+                      1e-12 if precision == "fp64" else 1e-6, precision=precision)
+    if precision == "fp64" and NATIVE_FP64:
+        pb.set_option("native_fp64", 1)
     if prob.force == "mesh":
         pb.set_force_mesh(prob.tri, prob.Xref, prob.stiffness)
     else:
@@ -154,6 +161,152 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def roofline_of(site, prec, pk, pk_src, fp64_peak, fp32_peak):
+    """Binding roofline of one launch site: HBM (algorithmic bytes) or ALU (algorithmic flops).
+
+    FP64 mode is compared with the measured native FP64 FMA rate (its flops are FP64-accurate
+    operations, carried out in double-float on the FP32 pipes); mixed mode with the FP32 FMA rate.
+    """
+    avg_ms = site["total_ms"] / site["launches"]
+    gbs = site["bytes"] / (avg_ms * 1e-3) / 1e9
+    gfl = site["flops"] / (avg_ms * 1e-3) / 1e9
+    alu_peak = fp64_peak if prec == "fp64" else fp32_peak
+    t_mem = site["bytes"] / (pk["hbm_gbs"] * 1e9)
+    t_alu = site["flops"] / (alu_peak * 1e9)
+    if t_alu > t_mem:
+        r = {"bound": "alu", "achieved": gfl / 1e3, "peak": alu_peak / 1e3, "unit": "TFLOP/s", "frac": gfl / alu_peak,
+             "peak_source": ("measured FP64 FMA rate (fsib_measure_peak kind 0)" if prec == "fp64" else
+                             "measured FP32 FMA rate (fsib_measure_peak kind 1)")}
+    else:
+        r = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+             "peak_source": f"MEASURED_PEAKS hbm_gbs ({pk_src})"}
+    r.update({"kernel": site["name"], "bytes_per_launch": site["bytes"], "flops_per_launch": site["flops"],
+              "avg_launch_ms": avg_ms, "hbm_frac": gbs / pk["hbm_gbs"],
+              "alu_frac": gfl / alu_peak if alu_peak else None})
+    return r
+
+
+def measure(fsib, torch, prob, prec, steps, warmup, dev, flush, world=1, barrier=None, sampler_idx=None,
+            nufft_reps=20, nprof=20):
+    """Time one workload: steps/s (CUDA events around each step, L2 flushed between steps),
+    NUFFT pts/s for type-1 and type-2, and the per-launch-site breakdown."""
+    stream = torch.cuda.current_stream()
+    pb = make_problem(fsib, prob, prec)
+    X = torch.from_numpy(prob.X0.copy()).to(dev)
+    u = pb.new_spec(device=dev)
+    U = pb.interp(u, X)
+    for _ in range(warmup):
+        pb.step(X, u, U, nsteps=1)
+    if barrier:
+        barrier()
+    sampler = ClockSampler(sampler_idx) if sampler_idx is not None else None
+    if sampler:
+        time.sleep(0.25)
+    ev = [_events(torch) for _ in range(steps)]
+    if barrier:
+        barrier()
+    for s in range(steps):
+        flush.zero_()  # L2 flush between timed iterations (outside the events)
+        ev[s][0].record(stream)
+        pb.step(X, u, U, nsteps=1)
+        ev[s][1].record(stream)
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    launches = int(pb.info("launches_per_step"))
+    # NUFFT throughput, type-1 and type-2 separately
+    c = pb.force(X)
+    fh = pb.new_spec(device=dev)
+    t1 = t2 = 0.0
+    for r in range(nufft_reps + 2):
+        for kind in (1, 2):
+            flush.zero_()
+            a, b = _events(torch)
+            a.record(stream)
+            if kind == 1:
+                pb.spread(X, c, None, out=fh)
+            else:
+                pb.interp(u, X, out=U)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r >= 2:
+                if kind == 1:
+                    t1 += a.elapsed_time(b)
+                else:
+                    t2 += a.elapsed_time(b)
+    # per-launch-site timing (CUDA events around each launch site, direct launches)
+    pb.profile(True)
+    pb.profile_reset()
+    Xp, up, Up = X.clone(), u.clone(), U.clone()
+    for _ in range(nprof):
+        flush.zero_()
+        pb.step(Xp, up, Up, nsteps=1)
+    sites = pb.profile_entries()
+    pb.profile(False)
+    info = {k: pb.info(k) for k in ("nf", "Nt", "width")}
+    return {"pb": pb, "X": X, "u": u, "U": U, "ms": ms, "launches": launches, "clocks": clocks,
+            "pts1": prob.M / (t1 / nufft_reps * 1e-3), "pts2": prob.M / (t2 / nufft_reps * 1e-3),
+            "sites": sites, "nprof": nprof, "info": info}
+
+
+def breakdown_of(sites, nprof, top=12):
+    tot = sum(s["total_ms"] for s in sites)
+    rows = sorted(({"site": s["name"], "ms_per_step": s["total_ms"] / nprof, "share": s["total_ms"] / tot,
+                    "gbs": s["bytes"] * s["launches"] / (s["total_ms"] * 1e-3) / 1e9,
+                    "gflops": s["flops"] * s["launches"] / (s["total_ms"] * 1e-3) / 1e9}
+                   for s in sites), key=lambda z: -z["ms_per_step"])
+    return rows[:top]
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def mixed_block(fsib, torch, dev, flush, pk, pk_src, fp64_peak, fp32_peak, steps, warmup):
+    """FP32-mixed workload (N = 128^3, M = 40322) with its error against an FP64 run of the same seed."""
+    prob = wl.config_ns3d_mixed()
+    m = measure(fsib, torch, prob, "mixed", steps, warmup, dev, flush, nufft_reps=10, nprof=10)
+    top = max(m["sites"], key=lambda s: s["total_ms"])
+    # error report: one transform each, and a few steps from the same initial state
+    pm = m["pb"]
+    p64 = make_problem(fsib, prob, "fp64")
+    X0 = torch.from_numpy(prob.X0.copy()).to(dev)
+    c = p64.force(X0)
+    f64 = p64.spread(X0, c).cpu().numpy()
+    f32 = pm.spread(X0, c).cpu().numpy().astype(np.complex128)
+    rng = np.random.default_rng(33)
+    H = (rng.standard_normal(p64.spec_shape) + 1j * rng.standard_normal(p64.spec_shape)) * 1e-3
+    u64 = torch.from_numpy(H).to(dev)
+    U64 = p64.interp(u64, X0).cpu().numpy()
+    U32 = pm.interp(u64.to(torch.complex64), X0).cpu().numpy()
+    nerr = 5
+    Xa, ua = X0.clone(), p64.new_spec(device=dev)
+    Ua = p64.interp(ua, Xa)
+    Xb, ub = X0.clone(), pm.new_spec(device=dev)
+    Ub = pm.interp(ub, Xb)
+    p64.step(Xa, ua, Ua, nsteps=nerr)
+    pm.step(Xb, ub, Ub, nsteps=nerr)
+    torch.cuda.synchronize()
+    x0 = prob.X0
+    errs = {"type1_rel_l2": rel_err(f32, f64), "type2_rel_l2": rel_err(U32, U64),
+            f"steps{nerr}_displacement_rel_l2": rel_err(Xb.cpu().numpy() - x0, Xa.cpu().numpy() - x0),
+            f"steps{nerr}_uhat_rel_l2": rel_err(ub.cpu().numpy().astype(np.complex128), ua.cpu().numpy())}
+    p64.close()
+    return {"workload": prob.name, "value": steps / (m["ms"] * 1e-3), "unit": "steps/s",
+            "ms_per_step": m["ms"] / steps, "steps": steps, "dtype": "f32 transforms, f64 positions/forces",
+            "nufft_pts_per_s": {"type1": m["pts1"], "type2": m["pts2"]},
+            "config": {"N": prob.N, "M": prob.M, "tol": prob.tol, **{k: int(v) for k, v in m["info"].items()}},
+            "error_vs_fp64_run": errs,
+            "roofline": roofline_of(top, "mixed", pk, pk_src, fp64_peak, fp32_peak),
+            "breakdown": breakdown_of(m["sites"], m["nprof"], 8)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -164,15 +317,6 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prob = wl.config_ns3d_fp64()
-    pb = make_problem(fsib, prob, "fp64")
-    if args.native_fp64:
-        pb.set_option("native_fp64", 1)  # re-plans; the mesh model survives
-    stream = torch.cuda.current_stream()
-
-    X = torch.from_numpy(prob.X0.copy()).to(dev)
-    u = pb.new_spec(device=dev)
-    U = pb.interp(u, X)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -180,90 +324,25 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        pb.step(X, u, U, nsteps=1)
-    barrier()
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if \
         os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
-    sampler = ClockSampler(gpu_index)
-    time.sleep(0.25)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    for s in range(args.steps):
-        flush.zero_()  # L2 flush between timed iterations (outside the events)
-        ev[s][0].record(stream)
-        pb.step(X, u, U, nsteps=1)
-        ev[s][1].record(stream)
-    barrier()
-    clocks = sampler.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_rank = torch.tensor([ms], dtype=torch.float64, device=dev)
+    prob = wl.config_ns3d_fp64()
+    prec = "fp64"
+    m = measure(fsib, torch, prob, prec, args.steps, args.warmup, dev, flush, world, barrier, gpu_index)
+    pb = m["pb"]
+    t_rank = torch.tensor([m["ms"]], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
     ms_max = float(t_rank.item())
     value = world * args.steps / (ms_max * 1e-3)
-    launches = int(pb.info("launches_per_step"))
 
-    # NUFFT throughput, type-1 and type-2 separately (same workload, FP64)
-    c = pb.force(X)
-    fh = pb.new_spec(device=dev)
-    reps = 20
-    t1 = t2 = 0.0
-    for r in range(reps + 2):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pb.spread(X, c, None, out=fh)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if r >= 2:
-            t1 += a.elapsed_time(b)
-        flush.zero_()
-        a.record(stream)
-        pb.interp(u, X, out=U)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if r >= 2:
-            t2 += a.elapsed_time(b)
-    pts1 = prob.M / (t1 / reps * 1e-3)
-    pts2 = prob.M / (t2 / reps * 1e-3)
-
-    # per-launch-site timing (CUDA events around each launch site, direct launches)
-    pb.profile(True)
-    pb.profile_reset()
-    nprof = max(3, min(args.steps, 20))
-    Xp, up, Up = X.clone(), u.clone(), U.clone()
-    for _ in range(nprof):
-        flush.zero_()
-        pb.step(Xp, up, Up, nsteps=1)
-    sites = pb.profile_entries()
-    pb.profile(False)
-    tot = sum(s["total_ms"] for s in sites)
-    top = max(sites, key=lambda s: s["total_ms"])
     pk, pk_src = peaks()
     fp64_peak = fsib.measure_peak(0)  # GFLOP/s
     fp32_peak = fsib.measure_peak(1)
-    avg_ms = top["total_ms"] / top["launches"]
-    gbs = top["bytes"] / (avg_ms * 1e-3) / 1e9
-    gfl = top["flops"] / (avg_ms * 1e-3) / 1e9
-    t_mem = top["bytes"] / (pk["hbm_gbs"] * 1e9)
-    t_alu = top["flops"] / (fp64_peak * 1e9)
-    if t_alu > t_mem:
-        roof = {"bound": "alu", "achieved": gfl / 1e3, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
-                "frac": gfl / fp64_peak}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"]}
-    roof.update({"traffic": None, "kernel": top["name"], "share": top["total_ms"] / tot,
-                 "bytes_per_launch": top["bytes"], "flops_per_launch": top["flops"],
-                 "avg_launch_ms": avg_ms, "peak_source": (pk_src if roof["bound"] == "hbm" else
-                                                          "measured FP64 FMA microbenchmark (fsib_measure_peak)"),
-                 "hbm_frac": gbs / pk["hbm_gbs"], "fp64_fma_peak_tflops": fp64_peak / 1e3,
-                 "fp32_fma_peak_tflops": fp32_peak / 1e3})
-    breakdown = sorted(({"site": s["name"], "ms_per_step": s["total_ms"] / nprof,
-                         "share": s["total_ms"] / tot,
-                         "gbs": s["bytes"] * s["launches"] / (s["total_ms"] * 1e-3) / 1e9,
-                         "gflops": s["flops"] * s["launches"] / (s["total_ms"] * 1e-3) / 1e9}
-                        for s in sites), key=lambda z: -z["ms_per_step"])
+    top = max(m["sites"], key=lambda s: s["total_ms"])
+    roof = roofline_of(top, prec, pk, pk_src, fp64_peak, fp32_peak)
+    roof.update({"traffic": None, "share": top["total_ms"] / sum(s["total_ms"] for s in m["sites"]),
+                 "fp64_fma_peak_tflops": fp64_peak / 1e3, "fp32_fma_peak_tflops": fp32_peak / 1e3})
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -280,6 +359,13 @@ def run_ours(args):
         nb = Xh.numel() * 8 + uh.numel() * uh.element_size() + Uh.numel() * 8
         e2e = {"value": world * ke / te, "unit": "steps/s", "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
 
+    mixed = None
+    if not args.no_mixed:
+        mixed = mixed_block(fsib, torch, dev, flush, pk, pk_src, fp64_peak, fp32_peak,
+                            steps=max(3, min(args.steps, 50)), warmup=max(3, args.warmup))
+        mixed["value"] *= world
+        mixed["nufft_pts_per_s"] = {k: v * world for k, v in mixed["nufft_pts_per_s"].items()}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         k = 2
@@ -291,20 +377,23 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": prob.name, "d": 3, "N": prob.N, "M": prob.M, "nf": int(pb.info("nf")),
-                           "Nt": int(pb.info("Nt")), "width": int(pb.info("width")), "tol": prob.tol,
+                "config": {"workload": prob.name, "d": 3, "N": prob.N, "M": prob.M,
+                           **{k: int(v) for k, v in m["info"].items()}, "tol": prob.tol,
+                           "arithmetic": "double-float transforms (FP64-accurate), FP64 positions/forces",
                            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{world}"},
-                "nufft_pts_per_s": {"type1": world * pts1, "type2": world * pts2},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches * args.steps, "launches_per_step": launches,
-                "breakdown": breakdown[:12]}
+                "nufft_pts_per_s": {"type1": world * m["pts1"], "type2": world * m["pts2"]},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": m["clocks"],
+                "gpu_launches": m["launches"] * args.steps, "launches_per_step": m["launches"],
+                "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
 def main():
+    global NATIVE_FP64
     args = parse()
+    NATIVE_FP64 = args.native_fp64
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -494,30 +494,36 @@ static void do_bin(fsib_plan* h, const double* X, cudaStream_t st, const double*
   else launch_point_prep<float>(p, h->ws, c, omega, st);
 }
 
+// Algorithmic flops of one spread or interp launch: for every cell of every point's
+// window, the weight product (d - 1 multiplications) and d multiply-adds (2 flops each).
+static double point_flops(const Plan& p) {
+  return (double)p.M * std::pow((double)p.w, p.d) * (3.0 * p.d - 1.0);
+}
+
 static double point_bytes(const Plan& p) {
   return (double)p.M * (4.0 + p.d * (4.0 + (p.prec == FSIB_FP64 ? 8.0 : 4.0) + 8.0));
 }
 
 template <typename TI>
 static void spread_points(fsib_plan* h, const double* c, const double* omega, TI* grid, cudaStream_t st) {
-  Prof pr(h, "spread", point_bytes(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  Prof pr(h, "spread", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
   launch_spread_gather<TI>(h->p, h->ws, grid, st);
 }
 template <>
 void spread_points<double>(fsib_plan* h, const double* c, const double* omega, double* grid, cudaStream_t st) {
   { Prof pr(h, "zero_grid", (double)h->ws.grid_bytes, 0.0, st);
     cudaMemsetAsync(h->ws.grid, 0, h->ws.grid_bytes, st); }
-  Prof pr(h, "spread", point_bytes(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  Prof pr(h, "spread", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
   launch_spread<double>(h->p, h->ws, c, omega, grid, st);
 }
 template <typename TI>
 static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st) {
-  Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
   launch_interp_warp<TI>(h->p, h->ws, grid, U, st);
 }
 template <>
 void interp_points<double>(fsib_plan* h, const double* grid, double* U, cudaStream_t st) {
-  Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, 0.0, st);
+  Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
   launch_interp<double>(h->p, h->ws, grid, U, st);
 }
 
