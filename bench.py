@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--native-fp64", action="store_true", help="FP64 arithmetic instead of double-float")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-mixed workload block")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workload block")
     return ap.parse_args()
 
 
@@ -307,6 +308,55 @@ def mixed_block(fsib, torch, dev, flush, pk, pk_src, fp64_peak, fp32_peak, steps
             "breakdown": breakdown_of(m["sites"], m["nprof"], 8)}
 
 
+def batched_block(fsib, torch, dev, flush, steps, warmup):
+    """64 independent problems (2D/3D, N in {32..128}, M in [128, 20000]), FP32-mixed, autotuned,
+    advanced by one CUDA graph launch per step."""
+    probs = wl.config_batched()
+    n = len(probs)
+    B = fsib.Batch([p.N for p in probs], [p.d for p in probs], [p.M for p in probs], [p.mu for p in probs],
+                   [p.rho for p in probs], [p.dt for p in probs], [p.tol for p in probs], precision="mixed")
+    X, u, U = [], [], []
+    for p, m in zip(probs, B.members):
+        if p.force == "mesh":
+            m.set_force_mesh(p.tri, p.Xref, p.stiffness)
+        else:
+            m.set_force_curve(p.stiffness)
+        Xi = torch.from_numpy(p.X0.copy()).to(dev)
+        X.append(Xi)
+        u.append(m.new_spec(device=dev))
+        U.append(torch.zeros_like(Xi))
+    t0 = time.perf_counter()
+    B.autotune(X, u, U)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        B.step(X, u, U, nsteps=1)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = _events(torch)
+        a.record(stream)
+        B.step(X, u, U, nsteps=1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    ok = all(bool(torch.isfinite(x).all()) for x in X)
+    tuned = {}
+    for p, m in zip(probs, B.members):
+        k = f"{p.d}d_N{p.N}"
+        tuned.setdefault(k, {kk: int(m.info(kk)) for kk in ("fft_tile", "fft_rows", "spread_slice")})
+    mtot = sum(p.M for p in probs)
+    out = {"workload": f"batched{n}_mixed", "problems": n, "value": n * steps / (ms * 1e-3),
+           "unit": "problem-steps/s", "batch_steps_per_s": steps / (ms * 1e-3), "ms_per_batch_step": ms / steps,
+           "boundary_points_per_s": mtot * steps / (ms * 1e-3), "total_points": mtot,
+           "launches_per_batch_step": int(B.info("launches_per_step")), "autotune_seconds": tune_s,
+           "finite": ok, "n_2d": sum(p.d == 2 for p in probs), "n_3d": sum(p.d == 3 for p in probs),
+           "tuned_shapes": tuned}
+    B.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -366,6 +416,12 @@ def run_ours(args):
         mixed["value"] *= world
         mixed["nufft_pts_per_s"] = {k: v * world for k, v in mixed["nufft_pts_per_s"].items()}
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_block(fsib, torch, dev, flush, steps=max(3, min(args.steps, 20)), warmup=max(3, args.warmup))
+        for k in ("value", "batch_steps_per_s", "boundary_points_per_s"):
+            batched[k] *= world
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         k = 2
@@ -384,7 +440,7 @@ def run_ours(args):
                 "nufft_pts_per_s": {"type1": world * m["pts1"], "type2": world * m["pts2"]},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": m["clocks"],
                 "gpu_launches": m["launches"] * args.steps, "launches_per_step": m["launches"],
-                "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed}
+                "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

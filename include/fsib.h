@@ -83,6 +83,7 @@ int fsib_set_stream(fsib_t h, void* stream);
  *               (pairs of floats, about 48 bits; default, fast on GB300's FP32
  *               pipes), 1 = transforms in FP64 arithmetic
  *  "graph"      1 = fsib_step replays a captured CUDA graph (default), 0 = direct launches
+ *  "fft_tile", "fft_rows", "spread_slice": launch shapes, see fsib_autotune
  *  "check_finite" 1 = fsib_step checks positions for NaN/Inf at the end
  *               (adds a synchronisation), 0 = no check (default)
  * Returns FSIB_EINVAL for an unknown key or out-of-range value. */
@@ -151,6 +152,37 @@ int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps);
  * out[5] dissipation mu L^d sum |k|^2 |u-hat|^2. uhat may be NULL (out[2..5] = 0).
  * Returns FSIB_ENONFINITE if X or uhat holds NaN/Inf. */
 int fsib_invariants(fsib_t h, const double* X, const void* uhat, double out[6]);
+
+/* Launch-shape options, exact reorderings that leave results unchanged to
+ * rounding: "fft_tile" (4, 8, 16: lines per strided-pass tile), "fft_rows"
+ * (2, 4, 8: row pairs per CTA in the row passes), "spread_slice" (128..4096:
+ * candidate points per slice of a 3D gather box). fsib_autotune picks them by
+ * timing whole steps on copies of the given state (X, uhat, U as for fsib_step;
+ * the arguments are not modified), one option at a time over the values above.
+ * Synchronous. Not an operation of the paper: a library service. */
+int fsib_autotune(fsib_t h, const double* X, const void* uhat, const double* U);
+
+/* Batches of independent problems (uneven N, d, M), advanced together.
+ * fsib_batch_create makes one member handle per problem (arrays of length
+ * nprob; precision FSIB_FP64 or FSIB_MIXED for all members). Set each member's
+ * force model through fsib_batch_member. fsib_batch_step advances every member
+ * by nsteps steps (as fsib_step) with one CUDA graph launch per step: the graph
+ * holds one branch per member, forked from and joined into the batch stream, so
+ * the members' kernels run concurrently. X, uhat, U: arrays of nprob device
+ * pointers (uhat[i], U[i] may be NULL for Stokes members). fsib_batch_autotune
+ * runs fsib_autotune on every member. Info keys: "nprob", "launches_per_step". */
+typedef struct fsib_batch* fsib_batch_t;
+int fsib_batch_create(fsib_batch_t* out, int nprob, const int* N, const int* d, const int* M,
+                      const double* mu, const double* rho, const double* dt, const double* tol,
+                      int precision);
+int fsib_batch_member(fsib_batch_t b, int i, fsib_t* h);
+int fsib_batch_set_stream(fsib_batch_t b, void* stream);
+int fsib_batch_autotune(fsib_batch_t b, double* const* X, void* const* uhat, double* const* U);
+int fsib_batch_step(fsib_batch_t b, double* const* X, void* const* uhat, double* const* U,
+                    int nsteps);
+int fsib_batch_info(fsib_batch_t b, const char* key, double* value);
+const char* fsib_batch_last_error(fsib_batch_t b);
+int fsib_batch_destroy(fsib_batch_t b);
 
 /* Per-launch-site profiling. When enabled, every call enqueues CUDA events
  * around each kernel launch site on the handle's stream and fsib_step launches

@@ -158,6 +158,8 @@ static int plan_sizes(Plan& p, std::string& err) {
   for (int a = 0; a < p.d; ++a) p.nbins *= p.nbin[a];
   make_fftlen(p.fl_nf, p.nf, 0);
   make_fftlen(p.fl_nt, p.Nt, p.nf);
+  p.fl_nf.tile_p = p.fl_nt.tile_p = p.fft_p;
+  p.fl_nf.rows_q = p.fl_nt.rows_q = p.fft_q;
   return FSIB_OK;
 }
 
@@ -256,6 +258,7 @@ static int dmalloc(P** ptr, size_t bytes, size_t& total) {
 }
 
 static size_t g_ws_bytes = 0;
+static const int kMinSlice = 128;  // smallest spread slice the workspace is sized for
 
 static int alloc_ws(fsib_plan* h) {
   Plan& p = h->p;
@@ -312,7 +315,7 @@ static int alloc_ws(fsib_plan* h) {
   rc |= dmalloc(&ws.box_so, sizeof(int) * (size_t)(p.nbins + 1), tot);
   rc |= dmalloc(&ws.box_po, sizeof(int) * (size_t)(p.nbins + 1), tot);
   // partial slots: boxes with K > 1 hold K slots, K <= 2 cand/256; sum cand <= 27 M
-  ws.part_slots = (d == 3) ? (size_t)(2 * 27 * (long long)p.M / 256 + 64) : 1;
+  ws.part_slots = (d == 3) ? (size_t)(2 * 27 * (long long)p.M / kMinSlice + 64) : 1;
   rc |= dmalloc(&ws.part, sizeof(double) * 3 * 512 * ws.part_slots, tot);
   if (rc != FSIB_OK) { free_ws(ws); h->err = "device allocation failed"; return FSIB_ENOMEM; }
   g_ws_bytes = tot;
@@ -776,6 +779,23 @@ int fsib_set_option(fsib_t h, const char* key, double v) {
   } else if (k == "bin") {
     if (!(v == 0 || (v >= 4 && v <= 64))) return fail(h, FSIB_EINVAL, "bin must be 0 or in [4, 64]");
     q.bin_opt = (int)v;
+  } else if (k == "fft_tile") {
+    if (!(v == 4 || v == 8 || v == 16)) return fail(h, FSIB_EINVAL, "fft_tile must be 4, 8 or 16");
+    h->p.fft_p = (int)v;
+    h->p.fl_nf.tile_p = h->p.fl_nt.tile_p = (int)v;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    return FSIB_OK;
+  } else if (k == "fft_rows") {
+    if (!(v == 2 || v == 4 || v == 8)) return fail(h, FSIB_EINVAL, "fft_rows must be 2, 4 or 8");
+    h->p.fft_q = (int)v;
+    h->p.fl_nf.rows_q = h->p.fl_nt.rows_q = (int)v;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    return FSIB_OK;
+  } else if (k == "spread_slice") {
+    if (!(v >= kMinSlice && v <= 4096)) return fail(h, FSIB_EINVAL, "spread_slice must be in [128, 4096]");
+    h->p.slice = (int)v;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    return FSIB_OK;
   } else if (k == "native_fp64") {
     q.native_fp64 = (v != 0);
   } else if (k == "graph") {
@@ -807,6 +827,9 @@ int fsib_get_info(fsib_t h, const char* key, double* value) {
   else if (k == "bin") *value = p.bins[0];
   else if (k == "sigma") *value = p.sigma;
   else if (k == "native_fp64") *value = p.native_fp64;
+  else if (k == "fft_tile") *value = p.fft_p;
+  else if (k == "fft_rows") *value = p.fft_q;
+  else if (k == "spread_slice") *value = p.slice;
   else if (k == "workspace_bytes") *value = (double)g_ws_bytes;
   else if (k == "launches_per_step") *value = h->graph_kernels;
   else return fail(h, FSIB_EINVAL, "unknown info key: " + k);
@@ -1253,5 +1276,245 @@ int fsib_spread_static(int N, int d, int M, double tol, int precision, const dou
 }
 
 const char* fsib_static_last_error(void) { return g_static_err.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: picks the launch shapes (strided-tile lines, row pairs per CTA, spread
+// slice size) that minimise the measured time of one step, by coordinate descent
+// over the candidate values, timing direct launches on copies of the caller's state.
+// ---------------------------------------------------------------------------
+static int time_steps(fsib_plan* h, double* X, void* u, double* U, const double* X0, const void* u0,
+                      const double* U0, int reps, float* ms_out) {
+  const Plan& p = h->p;
+  const size_t xb = pts_bytes(h), ub = spec_bytes(h);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto one = [&]() {
+    FSIB_DISPATCH(h, (do_step<float, float>(h, X, (C<float>*)u, U, h->own)),
+                  (do_step<dd, double>(h, X, (C<double>*)u, U, h->own)),
+                  (do_step<double, double>(h, X, (C<double>*)u, U, h->own)));
+  };
+  cudaMemcpyAsync(X, X0, xb, cudaMemcpyDeviceToDevice, h->own);
+  if (u0) cudaMemcpyAsync(u, u0, ub, cudaMemcpyDeviceToDevice, h->own);
+  if (U0) cudaMemcpyAsync(U, U0, xb, cudaMemcpyDeviceToDevice, h->own);
+  one();  // warm-up
+  cudaEventRecord(e0, h->own);
+  for (int r = 0; r < reps; ++r) one();
+  cudaEventRecord(e1, h->own);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)p;
+  if (e != cudaSuccess) return FSIB_ECUDA;
+  *ms_out = ms / reps;
+  return FSIB_OK;
+}
+
+extern "C" int fsib_autotune(fsib_t h, const double* X, const void* uhat, const double* U) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!X) return fail(h, FSIB_EINVAL, "X is NULL");
+  if (!h->ws.force_kind) return fail(h, FSIB_ESTATE, "no force model set");
+  const bool ns = !h->p.stokes;
+  if (ns && (!uhat || !U)) return fail(h, FSIB_EINVAL, "Navier-Stokes autotuning needs uhat and U");
+  Arg ax, au, aU;
+  if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 3, uhat, spec_bytes(h), true, au)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, U, pts_bytes(h), true, aU)) != FSIB_OK) return rc;
+  double *tX = nullptr, *tU = nullptr;
+  void* tu = nullptr;
+  size_t tot = 0;
+  rc |= dmalloc(&tX, pts_bytes(h), tot);
+  rc |= dmalloc(&tU, pts_bytes(h), tot);
+  rc |= dmalloc(&tu, spec_bytes(h), tot);
+  if (rc != FSIB_OK) { cudaFree(tX); cudaFree(tU); cudaFree(tu); return fail(h, FSIB_ENOMEM, "autotune allocation"); }
+  struct Knob { const char* key; int vals[3]; };
+  const Knob knobs[3] = {{"fft_tile", {4, 8, 16}}, {"fft_rows", {2, 4, 8}}, {"spread_slice", {128, 256, 512}}};
+  const int nk = (h->p.d == 3) ? 3 : 2;
+  for (int k = 0; k < nk && rc == FSIB_OK; ++k) {
+    double cur = 0;
+    fsib_get_info(h, knobs[k].key, &cur);
+    float best = 1e30f;
+    int bestv = (int)cur;
+    for (int v : knobs[k].vals) {
+      if ((rc = fsib_set_option(h, knobs[k].key, v)) != FSIB_OK) break;
+      float ms = 0;
+      rc = time_steps(h, tX, tu, tU, (const double*)ax.dev, au.dev, (const double*)aU.dev, 3, &ms);
+      if (rc != FSIB_OK) break;
+      if (ms < best) { best = ms; bestv = v; }
+    }
+    if (rc == FSIB_OK) rc = fsib_set_option(h, knobs[k].key, bestv);
+  }
+  cudaStreamSynchronize(h->own);
+  cudaFree(tX);
+  cudaFree(tU);
+  cudaFree(tu);
+  if (rc != FSIB_OK) return fail(h, rc, "autotune failed: " + h->err);
+  return finish(h, true);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of independent problems. Every member is a full handle; one captured CUDA
+// graph advances all of them, with one branch per member (forked from and joined
+// into the batch stream), so the members' kernels run concurrently.
+// ---------------------------------------------------------------------------
+struct fsib_batch {
+  std::vector<fsib_plan*> m;
+  cudaStream_t user = nullptr, own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> gkey;
+  int graph_kernels = 0;
+  std::string err;
+};
+
+static int bfail(fsib_batch* b, int code, const std::string& msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+extern "C" {
+
+int fsib_batch_destroy(fsib_batch* b) {
+  if (!b) return FSIB_OK;
+  if (b->own) cudaStreamSynchronize(b->own);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (auto* h : b->m) fsib_destroy(h);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->own) cudaStreamDestroy(b->own);
+  delete b;
+  return FSIB_OK;
+}
+
+int fsib_batch_create(fsib_batch** out, int nprob, const int* N, const int* d, const int* M, const double* mu,
+                      const double* rho, const double* dt, const double* tol, int precision) {
+  g_create_err.clear();
+  if (!out || nprob < 1 || !N || !d || !M || !mu || !rho || !dt || !tol ||
+      (precision != FSIB_FP64 && precision != FSIB_MIXED)) {
+    g_create_err = "bad batch arguments";
+    return FSIB_EINVAL;
+  }
+  *out = nullptr;
+  fsib_batch* b = new fsib_batch();
+  if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "CUDA stream/event creation failed";
+    fsib_batch_destroy(b);
+    return FSIB_ECUDA;
+  }
+  for (int i = 0; i < nprob; ++i) {
+    fsib_plan* h = nullptr;
+    int rc = fsib_create(&h, N[i], d[i], M[i], mu[i], rho[i], dt[i], tol[i]);
+    if (rc == FSIB_OK && precision == FSIB_MIXED) rc = fsib_set_option(h, "precision", 1);
+    if (rc != FSIB_OK) {
+      g_create_err = "member " + std::to_string(i) + ": " + (h ? h->err : g_create_err);
+      if (h) fsib_destroy(h);
+      fsib_batch_destroy(b);
+      return rc;
+    }
+    b->m.push_back(h);
+    cudaEvent_t e;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    b->join.push_back(e);
+  }
+  *out = b;
+  return FSIB_OK;
+}
+
+int fsib_batch_member(fsib_batch* b, int i, fsib_t* h) {
+  if (!b || !h || i < 0 || i >= (int)b->m.size()) return FSIB_EINVAL;
+  *h = b->m[i];
+  return FSIB_OK;
+}
+
+int fsib_batch_set_stream(fsib_batch* b, void* stream) {
+  if (!b) return FSIB_EINVAL;
+  b->user = (cudaStream_t)stream;
+  return FSIB_OK;
+}
+
+const char* fsib_batch_last_error(fsib_batch* b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+int fsib_batch_info(fsib_batch* b, const char* key, double* value) {
+  if (!b || !key || !value) return FSIB_EINVAL;
+  const std::string k(key);
+  if (k == "nprob") *value = (double)b->m.size();
+  else if (k == "launches_per_step") *value = b->graph_kernels;
+  else return bfail(b, FSIB_EINVAL, "unknown info key: " + k);
+  return FSIB_OK;
+}
+
+int fsib_batch_autotune(fsib_batch* b, double* const* X, void* const* uhat, double* const* U) {
+  if (!b || !X) return FSIB_EINVAL;
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    const int rc = fsib_autotune(b->m[i], X[i], uhat ? uhat[i] : nullptr, U ? U[i] : nullptr);
+    if (rc != FSIB_OK) return bfail(b, rc, "member " + std::to_string(i) + ": " + b->m[i]->err);
+  }
+  if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+  return FSIB_OK;
+}
+
+int fsib_batch_step(fsib_batch* b, double* const* X, void* const* uhat, double* const* U, int nsteps) {
+  if (!b || !X || nsteps < 0) return FSIB_EINVAL;
+  b->err.clear();
+  const size_t n = b->m.size();
+  std::vector<const void*> key;
+  for (size_t i = 0; i < n; ++i) {
+    fsib_plan* h = b->m[i];
+    const bool ns = !h->p.stokes;
+    void* u = uhat ? uhat[i] : nullptr;
+    double* Ui = U ? U[i] : nullptr;
+    if (!X[i] || !is_device_ptr(X[i]) || (u && !is_device_ptr(u)) || (Ui && !is_device_ptr(Ui)))
+      return bfail(b, FSIB_EINVAL, "fsib_batch_step takes device arrays (member " + std::to_string(i) + ")");
+    if (ns && (!u || !Ui)) return bfail(b, FSIB_EINVAL, "Navier-Stokes member needs uhat and U");
+    if (!h->ws.force_kind) return bfail(b, FSIB_ESTATE, "member " + std::to_string(i) + " has no force model");
+    key.push_back(X[i]); key.push_back(u); key.push_back(Ui);
+  }
+  if (cudaEventRecord(b->ev_in, b->user) != cudaSuccess || cudaStreamWaitEvent(b->own, b->ev_in, 0) != cudaSuccess)
+    return bfail(b, FSIB_ECUDA, "stream ordering failed");
+  if (!b->gexec || key != b->gkey) {
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return bfail(b, FSIB_ECUDA, "stream capture failed to start");
+    cudaEventRecord(b->fork, b->own);
+    for (size_t i = 0; i < n; ++i) {
+      fsib_plan* h = b->m[i];
+      cudaStreamWaitEvent(h->own, b->fork, 0);
+      void* u = uhat ? uhat[i] : nullptr;
+      double* Ui = U ? U[i] : nullptr;
+      FSIB_DISPATCH(h, (do_step<float, float>(h, X[i], (C<float>*)u, Ui, h->own)),
+                    (do_step<dd, double>(h, X[i], (C<double>*)u, Ui, h->own)),
+                    (do_step<double, double>(h, X[i], (C<double>*)u, Ui, h->own)));
+      cudaEventRecord(b->join[i], h->own);
+      cudaStreamWaitEvent(b->own, b->join[i], 0);
+    }
+    cudaError_t e = cudaStreamEndCapture(b->own, &g);
+    if (e != cudaSuccess || !g) return bfail(b, FSIB_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    b->graph_kernels = count_kernel_nodes(g);
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->gexec = nullptr; return bfail(b, FSIB_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+    b->gkey = key;
+  }
+  for (int s = 0; s < nsteps; ++s)
+    if (cudaGraphLaunch(b->gexec, b->own) != cudaSuccess) return bfail(b, FSIB_ECUDA, "graph launch failed");
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(b, FSIB_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+  if (cudaEventRecord(b->ev_out, b->own) != cudaSuccess || cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess)
+    return bfail(b, FSIB_ECUDA, "stream ordering failed");
+  return FSIB_OK;
+}
 
 }  // extern "C"

@@ -15,8 +15,8 @@
 
 namespace fsib {
 
-constexpr int kP = 8;        // adjacent lines per strided tile
-constexpr int kQrows = 4;    // row pairs per CTA in the row passes
+// Launch shapes (tunable per plan): fl.tile_p adjacent lines per strided tile,
+// fl.rows_q row pairs per CTA in the row passes.
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------------------
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kThreads)
 k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk,
               FftLen fl, Mult<T> mult, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = fl.n;
+  const int n = fl.n, kP = fl.tile_p;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* a = tw + n;
   C<T>* b = a + n * kP;
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads)
 k_rows_r2c(const void* __restrict__ in_, const unsigned long long* __restrict__ fxmax, int M,
            C<T>* __restrict__ out, long long npairs, int Nk, FftLen fl, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = fl.n, ls = n + 1, h = Nk / 2;
+  const int n = fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* a = tw + n;
   C<T>* b = a + kQrows * ls;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kThreads)
 k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
            FftLen fl, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = fl.n, ls = n + 1, h = Nk / 2;
+  const int n = fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* a = tw + n;
   C<T>* b = a + kQrows * ls;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kThreads)
 k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows,
                int Nk, FftLen fl, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = fl.n, ls = n + 1, h = Nk / 2;
+  const int n = fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
   const int np = d * (d + 1) / 2;
   const long long npairs = nrows / 2;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
@@ -256,6 +256,7 @@ template <typename T, typename Tin, typename Tout>
 void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, int inner, int Nk,
                         const FftLen& fl, bool inverse, Mult<T> mult, const C<T>* tw,
                         cudaStream_t st) {
+  const int kP = fl.tile_p;
   const int ntile = (inner + kP - 1) / kP;
   const long long blocks = (long long)ncomp * outer * ntile;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * fl.n * kP);
@@ -272,6 +273,7 @@ template <typename T>
 void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const FftLen& fl,
                          const C<T>* tw, cudaStream_t st) {
   const long long npairs = nrows / 2;
+  const int kQrows = fl.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
   set_smem(k_rows_r2c<T, false>, smem);
@@ -282,6 +284,7 @@ template <typename T>
 void launch_fft_rows_r2c_fx(const long long* in, const unsigned long long* fxmax, int M, C<T>* out,
                             long long nrows, int Nk, const FftLen& fl, const C<T>* tw, cudaStream_t st) {
   const long long npairs = nrows / 2;
+  const int kQrows = fl.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
   set_smem(k_rows_r2c<T, true>, smem);
@@ -296,6 +299,7 @@ template <typename T>
 void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
                          const C<T>* tw, cudaStream_t st) {
   const long long npairs = nrows / 2;
+  const int kQrows = fl.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
   set_smem(k_rows_c2r<T>, smem);
@@ -306,6 +310,7 @@ template <typename T>
 void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int Nk,
                          const FftLen& fl, const C<T>* tw, cudaStream_t st) {
   const long long npairs = nrows / 2;
+  const int kQrows = fl.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * 6 * (fl.n + 1));
   set_smem(k_rows_product<T>, smem);

@@ -83,6 +83,8 @@ struct FftLen {
   int nstages = 0;
   int radix[kMaxStages] = {0};
   int tw_off = 0;  // offset of exp(-2 pi i j/n), j = 0..n-1, in the twiddle table
+  int tile_p = 8;  // strided passes: adjacent lines per CTA
+  int rows_q = 4;  // row passes: row pairs per CTA
 };
 
 // Multiplier applied at the mode end of a strided pass:
@@ -106,6 +108,8 @@ struct Plan {
   int width_opt = 0, bin_opt = 0;
   int use_graph = 1, check_finite = 0;
   int native_fp64 = 0;  // FP64 mode: 0 = double-float transforms, 1 = native FP64 arithmetic
+  // launch-shape tunables (chosen by fsib_autotune)
+  int fft_p = 8, fft_q = 4, slice = 256;
 
   // derived
   int nf = 0;        // fine grid per axis

@@ -19,12 +19,14 @@ struct PointGeom {
   int d, M, nf, w;
   double L;
   int b[3], nb[3];
+  int slice;  // candidates per slice of a 3D gather box
 };
 
 static PointGeom geom(const Plan& p) {
   PointGeom g;
   g.d = p.d; g.M = p.M; g.nf = p.nf; g.w = p.w; g.L = p.L;
   for (int a = 0; a < 3; ++a) { g.b[a] = p.bins[a]; g.nb[a] = p.nbin[a]; }
+  g.slice = p.slice;
   return g;
 }
 
@@ -868,8 +870,7 @@ __device__ __forceinline__ float acc_norm(float a) { return a; }
 __device__ __forceinline__ dd acc_norm(dd a) { return dd_norm(a); }
 
 // Work list of the 3D gather: box b is split into K_b = max(1, ceil(cand_b / kSliceCand))
-// slices of at most kSliceCand candidates (cand_b = points in its neighbouring bins).
-constexpr int kSliceCand = 256;
+// slices of at most g.slice candidates (cand_b = points in its neighbouring bins).
 
 __device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int Bx, int By, int Bz, int lane,
                                        int* bin) {
@@ -900,7 +901,7 @@ __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restric
   int c = (lane < nnb) ? offsets[bin + 1] - offsets[bin] : 0;
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   if (lane == 0) {
-    const int K = max(1, (c + kSliceCand - 1) / kSliceCand);
+    const int K = max(1, (c + g.slice - 1) / g.slice);
     nslice[warp] = K;
     npart[warp] = (K > 1) ? K : 0;
   }
@@ -959,7 +960,7 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
     __syncthreads();
     const int nr = sNr;
     // this slice takes candidates [ks * kSliceCand, (ks + 1) * kSliceCand) of the concatenated ranges
-    int skip = ks * kSliceCand, take = kSliceCand;
+    int skip = ks * g.slice, take = g.slice;
     for (int ri = 0; ri < nr && take > 0; ++ri) {
       int r0 = sRange[2 * ri], r1 = sRange[2 * ri + 1];
       const int len = r1 - r0;

@@ -26,7 +26,9 @@ EXPORTS = ["fsib_create", "fsib_destroy", "fsib_set_stream", "fsib_set_option", 
            "fsib_set_force_curve", "fsib_set_force_mesh", "fsib_force", "fsib_spread", "fsib_interp",
            "fsib_fluid_step", "fsib_step", "fsib_invariants", "fsib_last_error", "fsib_version",
            "fsib_profile_enable", "fsib_profile_reset", "fsib_profile_count", "fsib_profile_entry",
-           "fsib_measure_peak", "fsib_spread_static", "fsib_static_last_error"]
+           "fsib_measure_peak", "fsib_spread_static", "fsib_static_last_error", "fsib_autotune",
+           "fsib_batch_create", "fsib_batch_member", "fsib_batch_set_stream", "fsib_batch_autotune",
+           "fsib_batch_step", "fsib_batch_info", "fsib_batch_last_error", "fsib_batch_destroy"]
 
 _lib = None
 
@@ -72,6 +74,15 @@ def load(path: str | None = None):
         "fsib_measure_peak": ([i_, dp], i_),
         "fsib_spread_static": ([i_, i_, i_, d_, i_, vp, vp, vp, vp, vp], i_),
         "fsib_static_last_error": ([], ctypes.c_char_p),
+        "fsib_autotune": ([vp, vp, vp, vp], i_),
+        "fsib_batch_create": ([ctypes.POINTER(vp), i_, vp, vp, vp, vp, vp, vp, vp, i_], i_),
+        "fsib_batch_member": ([vp, i_, ctypes.POINTER(vp)], i_),
+        "fsib_batch_set_stream": ([vp, vp], i_),
+        "fsib_batch_autotune": ([vp, vp, vp, vp], i_),
+        "fsib_batch_step": ([vp, vp, vp, vp, i_], i_),
+        "fsib_batch_info": ([vp, ctypes.c_char_p, dp], i_),
+        "fsib_batch_last_error": ([vp], ctypes.c_char_p),
+        "fsib_batch_destroy": ([vp], i_),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -215,6 +226,11 @@ class Problem:
         return dict(zip(keys, list(out)))
 
 
+    def autotune(self, X, uhat=None, U=None):
+        """fsib_autotune: pick launch shapes by timing steps on copies of (X, uhat, U)."""
+        self._call("fsib_autotune", _ptr(X), _ptr(uhat), _ptr(U))
+        return {k: int(self.info(k)) for k in ("fft_tile", "fft_rows", "spread_slice")}
+
     # -- profiling ------------------------------------------------------------------------------
     def profile(self, on=True):
         self._call("fsib_profile_enable", 1 if on else 0)
@@ -246,6 +262,79 @@ def measure_peak(kind):
     if rc != FSIB_OK:
         raise FsibError(rc, "peak measurement failed")
     return v.value
+
+
+class Member(Problem):
+    """A problem owned by a Batch (not destroyed on its own)."""
+
+    def __init__(self, lib, h, N, d, M, mu, rho, dt, tol, precision):
+        self.lib, self.h = lib, h
+        self.N, self.d, self.M = N, d, M
+        self.mu, self.rho, self.dt, self.tol = mu, rho, dt, tol
+        self.precision = precision
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """fsib_batch_*: independent problems advanced by one CUDA graph launch per step."""
+
+    def __init__(self, N, d, M, mu, rho, dt, tol, precision="mixed"):
+        self.lib = load()
+        n = len(N)
+        I = ctypes.c_int * n
+        D = ctypes.c_double * n
+        self._args = (I(*N), I(*d), I(*M), D(*mu), D(*rho), D(*dt), D(*tol))
+        b = ctypes.c_void_p()
+        rc = self.lib.fsib_batch_create(ctypes.byref(b), n, *[ctypes.cast(a, ctypes.c_void_p) for a in self._args],
+                                        FSIB_MIXED if precision == "mixed" else FSIB_FP64)
+        if rc != FSIB_OK:
+            raise FsibError(rc, self.lib.fsib_batch_last_error(None).decode())
+        self.b = b
+        self.members = []
+        for i in range(n):
+            h = ctypes.c_void_p()
+            _check(self.lib, None, self.lib.fsib_batch_member(b, i, ctypes.byref(h)))
+            self.members.append(Member(self.lib, h, N[i], d[i], M[i], mu[i], rho[i], dt[i], tol[i], precision))
+
+    def _ptrs(self, arrs):
+        if arrs is None:
+            return None
+        P = ctypes.c_void_p * len(arrs)
+        return P(*[_ptr(a) for a in arrs])
+
+    def _bcall(self, name, *args):
+        import torch
+        if torch.cuda.is_available():
+            self.lib.fsib_batch_set_stream(self.b, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        rc = getattr(self.lib, name)(self.b, *args)
+        if rc != FSIB_OK:
+            raise FsibError(rc, self.lib.fsib_batch_last_error(self.b).decode())
+
+    def step(self, X, uhat, U, nsteps=1):
+        self._bcall("fsib_batch_step", self._ptrs(X), self._ptrs(uhat), self._ptrs(U), int(nsteps))
+
+    def autotune(self, X, uhat, U):
+        self._bcall("fsib_batch_autotune", self._ptrs(X), self._ptrs(uhat), self._ptrs(U))
+
+    def info(self, key):
+        v = ctypes.c_double()
+        self._bcall("fsib_batch_info", key.encode(), ctypes.byref(v))
+        return v.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            for m in self.members:
+                m.close()
+            self.lib.fsib_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def spread_static(N, d, M, tol, precision, X, F, omega, fhat, stream=None):

@@ -1,0 +1,102 @@
+"""Batched problems (one graph launch advances every member) and the autotuner."""
+import numpy as np
+import pytest
+
+from oracle import spectral as sp
+from oracle import stepper as st
+from paper_2302_08694_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def rel2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def small_problems():
+    probs = []
+    for i, (d, N, M) in enumerate([(2, 16, 64), (3, 12, 0), (2, 24, 150), (3, 16, 0), (2, 32, 33)]):
+        if d == 2:
+            X0 = wl.ellipse(M, 0.25 + 0.01 * i, 0.18, (0.4 + 0.03 * i, 0.55))
+            probs.append(dict(d=2, N=N, M=M, X0=X0, force="curve"))
+        else:
+            Xref, tri = wl.latlong_sphere(4 + i, 8 + 2 * i, 0.25, (0.5, 0.48, 0.51))
+            X0 = 0.5 + (Xref - 0.5) * np.array([[1.1], [0.93], [1.0]])
+            probs.append(dict(d=3, N=N, M=X0.shape[1], X0=X0, force="mesh", Xref=Xref, tri=tri))
+    return probs
+
+
+def setup(pb, p, torch):
+    if p["force"] == "curve":
+        pb.set_force_curve(1.0)
+    else:
+        pb.set_force_mesh(p["tri"], torch.from_numpy(p["Xref"]).cuda(), 1.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_matches_individual_handles(lib, torch_mod, prec):
+    torch = torch_mod
+    probs = small_problems()
+    n = len(probs)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    B = lib.Batch([p["N"] for p in probs], [p["d"] for p in probs], [p["M"] for p in probs],
+                  [0.02] * n, [1.0] * n, [2e-3] * n, [tol] * n, precision=prec)
+    Xb, ub, Ub, singles = [], [], [], []
+    for p, m in zip(probs, B.members):
+        setup(m, p, torch)
+        X = torch.from_numpy(p["X0"].copy()).cuda()
+        Xb.append(X)
+        ub.append(m.new_spec())
+        Ub.append(torch.zeros_like(X))
+        s = lib.Problem(p["N"], p["d"], p["M"], 0.02, 1.0, 2e-3, tol, precision=prec)
+        setup(s, p, torch)
+        singles.append((s, X.clone(), s.new_spec(), torch.zeros_like(X)))
+    B.step(Xb, ub, Ub, nsteps=3)
+    for s, X, u, U in singles:
+        s.step(X, u, U, nsteps=3)
+    torch.cuda.synchronize()
+    assert B.info("launches_per_step") > 30 * n
+    t = 1e-12 if prec == "fp64" else 1e-5
+    for i, (p, (s, X, u, U)) in enumerate(zip(probs, singles)):
+        x0 = p["X0"]
+        assert rel2(Xb[i].cpu().numpy() - x0, X.cpu().numpy() - x0) <= t, i
+        assert rel2(ub[i].cpu().numpy(), u.cpu().numpy()) <= t, i
+    # and one member against the oracle
+    p = probs[0]
+    force = st.curve_model(1.0)
+    X, u, U = p["X0"].copy(), np.zeros((2, p["N"], p["N"]), complex), np.zeros_like(p["X0"])
+    for _ in range(3):
+        X, u, U = st.ns_step(X, u, U, force, p["N"], 0.02, 1.0, 2e-3)
+    assert rel2(Xb[0].cpu().numpy() - p["X0"], X - p["X0"]) <= (1e-10 if prec == "fp64" else 1e-4)
+    B.close()
+
+
+def test_autotune_keeps_results(lib, torch_mod):
+    torch = torch_mod
+    Xref, tri = wl.latlong_sphere(10, 20, 0.25, (0.5, 0.5, 0.5))
+    X0 = 0.5 + (Xref - 0.5) * np.array([[1.1], [0.95], [1.0]])
+    M = X0.shape[1]
+    res = []
+    for tune in (False, True):
+        pb = lib.Problem(24, 3, M, 0.01, 1.0, 1e-3, 1e-12)
+        pb.set_force_mesh(tri, Xref, 1.0)
+        X = torch.from_numpy(X0.copy()).cuda()
+        u = pb.new_spec()
+        U = torch.zeros_like(X)
+        if tune:
+            choice = pb.autotune(X, u, U)
+            assert choice["fft_tile"] in (4, 8, 16) and choice["fft_rows"] in (2, 4, 8)
+            assert np.array_equal(X.cpu().numpy(), X0)  # autotune does not touch the state
+        pb.step(X, u, U, nsteps=2)
+        torch.cuda.synchronize()
+        res.append((X.cpu().numpy(), u.cpu().numpy()))
+    assert rel2(res[1][0] - X0, res[0][0] - X0) <= 1e-12
+    assert rel2(res[1][1], res[0][1]) <= 1e-12
