@@ -145,6 +145,25 @@ int fsib_fluid_step(fsib_t h, const void* fhat, void* uhat, void* uhat_half);
  * Needs a force model. */
 int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps);
 
+/* Velocity gradient at the points: G[b][a][j] = d u_a/d x_b (X_j) for the field of
+ * uhat (half spectrum), i.e. the type-2 sums of i k_b u-hat_a (Eq. velo_intp_fini
+ * applied to the gradient). X: [d][M]; G: [d][d][M] double. */
+int fsib_interp_grad(fsib_t h, const void* uhat, const double* X, double* G);
+
+/* Reverse mode of K quasi-static Stokes steps (rho <= 0 handles only).
+ * Given X0 ([d][M]) and dL/dX^K ([d][M]) for the state after K steps of fsib_step,
+ * writes dL/dX^0 ([d][M]) and dL/dsigma (one double), sigma being the stiffness of
+ * the force model (K of the curve, sigma of the mesh; the force is linear in it).
+ * The velocity U(X) = interp(Stokeslet(spread(X, c(X))), X) has the transpose
+ * Jacobian J^T lam = (grad u)^T lam + (grad w)^T c + c(w), where w is the velocity
+ * of lam used as forces (spread and interp are adjoint, Sec. 4.4) and c(.) the
+ * (linear, symmetric) force law; a step X1 = X + dt U(X + dt/2 U(X)) is reversed as
+ * a = dt J(X_half)^T lam1, lam0 = lam1 + a + dt/2 J(X)^T a. Forward states are kept
+ * every ckpt_every steps and recomputed segment by segment. Allocates its
+ * checkpoint buffers on first use. */
+int fsib_step_adjoint(fsib_t h, const double* X0, int K, int ckpt_every, const double* dLdXK,
+                      double* dLdX0, double* dLdsigma);
+
 /* Diagnostics in double, synchronous (Sec. 4). out[0] enclosed volume (d = 3,
  * needs the mesh) or area (d = 2, curve order), out[1] elastic energy E_p,
  * out[2] kinetic energy E_K = rho/2 L^d sum |u-hat|^2 (rho = 1 for Stokes),

@@ -233,6 +233,11 @@ static void free_ws(Workspace& ws) {
   ws.wts = ws.cwp = nullptr;
   ws.box_ns = ws.box_np = ws.box_so = ws.box_po = nullptr;
   ws.part = nullptr;
+  void* adj[] = {ws.adj_spec, ws.adj_pts, ws.adj_ckpt, ws.adj_part, ws.adj_sig};
+  for (void* q : adj)
+    if (q) cudaFree(q);
+  ws.adj_spec = nullptr; ws.adj_pts = ws.adj_ckpt = ws.adj_part = ws.adj_sig = nullptr;
+  ws.adj_ckpt_bytes = 0;
   for (int i = 0; i < 4; ++i) {
     if (ws.stage[i]) cudaFree(ws.stage[i]);
     ws.stage[i] = nullptr; ws.stage_bytes[i] = 0;
@@ -842,6 +847,7 @@ int fsib_set_force_curve(fsib_t h, double K) {
   if (!std::isfinite(K)) return fail(h, FSIB_EINVAL, "K must be finite");
   h->ws.force_kind = 1;
   h->ws.curve_K = K;
+  h->ws.stiffness = K;
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   return FSIB_OK;
 }
@@ -895,6 +901,7 @@ int fsib_set_force_mesh(fsib_t h, const int* tri, int ntri, const double* Xref, 
   launch_mesh_stiffness((const double*)xr.dev, ws.tri, ntri, M, sigma, ws.csr_ptr, ws.csr_col, ws.csr_k,
                         ws.nnz, h->own);
   ws.force_kind = 2;
+  ws.stiffness = sigma;
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   return finish(h, true);
 }
@@ -1515,6 +1522,183 @@ int fsib_batch_step(fsib_batch* b, double* const* X, void* const* uhat, double* 
   if (cudaEventRecord(b->ev_out, b->own) != cudaSuccess || cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess)
     return bfail(b, FSIB_ECUDA, "stream ordering failed");
   return FSIB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Reverse mode of the quasi-static Stokes stepper (see include/fsib.h):
+//   velocity VJP:  J^T lam = (grad u)^T lam + (grad w)^T c + c(w),  d/dsigma: sum w.c / sigma,
+//   where u is the flow of the forces c(X) and w the flow of lam used as forces;
+//   step VJP for X1 = X + dt U(X + dt/2 U(X)):  a = dt J(X_half)^T lam1,
+//   lam0 = lam1 + a + dt/2 J(X)^T a.
+// The forward states are recomputed from checkpoints, one segment at a time.
+// ---------------------------------------------------------------------------
+static int ensure_adjoint(fsib_plan* h, int K, int ckpt) {
+  Workspace& ws = h->ws;
+  const Plan& p = h->p;
+  const size_t dm = (size_t)p.d * p.M;
+  size_t tot = 0;
+  int rc = FSIB_OK;
+  if (!ws.adj_spec) rc |= dmalloc(&ws.adj_spec, 3 * ws.spec_bytes, tot);
+  if (!ws.adj_pts) rc |= dmalloc(&ws.adj_pts, sizeof(double) * (2 * (size_t)p.d * dm + 10 * dm), tot);
+  if (!ws.adj_part) rc |= dmalloc(&ws.adj_part, sizeof(double) * 2 * 152 * 4, tot);
+  if (!ws.adj_sig) rc |= dmalloc(&ws.adj_sig, sizeof(double) * 2, tot);
+  const int nck = (K + ckpt - 1) / ckpt;
+  const size_t need = sizeof(double) * dm * (size_t)(nck + ckpt + 1);
+  if (ws.adj_ckpt_bytes < need) {
+    if (ws.adj_ckpt) cudaFree(ws.adj_ckpt);
+    ws.adj_ckpt = nullptr;
+    ws.adj_ckpt_bytes = 0;
+    rc |= dmalloc(&ws.adj_ckpt, need, tot);
+    if (rc == FSIB_OK) ws.adj_ckpt_bytes = need;
+  }
+  return rc == FSIB_OK ? FSIB_OK : FSIB_ENOMEM;
+}
+
+struct AdjBufs {
+  double *Gu, *Gw, *w, *fw, *c, *a, *Uxm, *Xh;
+};
+static AdjBufs adj_bufs(fsib_plan* h) {
+  const size_t dm = (size_t)h->p.d * h->p.M;
+  double* b = h->ws.adj_pts;
+  AdjBufs r;
+  r.Gu = b; b += (size_t)h->p.d * dm;
+  r.Gw = b; b += (size_t)h->p.d * dm;
+  r.w = b; b += dm;
+  r.fw = b; b += dm;
+  r.c = b; b += dm;
+  r.a = b; b += dm;
+  r.Uxm = b; b += dm;
+  r.Xh = b;
+  return r;
+}
+
+// G[b][a][j] = d u_a / d x_b at the points of the last binning.
+template <typename TI, typename TA>
+static void do_interp_grad(fsib_plan* h, const C<TA>* u, double* G, cudaStream_t st) {
+  const Plan& p = h->p;
+  C<TA>* tmp = (C<TA>*)((char*)h->ws.adj_spec + 2 * h->ws.spec_bytes);
+  for (int b = 0; b < p.d; ++b) {
+    { Prof pr(h, "mul_ik", 2.0 * (double)h->ws.spec_bytes, 0.0, st);
+      launch_mul_ik<TA>(p, b, u, tmp, st); }
+    do_interp_sorted<TI, TA>(h, tmp, G + (size_t)b * p.d * p.M, st);
+  }
+}
+
+// gX += s J(X)^T lam; sigma accumulator += s lam . dU/dsigma
+template <typename TI, typename TA>
+static void do_vjp(fsib_plan* h, const double* X, const double* lam, double s, double* gX, cudaStream_t st) {
+  const Plan& p = h->p;
+  Workspace& ws = h->ws;
+  AdjBufs B = adj_bufs(h);
+  C<TA>* uA = (C<TA>*)ws.adj_spec;
+  C<TA>* wB = (C<TA>*)((char*)ws.adj_spec + ws.spec_bytes);
+  C<TA>* fhat = (C<TA>*)ws.fhat;
+  do_force(h, X, B.c, st);
+  do_spread<TI, TA>(h, X, B.c, nullptr, fhat, st);
+  do_stokeslet<TA>(h, fhat, uA, st);
+  do_interp_grad<TI, TA>(h, uA, B.Gu, st);
+  do_spread<TI, TA>(h, X, lam, nullptr, fhat, st);
+  do_stokeslet<TA>(h, fhat, wB, st);
+  do_interp_sorted<TI, TA>(h, wB, B.w, st);
+  do_interp_grad<TI, TA>(h, wB, B.Gw, st);
+  do_force(h, B.w, B.fw, st);
+  Prof pr(h, "vjp_combine", 8.0 * p.M * (2.0 * p.d * p.d + 6.0 * p.d), 0.0, st);
+  launch_vjp_combine(p.d, p.M, s, ws.stiffness, B.Gu, B.Gw, lam, B.c, B.fw, B.w, gX, ws.adj_part, 2 * 152, ws.adj_sig, st);
+}
+
+// lam <- reverse of one midpoint Stokes step taken from X
+template <typename TI, typename TA>
+static void do_step_vjp(fsib_plan* h, const double* X, double* lam, cudaStream_t st) {
+  const Plan& p = h->p;
+  AdjBufs B = adj_bufs(h);
+  const long long dm = (long long)p.d * p.M;
+  C<TA>* uA = (C<TA>*)h->ws.adj_spec;
+  // recompute X_half = X + dt/2 U(X)
+  do_force(h, X, B.c, st);
+  do_spread<TI, TA>(h, X, B.c, nullptr, (C<TA>*)h->ws.fhat, st);
+  do_stokeslet<TA>(h, (C<TA>*)h->ws.fhat, uA, st);
+  do_interp_sorted<TI, TA>(h, uA, B.Uxm, st);
+  do_axpy(h, B.Xh, X, B.Uxm, 0.5 * p.dt, st);
+  cudaMemsetAsync(B.a, 0, sizeof(double) * dm, st);
+  do_vjp<TI, TA>(h, B.Xh, lam, p.dt, B.a, st);          // a = dt J(X_half)^T lam
+  do_axpy(h, lam, lam, B.a, 1.0, st);                   // lam += a
+  do_vjp<TI, TA>(h, X, B.a, 0.5 * p.dt, lam, st);       // lam += dt/2 J(X)^T a
+}
+
+template <typename TI, typename TA>
+static void do_adjoint(fsib_plan* h, const double* X0, int K, int ckpt, const double* dLdXK, double* dLdX0,
+                       double* dLdsig, cudaStream_t st) {
+  const Plan& p = h->p;
+  const size_t dm = (size_t)p.d * p.M;
+  const int nck = (K + ckpt - 1) / ckpt;
+  double* ck = h->ws.adj_ckpt;                   // nck checkpoints
+  double* seg = ck + (size_t)nck * dm;           // ckpt segment states
+  double* Xw = seg + (size_t)ckpt * dm;          // working state (reuses the last segment slot region)
+  (void)Xw;
+  // forward sweep, keeping X at steps 0, ckpt, 2 ckpt, ...
+  cudaMemcpyAsync(seg, X0, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
+  for (int m = 0; m < K; ++m) {
+    if (m % ckpt == 0) cudaMemcpyAsync(ck + (size_t)(m / ckpt) * dm, seg, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
+    do_step<TI, TA>(h, seg, nullptr, nullptr, st);
+  }
+  // reverse sweep
+  cudaMemcpyAsync(dLdX0, dLdXK, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(h->ws.adj_sig, 0, sizeof(double), st);
+  for (int s = nck - 1; s >= 0; --s) {
+    const int start = s * ckpt, len = std::min(ckpt, K - start);
+    cudaMemcpyAsync(seg, ck + (size_t)s * dm, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
+    for (int i = 1; i < len; ++i) {
+      cudaMemcpyAsync(seg + (size_t)i * dm, seg + (size_t)(i - 1) * dm, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
+      do_step<TI, TA>(h, seg + (size_t)i * dm, nullptr, nullptr, st);
+    }
+    for (int i = len - 1; i >= 0; --i) do_step_vjp<TI, TA>(h, seg + (size_t)i * dm, dLdX0, st);
+  }
+  cudaMemcpyAsync(dLdsig, h->ws.adj_sig, sizeof(double), cudaMemcpyDeviceToDevice, st);
+}
+
+extern "C" {
+
+int fsib_interp_grad(fsib_t h, const void* uhat, const double* X, double* G) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!uhat || !X || !G) return fail(h, FSIB_EINVAL, "NULL array");
+  if ((rc = ensure_adjoint(h, 1, 1)) != FSIB_OK) return fail(h, rc, "adjoint workspace allocation failed");
+  Arg ax, au, ag;
+  if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 3, uhat, spec_bytes(h), true, au)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, G, pts_bytes(h) * h->p.d, false, ag)) != FSIB_OK) return rc;
+  do_bin(h, (const double*)ax.dev, h->own);
+  FSIB_DISPATCH(h, (do_interp_grad<float, float>(h, (const C<float>*)au.dev, (double*)ag.dev, h->own)),
+                (do_interp_grad<dd, double>(h, (const C<double>*)au.dev, (double*)ag.dev, h->own)),
+                (do_interp_grad<double, double>(h, (const C<double>*)au.dev, (double*)ag.dev, h->own)));
+  if ((rc = unstage(h, ag)) != FSIB_OK) return rc;
+  return finish(h, ag.host != nullptr);
+}
+
+int fsib_step_adjoint(fsib_t h, const double* X0, int K, int ckpt_every, const double* dLdXK, double* dLdX0,
+                      double* dLdsigma) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!X0 || !dLdXK || !dLdX0 || !dLdsigma) return fail(h, FSIB_EINVAL, "NULL array");
+  if (!h->p.stokes) return fail(h, FSIB_EUNSUPPORTED, "the adjoint covers the quasi-static Stokes stepper");
+  if (!h->ws.force_kind) return fail(h, FSIB_ESTATE, "no force model set");
+  if (K < 1 || ckpt_every < 1) return fail(h, FSIB_EINVAL, "K and ckpt_every must be >= 1");
+  if (ckpt_every > K) ckpt_every = K;
+  if ((rc = ensure_adjoint(h, K, ckpt_every)) != FSIB_OK) return fail(h, rc, "adjoint workspace allocation failed");
+  Arg ax, al, ag, as;
+  if ((rc = stage(h, 0, X0, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, dLdXK, pts_bytes(h), true, al)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 2, dLdX0, pts_bytes(h), false, ag)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 3, dLdsigma, sizeof(double), false, as)) != FSIB_OK) return rc;
+  FSIB_DISPATCH(h,
+    (do_adjoint<float, float>(h, (const double*)ax.dev, K, ckpt_every, (const double*)al.dev, (double*)ag.dev, (double*)as.dev, h->own)),
+    (do_adjoint<dd, double>(h, (const double*)ax.dev, K, ckpt_every, (const double*)al.dev, (double*)ag.dev, (double*)as.dev, h->own)),
+    (do_adjoint<double, double>(h, (const double*)ax.dev, K, ckpt_every, (const double*)al.dev, (double*)ag.dev, (double*)as.dev, h->own)));
+  if ((rc = unstage(h, ag)) != FSIB_OK) return rc;
+  if ((rc = unstage(h, as)) != FSIB_OK) return rc;
+  return finish(h, ag.host != nullptr || as.host != nullptr);
 }
 
 }  // extern "C"

@@ -101,6 +101,21 @@ __global__ void k_ns_update(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool 
   }
 }
 
+// out_a = i k_b in_a on the half spectrum (the unpaired mode -N/2 set to zero)
+template <typename T>
+__global__ void k_mul_ik(SpecGeom g, int b, const C<T>* __restrict__ in, C<T>* __restrict__ out) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
+       idx += (long long)gridDim.x * blockDim.x) {
+    T k[3];
+    const bool ok = decode_mode<T>(g, idx, k);
+    for (int a = 0; a < g.d; ++a) {
+      C<T> v = mk<T>(T(0), T(0));
+      if (ok) v = cmul_i<T>(cscale<T>(in[a * g.nspec + idx], k[b]));
+      out[a * g.nspec + idx] = v;
+    }
+  }
+}
+
 static unsigned grid_for(long long n) {
   long long b = (n + 255) / 256;
   if (b > 65535LL * 8) b = 65535LL * 8;
@@ -121,6 +136,14 @@ void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C
   k_ns_update<T><<<grid_for(g.nspec), 256, 0, st>>>(g, (T)(1.0 / p.rho), (T)(p.mu * p.dt / p.rho),
                                                      (T)p.dt, half, prod, fhat, ubase, out);
 }
+
+template <typename T>
+void launch_mul_ik(const Plan& p, int b, const C<T>* in, C<T>* out, cudaStream_t st) {
+  const SpecGeom g = sgeom(p);
+  k_mul_ik<T><<<grid_for(g.nspec), 256, 0, st>>>(g, b, in, out);
+}
+template void launch_mul_ik<float>(const Plan&, int, const C<float>*, C<float>*, cudaStream_t);
+template void launch_mul_ik<double>(const Plan&, int, const C<double>*, C<double>*, cudaStream_t);
 
 template void launch_stokeslet<float>(const Plan&, const C<float>*, C<float>*, cudaStream_t);
 template void launch_stokeslet<double>(const Plan&, const C<double>*, C<double>*, cudaStream_t);

@@ -150,6 +150,7 @@ struct Workspace {
   // force models
   int force_kind = 0;         // 0 none, 1 curve, 2 mesh
   double curve_K = 0.0;
+  double stiffness = 1.0;     // K (curve) or sigma (mesh): the force is linear in it
   int* csr_ptr = nullptr; int* csr_col = nullptr; double* csr_k = nullptr; int nnz = 0;
   int* tri = nullptr; int ntri = 0;
   // reductions
@@ -165,6 +166,13 @@ struct Workspace {
   int* box_po = nullptr;             // [nbins + 1] partial-slot offsets
   void* part = nullptr;              // T[slots][3][512] partial boxes
   size_t part_slots = 0;
+  // reverse mode (allocated on first use)
+  void* adj_spec = nullptr;          // 3 spectra: u-hat, w-hat, i k_b * spectrum
+  double* adj_pts = nullptr;         // point buffers: Gu, Gw (d*d*M each), w, fw, c, a, lam, tmp (d*M each)
+  double* adj_ckpt = nullptr;        // checkpoints and segment positions
+  size_t adj_ckpt_bytes = 0;
+  double* adj_part = nullptr;        // sigma partial sums
+  double* adj_sig = nullptr;         // sigma gradient accumulator
   // staging for host pointers
   void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t stage_bytes[4] = {0, 0, 0, 0};
@@ -226,6 +234,12 @@ void launch_mesh_stiffness(const double* Xref, const int* tri, int ntri, int M, 
 template <typename T>
 int run_invariants(const Plan& p, Workspace& ws, const double* X, const C<T>* uhat,
                    double* out, cudaStream_t st);
+
+template <typename T>
+void launch_mul_ik(const Plan& p, int b, const C<T>* in, C<T>* out, cudaStream_t st);
+void launch_vjp_combine(int d, int M, double s, double sigma, const double* Gu, const double* Gw,
+                        const double* lam, const double* c, const double* fw, const double* w, double* gX,
+                        double* part, int nblk, double* gsig, cudaStream_t st);
 
 int check_last(const char* where);
 void raise_smem_limit(const void* kernel);

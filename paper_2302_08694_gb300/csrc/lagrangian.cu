@@ -112,6 +112,54 @@ void launch_mesh_stiffness(const double* Xref, const int* tri, int ntri, int M, 
 }
 
 // ---------------------------------------------------------------------------
+// Reverse mode of one velocity evaluation (quasi-static Stokes):
+//   gX_b += s (sum_a Gu[b][a] lam_a + sum_a Gw[b][a] c_a + fw_b),  gsig += s sum_a w_a c_a / sigma
+// with Gu = grad u, Gw = grad w at the points ([d][d][M]), fw = spring law applied to w.
+// The sigma term goes to per-block partial sums, added in block order by k_vjp_sigma.
+// ---------------------------------------------------------------------------
+constexpr int kVjpThreads = 256;
+__global__ void __launch_bounds__(kVjpThreads)
+k_vjp_combine(int d, int M, double s, double inv_sigma, const double* __restrict__ Gu, const double* __restrict__ Gw,
+              const double* __restrict__ lam, const double* __restrict__ c, const double* __restrict__ fw,
+              const double* __restrict__ w, double* __restrict__ gX, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    for (int b = 0; b < d; ++b) {
+      double v = fw[(long long)b * M + j];
+      for (int a = 0; a < d; ++a) {
+        const long long gi = ((long long)b * d + a) * M + j;
+        v += Gu[gi] * lam[(long long)a * M + j] + Gw[gi] * c[(long long)a * M + j];
+      }
+      gX[(long long)b * M + j] += s * v;
+    }
+    for (int a = 0; a < d; ++a) acc += w[(long long)a * M + j] * c[(long long)a * M + j];
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += sh[i];
+    part[blockIdx.x] = s * inv_sigma * t;
+  }
+}
+
+__global__ void k_vjp_sigma(const double* __restrict__ part, int nblk, double* __restrict__ gsig) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < nblk; ++i) t += part[i];
+  *gsig += t;
+}
+
+void launch_vjp_combine(int d, int M, double s, double sigma, const double* Gu, const double* Gw,
+                        const double* lam, const double* c, const double* fw, const double* w, double* gX,
+                        double* part, int nblk, double* gsig, cudaStream_t st) {
+  k_vjp_combine<<<nblk, kVjpThreads, 0, st>>>(d, M, s, 1.0 / sigma, Gu, Gw, lam, c, fw, w, gX, part);
+  k_vjp_sigma<<<1, 32, 0, st>>>(part, nblk, gsig);
+}
+
+// ---------------------------------------------------------------------------
 // Invariants: per-block partial sums, then one block adds the partials in a fixed
 // order (deterministic).
 // Slots: 0 volume/area, 1 E_p, 2 sum |u|^2 (full spectrum), 3..5 u(0) components (real parts),

@@ -28,7 +28,8 @@ EXPORTS = ["fsib_create", "fsib_destroy", "fsib_set_stream", "fsib_set_option", 
            "fsib_profile_enable", "fsib_profile_reset", "fsib_profile_count", "fsib_profile_entry",
            "fsib_measure_peak", "fsib_spread_static", "fsib_static_last_error", "fsib_autotune",
            "fsib_batch_create", "fsib_batch_member", "fsib_batch_set_stream", "fsib_batch_autotune",
-           "fsib_batch_step", "fsib_batch_info", "fsib_batch_last_error", "fsib_batch_destroy"]
+           "fsib_batch_step", "fsib_batch_info", "fsib_batch_last_error", "fsib_batch_destroy",
+           "fsib_interp_grad", "fsib_step_adjoint"]
 
 _lib = None
 
@@ -83,6 +84,8 @@ def load(path: str | None = None):
         "fsib_batch_info": ([vp, ctypes.c_char_p, dp], i_),
         "fsib_batch_last_error": ([vp], ctypes.c_char_p),
         "fsib_batch_destroy": ([vp], i_),
+        "fsib_interp_grad": ([vp, vp, vp, vp], i_),
+        "fsib_step_adjoint": ([vp, vp, i_, i_, vp, vp, vp], i_),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -226,6 +229,25 @@ class Problem:
         return dict(zip(keys, list(out)))
 
 
+    def interp_grad(self, uhat, X, out=None):
+        """G[b, a, j] = d u_a / d x_b at X_j."""
+        import torch
+        if out is None:
+            shape = (self.d, self.d, self.M)
+            out = torch.empty(shape, dtype=torch.float64, device=X.device) if hasattr(X, "device") \
+                else np.empty(shape)
+        self._call("fsib_interp_grad", _ptr(uhat), _ptr(X), _ptr(out))
+        return out
+
+    def step_adjoint(self, X0, K, ckpt_every, dLdXK, dLdX0=None):
+        """(dL/dX0, dL/dsigma) of K quasi-static Stokes steps from X0."""
+        import torch
+        if dLdX0 is None:
+            dLdX0 = torch.empty_like(X0) if hasattr(X0, "data_ptr") else np.empty_like(X0)
+        gs = torch.zeros(1, dtype=torch.float64, device=X0.device) if hasattr(X0, "device") else np.zeros(1)
+        self._call("fsib_step_adjoint", _ptr(X0), int(K), int(ckpt_every), _ptr(dLdXK), _ptr(dLdX0), _ptr(gs))
+        return dLdX0, gs
+
     def autotune(self, X, uhat=None, U=None):
         """fsib_autotune: pick launch shapes by timing steps on copies of (X, uhat, U)."""
         self._call("fsib_autotune", _ptr(X), _ptr(uhat), _ptr(U))
@@ -335,6 +357,43 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _rollout_function():
+    import torch
+
+    class StokesRollout(torch.autograd.Function):
+        """X^K = (K quasi-static Stokes steps)(X^0; sigma) with a hand-written adjoint.
+
+        forward: sets the mesh (or curve) force with stiffness sigma and runs fsib_step K
+        times; backward: fsib_step_adjoint with checkpoints every ckpt_every steps."""
+
+        @staticmethod
+        def forward(ctx, X0, sigma, pb, K, ckpt_every, tri=None, Xref=None):
+            s = float(sigma.detach().cpu().item())
+            if tri is not None:
+                pb.set_force_mesh(tri, Xref, s)
+            else:
+                pb.set_force_curve(s)
+            X = X0.detach().clone().contiguous()
+            pb.step(X, nsteps=int(K))
+            ctx.pb, ctx.K, ctx.ck = pb, int(K), int(ckpt_every)
+            ctx.sig_dev, ctx.sig_dtype = sigma.device, sigma.dtype
+            ctx.save_for_backward(X0.detach().clone())
+            return X
+
+        @staticmethod
+        def backward(ctx, gX):
+            (X0,) = ctx.saved_tensors
+            g0, gs = ctx.pb.step_adjoint(X0, ctx.K, ctx.ck, gX.detach().contiguous())
+            return g0, gs.reshape(()).to(device=ctx.sig_dev, dtype=ctx.sig_dtype), None, None, None, None, None
+
+    return StokesRollout
+
+
+def stokes_rollout(X0, sigma, pb, K, ckpt_every, tri=None, Xref=None):
+    """Differentiable K-step quasi-static Stokes rollout (torch.autograd.Function)."""
+    return _rollout_function().apply(X0, sigma, pb, K, ckpt_every, tri, Xref)
 
 
 def spread_static(N, d, M, tol, precision, X, F, omega, fhat, stream=None):
