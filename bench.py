@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--native-fp64", action="store_true", help="FP64 arithmetic instead of double-float")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-mixed workload block")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload block")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable workload block")
     return ap.parse_args()
 
 
@@ -357,6 +358,72 @@ def batched_block(fsib, torch, dev, flush, steps, warmup):
     return out
 
 
+def adjoint_block(fsib, torch, dev, reps=2):
+    """Differentiable 3D Stokes (N = 96^3, M = 20002, K = 50, checkpoints every 10): gradient of
+    sum_j (|X_j^K - c| - R)^2 w.r.t. X^0 and sigma by the FP32-mixed adjoint, checked against
+    central finite differences of the FP64 forward on random directions."""
+    prob = wl.config_stokes3d_adjoint()
+    K, ck = prob.nsteps, prob.extra["ckpt_every"]
+    R = prob.extra["target_radius"]
+    center = torch.from_numpy(prob.X0.mean(axis=1)).to(dev)[:, None]
+    pm = make_problem(fsib, prob, "mixed")
+    p64 = make_problem(fsib, prob, "fp64")
+    X0 = torch.from_numpy(prob.X0.copy()).to(dev)
+    sigma0 = prob.stiffness
+
+    def loss_grad(pb, x0, sig):
+        pb.set_force_mesh(prob.tri, prob.Xref, sig)
+        X = x0.clone()
+        pb.step(X, nsteps=K)
+        r = torch.sqrt(((X - center) ** 2).sum(0))
+        e = r - R
+        return float((e * e).sum()), (2 * e / r)[None, :] * (X - center)
+
+    L, dLdXK = loss_grad(pm, X0, sigma0)  # warm-up: first-call set-up (graph capture, buffers)
+    g0, gs = pm.step_adjoint(X0, K, ck, dLdXK)
+    torch.cuda.synchronize()
+    t_fwd = t_adj = 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        X = X0.clone()
+        pm.step(X, nsteps=K)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        g0, gs = pm.step_adjoint(X0, K, ck, dLdXK)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        t_fwd += (t1 - t0) / reps
+        t_adj += (t2 - t1) / reps
+    t_mixed = t_fwd + t_adj
+    _, dL64 = loss_grad(p64, X0, sigma0)
+    g64, gs64 = p64.step_adjoint(X0, K, ck, dL64)
+    rng = np.random.default_rng(55)
+    checks = []
+    eps = 1e-6
+    for _ in range(2):
+        v = torch.from_numpy(rng.standard_normal(prob.X0.shape)).to(dev)
+        lp, _ = loss_grad(p64, X0 + eps * v, sigma0)
+        lm, _ = loss_grad(p64, X0 - eps * v, sigma0)
+        fd = (lp - lm) / (2 * eps)
+        checks.append({"fd": fd, "adjoint_mixed": float((g0 * v).sum()), "adjoint_fp64": float((g64 * v).sum())})
+    lp, _ = loss_grad(p64, X0, sigma0 + eps)
+    lm, _ = loss_grad(p64, X0, sigma0 - eps)
+    fds = (lp - lm) / (2 * eps)
+    rel = lambda a, b: abs(a - b) / max(abs(b), 1e-300)
+    out = {"workload": prob.name, "K": K, "ckpt_every": ck, "loss": L,
+           "seconds_forward_plus_adjoint_mixed": t_mixed, "seconds_forward": t_fwd,
+           "seconds_adjoint": t_adj,
+           "steps_per_s_forward_plus_adjoint": K / t_mixed,
+           "grad_check_fd_fp64": {
+               "x0_rel_err_mixed": max(rel(c["adjoint_mixed"], c["fd"]) for c in checks),
+               "x0_rel_err_fp64": max(rel(c["adjoint_fp64"], c["fd"]) for c in checks),
+               "sigma_rel_err_mixed": rel(float(gs.cpu()), fds), "sigma_rel_err_fp64": rel(float(gs64.cpu()), fds),
+               "directions": len(checks)}}
+    pm.close()
+    p64.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -422,6 +489,10 @@ def run_ours(args):
         for k in ("value", "batch_steps_per_s", "boundary_points_per_s"):
             batched[k] *= world
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_block(fsib, torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         k = 2
@@ -440,7 +511,8 @@ def run_ours(args):
                 "nufft_pts_per_s": {"type1": world * m["pts1"], "type2": world * m["pts2"]},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": m["clocks"],
                 "gpu_launches": m["launches"] * args.steps, "launches_per_step": m["launches"],
-                "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched}
+                "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched,
+                "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
