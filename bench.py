@@ -167,6 +167,21 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def max_over_ranks(ms_local, world, device="cpu"):
+    """Slowest rank's time (ms): the whole job finishes when its last replica does."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(steps, ms_max, world):
+    """Whole-job throughput of independent replicas: every rank advanced `steps` steps."""
+    return world * steps / (ms_max * 1e-3)
+
+
 def roofline_of(site, prec, pk, pk_src, fp64_peak, fp32_peak):
     """Binding roofline of one launch site: HBM (algorithmic bytes) or ALU (algorithmic flops).
 
@@ -447,11 +462,8 @@ def run_ours(args):
     prec = "fp64"
     m = measure(fsib, torch, prob, prec, args.steps, args.warmup, dev, flush, world, barrier, gpu_index)
     pb = m["pb"]
-    t_rank = torch.tensor([m["ms"]], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-    ms_max = float(t_rank.item())
-    value = world * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(m["ms"], world, dev)
+    value = replica_value(args.steps, ms_max, world)
 
     pk, pk_src = peaks()
     fp64_peak = fsib.measure_peak(0)  # GFLOP/s
