@@ -1061,7 +1061,30 @@ k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] = T(0);
     if (on) {
-      for (int r = kg; r < nrow; r += K) {
+      // two rows per iteration: both rows' loads are issued before either row's arithmetic
+      int r = kg;
+      for (; r + K < nrow; r += 2 * K) {
+        T g0[D], g1[D], wyz[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int rr = r + u * K;
+          const int qy = rr % w, qz = (D == 3) ? rr / w : 0;
+          int gy = by + qy, gz = bz + qz;
+          gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
+          if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
+          const long long cell = ((long long)gz * nf + gy) * nf + gx;
+#pragma unroll
+          for (int a = 0; a < D; ++a) (u ? g1 : g0)[a] = grid[a * gcells + cell];
+          wyz[u] = ws[w + qy];
+          if (D == 3) wyz[u] = wyz[u] * ws[2 * w + qz];
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          fma_acc(acc[a], g0[a], wyz[0]);
+          fma_acc(acc[a], g1[a], wyz[1]);
+        }
+      }
+      for (; r < nrow; r += K) {
         const int qy = r % w, qz = (D == 3) ? r / w : 0;
         int gy = by + qy, gz = bz + qz;
         gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
@@ -1070,11 +1093,11 @@ k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__
         if (D == 3) wyz = wyz * ws[2 * w + qz];
         const long long cell = ((long long)gz * nf + gy) * nf + gx;
 #pragma unroll
-        for (int a = 0; a < D; ++a) acc[a] = acc[a] + grid[a * gcells + cell] * wyz;
+        for (int a = 0; a < D; ++a) fma_acc(acc[a], grid[a * gcells + cell], wyz);
       }
       const T wxq = ws[qx];
 #pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] = acc[a] * wxq;
+      for (int a = 0; a < D; ++a) acc[a] = acc_norm(acc[a]) * wxq;
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] = warp_sum(acc[a]);
