@@ -220,7 +220,7 @@ static double fft_flops(double lines, int n) { return lines * 5.0 * n * std::log
 static void free_ws(Workspace& ws) {
   void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.s1, ws.s2, ws.fhat, ws.uhalf, ws.bin_of,
                   ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
-                  ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.fx, ws.wts, ws.cwp,
+                  ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.wts, ws.cwp,
                   ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -229,7 +229,6 @@ static void free_ws(Workspace& ws) {
   ws.delta = nullptr;
   ws.Xh = ws.cw = ws.Uh = ws.omega_ones = ws.red = nullptr;
   ws.flag = nullptr;
-  ws.fx = nullptr;
   ws.wts = ws.cwp = nullptr;
   ws.box_ns = ws.box_np = ws.box_so = ws.box_po = nullptr;
   ws.part = nullptr;
@@ -312,7 +311,6 @@ static int alloc_ws(fsib_plan* h) {
   ws.red_blocks = 2 * 152;
   rc |= dmalloc(&ws.red, sizeof(double) * (size_t)(ws.red_blocks + 1) * 10, tot);
   rc |= dmalloc(&ws.flag, sizeof(int) * 4, tot);
-  rc |= dmalloc(&ws.fx, sizeof(unsigned long long) * 2, tot);
   rc |= dmalloc(&ws.wts, sizeof(double) * (size_t)p.M * d * p.w, tot);
   rc |= dmalloc(&ws.cwp, sizeof(double) * (size_t)p.M * d, tot);
   rc |= dmalloc(&ws.box_ns, sizeof(int) * (size_t)p.nbins, tot);
@@ -404,14 +402,14 @@ static void forward_fine(fsib_plan* h, const TI* grid, C<TA>* out, cudaStream_t 
   dec.dplane = (const TI*)ws.dplane;
   const double rs = sizeof(TI), cs = 2.0 * sizeof(TI);
   if (d == 3) {
-    { Prof pr(h, "t1.fx_rows_r2c", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
+    { Prof pr(h, "t1.rows_r2c", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
       rows_r2c_first<TI>(p, ws, grid, s1, (long long)d * n * n, tw, st); }
     { Prof pr(h, "t1.fy_strided", (double)d * n * hh * (n + N) * cs, fft_flops((double)d * n * hh, n), st);
       launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, false, none, tw, st); }
     { Prof pr(h, "t1.fz_strided_deconv", (double)d * N * hh * (n + N) * cs, fft_flops((double)d * N * hh, n), st);
       launch_fft_strided<TI, TI, TA>(s2, out, d, 1, N * hh, N, p.fl_nf, false, dec, tw, st); }
   } else {
-    { Prof pr(h, "t1.fx_rows_r2c", (double)d * n * n * rs + (double)d * n * hh * cs, fft_flops(0.5 * d * n, n), st);
+    { Prof pr(h, "t1.rows_r2c", (double)d * n * n * rs + (double)d * n * hh * cs, fft_flops(0.5 * d * n, n), st);
       rows_r2c_first<TI>(p, ws, grid, s1, (long long)d * n, tw, st); }
     { Prof pr(h, "t1.fy_strided_deconv", (double)d * hh * (n + N) * cs, fft_flops((double)d * hh, n), st);
       launch_fft_strided<TI, TI, TA>(s1, out, d, 1, hh, N, p.fl_nf, false, dec, tw, st); }

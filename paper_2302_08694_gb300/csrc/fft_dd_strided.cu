@@ -1,0 +1,6 @@
+// Strided transform passes in double-float arithmetic (FP64 mode).
+#include "fft_kernels.cuh"
+
+namespace fsib {
+FSIB_FFT_INST_S(dd, dd, dd)
+}  // namespace fsib

@@ -107,4 +107,71 @@ __device__ C<T>* smem_fft(C<T>* a, C<T>* b, int nl, int ls, int es, bool lines_f
   return a;
 }
 
+// ---------------------------------------------------------------------------
+// The same transform with the length N known at compile time: the radix plan,
+// the butterfly index arithmetic and the twiddle strides fold to constants.
+// lines_fast requires nl to be a power of two (lgnl = log2 nl).
+// ---------------------------------------------------------------------------
+constexpr int ct_radix(int n, int s) {
+  int m = n, st = 0;
+  while (m % 4 == 0) { if (st == s) return 4; m /= 4; ++st; }
+  while (m % 2 == 0) { if (st == s) return 2; m /= 2; ++st; }
+  while (m % 3 == 0) { if (st == s) return 3; m /= 3; ++st; }
+  return 0;
+}
+constexpr int ct_nstages(int n) {
+  int s = 0;
+  while (ct_radix(n, s)) ++s;
+  return s;
+}
+
+template <typename T, bool INV, int R, int N, int NS>
+__device__ __forceinline__ void stage_item_ct(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int l, int j,
+                                              int ls, int es, const C<T>* __restrict__ tw) {
+  constexpr int nb = N / R;
+  C<T> v[R];
+  const C<T>* s = src + l * ls;
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * es];
+  const int k = j % NS;
+  if (NS > 1) {
+    constexpr int step = N / (NS * R);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      C<T> w = tw[k * r * step];
+      if (INV) w = cconj<T>(w);
+      v[r] = cmul<T>(v[r], w);
+    }
+  }
+  if (R == 2) dft2<T, INV>(v);
+  if (R == 3) dft3<T, INV>(v);
+  if (R == 4) dft4<T, INV>(v);
+  C<T>* d = dst + l * ls;
+  const int o = (j / NS) * NS * R + k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) d[(o + r * NS) * es] = v[r];
+}
+
+template <typename T, bool INV, int N, int S = 0, int NS = 1>
+__device__ __forceinline__ C<T>* smem_fft_ct(C<T>* a, C<T>* b, int nl, int lgnl, int ls, int es, bool lines_fast,
+                                             const C<T>* __restrict__ tw) {
+  if constexpr (S == ct_nstages(N)) {
+    return a;
+  } else {
+    constexpr int R = ct_radix(N, S);
+    constexpr int nb = N / R;
+    const int total = nl * nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      int l, j;
+      if (lines_fast) { l = t & (nl - 1); j = t >> lgnl; } else { j = t % nb; l = t / nb; }
+      stage_item_ct<T, INV, R, N, NS>(a, b, l, j, ls, es, tw);
+    }
+    __syncthreads();
+    return smem_fft_ct<T, INV, N, S + 1, NS * R>(b, a, nl, lgnl, ls, es, lines_fast, tw);
+  }
+}
+
+// Dispatch on the FFT lengths used by the workloads; other lengths take the runtime plan (0).
+#define FSIB_FFT_SIZES(X) X(32) X(48) X(64) X(72) X(96) X(128) X(144) X(192) X(256)
+
 }  // namespace fsib

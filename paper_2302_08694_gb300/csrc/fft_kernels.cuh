@@ -11,6 +11,10 @@
 // of appendix A (division by the kernel's Fourier transform) or a plain scale is
 // applied where all mode indices are known: on the output of the last forward
 // pass and on the input of the first inverse pass.
+// Kernel and launcher templates; fft_float.cu, fft_dd.cu and fft_double.cu instantiate
+// them per arithmetic type so that the three compile in parallel.
+#pragma once
+#include <type_traits>
 #include "fft_device.cuh"
 
 namespace fsib {
@@ -19,15 +23,26 @@ namespace fsib {
 // fl.rows_q row pairs per CTA in the row passes.
 constexpr int kThreads = 256;
 
+// Run the line transforms with the compile-time plan when NC > 0.
+template <typename T, bool INV, int NC>
+__device__ __forceinline__ C<T>* fft_lines(C<T>* a, C<T>* b, int nl, int ls, int es, bool lines_fast,
+                                           const FftLen& fl, const C<T>* __restrict__ tw) {
+  if constexpr (NC > 0) {
+    return smem_fft_ct<T, INV, NC>(a, b, nl, lines_fast ? __ffs(nl) - 1 : 0, ls, es, lines_fast, tw);
+  } else {
+    return smem_fft<T, INV>(a, b, nl, ls, es, lines_fast, fl, tw);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Strided pass
 // ---------------------------------------------------------------------------
-template <typename T, bool INV, typename Tin, typename Tout>
+template <typename T, bool INV, typename Tin, typename Tout, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk,
               FftLen fl, Mult<T> mult, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = fl.n, kP = fl.tile_p;
+  const int n = NC ? NC : fl.n, kP = fl.tile_p, lgP = __ffs(kP) - 1;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* a = tw + n;
   C<T>* b = a + n * kP;
@@ -40,7 +55,7 @@ k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inne
   C<Tout>* dst = out + co * (long long)Lout * inner;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
   for (int t = threadIdx.x; t < n * kP; t += blockDim.x) {
-    const int p = t % kP, i = t / kP, q = q0 + p;
+    const int p = t & (kP - 1), i = t >> lgP, q = q0 + p;
     C<T> v = mk<T>(T(0), T(0));
     if (q < inner) {
       if (!INV) {
@@ -60,10 +75,10 @@ k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inne
     a[i * kP + p] = v;
   }
   __syncthreads();
-  C<T>* r = smem_fft<T, INV>(a, b, kP, 1, kP, true, fl, tw);
+  C<T>* r = fft_lines<T, INV, NC>(a, b, kP, 1, kP, true, fl, tw);
   if (!INV) {
     for (int t = threadIdx.x; t < Nk * kP; t += blockDim.x) {
-      const int p = t % kP, io = t / kP, q = q0 + p;
+      const int p = t & (kP - 1), io = t >> lgP, q = q0 + p;
       if (q >= inner) continue;
       C<T> v = mk<T>(T(0), T(0));
       if (io != h) {
@@ -78,7 +93,7 @@ k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inne
     }
   } else {
     for (int t = threadIdx.x; t < n * kP; t += blockDim.x) {
-      const int p = t % kP, i = t / kP, q = q0 + p;
+      const int p = t & (kP - 1), i = t >> lgP, q = q0 + p;
       if (q < inner) dst[(long long)i * inner + q] = ccvt<Tout, T>(r[i * kP + p]);
     }
   }
@@ -87,46 +102,32 @@ k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inne
 // ---------------------------------------------------------------------------
 // Row passes: real rows (length n) <-> half spectra (N/2 modes)
 // ---------------------------------------------------------------------------
-// FX: the input rows hold fixed-point integers (value = integer * 2^-k) written by the spread.
-template <typename T, bool FX>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
-k_rows_r2c(const void* __restrict__ in_, const unsigned long long* __restrict__ fxmax, int M,
-           C<T>* __restrict__ out, long long npairs, int Nk, FftLen fl, const C<T>* __restrict__ twg) {
+k_rows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk, FftLen fl,
+           const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
+  const int n = NC ? NC : fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* a = tw + n;
   C<T>* b = a + kQrows * ls;
   const long long pr0 = (long long)blockIdx.x * kQrows;
-  float isc = 1.0f;
-  if (FX) isc = pow2f(-fx_exponent(*fxmax, M));
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
   for (int t = threadIdx.x; t < kQrows * n; t += blockDim.x) {
     const int p = t / n, x = t % n;
     const long long pr = pr0 + p;
     C<T> v = mk<T>(T(0), T(0));
-    if (pr < npairs) {
-      if (FX) {
-        const long long* in = reinterpret_cast<const long long*>(in_);
-        T r0, r1;
-        fx_to(in[(2 * pr) * n + x], isc, r0);
-        fx_to(in[(2 * pr + 1) * n + x], isc, r1);
-        v = mk<T>(r0, r1);
-      } else {
-        const T* in = reinterpret_cast<const T*>(in_);
-        v = mk<T>(in[(2 * pr) * n + x], in[(2 * pr + 1) * n + x]);
-      }
-    }
+    if (pr < npairs) v = mk<T>(in[(2 * pr) * n + x], in[(2 * pr + 1) * n + x]);
     a[p * ls + x] = v;
   }
   __syncthreads();
-  C<T>* r = smem_fft<T, false>(a, b, kQrows, ls, 1, false, fl, tw);
+  C<T>* r = fft_lines<T, false, NC>(a, b, kQrows, ls, 1, false, fl, tw);
   for (int t = threadIdx.x; t < kQrows * h; t += blockDim.x) {
     const int p = t / h, k = t % h;
     const long long pr = pr0 + p;
     if (pr >= npairs) continue;
     const C<T> Z = r[p * ls + k];
-    const C<T> Zc = cconj<T>(r[p * ls + ((n - k) % n)]);
+    const C<T> Zc = cconj<T>(r[p * ls + (k == 0 ? 0 : n - k)]);
     const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
     out[(2 * pr) * h + k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
     out[(2 * pr + 1) * h + k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
@@ -149,12 +150,12 @@ __device__ __forceinline__ C<T> pack_rows(const C<T>* __restrict__ A, const C<T>
   return mk<T>(T(0), T(0));
 }
 
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
            FftLen fl, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
+  const int n = NC ? NC : fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* a = tw + n;
   C<T>* b = a + kQrows * ls;
@@ -168,7 +169,7 @@ k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, i
     a[p * ls + k] = v;
   }
   __syncthreads();
-  C<T>* r = smem_fft<T, true>(a, b, kQrows, ls, 1, false, fl, tw);
+  C<T>* r = fft_lines<T, true, NC>(a, b, kQrows, ls, 1, false, fl, tw);
   for (int t = threadIdx.x; t < kQrows * n; t += blockDim.x) {
     const int p = t / n, x = t % n;
     const long long pr = pr0 + p;
@@ -185,12 +186,12 @@ k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, i
 // the d(d+1)/2 products. Input [d][nrows][N/2], output [d(d+1)/2][nrows][N/2],
 // products ordered (xx, xy, xz, yy, yz, zz) in 3D and (xx, xy, yy) in 2D.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows,
                int Nk, FftLen fl, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
+  const int n = NC ? NC : fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
   const int np = d * (d + 1) / 2;
   const long long npairs = nrows / 2;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
@@ -209,7 +210,7 @@ k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long 
     a[line * ls + k] = v;
   }
   __syncthreads();
-  C<T>* r = smem_fft<T, true>(a, b, kQrows * d, ls, 1, false, fl, tw);
+  C<T>* r = fft_lines<T, true, NC>(a, b, kQrows * d, ls, 1, false, fl, tw);
   C<T>* o = (r == a) ? b : a;
   // products: re holds row 2p, im holds row 2p+1
   for (int t = threadIdx.x; t < kQrows * np * n; t += blockDim.x) {
@@ -226,13 +227,13 @@ k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long 
     o[line * ls + x] = mk<T>(ua.x * ub.x, ua.y * ub.y);
   }
   __syncthreads();
-  C<T>* f = smem_fft<T, false>(o, r, kQrows * np, ls, 1, false, fl, tw);
+  C<T>* f = fft_lines<T, false, NC>(o, r, kQrows * np, ls, 1, false, fl, tw);
   for (int t = threadIdx.x; t < kQrows * np * h; t += blockDim.x) {
     const int k = t % h, line = t / h, p = line / np, ab = line % np;
     const long long pr = pr0 + p;
     if (pr >= npairs) continue;
     const C<T> Z = f[line * ls + k];
-    const C<T> Zc = cconj<T>(f[line * ls + ((n - k) % n)]);
+    const C<T> Zc = cconj<T>(f[line * ls + (k == 0 ? 0 : n - k)]);
     const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
     C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
     ob[k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
@@ -241,15 +242,18 @@ k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long 
 }
 
 // ---------------------------------------------------------------------------
-// Launchers
+// Launchers: each dispatches on the FFT length (a compile-time kernel for the
+// lengths in FSIB_FFT_SIZES, the runtime-length kernel otherwise).
 // ---------------------------------------------------------------------------
-// Raise the dynamic shared-memory limit of a kernel to the device's opt-in maximum,
-// once per kernel (this is not a stream operation, so it is also safe while a
-// stream is being captured).
-template <typename K>
-static void set_smem(K kern, size_t bytes) {
-  raise_smem_limit(reinterpret_cast<const void*>(kern));
-  (void)bytes;
+// Calls f(std::integral_constant<int, NC>) with NC = n for a specialised length, else NC = 0.
+template <typename F>
+static void with_fft_len(int n, F&& f) {
+  switch (n) {
+#define FSIB_CASE(K) case K: f(std::integral_constant<int, K>()); return;
+    FSIB_FFT_SIZES(FSIB_CASE)
+#undef FSIB_CASE
+    default: f(std::integral_constant<int, 0>()); return;
+  }
 }
 
 template <typename T, typename Tin, typename Tout>
@@ -260,13 +264,23 @@ void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, in
   const int ntile = (inner + kP - 1) / kP;
   const long long blocks = (long long)ncomp * outer * ntile;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * fl.n * kP);
-  if (inverse) {
-    set_smem(k_fft_strided<T, true, Tin, Tout>, smem);
-    k_fft_strided<T, true, Tin, Tout><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
-  } else {
-    set_smem(k_fft_strided<T, false, Tin, Tout>, smem);
-    k_fft_strided<T, false, Tin, Tout><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
-  }
+  // A pass that converts between types runs in one direction only: a forward pass
+  // may narrow its output (Tout != T), an inverse pass may widen its input (Tin != T).
+  // The unused direction keeps the runtime-length kernel.
+  constexpr bool fwd_only = !std::is_same<Tout, T>::value, inv_only = !std::is_same<Tin, T>::value;
+  with_fft_len(fl.n, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    constexpr int NCI = fwd_only ? 0 : NC, NCF = inv_only ? 0 : NC;
+    if (inverse) {
+      auto k = k_fft_strided<T, true, Tin, Tout, NCI>;
+      raise_smem_limit(reinterpret_cast<const void*>(k));
+      k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
+    } else {
+      auto k = k_fft_strided<T, false, Tin, Tout, NCF>;
+      raise_smem_limit(reinterpret_cast<const void*>(k));
+      k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
+    }
+  });
 }
 
 template <typename T>
@@ -276,24 +290,12 @@ void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const 
   const int kQrows = fl.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
-  set_smem(k_rows_r2c<T, false>, smem);
-  k_rows_r2c<T, false><<<(unsigned)blocks, kThreads, smem, st>>>(in, nullptr, 0, out, npairs, Nk, fl, tw);
+  with_fft_len(fl.n, [&](auto nc) {
+    auto k = k_rows_r2c<T, decltype(nc)::value>;
+    raise_smem_limit(reinterpret_cast<const void*>(k));
+    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
+  });
 }
-
-template <typename T>
-void launch_fft_rows_r2c_fx(const long long* in, const unsigned long long* fxmax, int M, C<T>* out,
-                            long long nrows, int Nk, const FftLen& fl, const C<T>* tw, cudaStream_t st) {
-  const long long npairs = nrows / 2;
-  const int kQrows = fl.rows_q;
-  const long long blocks = (npairs + kQrows - 1) / kQrows;
-  const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
-  set_smem(k_rows_r2c<T, true>, smem);
-  k_rows_r2c<T, true><<<(unsigned)blocks, kThreads, smem, st>>>(in, fxmax, M, out, npairs, Nk, fl, tw);
-}
-template void launch_fft_rows_r2c_fx<dd>(const long long*, const unsigned long long*, int, C<dd>*, long long, int,
-                                         const FftLen&, const C<dd>*, cudaStream_t);
-template void launch_fft_rows_r2c_fx<float>(const long long*, const unsigned long long*, int, C<float>*, long long,
-                                            int, const FftLen&, const C<float>*, cudaStream_t);
 
 template <typename T>
 void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
@@ -302,8 +304,11 @@ void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const 
   const int kQrows = fl.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
-  set_smem(k_rows_c2r<T>, smem);
-  k_rows_c2r<T><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
+  with_fft_len(fl.n, [&](auto nc) {
+    auto k = k_rows_c2r<T, decltype(nc)::value>;
+    raise_smem_limit(reinterpret_cast<const void*>(k));
+    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
+  });
 }
 
 template <typename T>
@@ -313,30 +318,23 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
   const int kQrows = fl.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * 6 * (fl.n + 1));
-  set_smem(k_rows_product<T>, smem);
-  k_rows_product<T><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, d, nrows, Nk, fl, tw);
+  with_fft_len(fl.n, [&](auto nc) {
+    auto k = k_rows_product<T, decltype(nc)::value>;
+    raise_smem_limit(reinterpret_cast<const void*>(k));
+    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, d, nrows, Nk, fl, tw);
+  });
 }
 
-#define INST(T)                                                                                  \
+#define FSIB_FFT_INST(T)                                                                         \
   template void launch_fft_rows_r2c<T>(const T*, C<T>*, long long, int, const FftLen&,           \
                                        const C<T>*, cudaStream_t);                               \
   template void launch_fft_rows_c2r<T>(const C<T>*, T*, long long, int, const FftLen&,           \
                                        const C<T>*, cudaStream_t);                               \
   template void launch_rows_product<T>(const C<T>*, C<T>*, int, long long, int, const FftLen&,   \
                                        const C<T>*, cudaStream_t);
-INST(float)
-INST(double)
-INST(dd)
-#define INST_S(T, Ti, To)                                                                        \
+#define FSIB_FFT_INST_S(T, Ti, To)                                                               \
   template void launch_fft_strided<T, Ti, To>(const C<Ti>*, C<To>*, int, int, int, int,          \
                                               const FftLen&, bool, Mult<T>, const C<T>*,         \
                                               cudaStream_t);
-INST_S(float, float, float)
-INST_S(double, double, double)
-INST_S(dd, dd, dd)
-INST_S(dd, double, dd)
-INST_S(dd, dd, double)
-#undef INST_S
-#undef INST
 
 }  // namespace fsib

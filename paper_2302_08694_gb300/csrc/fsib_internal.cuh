@@ -50,29 +50,6 @@ __device__ __forceinline__ C<To> ccvt(const C<From>& i) {
 }
 
 // ---------------------------------------------------------------------------
-// Fixed-point grid values of the spread: value = integer * 2^-k.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }  // exact, |k| <= 126
-
-// k such that M * max|omega c| * 2^k < 2^61 (max passed as its IEEE bit pattern).
-__device__ __forceinline__ int fx_exponent(unsigned long long mbits, int M) {
-  const double m = __longlong_as_double((long long)mbits);
-  if (!(m > 0.0)) return 0;
-  int e = 0;
-  frexp(m * (double)M, &e);  // M max < 2^e
-  const int k = 61 - e;
-  return k > 100 ? 100 : (k < -100 ? -100 : k);
-}
-
-__device__ __forceinline__ void fx_to(long long x, float isc, float& o) { o = __ll2float_rn(x) * isc; }
-__device__ __forceinline__ void fx_to(long long x, float isc, double& o) { o = (double)x * (double)isc; }
-__device__ __forceinline__ void fx_to(long long x, float isc, dd& o) {
-  const float hi = __ll2float_rn(x);
-  const float lo = __ll2float_rn(x - __float2ll_rn(hi));
-  o = dd(hi * isc, lo * isc);
-}
-
-// ---------------------------------------------------------------------------
 // 1-D FFT plan of one length n = 2^a 3^b (radix stages of 4, 2 and 3).
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 12;
@@ -157,7 +134,6 @@ struct Workspace {
   double* red = nullptr;      // partial sums
   int red_blocks = 0;
   int* flag = nullptr;
-  unsigned long long* fx = nullptr;  // bit pattern of max |omega c| for the fixed-point spread
   void* wts = nullptr;               // T[M][d][w] kernel weights per sorted point
   void* cwp = nullptr;               // T[M][d] weighted forces per sorted point
   int* box_ns = nullptr;             // [nbins] slices per gather box (3D)
@@ -202,24 +178,12 @@ void launch_spread(const Plan& p, Workspace& ws, const double* cw, const double*
 template <typename T>
 void launch_interp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st);
 
-void launch_spread_dd(const Plan& p, Workspace& ws, const double* cw, const double* omega, dd* grid,
-                      cudaStream_t st);
-void launch_interp_dd(const Plan& p, Workspace& ws, const dd* grid, double* U, cudaStream_t st);
-// Fixed-point spread (grid: int64 when T = dd, float when T = float) and staged interp.
-template <typename T>
-void launch_spread_fx(const Plan& p, Workspace& ws, const double* cw, const double* omega, void* grid,
-                      cudaStream_t st);
-template <typename T>
-void launch_interp_staged(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st);
 template <typename T>
 void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const double* omega, cudaStream_t st);
 template <typename T>
 void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st);
 template <typename T>
 void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st);
-template <typename T>
-void launch_fft_rows_r2c_fx(const long long* in, const unsigned long long* fxmax, int M, C<T>* out,
-                            long long nrows, int Nk, const FftLen& fl, const C<T>* tw, cudaStream_t st);
 
 template <typename T>
 void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t st);

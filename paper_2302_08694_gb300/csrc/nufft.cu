@@ -360,182 +360,8 @@ k_interp(PointGeom g, T beta, const int* __restrict__ perm, const int* __restric
 }
 
 // ---------------------------------------------------------------------------
-// FP64-mode point kernels in double-float arithmetic. The kernel weights are
-// evaluated in FP64 (3w values per point) and split into dd; every per-cell
-// product and sum runs on the FP32 pipes. The grid holds dd values.
-// ---------------------------------------------------------------------------
-template <int D>
-__device__ __forceinline__ void point_weights_dd(dd* wts, const double* __restrict__ delta, long long s, int M,
-                                                 int w, double beta, int lane) {
-  if (lane < w) {
-    const double two_w = 2.0 / w;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const double z = two_w * ((double)lane + delta[(long long)a * M + s]);
-      wts[a * kMaxW + lane] = dd(es_kernel<double>(z, beta));
-    }
-  }
-  __syncwarp();
-}
-
-// Accumulate v into the float pair (hi, lo) of shared or global memory: the rounding
-// error of the atomic addition on hi is recovered exactly (TwoSum on the returned
-// old value) and added to lo together with v.lo.
-__device__ __forceinline__ void atomic_add_dd(float* hi, float* lo, dd v) {
-  const float old = atomicAdd(hi, v.hi);
-  float s, e;
-  two_sum(old, v.hi, s, e);
-  const float r = __fadd_rn(e, v.lo);
-  if (r != 0.0f) atomicAdd(lo, r);
-}
-
-template <int D>
-__global__ void __launch_bounds__(kSpreadThreads)
-k_spread_dd(PointGeom g, double beta, const double* __restrict__ cw, const double* __restrict__ omega,
-            const int* __restrict__ perm, const int* __restrict__ offsets, const int* __restrict__ occ,
-            const int* __restrict__ nocc, const int* __restrict__ i0s, const double* __restrict__ delta,
-            dd* __restrict__ grid) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int w = g.w, nf = g.nf, M = g.M;
-  const int Tx = g.b[0] + w, Ty = g.b[1] + w, Tz = (D == 3) ? g.b[2] + w : 1;
-  const int tcells = Tx * Ty * Tz;
-  const int nwarp = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  dd* wts_all = reinterpret_cast<dd*>(smem_raw);          // [nwarp][D][kMaxW]
-  float* thi = reinterpret_cast<float*>(wts_all + nwarp * D * kMaxW);  // [D][tcells]
-  float* tlo = thi + D * tcells;                          // [D][tcells]
-  dd* wts = wts_all + warp * D * kMaxW;
-  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
-  const int nrow = (D == 3) ? w * w : w;
-  const int nb_occ = *nocc;
-  for (int k = blockIdx.x; k < nb_occ; k += gridDim.x) {
-    const int bin = occ[k];
-    const int Bx = bin % g.nb[0];
-    const int By = (bin / g.nb[0]) % g.nb[1];
-    const int Bz = (D == 3) ? bin / (g.nb[0] * g.nb[1]) : 0;
-    const int half = w / 2;
-    const int ox = Bx * g.b[0] - half, oy = By * g.b[1] - half, oz = (D == 3) ? Bz * g.b[2] - half : 0;
-    for (int i = threadIdx.x; i < D * tcells; i += blockDim.x) { thi[i] = 0.0f; tlo[i] = 0.0f; }
-    __syncthreads();
-    const int s0 = offsets[bin], s1 = offsets[bin + 1];
-    for (int s = s0 + warp; s < s1; s += nwarp) {
-      const int j = perm[s];
-      point_weights_dd<D>(wts, delta, s, M, w, beta, lane);
-      const double om = omega ? omega[j] : 1.0;
-      dd cv[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) cv[a] = dd(om * cw[(long long)a * M + j]);
-      const int bx = i0s[s] - ox, by = i0s[(long long)M + s] - oy;
-      const int bz = (D == 3) ? i0s[2LL * M + s] - oz : 0;
-      for (int r = lane; r < nrow; r += 32) {  // one (y, z) row of the window per lane
-        const int qy = r % w, qz = (D == 3) ? r / w : 0;
-        dd wyz = wts[kMaxW + qy];
-        if (D == 3) wyz = wyz * wts[2 * kMaxW + qz];
-        dd t[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) t[a] = cv[a] * wyz;
-        const int rowc = ((bz + qz) * Ty + (by + qy)) * Tx + bx;
-        for (int qx = 0; qx < w; ++qx) {
-          const dd wx = wts[qx];
-#pragma unroll
-          for (int a = 0; a < D; ++a)
-            atomic_add_dd(&thi[a * tcells + rowc + qx], &tlo[a * tcells + rowc + qx], t[a] * wx);
-        }
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < tcells; i += blockDim.x) {
-      const int cx = i % Tx, cy = (i / Tx) % Ty, cz = i / (Tx * Ty);
-      int gx = ox + cx, gy = oy + cy, gz = oz + cz;
-      gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
-      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
-      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
-      const long long gi = ((long long)gz * nf + gy) * nf + gx;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        float h, l;
-        quick_two_sum(thi[a * tcells + i], tlo[a * tcells + i], h, l);
-        if (h != 0.0f) {
-          dd* gp = &grid[a * gcells + gi];
-          atomic_add_dd(&gp->hi, &gp->lo, dd(h, l));
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <int D>
-__global__ void __launch_bounds__(kSpreadThreads)
-k_interp_dd(PointGeom g, double beta, const int* __restrict__ perm, const int* __restrict__ i0s,
-            const double* __restrict__ delta, const dd* __restrict__ grid, double* __restrict__ U) {
-  __shared__ dd wts_all[(kSpreadThreads / 32) * 3 * kMaxW];
-  const int w = g.w, nf = g.nf, M = g.M;
-  const int nwarp = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  dd* wts = wts_all + warp * D * kMaxW;
-  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
-  const int nrow = (D == 3) ? w * w : w;
-  for (long long s = (long long)blockIdx.x * nwarp + warp; s < M; s += (long long)gridDim.x * nwarp) {
-    point_weights_dd<D>(wts, delta, s, M, w, beta, lane);
-    const int bx = i0s[s], by = i0s[(long long)M + s], bz = (D == 3) ? i0s[2LL * M + s] : 0;
-    dd acc[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] = dd(0.0f, 0.0f);
-    for (int r = lane; r < nrow; r += 32) {
-      const int qy = r % w, qz = (D == 3) ? r / w : 0;
-      int gy = by + qy, gz = bz + qz;
-      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
-      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
-      const long long row = ((long long)gz * nf + gy) * nf;
-      dd srow[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) srow[a] = dd(0.0f, 0.0f);
-      for (int qx = 0; qx < w; ++qx) {
-        int gx = bx + qx;
-        gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
-        const dd wx = wts[qx];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          const dd gv = grid[a * gcells + row + gx];
-          srow[a] = srow[a] + gv * wx;
-        }
-      }
-      dd wyz = wts[kMaxW + qy];
-      if (D == 3) wyz = wyz * wts[2 * kMaxW + qz];
-#pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] = acc[a] + srow[a] * wyz;
-    }
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      dd v = acc[a];
-      for (int off = 16; off > 0; off >>= 1) {
-        const dd o(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
-        v = v + o;
-      }
-      acc[a] = v;
-    }
-    if (lane == 0) {
-      const int j = perm[s];
-#pragma unroll
-      for (int a = 0; a < D; ++a) U[(long long)a * M + j] = acc[a].to_double();
-    }
-    __syncwarp();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Spread by exact fixed-point accumulation (transform modes: float and dd).
-//
-// Each contribution c_j phi_x phi_y phi_z is computed in the transform arithmetic
-// T, rounded to an integer multiple of 2^-k and added as a 64-bit integer, so the
-// accumulated grid value does not depend on the order of the additions
-// (deterministic) and carries no accumulation error beyond that rounding. The
-// scale 2^k is chosen on the device from B = M max_j |omega_j c_j|, a bound on
-// any grid value (phi <= 1), so that B 2^k < 2^61.
-// One block owns one occupied bin and its (b + w)^D tile in shared memory; the
-// points of the bin are taken one at a time by all threads of the block (the
-// cells of one window are distinct, so the tile needs no atomics), with the
-// kernel weights of the next point computed during the current one.
+// Kernel weights in the transform arithmetic: float evaluates phi in FP32, dd
+// evaluates it in FP64 and splits the value into a double-float pair.
 // ---------------------------------------------------------------------------
 template <typename T> struct DeltaT;
 template <> struct DeltaT<float> { using type = float; };
@@ -556,190 +382,6 @@ __device__ __forceinline__ dd weight_of<dd>(double delta, int q, int w, double b
   return dd(es_kernel<double>(z, beta));
 }
 
-
-__device__ __forceinline__ long long to_fixed(float v, float s) { return __float2ll_rn(v * s); }
-__device__ __forceinline__ long long to_fixed(dd v, float s) {
-  return __float2ll_rn(v.hi * s) + __float2ll_rn(v.lo * s);
-}
-
-
-__global__ void k_fx_max(const double* __restrict__ cw, const double* __restrict__ omega, int d, int M,
-                         unsigned long long* __restrict__ mx) {
-  double m = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-    const double om = omega ? fabs(omega[j]) : 1.0;
-    for (int a = 0; a < d; ++a) m = fmax(m, fabs(cw[(long long)a * M + j]) * om);
-  }
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
-}
-
-template <typename T, int D, bool FXGRID>
-__global__ void __launch_bounds__(kSpreadThreads)
-k_spread_fx(PointGeom g, double beta, const double* __restrict__ cw, const double* __restrict__ omega,
-            const int* __restrict__ perm, const int* __restrict__ offsets, const int* __restrict__ occ,
-            const int* __restrict__ nocc, const int* __restrict__ i0s,
-            const typename DeltaT<T>::type* __restrict__ delta, const unsigned long long* __restrict__ fxmax,
-            void* __restrict__ grid_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int w = g.w, nf = g.nf, M = g.M;
-  const int Tx = g.b[0] + w, Ty = g.b[1] + w, Tz = (D == 3) ? g.b[2] + w : 1;
-  const int tcells = Tx * Ty * Tz;
-  long long* tile = reinterpret_cast<long long*>(smem_raw);                // [D][tcells]
-  T* wbuf = reinterpret_cast<T*>(tile + (size_t)D * tcells);              // [2][D][kMaxW]
-  T* cbuf = wbuf + 2 * D * kMaxW;                                          // [2][D]
-  int* obuf = reinterpret_cast<int*>(cbuf + 2 * D);                        // [2][3] window offsets in the tile
-  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
-  const int wd = (D == 3) ? w * w * w : w * w;
-  const int k = fx_exponent(*fxmax, M);
-  const float sc = pow2f(k), isc = pow2f(-k);
-  const int nb_occ = *nocc;
-  for (int kb = blockIdx.x; kb < nb_occ; kb += gridDim.x) {
-    const int bin = occ[kb];
-    const int Bx = bin % g.nb[0];
-    const int By = (bin / g.nb[0]) % g.nb[1];
-    const int Bz = (D == 3) ? bin / (g.nb[0] * g.nb[1]) : 0;
-    const int half = w / 2;
-    const int ox = Bx * g.b[0] - half, oy = By * g.b[1] - half, oz = (D == 3) ? Bz * g.b[2] - half : 0;
-    const int s0 = offsets[bin], s1 = offsets[bin + 1];
-    for (int i = threadIdx.x; i < D * tcells; i += blockDim.x) tile[i] = 0;
-    // weights, weighted force and window offsets of point s into buffer b
-    auto prepare = [&](int s, int b) {
-      const int t = threadIdx.x;
-      if (t < D * w) {
-        const int a = t / w, q = t % w;
-        wbuf[(b * D + a) * kMaxW + q] = weight_of<T>(delta[(long long)a * M + s], q, w, beta);
-      } else if (t < D * w + D) {
-        const int a = t - D * w;
-        const int j = perm[s];
-        const double om = omega ? omega[j] : 1.0;
-        cbuf[b * D + a] = T(om * cw[(long long)a * M + j]);
-      } else if (t == D * w + D) {
-        obuf[b * 3 + 0] = i0s[s] - ox;
-        obuf[b * 3 + 1] = i0s[(long long)M + s] - oy;
-        obuf[b * 3 + 2] = (D == 3) ? i0s[2LL * M + s] - oz : 0;
-      }
-    };
-    if (s0 < s1) prepare(s0, 0);
-    __syncthreads();
-    for (int s = s0; s < s1; ++s) {
-      const int b = (s - s0) & 1;
-      if (s + 1 < s1) prepare(s + 1, b ^ 1);
-      const T* wx = wbuf + (b * D + 0) * kMaxW;
-      const T* wy = wbuf + (b * D + 1) * kMaxW;
-      const T* wz = wbuf + (b * D + 2 % D) * kMaxW;
-      const int bx = obuf[b * 3], by = obuf[b * 3 + 1], bz = obuf[b * 3 + 2];
-      T cv[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) cv[a] = cbuf[b * D + a];
-      for (int i = threadIdx.x; i < wd; i += blockDim.x) {
-        const int qx = i % w, qy = (i / w) % w, qz = (D == 3) ? i / (w * w) : 0;
-        T wt = wx[qx] * wy[qy];
-        if (D == 3) wt = wt * wz[qz];
-        const int cell = ((bz + qz) * Ty + (by + qy)) * Tx + (bx + qx);
-#pragma unroll
-        for (int a = 0; a < D; ++a) tile[a * tcells + cell] += to_fixed(cv[a] * wt, sc);
-      }
-      __syncthreads();
-    }
-    for (int i = threadIdx.x; i < tcells; i += blockDim.x) {
-      const int cx = i % Tx, cy = (i / Tx) % Ty, cz = i / (Tx * Ty);
-      int gx = ox + cx, gy = oy + cy, gz = oz + cz;
-      gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
-      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
-      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
-      const long long gi = ((long long)gz * nf + gy) * nf + gx;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const long long v = tile[a * tcells + i];
-        if (v != 0) {
-          if (FXGRID)
-            atomicAdd(reinterpret_cast<unsigned long long*>(grid_out) + a * gcells + gi, (unsigned long long)v);
-          else
-            atomicAdd(reinterpret_cast<float*>(grid_out) + a * gcells + gi, (float)v * isc);
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Interp with the bin's tile staged in shared memory (transform modes: float and dd).
-// ---------------------------------------------------------------------------
-template <typename T, int D>
-__global__ void __launch_bounds__(kSpreadThreads)
-k_interp_staged(PointGeom g, double beta, const int* __restrict__ perm, const int* __restrict__ offsets,
-                const int* __restrict__ occ, const int* __restrict__ nocc, const int* __restrict__ i0s,
-                const typename DeltaT<T>::type* __restrict__ delta, const T* __restrict__ grid,
-                double* __restrict__ U) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int w = g.w, nf = g.nf, M = g.M;
-  const int Tx = g.b[0] + w, Ty = g.b[1] + w, Tz = (D == 3) ? g.b[2] + w : 1;
-  const int tcells = Tx * Ty * Tz;
-  const int nwarp = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  T* tile = reinterpret_cast<T*>(smem_raw);                  // [D][tcells]
-  T* wts = tile + (size_t)D * tcells + warp * D * kMaxW;     // per warp [D][kMaxW]
-  const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
-  const int nrow = (D == 3) ? w * w : w;
-  const int nb_occ = *nocc;
-  for (int kb = blockIdx.x; kb < nb_occ; kb += gridDim.x) {
-    const int bin = occ[kb];
-    const int Bx = bin % g.nb[0];
-    const int By = (bin / g.nb[0]) % g.nb[1];
-    const int Bz = (D == 3) ? bin / (g.nb[0] * g.nb[1]) : 0;
-    const int half = w / 2;
-    const int ox = Bx * g.b[0] - half, oy = By * g.b[1] - half, oz = (D == 3) ? Bz * g.b[2] - half : 0;
-    for (int i = threadIdx.x; i < tcells; i += blockDim.x) {
-      const int cx = i % Tx, cy = (i / Tx) % Ty, cz = i / (Tx * Ty);
-      int gx = ox + cx, gy = oy + cy, gz = oz + cz;
-      gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
-      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
-      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
-      const long long gi = ((long long)gz * nf + gy) * nf + gx;
-#pragma unroll
-      for (int a = 0; a < D; ++a) tile[a * tcells + i] = grid[a * gcells + gi];
-    }
-    __syncthreads();
-    const int s0 = offsets[bin], s1 = offsets[bin + 1];
-    for (int s = s0 + warp; s < s1; s += nwarp) {
-      if (lane < w) {
-#pragma unroll
-        for (int a = 0; a < D; ++a) wts[a * kMaxW + lane] = weight_of<T>(delta[(long long)a * M + s], lane, w, beta);
-      }
-      __syncwarp();
-      const int bx = i0s[s] - ox, by = i0s[(long long)M + s] - oy, bz = (D == 3) ? i0s[2LL * M + s] - oz : 0;
-      T acc[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] = T(0);
-      for (int r = lane; r < nrow; r += 32) {
-        const int qy = r % w, qz = (D == 3) ? r / w : 0;
-        const int rowc = ((bz + qz) * Ty + (by + qy)) * Tx + bx;
-        T srow[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) srow[a] = T(0);
-        for (int qx = 0; qx < w; ++qx) {
-          const T wxq = wts[qx];
-#pragma unroll
-          for (int a = 0; a < D; ++a) srow[a] = srow[a] + tile[a * tcells + rowc + qx] * wxq;
-        }
-        T wyz = wts[kMaxW + qy];
-        if (D == 3) wyz = wyz * wts[2 * kMaxW + qz];
-#pragma unroll
-        for (int a = 0; a < D; ++a) acc[a] = acc[a] + srow[a] * wyz;
-      }
-#pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] = warp_sum(acc[a]);
-      if (lane == 0) {
-        const int j = perm[s];
-#pragma unroll
-        for (int a = 0; a < D; ++a) U[(long long)a * M + j] = to_double_val(acc[a]);
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Transform modes float / dd, gather formulation.
@@ -1157,70 +799,6 @@ void launch_interp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaS
     k_interp<T, 2><<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, beta, ws.perm, ws.i0, (const T*)ws.delta, grid, U);
 }
 
-void launch_spread_dd(const Plan& p, Workspace& ws, const double* cw, const double* omega, dd* grid,
-                      cudaStream_t st) {
-  const PointGeom g = geom(p);
-  const int D = p.d;
-  const int tcells = (g.b[0] + g.w) * (g.b[1] + g.w) * (D == 3 ? g.b[2] + g.w : 1);
-  const size_t smem = sizeof(dd) * (size_t)((kSpreadThreads / 32) * D * kMaxW) + 2 * sizeof(float) * (size_t)D * tcells;
-  const int blocks = 4 * num_sms();
-  auto kern = (D == 3) ? k_spread_dd<3> : k_spread_dd<2>;
-  raise_smem_limit(reinterpret_cast<const void*>(kern));
-  kern<<<blocks, kSpreadThreads, smem, st>>>(g, p.beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
-                                             (const double*)ws.delta, grid);
-}
-
-void launch_interp_dd(const Plan& p, Workspace& ws, const dd* grid, double* U, cudaStream_t st) {
-  const PointGeom g = geom(p);
-  const int nwarp = kSpreadThreads / 32;
-  long long blocks = (p.M + nwarp - 1) / nwarp;
-  if (blocks > 16LL * num_sms()) blocks = 16LL * num_sms();
-  if (p.d == 3)
-    k_interp_dd<3><<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, p.beta, ws.perm, ws.i0, (const double*)ws.delta, grid, U);
-  else
-    k_interp_dd<2><<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, p.beta, ws.perm, ws.i0, (const double*)ws.delta, grid, U);
-}
-
-template <typename T>
-void launch_spread_fx(const Plan& p, Workspace& ws, const double* cw, const double* omega, void* grid,
-                      cudaStream_t st) {
-  const PointGeom g = geom(p);
-  const int D = p.d;
-  cudaMemsetAsync(ws.fx, 0, sizeof(unsigned long long), st);
-  k_fx_max<<<std::min(64, (p.M + 255) / 256), 256, 0, st>>>(cw, omega, D, p.M, ws.fx);
-  const int tcells = (g.b[0] + g.w) * (g.b[1] + g.w) * (D == 3 ? g.b[2] + g.w : 1);
-  const size_t smem = sizeof(long long) * (size_t)D * tcells + sizeof(T) * (size_t)(2 * D * kMaxW + 2 * D) +
-                      sizeof(int) * 8;
-  const int blocks = 2 * num_sms();
-  using Td = typename DeltaT<T>::type;
-  const bool fxgrid = std::is_same<T, dd>::value;
-  if (D == 3) {
-    auto kern = fxgrid ? k_spread_fx<T, 3, true> : k_spread_fx<T, 3, false>;
-    raise_smem_limit(reinterpret_cast<const void*>(kern));
-    kern<<<blocks, kSpreadThreads, smem, st>>>(g, p.beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
-                                               (const Td*)ws.delta, ws.fx, grid);
-  } else {
-    auto kern = fxgrid ? k_spread_fx<T, 2, true> : k_spread_fx<T, 2, false>;
-    raise_smem_limit(reinterpret_cast<const void*>(kern));
-    kern<<<blocks, kSpreadThreads, smem, st>>>(g, p.beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
-                                               (const Td*)ws.delta, ws.fx, grid);
-  }
-}
-
-template <typename T>
-void launch_interp_staged(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st) {
-  const PointGeom g = geom(p);
-  const int D = p.d;
-  const int tcells = (g.b[0] + g.w) * (g.b[1] + g.w) * (D == 3 ? g.b[2] + g.w : 1);
-  const size_t smem = sizeof(T) * ((size_t)D * tcells + (size_t)(kSpreadThreads / 32) * D * kMaxW);
-  const int blocks = 2 * num_sms();
-  using Td = typename DeltaT<T>::type;
-  auto kern = (D == 3) ? k_interp_staged<T, 3> : k_interp_staged<T, 2>;
-  raise_smem_limit(reinterpret_cast<const void*>(kern));
-  kern<<<blocks, kSpreadThreads, smem, st>>>(g, p.beta, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
-                                             (const Td*)ws.delta, grid, U);
-}
-
 template <typename T>
 void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const double* omega, cudaStream_t st) {
   const PointGeom g = geom(p);
@@ -1272,10 +850,6 @@ template void launch_spread_gather<dd>(const Plan&, Workspace&, dd*, cudaStream_
 template void launch_interp_warp<float>(const Plan&, Workspace&, const float*, double*, cudaStream_t);
 template void launch_interp_warp<dd>(const Plan&, Workspace&, const dd*, double*, cudaStream_t);
 
-template void launch_spread_fx<float>(const Plan&, Workspace&, const double*, const double*, void*, cudaStream_t);
-template void launch_spread_fx<dd>(const Plan&, Workspace&, const double*, const double*, void*, cudaStream_t);
-template void launch_interp_staged<float>(const Plan&, Workspace&, const float*, double*, cudaStream_t);
-template void launch_interp_staged<dd>(const Plan&, Workspace&, const dd*, double*, cudaStream_t);
 
 template void launch_spread<float>(const Plan&, Workspace&, const double*, const double*, float*, cudaStream_t);
 template void launch_spread<double>(const Plan&, Workspace&, const double*, const double*, double*, cudaStream_t);
