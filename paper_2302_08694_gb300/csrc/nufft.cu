@@ -39,12 +39,14 @@ __device__ __forceinline__ double grid_coord(double x, double L, int nf) {
   return t;
 }
 
-// Window start i0 = ceil(t - w/2) of a point; its bin is B = (i0 + floor(w/2)) div b,
-// clamped to the last bin. Then i0 - (B b - floor(w/2)) lies in [0, b], so the
-// w-wide window of every point of bin B fits the (b + w)-wide tile at B b - floor(w/2).
+// Window start i0 = ceil(t - w/2) of a point (i0 >= -w/2, so it may be negative); its bin
+// is B = (i0 mod nf) div b. Then (i0 - B b) mod nf lies in [0, b), so the w-wide window of
+// every point of bin B fits the (b + w - 1)-wide tile at B b, and the windows that meet the
+// box [B b, B b + b) start in bins B - ceil((w - 1)/b) .. B: two bins per axis when w <= b + 1.
 __device__ __forceinline__ int window_start(double t, int w) { return (int)ceil(t - 0.5 * w); }
-__device__ __forceinline__ int bin_of_start(int i0, int w, int b, int nb) {
-  return min(max((i0 + w / 2) / b, 0), nb - 1);
+__device__ __forceinline__ int bin_of_start(int i0, int nf, int b, int nb) {
+  const int r = (i0 < 0) ? i0 + nf : (i0 >= nf ? i0 - nf : i0);
+  return min(r / b, nb - 1);
 }
 
 __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of,
@@ -53,7 +55,7 @@ __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __re
     long long bin = 0, mul = 1;
     for (int a = 0; a < g.d; ++a) {
       const double t = grid_coord(X[(long long)a * g.M + j], g.L, g.nf);
-      const int B = bin_of_start(window_start(t, g.w), g.w, g.b[a], g.nb[a]);
+      const int B = bin_of_start(window_start(t, g.w), g.nf, g.b[a], g.nb[a]);
       bin += B * mul;
       mul *= g.nb[a];
     }
@@ -263,8 +265,7 @@ k_spread(PointGeom g, T beta, const double* __restrict__ cw, const double* __res
     const int Bx = bin % g.nb[0];
     const int By = (bin / g.nb[0]) % g.nb[1];
     const int Bz = (D == 3) ? bin / (g.nb[0] * g.nb[1]) : 0;
-    const int half = w / 2;
-    const int ox = Bx * g.b[0] - half, oy = By * g.b[1] - half, oz = (D == 3) ? Bz * g.b[2] - half : 0;
+    const int ox = Bx * g.b[0], oy = By * g.b[1], oz = (D == 3) ? Bz * g.b[2] : 0;
     for (int i = threadIdx.x; i < D * tcells; i += blockDim.x) {
       tile[i] = T(0);
       if (COMP) lo[i] = 0.0f;
@@ -278,8 +279,9 @@ k_spread(PointGeom g, T beta, const double* __restrict__ cw, const double* __res
       T cv[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) cv[a] = (T)(om * cw[(long long)a * M + j]);
-      const int bx = i0s[s] - ox, by = i0s[(long long)M + s] - oy;
-      const int bz = (D == 3) ? i0s[2LL * M + s] - oz : 0;
+      int bx = i0s[s] - ox, by = i0s[(long long)M + s] - oy;  // in [0, b) after the periodic wrap
+      int bz = (D == 3) ? i0s[2LL * M + s] - oz : 0;
+      bx += (bx < 0) ? nf : 0; by += (by < 0) ? nf : 0; bz += (bz < 0) ? nf : 0;
       const int wd = (D == 3) ? w * w * w : w * w;
       for (int idx = lane; idx < wd; idx += 32) {
         const int qx = idx % w, qy = (idx / w) % w, qz = (D == 3) ? idx / (w * w) : 0;
@@ -543,9 +545,44 @@ __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restric
   int c = (lane < nnb) ? offsets[bin + 1] - offsets[bin] : 0;
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   if (lane == 0) {
-    const int K = max(1, (c + g.slice - 1) / g.slice);
+    const int K = (c + g.slice - 1) / g.slice;  // 0 for a box that no window reaches
     nslice[warp] = K;
     npart[warp] = (K > 1) ? K : 0;
+  }
+}
+
+// Box of every slice: box_item[slice_off[b] + k] = b for k < K_b.
+__global__ void k_slice_boxes(int nbox, const int* __restrict__ slice_off, int* __restrict__ box_item) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x)
+    for (int k = slice_off[b]; k < slice_off[b + 1]; ++k) box_item[k] = b;
+}
+
+// Zero the boxes that no window reaches: warp per run of 32 boxes, 16-byte stores along x.
+template <typename T>
+__device__ __forceinline__ void zero_empty_boxes(const PointGeom& g, const int* __restrict__ slice_off, int nbox,
+                                                 T* __restrict__ grid) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "grid element");
+  constexpr int v_per_row = 8 * (int)sizeof(T) / 16;  // 16-byte vectors per 8-cell box row
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int nf = g.nf;
+  const long long gcells = (long long)nf * nf * nf;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int b0 = gw * 32; b0 < nbox; b0 += nw * 32) {
+    const int bb = b0 + lane;
+    const bool empty = (bb < nbox) && (slice_off[bb + 1] == slice_off[bb]);
+    unsigned m = __ballot_sync(0xffffffffu, empty);
+    while (m) {
+      const int box = b0 + __ffs(m) - 1;
+      m &= m - 1;
+      const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
+      for (int i = lane; i < 3 * 64 * v_per_row; i += 32) {
+        const int v = i % v_per_row, row = i / v_per_row;  // row = (a * 8 + z) * 8 + y
+        const int y = row & 7, z = (row >> 3) & 7, a = row >> 6;
+        T* r = grid + a * gcells + ((long long)(Bz * 8 + z) * nf + (By * 8 + y)) * nf + Bx * 8;
+        reinterpret_cast<float4*>(r)[v] = z4;
+      }
+    }
   }
 }
 
@@ -559,7 +596,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
               const T* __restrict__ W, const T* __restrict__ Cw, const int* __restrict__ slice_off,
-              const int* __restrict__ part_off, T* __restrict__ part, T* __restrict__ grid) {
+              const int* __restrict__ box_item, const int* __restrict__ part_off, T* __restrict__ part,
+              T* __restrict__ grid) {
   __shared__ T sW[kBoxChunk * 3 * kMaxW];
   __shared__ T sC[kBoxChunk * 3];
   __shared__ int sI[kBoxChunk * 3];
@@ -570,13 +608,7 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
   const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
   const int nslices = slice_off[nbox];
   for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
-    // box of this slice: last b with slice_off[b] <= sl
-    int lo = 0, hi = nbox - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (slice_off[mid] <= sl) lo = mid; else hi = mid - 1;
-    }
-    const int box = lo, ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
+    const int box = box_item[sl], ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
     const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
     const int ox = Bx * 8, oy = By * 8, oz = Bz * 8;
     const int cx = ox + (lane & 7), cy0 = oy + (lane >> 3), cz = oz + warp;
@@ -662,6 +694,7 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
       }
     }
   }
+  zero_empty_boxes<T>(g, slice_off, nbox, grid);
 }
 
 // Boxes split into several slices: add their partials in slice order and store the box.
@@ -816,17 +849,18 @@ void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const dou
 template <typename T>
 void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st) {
   const PointGeom g = geom(p);
-  const int h = p.w / 2, b = p.bins[0];
-  // neighbour bins holding window starts that reach the box: floor((-w + 1 + h)/b) .. floor((b - 1 + h)/b)
-  auto fl = [](int a, int bb) { return (a >= 0) ? a / bb : -((-a + bb - 1) / bb); };
-  const int dlo = fl(-p.w + 1 + h, b), dhi = fl(b - 1 + h, b);
+  const int b = p.bins[0];
+  // neighbour bins holding window starts that reach the box: floor((-w + 1)/b) .. 0
+  const int dlo = -((p.w - 1 + b - 1) / b), dhi = 0;
   const int nbox = (int)p.nbins;
   if (p.d == 3) {
     // slices per box, their prefix sums, then the sliced gather and the partial reduction
     k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np);
     k_scan2<<<1, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
+    k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item);
     k_spread_box3<T><<<6 * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
-                                                    (const T*)ws.cwp, ws.box_so, ws.box_po, (T*)ws.part, grid);
+                                                    (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
+                                                    (T*)ws.part, grid);
     k_box_reduce<T><<<nbox, 256, 0, st>>>(g, ws.box_so, ws.box_po, (const T*)ws.part, grid);
   } else
     k_spread_gather<T, 2><<<nbox, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
