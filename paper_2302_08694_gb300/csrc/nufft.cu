@@ -397,8 +397,10 @@ __device__ __forceinline__ dd weight_of<dd>(double delta, int q, int w, double b
 //   thread adds the contributions to its own run of 8 cells of one component in
 //   registers. Each grid cell is written once, by plain stores (no atomics, no
 //   separate zero fill); boxes with no candidate write zeros.
-// k_interp_warp: one warp per point; lane = qx + w k reads row segments of the window
-//   (coalesced along x) and accumulates g * (w_y w_z), then multiplies by w_x.
+// k_interp_warp: one warp per point; the warp first tabulates the window's rows (their
+//   grid offsets and weight products w_y w_z) in shared memory, then lane = qx + w k reads
+//   row segments of the window (coalesced along x), four rows at a time, accumulates
+//   g * (w_y w_z), and finally multiplies by w_x.
 // ---------------------------------------------------------------------------
 constexpr int kSeg = 8;  // cells per thread run along x in the gather
 
@@ -588,108 +590,123 @@ __device__ __forceinline__ void zero_empty_boxes(const PointGeom& g, const int* 
 
 // 3D gather with an 8^3 box: warp z owns the box plane oz + z, lane l owns the cells
 // (x, y) = (l % 8, l / 8) and (l % 8, l / 8 + 4) of that plane for all three
-// components, in registers. The candidates (points of the 27 neighbouring bins) are
-// staged in shared memory; a candidate whose window misses a warp's plane is skipped
-// by the whole warp.
+// components, in registers. The candidates (points of the neighbouring bins, taken in
+// bin order) are staged in shared memory, a chunk at a time and double buffered, as
+// box-relative weights: for axis a and box offset l, the kernel weight of the cell
+// o_a + l, or zero where the point's window misses it. A lane then needs no index
+// arithmetic (a zero weight adds nothing), and a candidate whose window misses a
+// warp's plane is skipped by the whole warp.
 constexpr int kBoxChunk = 64;
+__device__ __forceinline__ bool is_zero(float v) { return v == 0.0f; }
+__device__ __forceinline__ bool is_zero(dd v) { return v.hi == 0.0f; }
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
               const T* __restrict__ W, const T* __restrict__ Cw, const int* __restrict__ slice_off,
               const int* __restrict__ box_item, const int* __restrict__ part_off, T* __restrict__ part,
               T* __restrict__ grid) {
-  __shared__ T sW[kBoxChunk * 3 * kMaxW];
-  __shared__ T sC[kBoxChunk * 3];
-  __shared__ int sI[kBoxChunk * 3];
-  __shared__ int sRange[2 * 32];
+  __shared__ T sB[2][kBoxChunk * 24];  // [c][axis][8] box-relative weights
+  __shared__ T sC[2][kBoxChunk * 3];
+  __shared__ int sStart[32], sPre[33];  // non-empty neighbour ranges: first point, prefix of lengths
   __shared__ int sNr;
   const int w = g.w, nf = g.nf, M = g.M;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int lx = lane & 7, ly = lane >> 3;
   const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
   const int nslices = slice_off[nbox];
   for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
     const int box = box_item[sl], ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
     const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
-    const int ox = Bx * 8, oy = By * 8, oz = Bz * 8;
-    const int cx = ox + (lane & 7), cy0 = oy + (lane >> 3), cz = oz + warp;
+    const int o[3] = {Bx * 8, By * 8, Bz * 8};
     __syncthreads();
     if (warp == 0) {  // candidate ranges of the neighbouring bins, in one round trip
       int bin = 0;
       const int nnb = nb_list(g, dlo, dhi, Bx, By, Bz, lane, &bin);
-      int p0 = 0, p1 = 0;
-      if (lane < nnb) { p0 = offsets[bin]; p1 = offsets[bin + 1]; }
-      const unsigned nonempty = __ballot_sync(0xffffffffu, p1 > p0);
-      if (p1 > p0) {
-        const int slot = __popc(nonempty & ((1u << lane) - 1u));
-        sRange[2 * slot] = p0;
-        sRange[2 * slot + 1] = p1;
+      int p0 = 0, len = 0;
+      if (lane < nnb) { p0 = offsets[bin]; len = offsets[bin + 1] - p0; }
+      int incl = len;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
       }
-      if (lane == 0) sNr = __popc(nonempty);
+      const unsigned nonempty = __ballot_sync(0xffffffffu, len > 0);
+      if (len > 0) {
+        const int slot = __popc(nonempty & ((1u << lane) - 1u));
+        sStart[slot] = p0;
+        sPre[slot] = incl - len;
+      }
+      if (lane == 31) { sNr = __popc(nonempty); sPre[__popc(nonempty)] = incl; }
     }
+    __syncthreads();
+    const int nr = sNr;
+    // this slice takes candidates [ks * slice, (ks + 1) * slice) of the concatenated ranges
+    const int f0 = ks * g.slice, f1 = min(sPre[nr], f0 + g.slice);
+    // stage candidates [fa, fb) into buffer bb: one thread per (candidate, axis)
+    auto stage = [&](int fa, int fb, int bb) {
+      for (int i = threadIdx.x; i < (fb - fa) * 3; i += blockDim.x) {
+        const int c = i / 3, a = i - 3 * c, f = fa + c;
+        int lo = 0, hi = nr - 1;  // last range with sPre <= f
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sPre[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const long long sp = sStart[lo] + (f - sPre[lo]);
+        int q0 = o[a] - i0s[(long long)a * M + sp];  // (o_a - i0) mod nf
+        q0 += (q0 < 0) ? nf : 0; q0 -= (q0 >= nf) ? nf : 0;
+        const T* wsrc = W + sp * 3 * w + a * w;
+        T* dst = &sB[bb][(c * 3 + a) * 8];
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+          int q = q0 + l;
+          q -= (q >= nf) ? nf : 0;
+          dst[l] = (q < w) ? wsrc[q] : T(0);
+        }
+        sC[bb][c * 3 + a] = Cw[sp * 3 + a];
+      }
+    };
     T acc[2][3];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
       for (int a = 0; a < 3; ++a) acc[k][a] = T(0);
+    int bb = 0;
+    stage(f0, min(f1, f0 + kBoxChunk), 0);
     __syncthreads();
-    const int nr = sNr;
-    // this slice takes candidates [ks * kSliceCand, (ks + 1) * kSliceCand) of the concatenated ranges
-    int skip = ks * g.slice, take = g.slice;
-    for (int ri = 0; ri < nr && take > 0; ++ri) {
-      int r0 = sRange[2 * ri], r1 = sRange[2 * ri + 1];
-      const int len = r1 - r0;
-      if (skip >= len) { skip -= len; continue; }
-      r0 += skip;
-      skip = 0;
-      r1 = min(r1, r0 + take);
-      take -= r1 - r0;
-      for (int c0 = r0; c0 < r1; c0 += kBoxChunk) {
-        const int nc = min(kBoxChunk, r1 - c0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nc * 3 * w; i += blockDim.x) {
-          const int c = i / (3 * w), r = i - c * (3 * w);
-          sW[c * 3 * kMaxW + r] = W[(long long)(c0 + c) * 3 * w + r];
-        }
-        for (int i = threadIdx.x; i < nc * 3; i += blockDim.x) {
-          sC[i] = Cw[(long long)c0 * 3 + i];
-          const int c = i / 3, a = i - 3 * c;
-          sI[c * 3 + a] = i0s[(long long)a * M + c0 + c];
-        }
-        __syncthreads();
-        for (int c = 0; c < nc; ++c) {
-          int qz = cz - sI[c * 3 + 2];
-          qz += (qz < 0) ? nf : 0; qz -= (qz >= nf) ? nf : 0;
-          if (qz >= w) continue;  // uniform across the warp
-          int qx = cx - sI[c * 3 + 0];
-          qx += (qx < 0) ? nf : 0; qx -= (qx >= nf) ? nf : 0;
-          if (qx >= w) continue;
-          const T* wc = sW + c * 3 * kMaxW;  // axis a at offset a * w
-          const T wxz = wc[qx] * wc[2 * w + qz];
+    for (int c0 = f0; c0 < f1; c0 += kBoxChunk) {
+      const int nc = min(kBoxChunk, f1 - c0);
+      if (c0 + kBoxChunk < f1) stage(c0 + kBoxChunk, min(f1, c0 + 2 * kBoxChunk), bb ^ 1);
+      const T* B = sB[bb];
+      const T* Cc = sC[bb];
+      for (int c = 0; c < nc; ++c) {
+        const T wz = B[c * 24 + 16 + warp];
+        if (is_zero(wz)) continue;  // uniform across the warp
+        const T wxz = B[c * 24 + lx] * wz;
+        const T t0 = wxz * B[c * 24 + 8 + ly], t1 = wxz * B[c * 24 + 12 + ly];
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            int qy = cy0 + 4 * k - sI[c * 3 + 1];
-            qy += (qy < 0) ? nf : 0; qy -= (qy >= nf) ? nf : 0;
-            if (qy < w) {
-              const T wt = wxz * wc[w + qy];
-#pragma unroll
-              for (int a = 0; a < 3; ++a) fma_acc(acc[k][a], sC[c * 3 + a], wt);
-            }
-          }
+        for (int a = 0; a < 3; ++a) {
+          const T cv = Cc[c * 3 + a];
+          fma_acc(acc[0][a], cv, t0);
+          fma_acc(acc[1][a], cv, t1);
         }
       }
+      __syncthreads();
+      bb ^= 1;
     }
     const long long gcells = (long long)nf * nf * nf;
+    const int cx = o[0] + lx, cz = o[2] + warp;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const int ly = (lane >> 3) + 4 * k;
+      const int yk = ly + 4 * k;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T v = acc_norm(acc[k][a]);
         if (K == 1) {
-          grid[a * gcells + ((long long)cz * nf + (cy0 + 4 * k)) * nf + cx] = v;
+          grid[a * gcells + ((long long)cz * nf + (o[1] + yk)) * nf + cx] = v;
         } else {
           // partial box, layout [slot][a][z][y][x]
-          part[((long long)(part_off[box] + ks) * 3 + a) * 512 + (warp * 8 + ly) * 8 + (lane & 7)] = v;
+          part[((long long)(part_off[box] + ks) * 3 + a) * 512 + (warp * 8 + yk) * 8 + lx] = v;
         }
       }
     }
@@ -720,6 +737,10 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256)
 k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__ i0s, const T* __restrict__ W,
               const T* __restrict__ grid, double* __restrict__ U) {
+  // per warp: the window's rows (y, z) as grid offsets and their weight products w_y w_z
+  constexpr int kRows = (D == 3) ? kMaxW * kMaxW : kMaxW;
+  __shared__ int sOff[8][kRows];
+  __shared__ T sWyz[8][kRows];
   const int w = g.w, nf = g.nf, M = g.M;
   const int nwarp = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int K = 32 / w;                 // lane groups
@@ -727,48 +748,51 @@ k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__
   const bool on = kg < K;
   const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
   const int nrow = (D == 3) ? w * w : w;
+  int* off = sOff[warp];
+  T* wyz = sWyz[warp];
   for (long long s = (long long)blockIdx.x * nwarp + warp; s < M; s += (long long)gridDim.x * nwarp) {
     const T* ws = W + s * D * w;
     const int bx = i0s[s], by = i0s[(long long)M + s], bz = (D == 3) ? i0s[2LL * M + s] : 0;
+    __syncwarp();
+    for (int r = lane; r < nrow; r += 32) {
+      const int qz = (D == 3) ? r / w : 0, qy = r - qz * w;
+      int gy = by + qy, gz = bz + qz;
+      gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
+      if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
+      off[r] = (D == 3) ? (gz * nf + gy) * nf : gy * nf;
+      T v = ws[w + qy];
+      if (D == 3) v = v * ws[2 * w + qz];
+      wyz[r] = v;
+    }
+    __syncwarp();
     int gx = bx + qx;
     gx += (gx < 0) ? nf : 0; gx -= (gx >= nf) ? nf : 0;
+    const T* gp = grid + gx;
     T acc[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] = T(0);
     if (on) {
-      // two rows per iteration: both rows' loads are issued before either row's arithmetic
+      // four rows per iteration: all loads are issued before the arithmetic
       int r = kg;
-      for (; r + K < nrow; r += 2 * K) {
-        T g0[D], g1[D], wyz[2];
+      for (; r + 3 * K < nrow; r += 4 * K) {
+        T gv[4][D], wv[4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int rr = r + u * K;
-          const int qy = rr % w, qz = (D == 3) ? rr / w : 0;
-          int gy = by + qy, gz = bz + qz;
-          gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
-          if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
-          const long long cell = ((long long)gz * nf + gy) * nf + gx;
+        for (int u = 0; u < 4; ++u) {
+          const int o = off[r + u * K];
 #pragma unroll
-          for (int a = 0; a < D; ++a) (u ? g1 : g0)[a] = grid[a * gcells + cell];
-          wyz[u] = ws[w + qy];
-          if (D == 3) wyz[u] = wyz[u] * ws[2 * w + qz];
+          for (int a = 0; a < D; ++a) gv[u][a] = gp[a * gcells + o];
+          wv[u] = wyz[r + u * K];
         }
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          fma_acc(acc[a], g0[a], wyz[0]);
-          fma_acc(acc[a], g1[a], wyz[1]);
-        }
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int a = 0; a < D; ++a) fma_acc(acc[a], gv[u][a], wv[u]);
       }
       for (; r < nrow; r += K) {
-        const int qy = r % w, qz = (D == 3) ? r / w : 0;
-        int gy = by + qy, gz = bz + qz;
-        gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
-        if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
-        T wyz = ws[w + qy];
-        if (D == 3) wyz = wyz * ws[2 * w + qz];
-        const long long cell = ((long long)gz * nf + gy) * nf + gx;
+        const int o = off[r];
+        const T wv = wyz[r];
 #pragma unroll
-        for (int a = 0; a < D; ++a) fma_acc(acc[a], grid[a * gcells + cell], wyz);
+        for (int a = 0; a < D; ++a) fma_acc(acc[a], gp[a * gcells + o], wv);
       }
       const T wxq = ws[qx];
 #pragma unroll
@@ -858,7 +882,12 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
     k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np);
     k_scan2<<<1, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
     k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item);
-    k_spread_box3<T><<<6 * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
+    static const int per_sm = [] {
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spread_box3<T>, 256, 0) != cudaSuccess || n < 1) n = 4;
+      return n;
+    }();
+    k_spread_box3<T><<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
                                                     (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
                                                     (T*)ws.part, grid);
     k_box_reduce<T><<<nbox, 256, 0, st>>>(g, ws.box_so, ws.box_po, (const T*)ws.part, grid);
