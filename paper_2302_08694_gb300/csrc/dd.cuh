@@ -13,7 +13,7 @@
 
 namespace fsib {
 
-struct dd {
+struct __align__(8) dd {
   float hi, lo;
   dd() = default;
   __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
@@ -25,7 +25,7 @@ struct dd {
   __host__ __device__ double to_double() const { return (double)hi + (double)lo; }
 };
 
-struct dd2 {
+struct __align__(16) dd2 {  // 16-byte aligned so that a complex value moves as one vector
   dd x, y;
 };
 

@@ -21,6 +21,15 @@ template <> __device__ __forceinline__ dd sqrt3_2<dd>() {
   return v;
 }
 
+// 1/sqrt(2) in each arithmetic type
+template <typename T> __device__ __forceinline__ T rsqrt2();
+template <> __device__ __forceinline__ float rsqrt2<float>() { return 0.707106781186547524400844362104849039f; }
+template <> __device__ __forceinline__ double rsqrt2<double>() { return 0.707106781186547524400844362104849039; }
+template <> __device__ __forceinline__ dd rsqrt2<dd>() {
+  constexpr dd v(0.707106781186547524400844362104849039);
+  return v;
+}
+
 template <typename T, bool INV>
 __device__ __forceinline__ void dft2(C<T>* v) {
   C<T> a = v[0], b = v[1];

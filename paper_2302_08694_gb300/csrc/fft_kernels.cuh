@@ -14,8 +14,9 @@
 // Kernel and launcher templates; fft_float.cu, fft_dd.cu and fft_double.cu instantiate
 // them per arithmetic type so that the three compile in parallel.
 #pragma once
+#include <algorithm>
 #include <type_traits>
-#include "fft_device.cuh"
+#include "wfft.cuh"
 
 namespace fsib {
 
@@ -242,6 +243,158 @@ k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long 
 }
 
 // ---------------------------------------------------------------------------
+// Row passes with the warp-level transform (lengths with a warp plan, wfft.cuh).
+// Persistent blocks; each warp takes 32/L row pairs at a time, one per L lanes.
+// Shared memory: the twiddle table (N values), then per line its exchange buffer
+// (and, in the product pass, the d inverse-transformed components).
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(256)
+k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
+            const C<T>* __restrict__ twg) {
+  constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int l = lane % L, sub = lane / L;
+  C<T>* buf = tw + N + (warp * LPW + sub) * SL;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  __syncthreads();
+  const int h = Nk / 2;
+  for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
+    const long long pr = g * LPW + sub;
+    const bool valid = pr < npairs;
+    C<T> v[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+      v[i] = valid ? pack_rows<T>(in + (2 * pr) * h, in + (2 * pr + 1) * h, l + L * i, N, h) : mk<T>(T(0), T(0));
+    wfft<T, true, N>(v, buf, l, tw);
+    if (valid) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const int x = wfft_out_index<N>(l, i);
+        out[(2 * pr) * N + x] = v[i].x;
+        out[(2 * pr + 1) * N + x] = v[i].y;
+      }
+    }
+  }
+}
+
+// Untangle the spectra of two real rows packed as Z = A + iB: A[k] = (Z[k] + conj Z[N-k]) / 2,
+// B[k] = (Z[k] - conj Z[N-k]) / 2i, for the kept modes k < h. v holds Z in output order.
+template <typename T, int N>
+__device__ __forceinline__ void wfft_untangle(const C<T> (&v)[wfft_M(N)], C<T>* buf, int l, bool valid, int h,
+                                              C<T>* __restrict__ outA, C<T>* __restrict__ outB) {
+  constexpr int M = wfft_M(N), L = wfft_L(N);
+#pragma unroll
+  for (int i = 0; i < M; ++i) buf[wfft_out_index<N>(l, i)] = v[i];
+  __syncwarp();
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int k = l + L * i;
+      if (k < h) {
+        const C<T> Z = buf[k];
+        const C<T> Zc = cconj<T>(buf[k == 0 ? 0 : N - k]);
+        const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
+        outA[k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
+        outB[k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256)
+k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
+            const C<T>* __restrict__ twg) {
+  constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int l = lane % L, sub = lane / L;
+  C<T>* buf = tw + N + (warp * LPW + sub) * SL;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  __syncthreads();
+  const int h = Nk / 2;
+  for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
+    const long long pr = g * LPW + sub;
+    const bool valid = pr < npairs;
+    C<T> v[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int x = l + L * i;
+      v[i] = valid ? mk<T>(in[(2 * pr) * N + x], in[(2 * pr + 1) * N + x]) : mk<T>(T(0), T(0));
+    }
+    wfft<T, false, N>(v, buf, l, tw);
+    wfft_untangle<T, N>(v, buf, l, valid, h, out + (2 * pr) * h, out + (2 * pr + 1) * h);
+  }
+}
+
+// Products of the velocity components (three-halves rule), one row pair per L lanes:
+// inverse transforms of the d components into shared memory, then for each product
+// u_a u_b its forward transform and untangle. Blocks of 128 threads.
+template <typename T, int N>
+__global__ void __launch_bounds__(128)
+k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows, int Nk,
+                const C<T>* __restrict__ twg) {
+  constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int l = lane % L, sub = lane / L;
+  C<T>* U = tw + N + (warp * LPW + sub) * 4 * SL;  // [d][SL] components, then the exchange buffer
+  C<T>* buf = U + 3 * SL;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  __syncthreads();
+  const int h = Nk / 2, np = d * (d + 1) / 2;
+  const long long npairs = nrows / 2;
+  for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
+    const long long pr = g * LPW + sub;
+    const bool valid = pr < npairs;
+    for (int c = 0; c < d; ++c) {
+      C<T> v[M];
+      const C<T>* base = in + ((long long)c * nrows + 2 * pr) * h;
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+        v[i] = valid ? pack_rows<T>(base, base + h, l + L * i, N, h) : mk<T>(T(0), T(0));
+      wfft<T, true, N>(v, buf, l, tw);
+#pragma unroll
+      for (int i = 0; i < M; ++i) U[c * SL + wfft_out_index<N>(l, i)] = v[i];
+    }
+    __syncwarp();
+    // products: the real part holds row 2p, the imaginary part row 2p+1
+    for (int ab = 0; ab < np; ++ab) {
+      int ca, cb;
+      if (d == 3) { ca = (ab < 3) ? 0 : (ab < 5 ? 1 : 2); cb = (ab < 3) ? ab : (ab < 5 ? ab - 2 : 2); }
+      else { ca = (ab < 2) ? 0 : 1; cb = (ab < 2) ? ab : 1; }
+      C<T> v[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const C<T> ua = U[ca * SL + l + L * i], ub = U[cb * SL + l + L * i];
+        v[i] = mk<T>(ua.x * ub.x, ua.y * ub.y);
+      }
+      wfft<T, false, N>(v, buf, l, tw);
+      C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
+      wfft_untangle<T, N>(v, buf, l, valid, h, ob, ob + h);
+    }
+  }
+}
+
+// Persistent grid of a warp-transform kernel: resident blocks per SM times the SMs,
+// or fewer when there is less work.
+template <typename K>
+static unsigned wrows_grid(K kern, int threads, size_t smem, long long groups) {
+  int dev = 0, sms = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess || per < 1) per = 1;
+  const long long need = (groups + threads / 32 - 1) / (threads / 32);
+  return (unsigned)std::max<long long>(1, std::min<long long>(need, (long long)per * sms));
+}
+
+// ---------------------------------------------------------------------------
 // Launchers: each dispatches on the FFT length (a compile-time kernel for the
 // lengths in FSIB_FFT_SIZES, the runtime-length kernel otherwise).
 // ---------------------------------------------------------------------------
@@ -291,6 +444,15 @@ void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const 
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
   with_fft_len(fl.n, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    if constexpr (wfft_has(NC)) {
+      constexpr int LPW = 32 / wfft_L(NC);
+      const size_t ws = sizeof(C<T>) * (size_t)(NC + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
+      auto k = k_wrows_r2c<T, NC>;
+      raise_smem_limit(reinterpret_cast<const void*>(k));
+      k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off);
+      return;
+    }
     auto k = k_rows_r2c<T, decltype(nc)::value>;
     raise_smem_limit(reinterpret_cast<const void*>(k));
     k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
@@ -305,6 +467,15 @@ void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const 
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
   with_fft_len(fl.n, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    if constexpr (wfft_has(NC)) {
+      constexpr int LPW = 32 / wfft_L(NC);
+      const size_t ws = sizeof(C<T>) * (size_t)(NC + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
+      auto k = k_wrows_c2r<T, NC>;
+      raise_smem_limit(reinterpret_cast<const void*>(k));
+      k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off);
+      return;
+    }
     auto k = k_rows_c2r<T, decltype(nc)::value>;
     raise_smem_limit(reinterpret_cast<const void*>(k));
     k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
@@ -319,6 +490,15 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * 6 * (fl.n + 1));
   with_fft_len(fl.n, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    if constexpr (wfft_has(NC)) {
+      constexpr int LPW = 32 / wfft_L(NC);
+      const size_t ws = sizeof(C<T>) * (size_t)(NC + 4 * LPW * 4 * wfft_stride(NC, (int)sizeof(C<T>)));
+      auto k = k_wrows_product<T, NC>;
+      raise_smem_limit(reinterpret_cast<const void*>(k));
+      k<<<wrows_grid(k, 128, ws, (npairs + LPW - 1) / LPW), 128, ws, st>>>(in, out, d, nrows, Nk, tw + fl.tw_off);
+      return;
+    }
     auto k = k_rows_product<T, decltype(nc)::value>;
     raise_smem_limit(reinterpret_cast<const void*>(k));
     k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, d, nrows, Nk, fl, tw);

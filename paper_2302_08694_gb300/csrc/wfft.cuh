@@ -1,0 +1,159 @@
+// Warp-level FFT of one line held in registers (row passes of the lengths below).
+//
+// A line of length N is owned by L lanes of a warp (32/L lines per warp); lane l holds
+// M = N/L elements. The transform is the self-sorting (Stockham) factorisation of
+// fft_device.cuh with the radix sequence R_0 = M, R_1, ... chosen so that every radix
+// divides M: in stage s each lane computes M/R_s butterflies j = l + L b entirely in
+// registers. Stage 0 reads x[l + L i] (i < M), which is the order in which the lane
+// loads its line from global memory. Between stages the lanes exchange values through a
+// per-line shared-memory buffer, synchronised with __syncwarp only; each exchange uses an
+// XOR swizzle of the element index (e ^ ((e >> sh) & mk)) chosen so that the stores and
+// the loads of a warp hit distinct banks. After the last stage lane l holds
+// X[l + L b + (N/R_last) r] in v[b R_last + r].
+#pragma once
+#include "fft_device.cuh"
+
+namespace fsib {
+
+// Lengths with a warp plan: 64, 128, 256 (M = 8) and 48, 96, 192 (M = 12).
+constexpr bool wfft_has(int n) { return n == 64 || n == 128 || n == 256 || n == 48 || n == 96 || n == 192; }
+constexpr int wfft_M(int n) { return (n == 48 || n == 96 || n == 192) ? 12 : 8; }
+constexpr int wfft_L(int n) { return n / wfft_M(n); }
+constexpr int wfft_radix(int n, int s) {
+  return n == 64    ? (s == 0 ? 8 : s == 1 ? 8 : 0)
+         : n == 128 ? (s == 0 ? 8 : s == 1 ? 4 : s == 2 ? 4 : 0)
+         : n == 256 ? (s == 0 ? 8 : s == 1 ? 8 : s == 2 ? 4 : 0)
+         : n == 48  ? (s == 0 ? 12 : s == 1 ? 4 : 0)
+         : n == 96  ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 2 : 0)
+         : n == 192 ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 4 : 0)
+                    : 0;
+}
+constexpr int wfft_nstages(int n) {
+  int s = 0;
+  while (wfft_radix(n, s)) ++s;
+  return s;
+}
+// Swizzle of the exchange after stage ex for elements of E bytes: shift (hi 8 bits) and mask.
+constexpr int wfft_swz(int n, int E, int ex) {
+  return E == 8 ? (n == 64    ? (ex == 0 ? (3 << 8 | 7) : 0)
+                   : n == 128 ? (ex == 0 ? (3 << 8 | 15) : ex == 1 ? (2 << 8 | 15) : 0)
+                   : n == 256 ? (ex == 0 ? (3 << 8 | 15) : ex == 1 ? (3 << 8 | 15) : 0)
+                   : n == 48  ? (ex == 0 ? (2 << 8 | 3) : 0)
+                   : n == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
+                   : n == 192 ? (ex == 0 ? (2 << 8 | 15) : ex == 1 ? (2 << 8 | 7) : 0)
+                              : 0)
+                : (n == 64    ? (ex == 0 ? (3 << 8 | 7) : 0)
+                   : n == 128 ? (ex == 0 ? (3 << 8 | 7) : 0)
+                   : n == 256 ? (ex == 0 ? (3 << 8 | 7) : 0)
+                   : n == 48  ? (ex == 0 ? (2 << 8 | 3) : 0)
+                   : n == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
+                   : n == 192 ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
+                              : 0);
+}
+// Elements per line buffer (N plus bank padding).
+constexpr int wfft_stride(int n, int E) {
+  return n + (E == 8 ? (n == 64 ? 8 : n == 48 ? 4 : n == 96 ? 8 : 0) : (n == 48 ? 4 : 0));
+}
+template <int SW>
+__device__ __forceinline__ int wswz(int e) {
+  return (SW & 255) ? (e ^ ((e >> (SW >> 8)) & (SW & 255))) : e;
+}
+
+// 8-point DFT: radix-2 split into two 4-point DFTs.
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8(C<T>* v) {
+  C<T> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<T, INV>(e);
+  dft4<T, INV>(o);
+  const T h = rsqrt2<T>();
+  // w^k o[k], w = exp(-+ 2 pi i / 8)
+  const C<T> o1 = INV ? mk<T>((o[1].x - o[1].y) * h, (o[1].x + o[1].y) * h)
+                      : mk<T>((o[1].x + o[1].y) * h, (o[1].y - o[1].x) * h);
+  const C<T> o2 = INV ? cmul_i<T>(o[2]) : cmul_mi<T>(o[2]);
+  const C<T> o3 = INV ? mk<T>(-(o[3].x + o[3].y) * h, (o[3].x - o[3].y) * h)
+                      : mk<T>((o[3].y - o[3].x) * h, -(o[3].x + o[3].y) * h);
+  v[0] = cadd<T>(e[0], o[0]); v[4] = csub<T>(e[0], o[0]);
+  v[1] = cadd<T>(e[1], o1);   v[5] = csub<T>(e[1], o1);
+  v[2] = cadd<T>(e[2], o2);   v[6] = csub<T>(e[2], o2);
+  v[3] = cadd<T>(e[3], o3);   v[7] = csub<T>(e[3], o3);
+}
+
+// 12-point DFT by the prime-factor mapping 12 = 3 x 4 (no twiddles): input index
+// (4 n1 + 3 n2) mod 12, output index (4 k1 + 9 k2) mod 12.
+template <typename T, bool INV>
+__device__ __forceinline__ void dft12(C<T>* v) {
+  C<T> a[4][3];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 3; ++n1) a[n2][n1] = v[(4 * n1 + 3 * n2) % 12];
+    dft3<T, INV>(a[n2]);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    C<T> b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4<T, INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[(4 * k1 + 9 * k2) % 12] = b[k2];
+  }
+}
+
+template <typename T, bool INV, int R>
+__device__ __forceinline__ void dft_r(C<T>* v) {
+  if constexpr (R == 2) dft2<T, INV>(v);
+  else if constexpr (R == 4) dft4<T, INV>(v);
+  else if constexpr (R == 8) dft8<T, INV>(v);
+  else if constexpr (R == 12) dft12<T, INV>(v);
+}
+
+// Stage S of the warp transform (NS = product of the earlier radices). buf: this line's
+// exchange buffer; tw: the length-N twiddle table exp(-2 pi i k / N) in shared memory.
+template <typename T, bool INV, int N, int S = 0, int NS = 1>
+__device__ __forceinline__ void wfft(C<T> (&v)[wfft_M(N)], C<T>* buf, int l, const C<T>* __restrict__ tw) {
+  constexpr int M = wfft_M(N), L = wfft_L(N), R = wfft_radix(N, S), NB = M / R;
+  constexpr int E = (int)sizeof(C<T>);
+  if constexpr (S > 0) {
+    // gather this stage's inputs x[j + r N/R], j = l + L b, from the previous stage's outputs
+    constexpr int SW = wfft_swz(N, E, S - 1);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b * R + r] = buf[wswz<SW>(l + L * b + r * (N / R))];
+    __syncwarp();
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = l + L * b;
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C<T> w = tw[k * r * (N / (NS * R))];
+        if (INV) w = cconj<T>(w);
+        v[b * R + r] = cmul<T>(v[b * R + r], w);
+      }
+    }
+    dft_r<T, INV, R>(&v[b * R]);
+  }
+  if constexpr (S + 1 < wfft_nstages(N)) {
+    constexpr int SW = wfft_swz(N, E, S);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = l + L * b;
+      const int o = (j / NS) * NS * R + j % NS;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[wswz<SW>(o + r * NS)] = v[b * R + r];
+    }
+    __syncwarp();
+    wfft<T, INV, N, S + 1, NS * R>(v, buf, l, tw);
+  }
+}
+
+// Natural index of register slot i after the last stage.
+template <int N>
+__device__ __forceinline__ int wfft_out_index(int l, int i) {
+  constexpr int RL = wfft_radix(N, wfft_nstages(N) - 1);
+  return l + wfft_L(N) * (i / RL) + (N / RL) * (i % RL);
+}
+
+}  // namespace fsib
