@@ -245,7 +245,7 @@ k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long 
 // ---------------------------------------------------------------------------
 // Row passes with the warp-level transform (lengths with a warp plan, wfft.cuh).
 // Persistent blocks; each warp takes 32/L row pairs at a time, one per L lanes.
-// Shared memory: the twiddle table (N values), then per line its exchange buffer
+// Shared memory: the lane-ordered twiddle table, then per line its exchange buffer
 // (and, in the product pass, the d inverse-transformed components).
 // ---------------------------------------------------------------------------
 template <typename T, int N>
@@ -254,11 +254,11 @@ k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, 
             const C<T>* __restrict__ twg) {
   constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int l = lane % L, sub = lane / L;
-  C<T>* buf = tw + N + (warp * LPW + sub) * SL;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  C<T>* buf = tw + wfft_tw_size(N) + (warp * LPW + sub) * SL;
+  wfft_build_twiddles<T, N>(tw, twg);
   __syncthreads();
   const int h = Nk / 2;
   for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
@@ -311,11 +311,11 @@ k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, 
             const C<T>* __restrict__ twg) {
   constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int l = lane % L, sub = lane / L;
-  C<T>* buf = tw + N + (warp * LPW + sub) * SL;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  C<T>* buf = tw + wfft_tw_size(N) + (warp * LPW + sub) * SL;
+  wfft_build_twiddles<T, N>(tw, twg);
   __syncthreads();
   const int h = Nk / 2;
   for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
@@ -341,12 +341,12 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
                 const C<T>* __restrict__ twg) {
   constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int l = lane % L, sub = lane / L;
-  C<T>* U = tw + N + (warp * LPW + sub) * 4 * SL;  // [d][SL] components, then the exchange buffer
+  C<T>* U = tw + wfft_tw_size(N) + (warp * LPW + sub) * 4 * SL;  // [d][SL] components, then the exchange buffer
   C<T>* buf = U + 3 * SL;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  wfft_build_twiddles<T, N>(tw, twg);
   __syncthreads();
   const int h = Nk / 2, np = d * (d + 1) / 2;
   const long long npairs = nrows / 2;
@@ -378,6 +378,86 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
       wfft<T, false, N>(v, buf, l, tw);
       C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
       wfft_untangle<T, N>(v, buf, l, valid, h, ob, ob + h);
+    }
+  }
+}
+
+// Strided pass with the warp-level transform. A tile of kWP adjacent lines (along the
+// contiguous index q) x N positions is staged in shared memory with a row stride of
+// kWP + 1 elements, so that the column a line occupies is read and written without bank
+// conflicts; the sub-warps of a warp take lines kWP/LPW apart for the same reason. Loads
+// and stores move rows of kWP consecutive complex values. The pad/prune and the
+// multipliers are applied on the way in (inverse) or out (forward), as in k_fft_strided.
+constexpr int kWP = 16;
+template <typename T, bool INV, typename Tin, typename Tout, int N>
+__global__ void __launch_bounds__(256)
+k_wfft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, long long ntiles,
+               int ntile, Mult<T> mult, const C<T>* __restrict__ twg) {
+  constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
+  constexpr int PS = kWP + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* twl = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* tile = twl + wfft_tw_size(N);                    // [N][PS]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int l = lane % L, sub = lane / L;
+  C<T>* buf = tile + N * PS + (warp * LPW + sub) * SL;  // exchange buffer of this lane's line
+  wfft_build_twiddles<T, N>(twl, twg);
+  const int Lin = INV ? Nk : N, Lout = INV ? N : Nk;
+  const int h = Nk / 2;
+  for (long long blk = blockIdx.x; blk < ntiles; blk += gridDim.x) {
+    const long long co = blk / ntile;  // component * outer + outer index
+    const int q0 = (int)(blk % ntile) * kWP;
+    const C<Tin>* src = in + co * (long long)Lin * inner;
+    C<Tout>* dst = out + co * (long long)Lout * inner;
+    __syncthreads();  // the previous tile has been stored (and the twiddles are built)
+    for (int t = threadIdx.x; t < N * kWP; t += blockDim.x) {
+      const int p = t % kWP, i = t / kWP, q = q0 + p;
+      C<T> v = mk<T>(T(0), T(0));
+      if (q < inner) {
+        if (!INV) {
+          v = ccvt<T, Tin>(src[(long long)i * inner + q]);
+        } else {
+          const int si = (i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1);
+          if (si >= 0) {
+            T sc = mult.scale;
+            if (mult.dline) sc *= mult.dline[si];
+            if (mult.dplane) sc *= mult.dplane[q];
+            v = cscale<T>(ccvt<T, Tin>(src[(long long)si * inner + q]), sc);
+          }
+        }
+      }
+      tile[i * PS + p] = v;
+    }
+    __syncthreads();
+    for (int pb = warp; pb < kWP / LPW; pb += nwarp) {
+      const int p = pb + sub * (kWP / LPW);
+      C<T> v[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) v[i] = tile[(l + L * i) * PS + p];
+      wfft<T, INV, N>(v, buf, l, twl);
+#pragma unroll
+      for (int i = 0; i < M; ++i) tile[wfft_out_index<N>(l, i) * PS + p] = v[i];
+    }
+    __syncthreads();
+    if (!INV) {
+      for (int t = threadIdx.x; t < Nk * kWP; t += blockDim.x) {
+        const int p = t % kWP, io = t / kWP, q = q0 + p;
+        if (q >= inner) continue;
+        C<T> v = mk<T>(T(0), T(0));
+        if (io != h) {
+          const int fi = (io < h) ? io : io + (N - Nk);
+          T sc = mult.scale;
+          if (mult.dline) sc *= mult.dline[io];
+          if (mult.dplane) sc *= mult.dplane[q];
+          v = cscale<T>(tile[fi * PS + p], sc);
+        }
+        dst[(long long)io * inner + q] = ccvt<Tout, T>(v);
+      }
+    } else {
+      for (int t = threadIdx.x; t < N * kWP; t += blockDim.x) {
+        const int p = t % kWP, i = t / kWP, q = q0 + p;
+        if (q < inner) dst[(long long)i * inner + q] = ccvt<Tout, T>(tile[i * PS + p]);
+      }
     }
   }
 }
@@ -424,6 +504,25 @@ void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, in
   with_fft_len(fl.n, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
     constexpr int NCI = fwd_only ? 0 : NC, NCF = inv_only ? 0 : NC;
+    if constexpr (wfft_has(NC)) {
+      constexpr int LPW = 32 / wfft_L(NC);
+      const int wt = (inner + kWP - 1) / kWP;
+      const long long tiles = (long long)ncomp * outer * wt;
+      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + NC * (kWP + 1) +
+                                                8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
+      if (inverse && !fwd_only) {
+        auto k = k_wfft_strided<T, true, Tin, Tout, NC>;
+        raise_smem_limit(reinterpret_cast<const void*>(k));
+        k<<<wrows_grid(k, 256, ws, tiles * 8), 256, ws, st>>>(in, out, inner, Nk, tiles, wt, mult, tw + fl.tw_off);
+        return;
+      }
+      if (!inverse && !inv_only) {
+        auto k = k_wfft_strided<T, false, Tin, Tout, NC>;
+        raise_smem_limit(reinterpret_cast<const void*>(k));
+        k<<<wrows_grid(k, 256, ws, tiles * 8), 256, ws, st>>>(in, out, inner, Nk, tiles, wt, mult, tw + fl.tw_off);
+        return;
+      }
+    }
     if (inverse) {
       auto k = k_fft_strided<T, true, Tin, Tout, NCI>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
@@ -447,7 +546,7 @@ void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const 
     constexpr int NC = decltype(nc)::value;
     if constexpr (wfft_has(NC)) {
       constexpr int LPW = 32 / wfft_L(NC);
-      const size_t ws = sizeof(C<T>) * (size_t)(NC + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
+      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_r2c<T, NC>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
       k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off);
@@ -470,7 +569,7 @@ void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const 
     constexpr int NC = decltype(nc)::value;
     if constexpr (wfft_has(NC)) {
       constexpr int LPW = 32 / wfft_L(NC);
-      const size_t ws = sizeof(C<T>) * (size_t)(NC + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
+      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_c2r<T, NC>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
       k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off);
@@ -493,7 +592,7 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
     constexpr int NC = decltype(nc)::value;
     if constexpr (wfft_has(NC)) {
       constexpr int LPW = 32 / wfft_L(NC);
-      const size_t ws = sizeof(C<T>) * (size_t)(NC + 4 * LPW * 4 * wfft_stride(NC, (int)sizeof(C<T>)));
+      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 4 * LPW * 4 * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_product<T, NC>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
       k<<<wrows_grid(k, 128, ws, (npairs + LPW - 1) / LPW), 128, ws, st>>>(in, out, d, nrows, Nk, tw + fl.tw_off);

@@ -35,20 +35,36 @@ __global__ void k_force_curve(const double* __restrict__ X, double* __restrict__
 }
 
 // Springs: c_i = sum_j K_ij (X_j - X_i), CSR adjacency (omega = 1).
+// Eight lanes per vertex: the lanes take the vertex's CSR entries in strides of eight
+// and reduce with shuffles, so that a vertex of high degree (a pole of a latitude-
+// longitude mesh joins every point of the first ring) costs few rounds.
 __global__ void k_force_mesh(const double* __restrict__ X, double* __restrict__ c, int M,
                              const int* __restrict__ ptr, const int* __restrict__ col,
                              const double* __restrict__ kv) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+  const int sl = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3;
+  // warp-uniform loop over groups of four vertices (the shuffles need the whole warp)
+  for (long long w0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; w0 < M;
+       w0 += (((long long)gridDim.x * blockDim.x) >> 5) * 4) {
+    const int i = (int)(w0 + sub);
+    const bool ok = i < M;
     double f0 = 0, f1 = 0, f2 = 0;
-    const double x0 = X[i], x1 = X[M + i], x2 = X[2LL * M + i];
-    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
-      const int j = col[e];
-      const double k = kv[e];
-      f0 += k * (X[j] - x0);
-      f1 += k * (X[M + j] - x1);
-      f2 += k * (X[2LL * M + j] - x2);
+    if (ok) {
+      const double x0 = X[i], x1 = X[M + i], x2 = X[2LL * M + i];
+      for (int e = ptr[i] + sl; e < ptr[i + 1]; e += 8) {
+        const int j = col[e];
+        const double k = kv[e];
+        f0 += k * (X[j] - x0);
+        f1 += k * (X[M + j] - x1);
+        f2 += k * (X[2LL * M + j] - x2);
+      }
     }
-    c[i] = f0; c[M + i] = f1; c[2LL * M + i] = f2;
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+      f0 += __shfl_xor_sync(0xffffffffu, f0, off, 8);
+      f1 += __shfl_xor_sync(0xffffffffu, f1, off, 8);
+      f2 += __shfl_xor_sync(0xffffffffu, f2, off, 8);
+    }
+    if (ok && sl == 0) { c[i] = f0; c[M + i] = f1; c[2LL * M + i] = f2; }
   }
 }
 
@@ -57,7 +73,7 @@ void launch_force(const Plan& p, const Workspace& ws, const double* X, double* c
     const double dth = 2.0 * 3.14159265358979323846 / p.M;
     k_force_curve<<<blocks_for(p.M), 256, 0, st>>>(X, c, p.M, ws.curve_K / dth);
   } else {
-    k_force_mesh<<<blocks_for(p.M), 256, 0, st>>>(X, c, p.M, ws.csr_ptr, ws.csr_col, ws.csr_k);
+    k_force_mesh<<<blocks_for(8LL * p.M), 256, 0, st>>>(X, c, p.M, ws.csr_ptr, ws.csr_col, ws.csr_k);
   }
 }
 

@@ -49,119 +49,170 @@ __device__ __forceinline__ int bin_of_start(int i0, int nf, int b, int nb) {
   return min(r / b, nb - 1);
 }
 
+// Bin of every point and its rank within the bin. Lanes of a warp that fall in the same
+// bin (neighbouring points usually do) share one atomic increment.
 __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of,
                             int* __restrict__ rank, int* __restrict__ counts) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.M; j += gridDim.x * blockDim.x) {
-    long long bin = 0, mul = 1;
-    for (int a = 0; a < g.d; ++a) {
-      const double t = grid_coord(X[(long long)a * g.M + j], g.L, g.nf);
-      const int B = bin_of_start(window_start(t, g.w), g.nf, g.b[a], g.nb[a]);
-      bin += B * mul;
-      mul *= g.nb[a];
+  const int lane = threadIdx.x & 31;
+  for (long long j0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; j0 < g.M;
+       j0 += (long long)gridDim.x * blockDim.x) {
+    const long long j = j0 + lane;
+    const bool ok = j < g.M;
+    int bin = -1;
+    if (ok) {
+      long long b = 0, mul = 1;
+      for (int a = 0; a < g.d; ++a) {
+        const double t = grid_coord(X[(long long)a * g.M + j], g.L, g.nf);
+        const int B = bin_of_start(window_start(t, g.w), g.nf, g.b[a], g.nb[a]);
+        b += B * mul;
+        mul *= g.nb[a];
+      }
+      bin = (int)b;
     }
-    bin_of[j] = (int)bin;
-    rank[j] = atomicAdd(&counts[bin], 1);
+    const unsigned same = __match_any_sync(0xffffffffu, bin);
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (ok && lane == leader) base = atomicAdd(&counts[bin], __popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (ok) {
+      bin_of[j] = bin;
+      rank[j] = base + __popc(same & ((1u << lane) - 1u));
+    }
   }
 }
 
-// Exclusive scan of the bin counts and the list of occupied bins, in one block.
-// The bins are processed in tiles of kScanThreads * 8; each thread owns 8
-// consecutive bins of a tile (one 32-byte load), warps scan with shuffles, and
-// a running carry links the tiles.
+// Single-block exclusive scans. A tile is kScanThreads x kScanPer consecutive entries;
+// each thread owns kScanPer of them (eight 16-byte loads when the tile is full), scans
+// them in registers, and the block combines the thread totals with warp shuffles and one
+// pair of barriers per tile; a running carry links the tiles.
 constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 8;
+constexpr int kScanPer = 32;
+
+template <int PER>
+__device__ __forceinline__ void scan_load(const int* __restrict__ p, long long i0, long long n, int (&c)[PER]) {
+  if (i0 + PER <= n) {
+    const int4* q = reinterpret_cast<const int4*>(p + i0);
+#pragma unroll
+    for (int k = 0; k < PER / 4; ++k) {
+      const int4 v = q[k];
+      c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) c[k] = (i0 + k < n) ? p[i0 + k] : 0;
+  }
+}
+
+template <int PER>
+__device__ __forceinline__ void scan_store(int* __restrict__ p, long long i0, long long n, const int (&c)[PER]) {
+  if (i0 + PER <= n) {
+    int4* q = reinterpret_cast<int4*>(p + i0);
+#pragma unroll
+    for (int k = 0; k < PER / 4; ++k) q[k] = make_int4(c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+      if (i0 + k < n) p[i0 + k] = c[k];
+  }
+}
+
+// Block-wide exclusive prefix of NV per-thread totals (in place); tot receives the block totals.
+template <int NV>
+__device__ __forceinline__ void block_prefix(int (&v)[NV], int (&tot)[NV], int (*wsum)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    incl[q] = v[q];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl[q], off);
+      if (lane >= off) incl[q] += t;
+    }
+    if (lane == 31) wsum[q][warp] = incl[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      int x = wsum[q][lane];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += t;
+      }
+      wsum[q][lane] = x;  // inclusive over warps
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    v[q] = (warp ? wsum[q][warp - 1] : 0) + incl[q] - v[q];
+    tot[q] = wsum[q][31];
+  }
+  __syncthreads();  // wsum is reused by the next tile
+}
+
+// Bin offsets (exclusive scan of the counts, total at [nbins]) and the list of occupied bins.
 __global__ void __launch_bounds__(kScanThreads)
 k_bin_scan(const int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
            int* __restrict__ occ, int* __restrict__ nocc) {
-  __shared__ int w_sum[32], w_occ[32];
-  __shared__ int carry[2];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) { carry[0] = 0; carry[1] = 0; }
-  __syncthreads();
+  __shared__ int wsum[2][32];
+  int carry = 0, carry_o = 0;
   for (long long base = 0; base < nbins; base += (long long)kScanThreads * kScanPer) {
-    const long long i0 = base + (long long)tid * kScanPer;
+    const long long i0 = base + (long long)threadIdx.x * kScanPer;
     int c[kScanPer];
-    int s = 0, o = 0;
+    scan_load(counts, i0, nbins, c);
+    int v[2] = {0, 0}, tot[2];
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) { v[0] += c[k]; v[1] += (c[k] > 0); }
+    block_prefix<2>(v, tot, wsum);
+    int run = carry + v[0], runo = carry_o + v[1];
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      c[k] = (i0 + k < nbins) ? counts[i0 + k] : 0;
-      s += c[k];
-      o += (c[k] > 0);
+      if (c[k] > 0) occ[runo++] = (int)(i0 + k);
+      const int t = c[k];
+      c[k] = run;
+      run += t;
     }
-    int is = s, io = o;  // warp inclusive scan
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int ts = __shfl_up_sync(0xffffffffu, is, off), to = __shfl_up_sync(0xffffffffu, io, off);
-      if (lane >= off) { is += ts; io += to; }
-    }
-    if (lane == 31) { w_sum[warp] = is; w_occ[warp] = io; }
-    __syncthreads();
-    if (warp == 0) {
-      int ws = w_sum[lane], wo = w_occ[lane];
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int ts = __shfl_up_sync(0xffffffffu, ws, off), to = __shfl_up_sync(0xffffffffu, wo, off);
-        if (lane >= off) { ws += ts; wo += to; }
-      }
-      w_sum[lane] = ws;  // inclusive over warps
-      w_occ[lane] = wo;
-    }
-    __syncthreads();
-    int run = carry[0] + (warp ? w_sum[warp - 1] : 0) + is - s;
-    int runo = carry[1] + (warp ? w_occ[warp - 1] : 0) + io - o;
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-      if (i0 + k < nbins) {
-        offsets[i0 + k] = run;
-        if (c[k] > 0) occ[runo++] = (int)(i0 + k);
-      }
-      run += c[k];
-    }
-    __syncthreads();
-    if (tid == 0) { carry[0] += w_sum[31]; carry[1] += w_occ[31]; }
-    __syncthreads();
+    scan_store(offsets, i0, nbins, c);
+    carry += tot[0];
+    carry_o += tot[1];
   }
-  if (tid == 0) { offsets[nbins] = carry[0]; *nocc = carry[1]; }
+  if (threadIdx.x == 0) { offsets[nbins] = carry; *nocc = carry_o; }
 }
 
 // Exclusive scans of two int arrays of length n in one block; out arrays hold n + 1 entries.
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kScanThreads)
 k_scan2(const int* __restrict__ a, const int* __restrict__ b, int n, int* __restrict__ oa, int* __restrict__ ob) {
-  __shared__ int wa[32], wb[32];
-  __shared__ int carry[2];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) { carry[0] = 0; carry[1] = 0; }
-  __syncthreads();
-  for (int base = 0; base < n; base += 1024) {
-    const int i = base + tid;
-    const int va = (i < n) ? a[i] : 0, vb = (i < n) ? b[i] : 0;
-    int sa = va, sb = vb;
+  __shared__ int wsum[2][32];
+  int ca = 0, cb = 0;
+  constexpr int PER = kScanPer / 2;  // two arrays in registers
+  for (long long base = 0; base < n; base += (long long)kScanThreads * PER) {
+    const long long i0 = base + (long long)threadIdx.x * PER;
+    int x[PER];
+    int v[2] = {0, 0}, tot[2];
+    scan_load(a, i0, n, x);
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int ta = __shfl_up_sync(0xffffffffu, sa, off), tb = __shfl_up_sync(0xffffffffu, sb, off);
-      if (lane >= off) { sa += ta; sb += tb; }
-    }
-    if (lane == 31) { wa[warp] = sa; wb[warp] = sb; }
-    __syncthreads();
-    if (warp == 0) {
-      int xa = wa[lane], xb = wb[lane];
+    for (int k = 0; k < PER; ++k) v[0] += x[k];
+    int y[PER];
+    scan_load(b, i0, n, y);
 #pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int ta = __shfl_up_sync(0xffffffffu, xa, off), tb = __shfl_up_sync(0xffffffffu, xb, off);
-        if (lane >= off) { xa += ta; xb += tb; }
-      }
-      wa[lane] = xa; wb[lane] = xb;
+    for (int k = 0; k < PER; ++k) v[1] += y[k];
+    block_prefix<2>(v, tot, wsum);
+    int ra = ca + v[0], rb = cb + v[1];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int ta = x[k], tb = y[k];
+      x[k] = ra; y[k] = rb;
+      ra += ta; rb += tb;
     }
-    __syncthreads();
-    if (i < n) {
-      oa[i] = carry[0] + (warp ? wa[warp - 1] : 0) + sa - va;
-      ob[i] = carry[1] + (warp ? wb[warp - 1] : 0) + sb - vb;
-    }
-    __syncthreads();
-    if (tid == 0) { carry[0] += wa[31]; carry[1] += wb[31]; }
-    __syncthreads();
+    scan_store(oa, i0, n, x);
+    scan_store(ob, i0, n, y);
+    ca += tot[0];
+    cb += tot[1];
   }
-  if (tid == 0) { oa[n] = carry[0]; ob[n] = carry[1]; }
+  if (threadIdx.x == 0) { oa[n] = ca; ob[n] = cb; }
 }
 
 template <typename T>
@@ -715,21 +766,26 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
 }
 
 // Boxes split into several slices: add their partials in slice order and store the box.
+// Persistent blocks walk the slice list and take the first slice of each split box.
 template <typename T>
-__global__ void k_box_reduce(PointGeom g, const int* __restrict__ slice_off, const int* __restrict__ part_off,
-                             const T* __restrict__ part, T* __restrict__ grid) {
-  const int box = blockIdx.x;
-  const int K = slice_off[box + 1] - slice_off[box];
-  if (K <= 1) return;
+__global__ void k_box_reduce(PointGeom g, const int* __restrict__ slice_off, const int* __restrict__ box_item,
+                             const int* __restrict__ part_off, const T* __restrict__ part, T* __restrict__ grid) {
   const int nf = g.nf;
-  const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
+  const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
+  const int nslices = slice_off[nbox];
   const long long gcells = (long long)nf * nf * nf;
-  for (int i = threadIdx.x; i < 3 * 512; i += blockDim.x) {
-    const int a = i / 512, c = i % 512;
-    T v = T(0);
-    for (int k = 0; k < K; ++k) v = v + part[((long long)(part_off[box] + k) * 3 + a) * 512 + c];
-    const int x = c % 8, y = (c / 8) % 8, z = c / 64;
-    grid[a * gcells + ((long long)(Bz * 8 + z) * nf + (By * 8 + y)) * nf + (Bx * 8 + x)] = v;
+  for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+    const int box = box_item[sl];
+    const int K = slice_off[box + 1] - slice_off[box];
+    if (K <= 1 || sl != slice_off[box]) continue;  // uniform across the block
+    const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
+    for (int i = threadIdx.x; i < 3 * 512; i += blockDim.x) {
+      const int a = i / 512, c = i % 512;
+      T v = T(0);
+      for (int k = 0; k < K; ++k) v = v + part[((long long)(part_off[box] + k) * 3 + a) * 512 + c];
+      const int x = c % 8, y = (c / 8) % 8, z = c / 64;
+      grid[a * gcells + ((long long)(Bz * 8 + z) * nf + (By * 8 + y)) * nf + (Bx * 8 + x)] = v;
+    }
   }
 }
 
@@ -890,7 +946,7 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
     k_spread_box3<T><<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
                                                     (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
                                                     (T*)ws.part, grid);
-    k_box_reduce<T><<<nbox, 256, 0, st>>>(g, ws.box_so, ws.box_po, (const T*)ws.part, grid);
+    k_box_reduce<T><<<4 * num_sms(), 256, 0, st>>>(g, ws.box_so, ws.box_item, ws.box_po, (const T*)ws.part, grid);
   } else
     k_spread_gather<T, 2><<<nbox, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
 }

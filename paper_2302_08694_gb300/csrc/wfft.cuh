@@ -106,10 +106,34 @@ __device__ __forceinline__ void dft_r(C<T>* v) {
   else if constexpr (R == 12) dft12<T, INV>(v);
 }
 
+// Twiddles in lane order: for stage s >= 1, butterfly slot b, r = 1..R-1 and lane l, entry
+// wfft_tw_off(N, s) + (b (R-1) + r - 1) L + l holds w^{(j mod NS) r N/(NS R)}, j = l + L b,
+// w = exp(-2 pi i / N), so that the lanes of a warp read consecutive entries.
+constexpr int wfft_tw_off(int n, int s) {
+  int off = 0;
+  for (int t = 1; t < s; ++t) off += (n / wfft_radix(n, t)) * (wfft_radix(n, t) - 1);
+  return off;
+}
+constexpr int wfft_tw_size(int n) { return wfft_tw_off(n, wfft_nstages(n)); }
+
+// Build the lane-ordered table from the natural table tw[k] = exp(-2 pi i k / N) (global).
+template <typename T, int N>
+__device__ __forceinline__ void wfft_build_twiddles(C<T>* twl, const C<T>* __restrict__ tw) {
+  constexpr int L = wfft_L(N);
+  for (int e = threadIdx.x; e < wfft_tw_size(N); e += blockDim.x) {
+    int s = 1, NS = wfft_radix(N, 0);
+    while (e >= wfft_tw_off(N, s + 1)) { NS *= wfft_radix(N, s); ++s; }
+    const int R = wfft_radix(N, s), q = e - wfft_tw_off(N, s);
+    const int l = q % L, br = q / L, b = br / (R - 1), r = br % (R - 1) + 1;
+    const int j = l + L * b;
+    twl[e] = tw[(j % NS) * r * (N / (NS * R))];
+  }
+}
+
 // Stage S of the warp transform (NS = product of the earlier radices). buf: this line's
-// exchange buffer; tw: the length-N twiddle table exp(-2 pi i k / N) in shared memory.
+// exchange buffer; twl: the lane-ordered twiddle table in shared memory.
 template <typename T, bool INV, int N, int S = 0, int NS = 1>
-__device__ __forceinline__ void wfft(C<T> (&v)[wfft_M(N)], C<T>* buf, int l, const C<T>* __restrict__ tw) {
+__device__ __forceinline__ void wfft(C<T> (&v)[wfft_M(N)], C<T>* buf, int l, const C<T>* __restrict__ twl) {
   constexpr int M = wfft_M(N), L = wfft_L(N), R = wfft_radix(N, S), NB = M / R;
   constexpr int E = (int)sizeof(C<T>);
   if constexpr (S > 0) {
@@ -123,12 +147,10 @@ __device__ __forceinline__ void wfft(C<T> (&v)[wfft_M(N)], C<T>* buf, int l, con
   }
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
-    const int j = l + L * b;
     if constexpr (NS > 1) {
-      const int k = j % NS;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        C<T> w = tw[k * r * (N / (NS * R))];
+        C<T> w = twl[wfft_tw_off(N, S) + (b * (R - 1) + r - 1) * L + l];
         if (INV) w = cconj<T>(w);
         v[b * R + r] = cmul<T>(v[b * R + r], w);
       }
@@ -145,7 +167,7 @@ __device__ __forceinline__ void wfft(C<T> (&v)[wfft_M(N)], C<T>* buf, int l, con
       for (int r = 0; r < R; ++r) buf[wswz<SW>(o + r * NS)] = v[b * R + r];
     }
     __syncwarp();
-    wfft<T, INV, N, S + 1, NS * R>(v, buf, l, tw);
+    wfft<T, INV, N, S + 1, NS * R>(v, buf, l, twl);
   }
 }
 
