@@ -22,6 +22,8 @@ struct fsib_plan {
   cudaStream_t user = nullptr;
   cudaStream_t own = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t side = nullptr;                        // second branch of a Navier-Stokes step
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
   bool ready = false;  // workspaces allocated for the current plan
   // per-launch-site profiler
@@ -218,13 +220,13 @@ static double fft_flops(double lines, int n) { return lines * 5.0 * n * std::log
 // Workspaces
 // ---------------------------------------------------------------------------
 static void free_ws(Workspace& ws) {
-  void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.s1, ws.s2, ws.fhat, ws.uhalf, ws.bin_of,
+  void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.s1, ws.s2, ws.s3, ws.s4, ws.fhat, ws.uhalf, ws.bin_of,
                   ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
                   ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.wts, ws.cwp,
                   ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.box_item, ws.part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  ws.tw = ws.dline = ws.dplane = ws.grid = ws.s1 = ws.s2 = ws.fhat = ws.uhalf = nullptr;
+  ws.tw = ws.dline = ws.dplane = ws.grid = ws.s1 = ws.s2 = ws.s3 = ws.s4 = ws.fhat = ws.uhalf = nullptr;
   ws.bin_of = ws.rank = ws.counts = ws.offsets = ws.occ = ws.nocc = ws.perm = ws.i0 = nullptr;
   ws.delta = nullptr;
   ws.Xh = ws.cw = ws.Uh = ws.omega_ones = ws.red = nullptr;
@@ -294,6 +296,10 @@ static int alloc_ws(fsib_plan* h) {
   rc |= dmalloc(&ws.grid, ws.grid_bytes, tot);
   rc |= dmalloc(&ws.s1, ws.s1_bytes, tot);
   rc |= dmalloc(&ws.s2, ws.s2_bytes, tot);
+  if (!p.stokes) {
+    rc |= dmalloc(&ws.s3, ws.s1_bytes, tot);
+    rc |= dmalloc(&ws.s4, ws.s1_bytes, tot);
+  }
   rc |= dmalloc(&ws.fhat, ws.spec_bytes, tot);
   rc |= dmalloc(&ws.uhalf, ws.spec_bytes, tot);
   rc |= dmalloc(&ws.bin_of, sizeof(int) * p.M, tot);
@@ -448,13 +454,13 @@ static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t s
 
 // Fourier coefficients on K_N of the products u_a u_b (three-halves rule), as TA; returns the buffer.
 template <typename TI, typename TA>
-static const C<TA>* products(fsib_plan* h, const C<TA>* u, cudaStream_t st) {
+static const C<TA>* products(fsib_plan* h, const C<TA>* u, cudaStream_t st, void* scratch1, void* scratch2) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const int N = p.N, hh = N / 2, nt = p.Nt, d = p.d;
   const C<TI>* tw = (const C<TI>*)ws.tw;
-  C<TI>* s1 = (C<TI>*)ws.s1;
-  C<TI>* s2 = (C<TI>*)ws.s2;
+  C<TI>* s1 = (C<TI>*)scratch1;
+  C<TI>* s2 = (C<TI>*)scratch2;
   Mult<TI> none;
   Mult<TI> sc;
   const double cs = 2.0 * sizeof(TI);
@@ -557,17 +563,19 @@ static void do_stokeslet(fsib_plan* h, const C<TA>* fhat, C<TA>* u, cudaStream_t
 }
 
 template <typename TI, typename TA>
-static void do_fluid(fsib_plan* h, const C<TA>* fhat, C<TA>* u, C<TA>* uhalf, cudaStream_t st) {
+// P0: the product coefficients of u^m when they were computed beforehand (see do_step).
+static void do_fluid(fsib_plan* h, const C<TA>* fhat, C<TA>* u, C<TA>* uhalf, cudaStream_t st,
+                     const C<TA>* P0 = nullptr) {
   if (h->p.stokes) {
     do_stokeslet<TA>(h, fhat, u, st);
     return;
   }
   const int d = h->p.d, np = d * (d + 1) / 2;
   const double ub = (double)h->ws.spec_bytes / d * (np + 3 * d);
-  const C<TA>* P = products<TI, TA>(h, u, st);
+  const C<TA>* P = P0 ? P0 : products<TI, TA>(h, u, st, h->ws.s1, h->ws.s2);
   { Prof pr(h, "ns_update", ub, 0.0, st);
     launch_ns_update<TA>(h->p, P, fhat, u, uhalf, true, st); }
-  P = products<TI, TA>(h, uhalf, st);
+  P = products<TI, TA>(h, uhalf, st, h->ws.s1, h->ws.s2);
   { Prof pr(h, "ns_update", ub, 0.0, st);
     launch_ns_update<TA>(h->p, P, fhat, u, u, false, st); }
 }
@@ -593,10 +601,17 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
   C<TA>* fhat = (C<TA>*)ws.fhat;
   C<TA>* uh = (C<TA>*)ws.uhalf;
   if (!p.stokes) {
+    // The nonlinear term of u^m does not depend on the boundary: its transforms run on a
+    // second stream (own scratch s3, s4) while the force and the type-1 NUFFT run here.
+    cudaEventRecord(h->ev_fork, st);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    const C<TA>* P0 = products<TI, TA>(h, uhat, h->side, ws.s3, ws.s4);
+    cudaEventRecord(h->ev_join, h->side);
     do_axpy(h, ws.Xh, X, U, 0.5 * p.dt, st);                    // Eq. spatial_1
     do_force(h, ws.Xh, ws.cw, st);                               // F^{m+1/2}
     do_spread<TI, TA>(h, ws.Xh, ws.cw, nullptr, fhat, st);       // type-1 NUFFT
-    do_fluid<TI, TA>(h, fhat, uhat, uh, st);                     // Eqs. spatial_2, spatial_3
+    cudaStreamWaitEvent(st, h->ev_join, 0);
+    do_fluid<TI, TA>(h, fhat, uhat, uh, st, P0);                 // Eqs. spatial_2, spatial_3
     do_interp_sorted<TI, TA>(h, uh, ws.Uh, st);                  // U^{m+1/2} at X^{m+1/2}
     do_axpy(h, X, X, ws.Uh, p.dt, st);                           // Eq. spatial_4
     do_bin(h, X, st);
@@ -730,8 +745,11 @@ int fsib_create(fsib_t* out, int N, int d, int M, double mu, double rho, double 
   int rc = plan_sizes(p, h->err);
   if (rc != FSIB_OK) { g_create_err = h->err; delete h; return rc; }
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     g_create_err = "CUDA stream/event creation failed (no device?)";
     delete h;
@@ -755,9 +773,13 @@ int fsib_destroy(fsib_t h) {
   for (auto e : h->pool) cudaEventDestroy(e);
   free_ws(h->ws);
   free_mesh(h->ws);
+  if (h->side) cudaStreamSynchronize(h->side);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->own) cudaStreamDestroy(h->own);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
   return FSIB_OK;
 }

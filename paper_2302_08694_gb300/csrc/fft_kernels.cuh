@@ -382,86 +382,6 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
   }
 }
 
-// Strided pass with the warp-level transform. A tile of kWP adjacent lines (along the
-// contiguous index q) x N positions is staged in shared memory with a row stride of
-// kWP + 1 elements, so that the column a line occupies is read and written without bank
-// conflicts; the sub-warps of a warp take lines kWP/LPW apart for the same reason. Loads
-// and stores move rows of kWP consecutive complex values. The pad/prune and the
-// multipliers are applied on the way in (inverse) or out (forward), as in k_fft_strided.
-constexpr int kWP = 16;
-template <typename T, bool INV, typename Tin, typename Tout, int N>
-__global__ void __launch_bounds__(256)
-k_wfft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, long long ntiles,
-               int ntile, Mult<T> mult, const C<T>* __restrict__ twg) {
-  constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
-  constexpr int PS = kWP + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T>* twl = reinterpret_cast<C<T>*>(smem_raw);
-  C<T>* tile = twl + wfft_tw_size(N);                    // [N][PS]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  const int l = lane % L, sub = lane / L;
-  C<T>* buf = tile + N * PS + (warp * LPW + sub) * SL;  // exchange buffer of this lane's line
-  wfft_build_twiddles<T, N>(twl, twg);
-  const int Lin = INV ? Nk : N, Lout = INV ? N : Nk;
-  const int h = Nk / 2;
-  for (long long blk = blockIdx.x; blk < ntiles; blk += gridDim.x) {
-    const long long co = blk / ntile;  // component * outer + outer index
-    const int q0 = (int)(blk % ntile) * kWP;
-    const C<Tin>* src = in + co * (long long)Lin * inner;
-    C<Tout>* dst = out + co * (long long)Lout * inner;
-    __syncthreads();  // the previous tile has been stored (and the twiddles are built)
-    for (int t = threadIdx.x; t < N * kWP; t += blockDim.x) {
-      const int p = t % kWP, i = t / kWP, q = q0 + p;
-      C<T> v = mk<T>(T(0), T(0));
-      if (q < inner) {
-        if (!INV) {
-          v = ccvt<T, Tin>(src[(long long)i * inner + q]);
-        } else {
-          const int si = (i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1);
-          if (si >= 0) {
-            T sc = mult.scale;
-            if (mult.dline) sc *= mult.dline[si];
-            if (mult.dplane) sc *= mult.dplane[q];
-            v = cscale<T>(ccvt<T, Tin>(src[(long long)si * inner + q]), sc);
-          }
-        }
-      }
-      tile[i * PS + p] = v;
-    }
-    __syncthreads();
-    for (int pb = warp; pb < kWP / LPW; pb += nwarp) {
-      const int p = pb + sub * (kWP / LPW);
-      C<T> v[M];
-#pragma unroll
-      for (int i = 0; i < M; ++i) v[i] = tile[(l + L * i) * PS + p];
-      wfft<T, INV, N>(v, buf, l, twl);
-#pragma unroll
-      for (int i = 0; i < M; ++i) tile[wfft_out_index<N>(l, i) * PS + p] = v[i];
-    }
-    __syncthreads();
-    if (!INV) {
-      for (int t = threadIdx.x; t < Nk * kWP; t += blockDim.x) {
-        const int p = t % kWP, io = t / kWP, q = q0 + p;
-        if (q >= inner) continue;
-        C<T> v = mk<T>(T(0), T(0));
-        if (io != h) {
-          const int fi = (io < h) ? io : io + (N - Nk);
-          T sc = mult.scale;
-          if (mult.dline) sc *= mult.dline[io];
-          if (mult.dplane) sc *= mult.dplane[q];
-          v = cscale<T>(tile[fi * PS + p], sc);
-        }
-        dst[(long long)io * inner + q] = ccvt<Tout, T>(v);
-      }
-    } else {
-      for (int t = threadIdx.x; t < N * kWP; t += blockDim.x) {
-        const int p = t % kWP, i = t / kWP, q = q0 + p;
-        if (q < inner) dst[(long long)i * inner + q] = ccvt<Tout, T>(tile[i * PS + p]);
-      }
-    }
-  }
-}
-
 // Persistent grid of a warp-transform kernel: resident blocks per SM times the SMs,
 // or fewer when there is less work.
 template <typename K>
@@ -504,25 +424,6 @@ void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, in
   with_fft_len(fl.n, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
     constexpr int NCI = fwd_only ? 0 : NC, NCF = inv_only ? 0 : NC;
-    if constexpr (wfft_has(NC)) {
-      constexpr int LPW = 32 / wfft_L(NC);
-      const int wt = (inner + kWP - 1) / kWP;
-      const long long tiles = (long long)ncomp * outer * wt;
-      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + NC * (kWP + 1) +
-                                                8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
-      if (inverse && !fwd_only) {
-        auto k = k_wfft_strided<T, true, Tin, Tout, NC>;
-        raise_smem_limit(reinterpret_cast<const void*>(k));
-        k<<<wrows_grid(k, 256, ws, tiles * 8), 256, ws, st>>>(in, out, inner, Nk, tiles, wt, mult, tw + fl.tw_off);
-        return;
-      }
-      if (!inverse && !inv_only) {
-        auto k = k_wfft_strided<T, false, Tin, Tout, NC>;
-        raise_smem_limit(reinterpret_cast<const void*>(k));
-        k<<<wrows_grid(k, 256, ws, tiles * 8), 256, ws, st>>>(in, out, inner, Nk, tiles, wt, mult, tw + fl.tw_off);
-        return;
-      }
-    }
     if (inverse) {
       auto k = k_fft_strided<T, true, Tin, Tout, NCI>;
       raise_smem_limit(reinterpret_cast<const void*>(k));

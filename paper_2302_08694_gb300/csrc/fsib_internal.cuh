@@ -107,6 +107,8 @@ struct Workspace {
   void* grid = nullptr;  size_t grid_bytes = 0;
   void* s1 = nullptr;    size_t s1_bytes = 0;
   void* s2 = nullptr;    size_t s2_bytes = 0;
+  void* s3 = nullptr;    // second scratch pair (s1_bytes each, Navier-Stokes only): the
+  void* s4 = nullptr;    // nonlinear term of u^m, computed beside the point side of the step
   void* fhat = nullptr;  size_t spec_bytes = 0;  // d * N^{d-1} * N/2 complex
   void* uhalf = nullptr;
   // sort
