@@ -218,6 +218,9 @@ def measure(fsib, torch, prob, prec, steps, warmup, dev, flush, world=1, barrier
     X = torch.from_numpy(prob.X0.copy()).to(dev)
     u = pb.new_spec(device=dev)
     U = pb.interp(u, X)
+    t_tune = time.perf_counter()
+    shapes = pb.autotune(X, u, U) if prob.rho > 0 else pb.autotune(X)  # on copies; X, u, U unchanged
+    t_tune = time.perf_counter() - t_tune
     for _ in range(warmup):
         pb.step(X, u, U, nsteps=1)
     if barrier:
@@ -270,6 +273,7 @@ def measure(fsib, torch, prob, prec, steps, warmup, dev, flush, world=1, barrier
     pb.profile(False)
     info = {k: pb.info(k) for k in ("nf", "Nt", "width")}
     return {"pb": pb, "X": X, "u": u, "U": U, "ms": ms, "launches": launches, "clocks": clocks,
+            "launch_shapes": dict(shapes, autotune_seconds=round(t_tune, 2)),
             "pts1": prob.M / (t1 / nufft_reps * 1e-3), "pts2": prob.M / (t2 / nufft_reps * 1e-3),
             "sites": sites, "nprof": nprof, "info": info}
 
@@ -321,7 +325,7 @@ def mixed_block(fsib, torch, dev, flush, pk, pk_src, fp64_peak, fp32_peak, steps
             "ms_per_step": m["ms"] / steps, "steps": steps, "dtype": "f32 transforms, f64 positions/forces",
             "nufft_pts_per_s": {"type1": m["pts1"], "type2": m["pts2"]},
             "config": {"N": prob.N, "M": prob.M, "tol": prob.tol, **{k: int(v) for k, v in m["info"].items()}},
-            "error_vs_fp64_run": errs,
+            "error_vs_fp64_run": errs, "launch_shapes": m["launch_shapes"],
             "roofline": roofline_of(top, "mixed", pk, pk_src, fp64_peak, fp32_peak),
             "breakdown": breakdown_of(m["sites"], m["nprof"], 8)}
 
@@ -529,6 +533,7 @@ def run_ours(args):
                 "nufft_pts_per_s": {"type1": world * m["pts1"], "type2": world * m["pts2"]},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": m["clocks"],
                 "gpu_launches": m["launches"] * args.steps, "launches_per_step": m["launches"],
+                "launch_shapes": m["launch_shapes"],
                 "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched,
                 "adjoint": adjoint}
         print(json.dumps(line), flush=True)
