@@ -165,6 +165,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the spread site
+# (k_box_slices, k_scan2, k_slice_boxes, k_spread_box3, k_box_reduce), from one ncu capture of
+# the current kernels per workload; profiles/spread_site_traffic.txt has the command and the
+# per-kernel figures. Set an entry to None when those kernels change.
+SITE_TRAFFIC = {("ns3d_N64_M10082_fp64", "spread"): 20492288.0,
+                ("ns3d_N128_M40322_mixed", "spread"): 157699584.0}
+
+
 def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -326,7 +334,8 @@ def mixed_block(fsib, torch, dev, flush, pk, pk_src, fp64_peak, fp32_peak, steps
             "nufft_pts_per_s": {"type1": m["pts1"], "type2": m["pts2"]},
             "config": {"N": prob.N, "M": prob.M, "tol": prob.tol, **{k: int(v) for k, v in m["info"].items()}},
             "error_vs_fp64_run": errs, "launch_shapes": m["launch_shapes"],
-            "roofline": roofline_of(top, "mixed", pk, pk_src, fp64_peak, fp32_peak),
+            "roofline": dict(roofline_of(top, "mixed", pk, pk_src, fp64_peak, fp32_peak),
+                             traffic=SITE_TRAFFIC.get((prob.name, top["name"]))),
             "breakdown": breakdown_of(m["sites"], m["nprof"], 8)}
 
 
@@ -478,7 +487,8 @@ def run_ours(args):
     fp32_peak = fsib.measure_peak(1)
     top = max(m["sites"], key=lambda s: s["total_ms"])
     roof = roofline_of(top, prec, pk, pk_src, fp64_peak, fp32_peak)
-    roof.update({"traffic": None, "share": top["total_ms"] / sum(s["total_ms"] for s in m["sites"]),
+    roof.update({"traffic": SITE_TRAFFIC.get((prob.name, top["name"])),
+                 "share": top["total_ms"] / sum(s["total_ms"] for s in m["sites"]),
                  "fp64_fma_peak_tflops": fp64_peak / 1e3, "fp32_fma_peak_tflops": fp32_peak / 1e3})
 
     # end to end through the public API with pinned host buffers
