@@ -382,6 +382,107 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
   }
 }
 
+// ---------------------------------------------------------------------------
+// Strided pass in two register stages, N = R1 x R2 (radices up to 16; the lengths below).
+// A block holds a tile of S2P adjacent lines (16 x S2P threads); line p of the tile is
+// column p of a [N][S2P] shared array, so the threads of a warp (consecutive lines, then
+// consecutive butterflies) touch consecutive addresses. Stage 1 (radix R1, no twiddles)
+// reads x[j + r N/R1] and writes y[j R1 + r] after a barrier (in place); stage 2 (radix R2)
+// reads y[j + r R1], multiplies by w^{j r} and writes back to the same places, which leaves
+// the transform in natural order. Loads, pruning, padding and multipliers as in k_fft_strided.
+// ---------------------------------------------------------------------------
+constexpr bool s2_has(int n) {
+  return n == 48 || n == 64 || n == 72 || n == 96 || n == 128 || n == 144 || n == 192 || n == 256;
+}
+constexpr int s2_R1(int n) {
+  return n == 48 ? 12 : n == 64 ? 8 : n == 72 ? 8 : n == 96 ? 12 : n == 128 ? 16 : n == 144 ? 12 : 16;
+}
+constexpr int s2_P(int E) { return E == 8 ? 16 : 8; }  // lines per tile: 128-byte rows
+
+template <typename T, bool INV, typename Tin, typename Tout, int N>
+__global__ void __launch_bounds__(16 * s2_P((int)sizeof(C<T>)))
+k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
+         Mult<T> mult, const C<T>* __restrict__ twg) {
+  constexpr int P = s2_P((int)sizeof(C<T>)), R1 = s2_R1(N), R2 = N / R1, NT = 16 * P;
+  constexpr int RM = R1 > R2 ? R1 : R2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* tile = tw + N;  // [N][P]
+  const long long co = blockIdx.x / ntile;
+  const int q0 = (blockIdx.x % ntile) * P;
+  const int Lin = INV ? Nk : N, Lout = INV ? N : Nk;
+  const int h = Nk / 2;
+  const C<Tin>* src = in + co * (long long)Lin * inner;
+  C<Tout>* dst = out + co * (long long)Lout * inner;
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  for (int t = threadIdx.x; t < N * P; t += NT) {
+    const int p = t % P, i = t / P, q = q0 + p;
+    C<T> v = mk<T>(T(0), T(0));
+    if (q < inner) {
+      if (!INV) {
+        v = ccvt<T, Tin>(src[(long long)i * inner + q]);
+      } else {
+        const int si = (i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1);
+        if (si >= 0) {
+          T sc = mult.scale;
+          if (mult.dline) sc *= mult.dline[si];
+          if (mult.dplane) sc *= mult.dplane[q];
+          v = cscale<T>(ccvt<T, Tin>(src[(long long)si * inner + q]), sc);
+        }
+      }
+    }
+    tile[t] = v;  // t = i * P + p
+  }
+  __syncthreads();
+  const int p = threadIdx.x % P, j = threadIdx.x / P;  // j < 16
+  C<T> v[RM];
+  if (j < N / R1) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) v[r] = tile[(j + r * (N / R1)) * P + p];
+    dft_r<T, INV, R1>(v);
+  }
+  __syncthreads();
+  if (j < N / R1) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) tile[(j * R1 + r) * P + p] = v[r];
+  }
+  __syncthreads();
+  if (j < R1) {
+#pragma unroll
+    for (int r = 0; r < R2; ++r) v[r] = tile[(j + r * R1) * P + p];
+#pragma unroll
+    for (int r = 1; r < R2; ++r) {
+      C<T> w = tw[j * r];
+      if (INV) w = cconj<T>(w);
+      v[r] = cmul<T>(v[r], w);
+    }
+    dft_r<T, INV, R2>(v);
+#pragma unroll
+    for (int r = 0; r < R2; ++r) tile[(j + r * R1) * P + p] = v[r];
+  }
+  __syncthreads();
+  if (!INV) {
+    for (int t = threadIdx.x; t < Nk * P; t += NT) {
+      const int pp = t % P, io = t / P, q = q0 + pp;
+      if (q >= inner) continue;
+      C<T> v = mk<T>(T(0), T(0));
+      if (io != h) {
+        const int fi = (io < h) ? io : io + (N - Nk);
+        T sc = mult.scale;
+        if (mult.dline) sc *= mult.dline[io];
+        if (mult.dplane) sc *= mult.dplane[q];
+        v = cscale<T>(tile[fi * P + pp], sc);
+      }
+      dst[(long long)io * inner + q] = ccvt<Tout, T>(v);
+    }
+  } else {
+    for (int t = threadIdx.x; t < N * P; t += NT) {
+      const int pp = t % P, i = t / P, q = q0 + pp;
+      if (q < inner) dst[(long long)i * inner + q] = ccvt<Tout, T>(tile[t]);
+    }
+  }
+}
+
 // Persistent grid of a warp-transform kernel: resident blocks per SM times the SMs,
 // or fewer when there is less work.
 template <typename K>
@@ -424,6 +525,24 @@ void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, in
   with_fft_len(fl.n, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
     constexpr int NCI = fwd_only ? 0 : NC, NCF = inv_only ? 0 : NC;
+    if constexpr (s2_has(NC)) {
+      constexpr int P2 = s2_P((int)sizeof(C<T>));
+      const int nt2 = (inner + P2 - 1) / P2;
+      const long long blocks2 = (long long)ncomp * outer * nt2;
+      const size_t smem2 = sizeof(C<T>) * (size_t)(NC + NC * P2);
+      if (inverse && !fwd_only) {
+        auto k = k_fft_s2<T, true, Tin, Tout, NC>;
+        raise_smem_limit(reinterpret_cast<const void*>(k));
+        k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off);
+        return;
+      }
+      if (!inverse && !inv_only) {
+        auto k = k_fft_s2<T, false, Tin, Tout, NC>;
+        raise_smem_limit(reinterpret_cast<const void*>(k));
+        k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off);
+        return;
+      }
+    }
     if (inverse) {
       auto k = k_fft_strided<T, true, Tin, Tout, NCI>;
       raise_smem_limit(reinterpret_cast<const void*>(k));

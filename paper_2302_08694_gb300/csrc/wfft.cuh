@@ -98,12 +98,91 @@ __device__ __forceinline__ void dft12(C<T>* v) {
   }
 }
 
+// Constants in each arithmetic type (the double-float values are split at compile time).
+#define FSIB_TRIG_CONST(name, val)                                                        \
+  template <typename T> __device__ __forceinline__ T name();                              \
+  template <> __device__ __forceinline__ float name<float>() { return (float)(val); }    \
+  template <> __device__ __forceinline__ double name<double>() { return (val); }         \
+  template <> __device__ __forceinline__ dd name<dd>() {                                  \
+    constexpr dd v(val);                                                                  \
+    return v;                                                                             \
+  }
+FSIB_TRIG_CONST(cos_pi8, 0.92387953251128675612818318939678829)
+FSIB_TRIG_CONST(sin_pi8, 0.38268343236508977172845998403039887)
+FSIB_TRIG_CONST(cos_2pi9, 0.76604444311897803520239265055541667)
+FSIB_TRIG_CONST(sin_2pi9, 0.64278760968653932632264340990727188)
+FSIB_TRIG_CONST(cos_4pi9, 0.17364817766693034885171662676931466)
+FSIB_TRIG_CONST(sin_4pi9, 0.98480775301220805936674302458952301)
+FSIB_TRIG_CONST(cos_8pi9, -0.93969262078590838405410927732473147)
+FSIB_TRIG_CONST(sin_8pi9, 0.34202014332566873304409961468225958)
+#undef FSIB_TRIG_CONST
+
+// v * (cr - i si) forward, v * (cr + i si) inverse: multiplication by w^m, w = exp(-+ 2 pi i / R).
+template <typename T, bool INV>
+__device__ __forceinline__ C<T> crot(C<T> v, T cr, T si) {
+  const T ci = INV ? si : -si;
+  return mk<T>(v.x * cr - v.y * ci, v.x * ci + v.y * cr);
+}
+
+// 16-point DFT: 4 x 4 Cooley-Tukey (inner twiddles w^{n2 k1}, w = exp(-+ 2 pi i / 16)).
+template <typename T, bool INV>
+__device__ __forceinline__ void dft16(C<T>* v) {
+  C<T> a[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    a[n2][0] = v[n2]; a[n2][1] = v[4 + n2]; a[n2][2] = v[8 + n2]; a[n2][3] = v[12 + n2];
+    dft4<T, INV>(a[n2]);
+  }
+  const T c1 = cos_pi8<T>(), s1 = sin_pi8<T>(), h = rsqrt2<T>();
+  a[1][1] = crot<T, INV>(a[1][1], c1, s1);   // w^1
+  a[1][2] = crot<T, INV>(a[1][2], h, h);     // w^2
+  a[1][3] = crot<T, INV>(a[1][3], s1, c1);   // w^3
+  a[2][1] = crot<T, INV>(a[2][1], h, h);     // w^2
+  a[2][2] = INV ? cmul_i<T>(a[2][2]) : cmul_mi<T>(a[2][2]);  // w^4
+  a[2][3] = crot<T, INV>(a[2][3], -h, h);    // w^6
+  a[3][1] = crot<T, INV>(a[3][1], s1, c1);   // w^3
+  a[3][2] = crot<T, INV>(a[3][2], -h, h);    // w^6
+  a[3][3] = crot<T, INV>(a[3][3], -c1, -s1); // w^9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C<T> b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4<T, INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+  }
+}
+
+// 9-point DFT: 3 x 3 Cooley-Tukey (inner twiddles w^{n2 k1}, w = exp(-+ 2 pi i / 9)).
+template <typename T, bool INV>
+__device__ __forceinline__ void dft9(C<T>* v) {
+  C<T> a[3][3];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+    a[n2][0] = v[n2]; a[n2][1] = v[3 + n2]; a[n2][2] = v[6 + n2];
+    dft3<T, INV>(a[n2]);
+  }
+  a[1][1] = crot<T, INV>(a[1][1], cos_2pi9<T>(), sin_2pi9<T>());  // w^1
+  a[1][2] = crot<T, INV>(a[1][2], cos_4pi9<T>(), sin_4pi9<T>());  // w^2
+  a[2][1] = crot<T, INV>(a[2][1], cos_4pi9<T>(), sin_4pi9<T>());  // w^2
+  a[2][2] = crot<T, INV>(a[2][2], cos_8pi9<T>(), sin_8pi9<T>());  // w^4
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    C<T> b[3] = {a[0][k1], a[1][k1], a[2][k1]};
+    dft3<T, INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) v[k1 + 3 * k2] = b[k2];
+  }
+}
+
 template <typename T, bool INV, int R>
 __device__ __forceinline__ void dft_r(C<T>* v) {
   if constexpr (R == 2) dft2<T, INV>(v);
+  else if constexpr (R == 3) dft3<T, INV>(v);
   else if constexpr (R == 4) dft4<T, INV>(v);
   else if constexpr (R == 8) dft8<T, INV>(v);
+  else if constexpr (R == 9) dft9<T, INV>(v);
   else if constexpr (R == 12) dft12<T, INV>(v);
+  else if constexpr (R == 16) dft16<T, INV>(v);
 }
 
 // Twiddles in lane order: for stage s >= 1, butterfly slot b, r = 1..R-1 and lane l, entry
