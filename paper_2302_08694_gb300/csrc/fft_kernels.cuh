@@ -415,23 +415,35 @@ k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, in
   const C<Tin>* src = in + co * (long long)Lin * inner;
   C<Tout>* dst = out + co * (long long)Lout * inner;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
-  for (int t = threadIdx.x; t < N * P; t += NT) {
-    const int p = t % P, i = t / P, q = q0 + p;
-    C<T> v = mk<T>(T(0), T(0));
-    if (q < inner) {
-      if (!INV) {
-        v = ccvt<T, Tin>(src[(long long)i * inner + q]);
-      } else {
+  {
+    // every load of this thread is issued before the first shared-memory store
+    constexpr int NL = N * P / NT;
+    const int p = threadIdx.x % P, q = q0 + p;
+    const bool qok = q < inner;
+    C<Tin> raw[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int i = (threadIdx.x + k * NT) / P;
+      const int si = INV ? ((i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1)) : i;
+      raw[k] = (qok && si >= 0) ? src[(long long)si * inner + q] : C<Tin>{};
+    }
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int t = threadIdx.x + k * NT, i = t / P;
+      C<T> v = ccvt<T, Tin>(raw[k]);
+      if (INV) {
         const int si = (i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1);
-        if (si >= 0) {
+        if (qok && si >= 0) {
           T sc = mult.scale;
           if (mult.dline) sc *= mult.dline[si];
           if (mult.dplane) sc *= mult.dplane[q];
-          v = cscale<T>(ccvt<T, Tin>(src[(long long)si * inner + q]), sc);
+          v = cscale<T>(v, sc);
+        } else {
+          v = mk<T>(T(0), T(0));
         }
       }
+      tile[t] = v;  // t = i * P + p
     }
-    tile[t] = v;  // t = i * P + p
   }
   __syncthreads();
   const int p = threadIdx.x % P, j = threadIdx.x / P;  // j < 16
