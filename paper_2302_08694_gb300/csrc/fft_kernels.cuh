@@ -248,6 +248,37 @@ k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long 
 // Shared memory: the lane-ordered twiddle table, then per line its exchange buffer
 // (and, in the product pass, the d inverse-transformed components).
 // ---------------------------------------------------------------------------
+// Packed line Z = A + iB of two half spectra in the warp transform's input order
+// (element l + L i). In FP32 every load is issued before any element is assembled; the
+// double-float version assembles element by element (its registers are the tighter limit).
+template <typename T, int N>
+__device__ __forceinline__ void wfft_load_packed(C<T> (&v)[wfft_M(N)], const C<T>* __restrict__ A,
+                                                 const C<T>* __restrict__ B, int l, int h, bool valid) {
+  constexpr int M = wfft_M(N), L = wfft_L(N);
+  if constexpr (sizeof(C<T>) != 8) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) v[i] = valid ? pack_rows<T>(A, B, l + L * i, N, h) : mk<T>(T(0), T(0));
+    return;
+  }
+  C<T> a[M], b[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int k = l + L * i;
+    const bool lo = k < h, hi = k > N - h;
+    const int kk = lo ? k : N - k;
+    const bool ok = valid && (lo || hi);
+    a[i] = ok ? A[kk] : mk<T>(T(0), T(0));
+    b[i] = ok ? B[kk] : mk<T>(T(0), T(0));
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int k = l + L * i;
+    if (k == 0) v[i] = mk<T>(a[i].x, b[i].x);                       // Hermitian part of m_x = 0
+    else if (k < h) v[i] = mk<T>(a[i].x - b[i].y, a[i].y + b[i].x);   // A + iB
+    else v[i] = mk<T>(a[i].x + b[i].y, b[i].x - a[i].y);              // conj(A) + i conj(B), or 0
+  }
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(256)
 k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
@@ -265,9 +296,7 @@ k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, 
     const long long pr = g * LPW + sub;
     const bool valid = pr < npairs;
     C<T> v[M];
-#pragma unroll
-    for (int i = 0; i < M; ++i)
-      v[i] = valid ? pack_rows<T>(in + (2 * pr) * h, in + (2 * pr + 1) * h, l + L * i, N, h) : mk<T>(T(0), T(0));
+    wfft_load_packed<T, N>(v, in + (2 * pr) * h, in + (2 * pr + 1) * h, l, h, valid);
     wfft<T, true, N>(v, buf, l, tw);
     if (valid) {
 #pragma unroll
@@ -356,9 +385,7 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
     for (int c = 0; c < d; ++c) {
       C<T> v[M];
       const C<T>* base = in + ((long long)c * nrows + 2 * pr) * h;
-#pragma unroll
-      for (int i = 0; i < M; ++i)
-        v[i] = valid ? pack_rows<T>(base, base + h, l + L * i, N, h) : mk<T>(T(0), T(0));
+      wfft_load_packed<T, N>(v, base, base + h, l, h, valid);
       wfft<T, true, N>(v, buf, l, tw);
 #pragma unroll
       for (int i = 0; i < M; ++i) U[c * SL + wfft_out_index<N>(l, i)] = v[i];

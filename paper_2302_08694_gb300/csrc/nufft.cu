@@ -765,6 +765,138 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
   zero_empty_boxes<T>(g, slice_off, nbox, grid);
 }
 
+// Double-float variant of the 3D gather. The per-lane work is six double-float
+// multiply-adds per candidate and plane, so the weight products are formed once per block
+// while staging: a group of eight threads per candidate evaluates the box-relative weights
+// of offset t on each axis, shares them by shuffles, and writes the candidate's 8 x 8 table
+// of w_x w_y products and its d x 8 values C_a w_z (plus w_z for the plane test).
+constexpr int kBoxChunkDD = 32;   // candidates per chunk (eight threads each)
+__global__ void __launch_bounds__(256)
+k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
+                 const dd* __restrict__ W, const dd* __restrict__ Cw, const int* __restrict__ slice_off,
+                 const int* __restrict__ box_item, const int* __restrict__ part_off, dd* __restrict__ part,
+                 dd* __restrict__ grid) {
+  __shared__ dd sXY[2][kBoxChunkDD * 64];  // [c][y][x] w_x w_y
+  __shared__ dd sCz[2][kBoxChunkDD * 24];  // [c][a][z] C_a w_z
+  __shared__ float sWz[2][kBoxChunkDD * 8];  // [c][z] w_z (high part: zero iff outside the window)
+  __shared__ int sStart[32], sPre[33];
+  __shared__ int sNr;
+  const int w = g.w, nf = g.nf, M = g.M;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int lx = lane & 7, ly = lane >> 3;
+  const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
+  const int nslices = slice_off[nbox];
+  for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+    const int box = box_item[sl], ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
+    const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
+    const int o[3] = {Bx * 8, By * 8, Bz * 8};
+    __syncthreads();
+    if (warp == 0) {  // candidate ranges of the neighbouring bins, in one round trip
+      int bin = 0;
+      const int nnb = nb_list(g, dlo, dhi, Bx, By, Bz, lane, &bin);
+      int p0 = 0, len = 0;
+      if (lane < nnb) { p0 = offsets[bin]; len = offsets[bin + 1] - p0; }
+      int incl = len;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+      }
+      const unsigned nonempty = __ballot_sync(0xffffffffu, len > 0);
+      if (len > 0) {
+        const int slot = __popc(nonempty & ((1u << lane) - 1u));
+        sStart[slot] = p0;
+        sPre[slot] = incl - len;
+      }
+      if (lane == 31) { sNr = __popc(nonempty); sPre[__popc(nonempty)] = incl; }
+    }
+    __syncthreads();
+    const int nr = sNr;
+    const int f0 = ks * g.slice, f1 = min(sPre[nr], f0 + g.slice);
+    // stage candidates [fa, fb) into buffer bb: eight threads per candidate, t = offset
+    auto stage = [&](int fa, int fb, int bb) {
+      const int c = threadIdx.x >> 3, t = threadIdx.x & 7;
+      const bool on = c < fb - fa;
+      dd wa[3] = {dd(0.0f), dd(0.0f), dd(0.0f)};
+      dd cv = dd(0.0f);
+      if (on) {
+        const int f = fa + c;
+        int lo = 0, hi = nr - 1;  // last range with sPre <= f
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sPre[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const long long sp = sStart[lo] + (f - sPre[lo]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          int q = o[a] + t - i0s[(long long)a * M + sp];  // (o_a + t - i0) mod nf
+          q += (q < 0) ? nf : 0; q -= (q >= nf) ? nf : 0; q -= (q >= nf) ? nf : 0;
+          wa[a] = (q < w) ? W[sp * 3 * w + a * w + q] : dd(0.0f);
+        }
+        if (t < 3) cv = Cw[sp * 3 + t];
+      }
+      // products: thread t owns row y = t of the x-y table and plane z = t of C w_z
+      dd* xy = &sXY[bb][c * 64 + t * 8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const float xh = __shfl_sync(0xffffffffu, wa[0].hi, (lane & ~7) | x);
+        const float xl = __shfl_sync(0xffffffffu, wa[0].lo, (lane & ~7) | x);
+        if (on) xy[x] = dd(xh, xl) * wa[1];
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float ch = __shfl_sync(0xffffffffu, cv.hi, (lane & ~7) | a);
+        const float cl = __shfl_sync(0xffffffffu, cv.lo, (lane & ~7) | a);
+        if (on) sCz[bb][c * 24 + a * 8 + t] = dd(ch, cl) * wa[2];
+      }
+      if (on) sWz[bb][c * 8 + t] = wa[2].hi;
+    };
+    dd acc[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) acc[k][a] = dd(0.0f);
+    int bb = 0;
+    stage(f0, min(f1, f0 + kBoxChunkDD), 0);
+    __syncthreads();
+    for (int c0 = f0; c0 < f1; c0 += kBoxChunkDD) {
+      const int nc = min(kBoxChunkDD, f1 - c0);
+      if (c0 + kBoxChunkDD < f1) stage(c0 + kBoxChunkDD, min(f1, c0 + 2 * kBoxChunkDD), bb ^ 1);
+      const dd* XY = sXY[bb];
+      const dd* CZ = sCz[bb];
+      const float* WZ = sWz[bb];
+      for (int c = 0; c < nc; ++c) {
+        if (WZ[c * 8 + warp] == 0.0f) continue;  // uniform across the warp
+        const dd t0 = XY[c * 64 + ly * 8 + lx], t1 = XY[c * 64 + (ly + 4) * 8 + lx];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const dd cz = CZ[c * 24 + a * 8 + warp];
+          dd_fma_acc(acc[0][a], cz, t0);
+          dd_fma_acc(acc[1][a], cz, t1);
+        }
+      }
+      __syncthreads();
+      bb ^= 1;
+    }
+    const long long gcells = (long long)nf * nf * nf;
+    const int cx = o[0] + lx, cz = o[2] + warp;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int yk = ly + 4 * k;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const dd v = dd_norm(acc[k][a]);
+        if (K == 1) {
+          grid[a * gcells + ((long long)cz * nf + (o[1] + yk)) * nf + cx] = v;
+        } else {
+          part[((long long)(part_off[box] + ks) * 3 + a) * 512 + (warp * 8 + yk) * 8 + lx] = v;
+        }
+      }
+    }
+  }
+  zero_empty_boxes<dd>(g, slice_off, nbox, grid);
+}
+
 // Boxes split into several slices: add their partials in slice order and store the box.
 // Persistent blocks walk the slice list and take the first slice of each split box.
 template <typename T>
@@ -938,14 +1070,25 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
     k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np);
     k_scan2<<<1, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
     k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item);
-    static const int per_sm = [] {
-      int n = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spread_box3<T>, 256, 0) != cudaSuccess || n < 1) n = 4;
-      return n;
-    }();
-    k_spread_box3<T><<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
-                                                    (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
-                                                    (T*)ws.part, grid);
+    if constexpr (std::is_same<T, dd>::value) {
+      static const int per_sm = [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spread_box3_dd, 256, 0) != cudaSuccess || n < 1) n = 4;
+        return n;
+      }();
+      k_spread_box3_dd<<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const dd*)ws.wts,
+                                                           (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
+                                                           (dd*)ws.part, grid);
+    } else {
+      static const int per_sm = [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spread_box3<T>, 256, 0) != cudaSuccess || n < 1) n = 4;
+        return n;
+      }();
+      k_spread_box3<T><<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
+                                                      (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
+                                                      (T*)ws.part, grid);
+    }
     k_box_reduce<T><<<4 * num_sms(), 256, 0, st>>>(g, ws.box_so, ws.box_item, ws.box_po, (const T*)ws.part, grid);
   } else
     k_spread_gather<T, 2><<<nbox, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
