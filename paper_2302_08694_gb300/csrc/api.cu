@@ -60,7 +60,13 @@ void raise_smem_limit(const void* kernel) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 48 * 1024;
   }
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  // the opt-in limit covers static and dynamic shared memory together
+  cudaFuncAttributes fa;
+  size_t stat = 0;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
+  const int dyn = optin - (int)stat;
+  if (dyn > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+    cudaGetLastError();
   done.insert(kernel);
 }
 

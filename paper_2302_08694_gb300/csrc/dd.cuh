@@ -88,4 +88,47 @@ __device__ __forceinline__ dd dd_norm(dd a) {
 }
 __device__ __forceinline__ dd& operator*=(dd& a, dd b) { a = a * b; return a; }
 
+// Square root of a non-negative value: one Newton correction of the FP32 root,
+// r + (a - r^2) / (2 r), with r^2 formed exactly by TwoProd (Karp and Markstein's form).
+__device__ __forceinline__ dd dd_sqrt(dd a) {
+  if (!(a.hi > 0.0f)) return dd(0.0f, 0.0f);
+  const float r = __fsqrt_rn(a.hi);
+  float p, e;
+  two_prod(r, r, p, e);
+  const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);  // a.hi - p is exact
+  const float c = __fmul_rn(res, __fdiv_rn(0.5f, r));
+  float h, l;
+  quick_two_sum(r, c, h, l);
+  return dd(h, l);
+}
+
+// exp(y) for -60 <= y <= 0 (the kernel's exponent). Range reduction y = k ln2 + t with
+// |t| <= ln2/2, ln2 split into three floats so that t is formed almost exactly (Cody and
+// Waite); e^t by its Taylor series to degree 14 (remainder below 1e-19) evaluated by
+// Horner's rule in double-float; the result is scaled by 2^k.
+__device__ __forceinline__ dd dd_exp_nonpos(dd y) {
+  const float k = rintf(__fmul_rn(y.hi, 1.4426950408889634f));
+  const float L1 = 0.693359375f, L2 = -2.1219444170128554e-4f, L3 = 1.6465949697480609e-12f;
+  const float a = __fsub_rn(y.hi, __fmul_rn(k, L1));  // exact: k L1 has at most 17 bits
+  float p2, e2;
+  two_prod(k, L2, p2, e2);
+  float s, se;
+  two_sum(a, -p2, s, se);
+  const float small = __fadd_rn(__fadd_rn(__fsub_rn(se, e2), -__fmul_rn(k, L3)), y.lo);
+  float th, tl;
+  quick_two_sum(s, small, th, tl);
+  const dd t(th, tl);
+  // 1/n! for n = 14 .. 0
+  constexpr dd c14(1.0 / 87178291200.0), c13(1.0 / 6227020800.0), c12(1.0 / 479001600.0),
+      c11(1.0 / 39916800.0), c10(1.0 / 3628800.0), c9(1.0 / 362880.0), c8(1.0 / 40320.0),
+      c7(1.0 / 5040.0), c6(1.0 / 720.0), c5(1.0 / 120.0), c4(1.0 / 24.0), c3(1.0 / 6.0), c2(0.5),
+      c1(1.0), c0(1.0);
+  dd P = c14;
+  P = P * t + c13; P = P * t + c12; P = P * t + c11; P = P * t + c10; P = P * t + c9;
+  P = P * t + c8;  P = P * t + c7;  P = P * t + c6;  P = P * t + c5;  P = P * t + c4;
+  P = P * t + c3;  P = P * t + c2;  P = P * t + c1;  P = P * t + c0;
+  const float sc = __int_as_float((127 + (int)k) << 23);  // 2^k, exact (k >= -87)
+  return dd(__fmul_rn(P.hi, sc), __fmul_rn(P.lo, sc));
+}
+
 }  // namespace fsib

@@ -422,17 +422,22 @@ template <> struct DeltaT<dd> { using type = double; };
 
 __device__ __forceinline__ float es_weight(float z, double beta) { return es_kernel<float>(z, (float)beta); }
 
+// s2w = 2/w and bdd = beta as double-float constants (used by the double-float version).
 template <typename T>
-__device__ __forceinline__ T weight_of(typename DeltaT<T>::type delta, int q, int w, double beta);
+__device__ __forceinline__ T weight_of(typename DeltaT<T>::type delta, int q, int w, double beta, dd s2w, dd bdd);
 template <>
-__device__ __forceinline__ float weight_of<float>(float delta, int q, int w, double beta) {
+__device__ __forceinline__ float weight_of<float>(float delta, int q, int w, double beta, dd, dd) {
   const float z = (2.0f / (float)w) * ((float)q + delta);
   return es_kernel<float>(z, (float)beta);
 }
 template <>
-__device__ __forceinline__ dd weight_of<dd>(double delta, int q, int w, double beta) {
-  const double z = (2.0 / (double)w) * ((double)q + delta);
-  return dd(es_kernel<double>(z, beta));
+__device__ __forceinline__ dd weight_of<dd>(double delta, int q, int, double, dd s2w, dd bdd) {
+  // phi(z) = exp(beta (sqrt(1 - z^2) - 1)), z = (2/w)(q + delta), in double-float on the FP32
+  // pipes (the FP64 pipe of this GPU is the slow one); q + delta is exact in FP64.
+  const dd z = dd((double)q + delta) * s2w;
+  const dd s = dd(1.0f) - z * z;
+  if (!(s.hi > 0.0f)) return dd(0.0f);
+  return dd_exp_nonpos((dd_sqrt(s) - dd(1.0f)) * bdd);
 }
 
 
@@ -440,7 +445,7 @@ __device__ __forceinline__ dd weight_of<dd>(double delta, int q, int w, double b
 // Transform modes float / dd, gather formulation.
 //
 // k_point_prep: for every sorted point s, the kernel weights W[s][a][q] =
-//   phi(2 (i0_a + q - t_a)/w) (evaluated in FP64 for dd, in float for float) and, for
+//   phi(2 (i0_a + q - t_a)/w) (in double-float on the FP32 pipes for dd, in float for float) and, for
 //   a spread, the weighted force C[s][a] = omega_j c_a,j.
 // k_spread_gather: one block per output box of bx * by (* bz) grid cells. Every point
 //   whose window meets the box lies in one of the neighbouring bins, so the block
@@ -458,13 +463,13 @@ constexpr int kSeg = 8;  // cells per thread run along x in the gather
 template <typename T, int D>
 __global__ void k_point_prep(PointGeom g, double beta, const typename DeltaT<T>::type* __restrict__ delta,
                              const int* __restrict__ perm, const double* __restrict__ cw,
-                             const double* __restrict__ omega, T* __restrict__ W, T* __restrict__ Cw) {
+                             const double* __restrict__ omega, T* __restrict__ W, T* __restrict__ Cw, dd s2w, dd bdd) {
   const int w = g.w, M = g.M;
   const long long nw = (long long)M * D * w;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nw; t += (long long)gridDim.x * blockDim.x) {
     const long long s = t / (D * w);
     const int r = (int)(t % (D * w)), a = r / w, q = r % w;
-    W[t] = weight_of<T>(delta[(long long)a * M + s], q, w, beta);
+    W[t] = weight_of<T>(delta[(long long)a * M + s], q, w, beta, s2w, bdd);
     if (Cw && q == 0) {
       const int j = perm[s];
       const double om = omega ? omega[j] : 1.0;
@@ -771,14 +776,18 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
 // of offset t on each axis, shares them by shuffles, and writes the candidate's 8 x 8 table
 // of w_x w_y products and its d x 8 values C_a w_z (plus w_z for the plane test).
 constexpr int kBoxChunkDD = 32;   // candidates per chunk (eight threads each)
+constexpr int kXYStride = 72;     // per-candidate stride of the x-y table (64 + 8: staging stores hit all banks)
 __global__ void __launch_bounds__(256)
 k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
                  const dd* __restrict__ W, const dd* __restrict__ Cw, const int* __restrict__ slice_off,
                  const int* __restrict__ box_item, const int* __restrict__ part_off, dd* __restrict__ part,
                  dd* __restrict__ grid) {
-  __shared__ dd sXY[2][kBoxChunkDD * 64];  // [c][y][x] w_x w_y
-  __shared__ dd sCz[2][kBoxChunkDD * 24];  // [c][a][z] C_a w_z
-  __shared__ float sWz[2][kBoxChunkDD * 8];  // [c][z] w_z (high part: zero iff outside the window)
+  // dynamic shared memory (above the 48 KB static limit): two buffers of
+  //   [c][y][x] w_x w_y (stride kXYStride), [c][a][z] C_a w_z, [c][z] w_z (high part)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dd (*sXY)[kBoxChunkDD * kXYStride] = reinterpret_cast<dd (*)[kBoxChunkDD * kXYStride]>(smem_raw);
+  dd (*sCz)[kBoxChunkDD * 24] = reinterpret_cast<dd (*)[kBoxChunkDD * 24]>(sXY + 2);
+  float (*sWz)[kBoxChunkDD * 8] = reinterpret_cast<float (*)[kBoxChunkDD * 8]>(sCz + 2);
   __shared__ int sStart[32], sPre[33];
   __shared__ int sNr;
   const int w = g.w, nf = g.nf, M = g.M;
@@ -835,13 +844,13 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
         }
         if (t < 3) cv = Cw[sp * 3 + t];
       }
-      // products: thread t owns row y = t of the x-y table and plane z = t of C w_z
-      dd* xy = &sXY[bb][c * 64 + t * 8];
+      // products: thread t owns column x = t of the x-y table and plane z = t of C w_z
+      dd* xy = &sXY[bb][c * kXYStride + t];
 #pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        const float xh = __shfl_sync(0xffffffffu, wa[0].hi, (lane & ~7) | x);
-        const float xl = __shfl_sync(0xffffffffu, wa[0].lo, (lane & ~7) | x);
-        if (on) xy[x] = dd(xh, xl) * wa[1];
+      for (int y = 0; y < 8; ++y) {
+        const float yh = __shfl_sync(0xffffffffu, wa[1].hi, (lane & ~7) | y);
+        const float yl = __shfl_sync(0xffffffffu, wa[1].lo, (lane & ~7) | y);
+        if (on) xy[y * 8] = wa[0] * dd(yh, yl);
       }
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -867,7 +876,7 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
       const float* WZ = sWz[bb];
       for (int c = 0; c < nc; ++c) {
         if (WZ[c * 8 + warp] == 0.0f) continue;  // uniform across the warp
-        const dd t0 = XY[c * 64 + ly * 8 + lx], t1 = XY[c * 64 + (ly + 4) * 8 + lx];
+        const dd t0 = XY[c * kXYStride + ly * 8 + lx], t1 = XY[c * kXYStride + (ly + 4) * 8 + lx];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const dd cz = CZ[c * 24 + a * 8 + warp];
@@ -1053,9 +1062,11 @@ void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const dou
   if (blocks > 64LL * num_sms()) blocks = 64LL * num_sms();
   T* Cw = cw ? (T*)ws.cwp : nullptr;
   if (p.d == 3)
-    k_point_prep<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw);
+    k_point_prep<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw,
+                                                      dd(2.0 / p.w), dd(p.beta));
   else
-    k_point_prep<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw);
+    k_point_prep<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw,
+                                                      dd(2.0 / p.w), dd(p.beta));
 }
 
 template <typename T>
@@ -1071,12 +1082,14 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
     k_scan2<<<1, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
     k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item);
     if constexpr (std::is_same<T, dd>::value) {
+      constexpr size_t smem = 2 * sizeof(dd) * kBoxChunkDD * (kXYStride + 24) + 2 * sizeof(float) * kBoxChunkDD * 8;
       static const int per_sm = [] {
+        raise_smem_limit(reinterpret_cast<const void*>(k_spread_box3_dd));
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spread_box3_dd, 256, 0) != cudaSuccess || n < 1) n = 4;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spread_box3_dd, 256, smem) != cudaSuccess || n < 1) n = 4;
         return n;
       }();
-      k_spread_box3_dd<<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const dd*)ws.wts,
+      k_spread_box3_dd<<<per_sm * num_sms(), 256, smem, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const dd*)ws.wts,
                                                            (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
                                                            (dd*)ws.part, grid);
     } else {
