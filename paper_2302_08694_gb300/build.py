@@ -76,7 +76,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         return obj
 
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 8))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = lib_path() + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

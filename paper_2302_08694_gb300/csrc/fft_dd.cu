@@ -2,5 +2,5 @@
 #include "fft_kernels.cuh"
 
 namespace fsib {
-FSIB_FFT_INST(dd)
+FSIB_FFT_INST_R(dd)
 }  // namespace fsib

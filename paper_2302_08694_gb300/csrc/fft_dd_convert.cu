@@ -1,7 +1,6 @@
-// Strided transform passes in double-float arithmetic that read or write FP64 spectra.
+// Strided transform passes in double-float arithmetic that read FP64 spectra (inverse).
 #include "fft_kernels.cuh"
 
 namespace fsib {
 FSIB_FFT_INST_S(dd, double, dd)
-FSIB_FFT_INST_S(dd, dd, double)
 }  // namespace fsib

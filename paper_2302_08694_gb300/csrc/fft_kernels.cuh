@@ -258,8 +258,7 @@ __device__ __forceinline__ void wfft_load_packed(C<T> (&v)[wfft_M(N)], const C<T
   if constexpr (sizeof(C<T>) != 8) {
 #pragma unroll
     for (int i = 0; i < M; ++i) v[i] = valid ? pack_rows<T>(A, B, l + L * i, N, h) : mk<T>(T(0), T(0));
-    return;
-  }
+  } else {
   C<T> a[M], b[M];
 #pragma unroll
   for (int i = 0; i < M; ++i) {
@@ -276,6 +275,7 @@ __device__ __forceinline__ void wfft_load_packed(C<T> (&v)[wfft_M(N)], const C<T
     if (k == 0) v[i] = mk<T>(a[i].x, b[i].x);                       // Hermitian part of m_x = 0
     else if (k < h) v[i] = mk<T>(a[i].x - b[i].y, a[i].y + b[i].x);   // A + iB
     else v[i] = mk<T>(a[i].x + b[i].y, b[i].x - a[i].y);              // conj(A) + i conj(B), or 0
+  }
   }
 }
 
@@ -663,13 +663,15 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
   });
 }
 
-#define FSIB_FFT_INST(T)                                                                         \
+#define FSIB_FFT_INST_R(T)                                                                       \
   template void launch_fft_rows_r2c<T>(const T*, C<T>*, long long, int, const FftLen&,           \
                                        const C<T>*, cudaStream_t);                               \
   template void launch_fft_rows_c2r<T>(const C<T>*, T*, long long, int, const FftLen&,           \
-                                       const C<T>*, cudaStream_t);                               \
+                                       const C<T>*, cudaStream_t);
+#define FSIB_FFT_INST_P(T)                                                                       \
   template void launch_rows_product<T>(const C<T>*, C<T>*, int, long long, int, const FftLen&,   \
                                        const C<T>*, cudaStream_t);
+#define FSIB_FFT_INST(T) FSIB_FFT_INST_R(T) FSIB_FFT_INST_P(T)
 #define FSIB_FFT_INST_S(T, Ti, To)                                                               \
   template void launch_fft_strided<T, Ti, To>(const C<Ti>*, C<To>*, int, int, int, int,          \
                                               const FftLen&, bool, Mult<T>, const C<T>*,         \
