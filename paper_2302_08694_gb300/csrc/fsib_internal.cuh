@@ -143,6 +143,7 @@ struct Workspace {
   int* box_so = nullptr;             // [nbins + 1] slice offsets
   int* box_po = nullptr;             // [nbins + 1] partial-slot offsets
   int* box_item = nullptr;           // [slices] box of each slice (non-empty boxes only)
+  int* box_work = nullptr;           // [2] gather work counters: next slice, next run of empty boxes
   void* part = nullptr;              // T[slots][3][512] partial boxes
   size_t part_slots = 0;
   // reverse mode (allocated on first use)

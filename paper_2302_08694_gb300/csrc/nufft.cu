@@ -610,36 +610,77 @@ __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restric
 }
 
 // Box of every slice: box_item[slice_off[b] + k] = b for k < K_b.
-__global__ void k_slice_boxes(int nbox, const int* __restrict__ slice_off, int* __restrict__ box_item) {
+// Also resets the gather's work counters for the launch that follows.
+__global__ void k_slice_boxes(int nbox, const int* __restrict__ slice_off, int* __restrict__ box_item,
+                              int* __restrict__ work) {
+  if (blockIdx.x == 0 && threadIdx.x < 2) work[threadIdx.x] = 0;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x)
     for (int k = slice_off[b]; k < slice_off[b + 1]; ++k) box_item[k] = b;
 }
 
-// Zero the boxes that no window reaches: warp per run of 32 boxes, 16-byte stores along x.
+// Next work of the calling block (dynamic scheduling, so that heavy and light slices spread
+// evenly over the SMs): a slice (work[0]) and, with it, a run of boxes to zero (work[1]), so
+// that the zero stores overlap the gathers. All threads of the block call it; it ends with
+// a barrier.
+__device__ __forceinline__ int next_slice(int* __restrict__ work, int* s_item, int* run) {
+  __syncthreads();  // every thread has read the previous item
+  if (threadIdx.x == 0) { s_item[0] = atomicAdd(&work[0], 1); s_item[1] = atomicAdd(&work[1], 1); }
+  __syncthreads();
+  *run = s_item[1];
+  return s_item[0];
+}
+
+// Zeroing of the boxes that no window reaches, in runs of 32 boxes claimed from a counter
+// (work[1]): 16-byte stores along x.
 template <typename T>
-__device__ __forceinline__ void zero_empty_boxes(const PointGeom& g, const int* __restrict__ slice_off, int nbox,
-                                                 T* __restrict__ grid) {
+__device__ __forceinline__ void zero_box(const PointGeom& g, int box, T* __restrict__ grid, int lane) {
   static_assert(sizeof(T) == 4 || sizeof(T) == 8, "grid element");
   constexpr int v_per_row = 8 * (int)sizeof(T) / 16;  // 16-byte vectors per 8-cell box row
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int nf = g.nf;
   const long long gcells = (long long)nf * nf * nf;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int b0 = gw * 32; b0 < nbox; b0 += nw * 32) {
-    const int bb = b0 + lane;
-    const bool empty = (bb < nbox) && (slice_off[bb + 1] == slice_off[bb]);
-    unsigned m = __ballot_sync(0xffffffffu, empty);
+  const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
+  for (int i = lane; i < 3 * 64 * v_per_row; i += 32) {
+    const int v = i % v_per_row, row = i / v_per_row;  // row = (a * 8 + z) * 8 + y
+    const int y = row & 7, z = (row >> 3) & 7, a = row >> 6;
+    T* r = grid + a * gcells + ((long long)(Bz * 8 + z) * nf + (By * 8 + y)) * nf + Bx * 8;
+    reinterpret_cast<float4*>(r)[v] = z4;
+  }
+}
+
+__device__ __forceinline__ bool box_empty(const int* __restrict__ slice_off, int nbox, int box) {
+  return box < nbox && slice_off[box + 1] == slice_off[box];
+}
+
+// One run by the whole block: warp w takes boxes 4w .. 4w + 3 of the run.
+template <typename T>
+__device__ __forceinline__ void zero_run_block(const PointGeom& g, const int* __restrict__ slice_off, int nbox,
+                                               T* __restrict__ grid, int run) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    const int box = run * 32 + warp * 4 + k;
+    if (box_empty(slice_off, nbox, box)) zero_box<T>(g, box, grid, lane);  // uniform across the warp
+  }
+}
+
+// The runs left when the slices are done, claimed warp by warp.
+template <typename T>
+__device__ __forceinline__ void zero_empty_boxes(const PointGeom& g, const int* __restrict__ slice_off, int nbox,
+                                                 T* __restrict__ grid, int* __restrict__ work) {
+  const int lane = threadIdx.x & 31;
+  const int nruns = (nbox + 31) / 32;
+  for (;;) {
+    int run = 0;
+    if (lane == 0) run = atomicAdd(&work[1], 1);
+    run = __shfl_sync(0xffffffffu, run, 0);
+    if (run >= nruns) break;
+    const int b0 = run * 32;
+    unsigned m = __ballot_sync(0xffffffffu, box_empty(slice_off, nbox, b0 + lane));
     while (m) {
       const int box = b0 + __ffs(m) - 1;
       m &= m - 1;
-      const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
-      for (int i = lane; i < 3 * 64 * v_per_row; i += 32) {
-        const int v = i % v_per_row, row = i / v_per_row;  // row = (a * 8 + z) * 8 + y
-        const int y = row & 7, z = (row >> 3) & 7, a = row >> 6;
-        T* r = grid + a * gcells + ((long long)(Bz * 8 + z) * nf + (By * 8 + y)) * nf + Bx * 8;
-        reinterpret_cast<float4*>(r)[v] = z4;
-      }
+      zero_box<T>(g, box, grid, lane);
     }
   }
 }
@@ -661,7 +702,7 @@ __global__ void __launch_bounds__(256)
 k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
               const T* __restrict__ W, const T* __restrict__ Cw, const int* __restrict__ slice_off,
               const int* __restrict__ box_item, const int* __restrict__ part_off, T* __restrict__ part,
-              T* __restrict__ grid) {
+              T* __restrict__ grid, int* __restrict__ work) {
   __shared__ T sB[2][kBoxChunk * 24];  // [c][axis][8] box-relative weights
   __shared__ T sC[2][kBoxChunk * 3];
   __shared__ int sStart[32], sPre[33];  // non-empty neighbour ranges: first point, prefix of lengths
@@ -671,7 +712,12 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
   const int lx = lane & 7, ly = lane >> 3;
   const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
   const int nslices = slice_off[nbox];
-  for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+  __shared__ int s_item[2];
+  for (;;) {
+    int run;
+    const int sl = next_slice(work, s_item, &run);
+    if (run < (nbox + 31) / 32) zero_run_block(g, slice_off, nbox, grid, run);
+    if (sl >= nslices) break;
     const int box = box_item[sl], ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
     const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
     const int o[3] = {Bx * 8, By * 8, Bz * 8};
@@ -767,7 +813,7 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
       }
     }
   }
-  zero_empty_boxes<T>(g, slice_off, nbox, grid);
+  zero_empty_boxes<T>(g, slice_off, nbox, grid, work);
 }
 
 // Double-float variant of the 3D gather. The per-lane work is six double-float
@@ -781,7 +827,7 @@ __global__ void __launch_bounds__(256)
 k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
                  const dd* __restrict__ W, const dd* __restrict__ Cw, const int* __restrict__ slice_off,
                  const int* __restrict__ box_item, const int* __restrict__ part_off, dd* __restrict__ part,
-                 dd* __restrict__ grid) {
+                 dd* __restrict__ grid, int* __restrict__ work) {
   // dynamic shared memory (above the 48 KB static limit): two buffers of
   //   [c][y][x] w_x w_y (stride kXYStride), [c][a][z] C_a w_z, [c][z] w_z (high part)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -795,7 +841,12 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
   const int lx = lane & 7, ly = lane >> 3;
   const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
   const int nslices = slice_off[nbox];
-  for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+  __shared__ int s_item[2];
+  for (;;) {
+    int run;
+    const int sl = next_slice(work, s_item, &run);
+    if (run < (nbox + 31) / 32) zero_run_block(g, slice_off, nbox, grid, run);
+    if (sl >= nslices) break;
     const int box = box_item[sl], ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
     const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
     const int o[3] = {Bx * 8, By * 8, Bz * 8};
@@ -903,7 +954,7 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
       }
     }
   }
-  zero_empty_boxes<dd>(g, slice_off, nbox, grid);
+  zero_empty_boxes<dd>(g, slice_off, nbox, grid, work);
 }
 
 // Boxes split into several slices: add their partials in slice order and store the box.
@@ -1080,7 +1131,7 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
     // slices per box, their prefix sums, then the sliced gather and the partial reduction
     k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np);
     k_scan2<<<1, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
-    k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item);
+    k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item, ws.box_work);
     if constexpr (std::is_same<T, dd>::value) {
       constexpr size_t smem = 2 * sizeof(dd) * kBoxChunkDD * (kXYStride + 24) + 2 * sizeof(float) * kBoxChunkDD * 8;
       static const int per_sm = [] {
@@ -1091,7 +1142,7 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
       }();
       k_spread_box3_dd<<<per_sm * num_sms(), 256, smem, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const dd*)ws.wts,
                                                            (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
-                                                           (dd*)ws.part, grid);
+                                                           (dd*)ws.part, grid, ws.box_work);
     } else {
       static const int per_sm = [] {
         int n = 0;
@@ -1100,7 +1151,7 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
       }();
       k_spread_box3<T><<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
                                                       (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
-                                                      (T*)ws.part, grid);
+                                                      (T*)ws.part, grid, ws.box_work);
     }
     k_box_reduce<T><<<4 * num_sms(), 256, 0, st>>>(g, ws.box_so, ws.box_item, ws.box_po, (const T*)ws.part, grid);
   } else
