@@ -444,19 +444,20 @@ k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, in
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
   {
     // every load of this thread is issued before the first shared-memory store
-    constexpr int NL = N * P / NT;
+    constexpr int NL = (N * P + NT - 1) / NT;  // N P need not be a multiple of the block size
     const int p = threadIdx.x % P, q = q0 + p;
     const bool qok = q < inner;
     C<Tin> raw[NL];
 #pragma unroll
     for (int k = 0; k < NL; ++k) {
       const int i = (threadIdx.x + k * NT) / P;
-      const int si = INV ? ((i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1)) : i;
+      const int si = (i >= N) ? -1 : INV ? ((i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1)) : i;
       raw[k] = (qok && si >= 0) ? src[(long long)si * inner + q] : C<Tin>{};
     }
 #pragma unroll
     for (int k = 0; k < NL; ++k) {
       const int t = threadIdx.x + k * NT, i = t / P;
+      if (t >= N * P) break;
       C<T> v = ccvt<T, Tin>(raw[k]);
       if (INV) {
         const int si = (i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1);

@@ -35,7 +35,7 @@ __device__ __forceinline__ double grid_coord(double x, double L, int nf) {
   double xm = x - L * floor(x / L);
   double t = xm * (double)nf / L;
   if (t >= (double)nf) t -= (double)nf;
-  if (t < 0.0) t = 0.0;
+  if (!(t >= 0.0 && t < (double)nf)) t = 0.0;  // also maps a non-finite position to a valid cell
   return t;
 }
 

@@ -60,7 +60,8 @@ def make(lib, N, d, M, prec, mu=1.0, rho=0.0, dt=1e-3, **kw):
 # --- type-1 / type-2 against the direct sums --------------------------------------------------
 
 @pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
-@pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1)])
+@pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1),
+                                   (3, 72, 211)])
 def test_spread_matches_oracle(lib, torch_mod, prec, d, N, M):
     torch = torch_mod
     rng = np.random.default_rng(100 + d * N + M)
@@ -77,7 +78,8 @@ def test_spread_matches_oracle(lib, torch_mod, prec, d, N, M):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
-@pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1)])
+@pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1),
+                                   (3, 72, 211)])
 def test_interp_matches_oracle(lib, torch_mod, prec, d, N, M):
     torch = torch_mod
     rng = np.random.default_rng(200 + d * N + M)
@@ -143,7 +145,7 @@ def test_stokeslet_matches_oracle(lib, torch_mod, prec, d, N):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
-@pytest.mark.parametrize("d,N", [(2, 16), (2, 10), (3, 8), (3, 12)])
+@pytest.mark.parametrize("d,N", [(2, 16), (2, 10), (3, 8), (3, 12), (3, 48), (3, 96)])
 def test_ns_substeps_match_oracle(lib, torch_mod, prec, d, N):
     torch = torch_mod
     rng = np.random.default_rng(400 + d + N)
