@@ -23,7 +23,7 @@ struct fsib_plan {
   cudaStream_t own = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaStream_t side = nullptr;                        // second branch of a Navier-Stokes step
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
   std::string err;
   bool ready = false;  // workspaces allocated for the current plan
   // per-launch-site profiler
@@ -226,13 +226,13 @@ static double fft_flops(double lines, int n) { return lines * 5.0 * n * std::log
 // Workspaces
 // ---------------------------------------------------------------------------
 static void free_ws(Workspace& ws) {
-  void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.s1, ws.s2, ws.s3, ws.s4, ws.fhat, ws.uhalf, ws.bin_of,
+  void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.grid2, ws.s1, ws.s2, ws.s3, ws.s4, ws.fhat, ws.uhalf, ws.bin_of,
                   ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
                   ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.wts, ws.cwp,
                   ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.box_item, ws.box_work, ws.part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  ws.tw = ws.dline = ws.dplane = ws.grid = ws.s1 = ws.s2 = ws.s3 = ws.s4 = ws.fhat = ws.uhalf = nullptr;
+  ws.tw = ws.dline = ws.dplane = ws.grid = ws.grid2 = ws.s1 = ws.s2 = ws.s3 = ws.s4 = ws.fhat = ws.uhalf = nullptr;
   ws.bin_of = ws.rank = ws.counts = ws.offsets = ws.occ = ws.nocc = ws.perm = ws.i0 = nullptr;
   ws.delta = nullptr;
   ws.Xh = ws.cw = ws.Uh = ws.omega_ones = ws.red = nullptr;
@@ -305,6 +305,7 @@ static int alloc_ws(fsib_plan* h) {
   if (!p.stokes) {
     rc |= dmalloc(&ws.s3, ws.s1_bytes, tot);
     rc |= dmalloc(&ws.s4, ws.s1_bytes, tot);
+    rc |= dmalloc(&ws.grid2, ws.grid_bytes, tot);
   }
   rc |= dmalloc(&ws.fhat, ws.spec_bytes, tot);
   rc |= dmalloc(&ws.uhalf, ws.spec_bytes, tot);
@@ -432,13 +433,15 @@ static void forward_fine(fsib_plan* h, const TI* grid, C<TA>* out, cudaStream_t 
 }
 
 template <typename TI, typename TA>
-static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t st) {
+// sa, sb: scratch pair (default S1, S2).
+static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t st, void* sa = nullptr,
+                         void* sb = nullptr) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const int N = p.N, hh = N / 2, n = p.nf, d = p.d;
   const C<TI>* tw = (const C<TI>*)ws.tw;
-  C<TI>* s1 = (C<TI>*)ws.s1;
-  C<TI>* s2 = (C<TI>*)ws.s2;
+  C<TI>* s1 = (C<TI>*)(sa ? sa : ws.s1);
+  C<TI>* s2 = (C<TI>*)(sb ? sb : ws.s2);
   Mult<TI> none;
   Mult<TI> dec;
   dec.dline = (const TI*)ws.dline;
@@ -624,10 +627,19 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     do_spread<TI, TA>(h, ws.Xh, ws.cw, nullptr, fhat, st);       // type-1 NUFFT
     if (fork) cudaStreamWaitEvent(st, h->ev_join, 0);
     do_fluid<TI, TA>(h, fhat, uhat, uh, st, P0);                 // Eqs. spatial_2, spatial_3
+    // The type-2 prep of u^{m+1} depends only on the fluid update: it runs on the second
+    // stream (scratch S3/S4, second fine grid) beside the U^{m+1/2} interp and the re-sort.
+    if (fork) {
+      cudaEventRecord(h->ev_fork2, st);
+      cudaStreamWaitEvent(h->side, h->ev_fork2, 0);
+    }
+    inverse_fine<TI, TA>(h, uhat, (TI*)ws.grid2, sb, ws.s3, ws.s4);
+    if (fork) cudaEventRecord(h->ev_join2, h->side);
     do_interp_sorted<TI, TA>(h, uh, ws.Uh, st);                  // U^{m+1/2} at X^{m+1/2}
     do_axpy(h, X, X, ws.Uh, p.dt, st);                           // Eq. spatial_4
     do_bin(h, X, st);
-    do_interp_sorted<TI, TA>(h, uhat, U, st);                    // U^{m+1} at X^{m+1}
+    if (fork) cudaStreamWaitEvent(st, h->ev_join2, 0);
+    interp_points<TI>(h, (const TI*)ws.grid2, U, st);            // U^{m+1} at X^{m+1}
   } else {
     // U(X^m)
     do_force(h, X, ws.cw, st);
@@ -761,7 +773,9 @@ int fsib_create(fsib_t* out, int N, int d, int M, double mu, double rho, double 
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     g_create_err = "CUDA stream/event creation failed (no device?)";
     delete h;
@@ -790,6 +804,8 @@ int fsib_destroy(fsib_t h) {
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_fork2) cudaEventDestroy(h->ev_fork2);
+  if (h->ev_join2) cudaEventDestroy(h->ev_join2);
   if (h->own) cudaStreamDestroy(h->own);
   if (h->side) cudaStreamDestroy(h->side);
   delete h;

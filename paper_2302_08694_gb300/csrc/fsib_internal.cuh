@@ -109,6 +109,7 @@ struct Workspace {
   void* s2 = nullptr;    size_t s2_bytes = 0;
   void* s3 = nullptr;    // second scratch pair (s1_bytes each, Navier-Stokes only): the
   void* s4 = nullptr;    // nonlinear term of u^m, computed beside the point side of the step
+  void* grid2 = nullptr;  // second fine grid (Navier-Stokes only): type-2 prep of u^{m+1} beside the U^{m+1/2} interp
   void* fhat = nullptr;  size_t spec_bytes = 0;  // d * N^{d-1} * N/2 complex
   void* uhalf = nullptr;
   // sort
