@@ -166,11 +166,11 @@ def run_reference(args):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the spread site
-# (k_box_slices, k_scan2, k_slice_boxes, k_spread_box3, k_box_reduce), from one ncu capture of
+# (k_box_slices, k_scan2, k_slice_boxes, k_spread_box3[_dd]), from one ncu capture of
 # the current kernels per workload; profiles/spread_site_traffic.txt has the command and the
 # per-kernel figures. Set an entry to None when those kernels change.
-SITE_TRAFFIC = {("ns3d_N64_M10082_fp64", "spread"): 19931904.0,
-                ("ns3d_N128_M40322_mixed", "spread"): 160440320.0}
+SITE_TRAFFIC = {("ns3d_N64_M10082_fp64", "spread"): None,
+                ("ns3d_N128_M40322_mixed", "spread"): None}
 
 
 def _events(torch):

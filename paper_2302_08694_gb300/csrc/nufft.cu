@@ -182,37 +182,33 @@ k_bin_scan(const int* __restrict__ counts, long long nbins, int* __restrict__ of
   if (threadIdx.x == 0) { offsets[nbins] = carry; *nocc = carry_o; }
 }
 
-// Exclusive scans of two int arrays of length n in one block; out arrays hold n + 1 entries.
+// Exclusive scans of two int arrays of length n, one per block (blockIdx.x = 0: a, 1: b);
+// out arrays hold n + 1 entries.
 __global__ void __launch_bounds__(kScanThreads)
 k_scan2(const int* __restrict__ a, const int* __restrict__ b, int n, int* __restrict__ oa, int* __restrict__ ob) {
-  __shared__ int wsum[2][32];
-  int ca = 0, cb = 0;
-  constexpr int PER = kScanPer / 2;  // two arrays in registers
-  for (long long base = 0; base < n; base += (long long)kScanThreads * PER) {
-    const long long i0 = base + (long long)threadIdx.x * PER;
-    int x[PER];
-    int v[2] = {0, 0}, tot[2];
-    scan_load(a, i0, n, x);
+  __shared__ int wsum[1][32];
+  const int* in = blockIdx.x ? b : a;
+  int* out = blockIdx.x ? ob : oa;
+  int carry = 0;
+  for (long long base = 0; base < n; base += (long long)kScanThreads * kScanPer) {
+    const long long i0 = base + (long long)threadIdx.x * kScanPer;
+    int x[kScanPer];
+    scan_load(in, i0, n, x);
+    int v[1] = {0}, tot[1];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) v[0] += x[k];
-    int y[PER];
-    scan_load(b, i0, n, y);
+    for (int k = 0; k < kScanPer; ++k) v[0] += x[k];
+    block_prefix<1>(v, tot, wsum);
+    int r = carry + v[0];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) v[1] += y[k];
-    block_prefix<2>(v, tot, wsum);
-    int ra = ca + v[0], rb = cb + v[1];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int ta = x[k], tb = y[k];
-      x[k] = ra; y[k] = rb;
-      ra += ta; rb += tb;
+    for (int k = 0; k < kScanPer; ++k) {
+      const int t = x[k];
+      x[k] = r;
+      r += t;
     }
-    scan_store(oa, i0, n, x);
-    scan_store(ob, i0, n, y);
-    ca += tot[0];
-    cb += tot[1];
+    scan_store(out, i0, n, x);
+    carry += tot[0];
   }
-  if (threadIdx.x == 0) { oa[n] = ca; ob[n] = cb; }
+  if (threadIdx.x == 0) out[n] = carry;
 }
 
 template <typename T>
@@ -593,7 +589,7 @@ __device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int
 
 // One warp per box: number of slices of the box.
 __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
-                             int* __restrict__ nslice, int* __restrict__ npart) {
+                             int* __restrict__ nslice, int* __restrict__ npart, int* __restrict__ done) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
   if (warp >= nbox) return;
@@ -606,6 +602,7 @@ __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restric
     const int K = (c + g.slice - 1) / g.slice;  // 0 for a box that no window reaches
     nslice[warp] = K;
     npart[warp] = (K > 1) ? K : 0;
+    done[warp] = 0;
   }
 }
 
@@ -685,6 +682,38 @@ __device__ __forceinline__ void zero_empty_boxes(const PointGeom& g, const int* 
   }
 }
 
+// Loads that bypass L1 (other blocks wrote the data during this kernel).
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ dd ld_cg(const dd* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return dd(v.x, v.y);
+}
+
+// After a block has stored the partial box of slice ks of a split box (K > 1 slices): the
+// block that finishes last adds the K partials in slice order and stores the box (the
+// fences make every partial visible before the count that reports it).
+template <typename T>
+__device__ __forceinline__ void finish_split_box(const PointGeom& g, int box, int K, const int* __restrict__ part_off,
+                                                 const T* part, T* __restrict__ grid, int* __restrict__ done,
+                                                 int* s_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_flag = (atomicAdd(&done[box], 1) == K - 1);
+  __syncthreads();
+  if (!*s_flag) return;
+  __threadfence();
+  const int nf = g.nf;
+  const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
+  const long long gcells = (long long)nf * nf * nf;
+  for (int i = threadIdx.x; i < 3 * 512; i += blockDim.x) {
+    const int a = i / 512, c = i % 512;
+    T v = T(0);
+    for (int k = 0; k < K; ++k) v = v + ld_cg(part + ((long long)(part_off[box] + k) * 3 + a) * 512 + c);
+    const int x = c % 8, y = (c / 8) % 8, z = c / 64;
+    grid[a * gcells + ((long long)(Bz * 8 + z) * nf + (By * 8 + y)) * nf + (Bx * 8 + x)] = v;
+  }
+}
+
 // 3D gather with an 8^3 box: warp z owns the box plane oz + z, lane l owns the cells
 // (x, y) = (l % 8, l / 8) and (l % 8, l / 8 + 4) of that plane for all three
 // components, in registers. The candidates (points of the neighbouring bins, taken in
@@ -702,7 +731,7 @@ __global__ void __launch_bounds__(256)
 k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
               const T* __restrict__ W, const T* __restrict__ Cw, const int* __restrict__ slice_off,
               const int* __restrict__ box_item, const int* __restrict__ part_off, T* __restrict__ part,
-              T* __restrict__ grid, int* __restrict__ work) {
+              T* __restrict__ grid, int* __restrict__ work, int* __restrict__ done) {
   __shared__ T sB[2][kBoxChunk * 24];  // [c][axis][8] box-relative weights
   __shared__ T sC[2][kBoxChunk * 3];
   __shared__ int sStart[32], sPre[33];  // non-empty neighbour ranges: first point, prefix of lengths
@@ -712,7 +741,7 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
   const int lx = lane & 7, ly = lane >> 3;
   const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
   const int nslices = slice_off[nbox];
-  __shared__ int s_item[2];
+  __shared__ int s_item[2], s_flag;
   for (;;) {
     int run;
     const int sl = next_slice(work, s_item, &run);
@@ -812,6 +841,7 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
         }
       }
     }
+    if (K > 1) finish_split_box<T>(g, box, K, part_off, part, grid, done, &s_flag);  // uniform across the block
   }
   zero_empty_boxes<T>(g, slice_off, nbox, grid, work);
 }
@@ -827,7 +857,7 @@ __global__ void __launch_bounds__(256)
 k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
                  const dd* __restrict__ W, const dd* __restrict__ Cw, const int* __restrict__ slice_off,
                  const int* __restrict__ box_item, const int* __restrict__ part_off, dd* __restrict__ part,
-                 dd* __restrict__ grid, int* __restrict__ work) {
+                 dd* __restrict__ grid, int* __restrict__ work, int* __restrict__ done) {
   // dynamic shared memory (above the 48 KB static limit): two buffers of
   //   [c][y][x] w_x w_y (stride kXYStride), [c][a][z] C_a w_z, [c][z] w_z (high part)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -841,7 +871,7 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
   const int lx = lane & 7, ly = lane >> 3;
   const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
   const int nslices = slice_off[nbox];
-  __shared__ int s_item[2];
+  __shared__ int s_item[2], s_flag;
   for (;;) {
     int run;
     const int sl = next_slice(work, s_item, &run);
@@ -953,33 +983,11 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
         }
       }
     }
+    if (K > 1) finish_split_box<dd>(g, box, K, part_off, part, grid, done, &s_flag);  // uniform across the block
   }
   zero_empty_boxes<dd>(g, slice_off, nbox, grid, work);
 }
 
-// Boxes split into several slices: add their partials in slice order and store the box.
-// Persistent blocks walk the slice list and take the first slice of each split box.
-template <typename T>
-__global__ void k_box_reduce(PointGeom g, const int* __restrict__ slice_off, const int* __restrict__ box_item,
-                             const int* __restrict__ part_off, const T* __restrict__ part, T* __restrict__ grid) {
-  const int nf = g.nf;
-  const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
-  const int nslices = slice_off[nbox];
-  const long long gcells = (long long)nf * nf * nf;
-  for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
-    const int box = box_item[sl];
-    const int K = slice_off[box + 1] - slice_off[box];
-    if (K <= 1 || sl != slice_off[box]) continue;  // uniform across the block
-    const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
-    for (int i = threadIdx.x; i < 3 * 512; i += blockDim.x) {
-      const int a = i / 512, c = i % 512;
-      T v = T(0);
-      for (int k = 0; k < K; ++k) v = v + part[((long long)(part_off[box] + k) * 3 + a) * 512 + c];
-      const int x = c % 8, y = (c / 8) % 8, z = c / 64;
-      grid[a * gcells + ((long long)(Bz * 8 + z) * nf + (By * 8 + y)) * nf + (Bx * 8 + x)] = v;
-    }
-  }
-}
 
 template <typename T, int D>
 __global__ void __launch_bounds__(256)
@@ -1129,8 +1137,9 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
   const int nbox = (int)p.nbins;
   if (p.d == 3) {
     // slices per box, their prefix sums, then the sliced gather and the partial reduction
-    k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np);
-    k_scan2<<<1, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
+    k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np,
+                                                           ws.box_done);
+    k_scan2<<<2, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
     k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item, ws.box_work);
     if constexpr (std::is_same<T, dd>::value) {
       constexpr size_t smem = 2 * sizeof(dd) * kBoxChunkDD * (kXYStride + 24) + 2 * sizeof(float) * kBoxChunkDD * 8;
@@ -1142,7 +1151,7 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
       }();
       k_spread_box3_dd<<<per_sm * num_sms(), 256, smem, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const dd*)ws.wts,
                                                            (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
-                                                           (dd*)ws.part, grid, ws.box_work);
+                                                           (dd*)ws.part, grid, ws.box_work, ws.box_done);
     } else {
       static const int per_sm = [] {
         int n = 0;
@@ -1151,9 +1160,8 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
       }();
       k_spread_box3<T><<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
                                                       (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
-                                                      (T*)ws.part, grid, ws.box_work);
+                                                      (T*)ws.part, grid, ws.box_work, ws.box_done);
     }
-    k_box_reduce<T><<<4 * num_sms(), 256, 0, st>>>(g, ws.box_so, ws.box_item, ws.box_po, (const T*)ws.part, grid);
   } else
     k_spread_gather<T, 2><<<nbox, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
 }
