@@ -361,9 +361,23 @@ k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, 
   }
 }
 
-// Products of the velocity components (three-halves rule), one row pair per L lanes:
-// inverse transforms of the d components into shared memory, then for each product
-// u_a u_b its forward transform and untangle. Blocks of 128 threads.
+// Schedule of the product pass (see k_wrows_product): kind 0 = inverse transform of
+// component a into slot b; kind 1 = product ab of slots a and b; x = slot used for the
+// transform's exchanges (encoded kind | a << 4 | b << 8 | x << 12 | ab << 16).
+static __constant__ int kProdSched3[9] = {0 | 0 << 4 | 0 << 8 | 2 << 12,            1 << 4 | 1 << 8 | 2 << 12,
+                                    1 | 0 << 4 | 0 << 8 | 2 << 12 | 0 << 16,  1 | 0 << 4 | 1 << 8 | 2 << 12 | 1 << 16,
+                                    1 | 1 << 4 | 1 << 8 | 2 << 12 | 3 << 16,  0 | 2 << 4 | 2 << 8 | 2 << 12,
+                                    1 | 0 << 4 | 2 << 8 | 0 << 12 | 2 << 16,  1 | 1 << 4 | 2 << 8 | 1 << 12 | 4 << 16,
+                                    1 | 2 << 4 | 2 << 8 | 2 << 12 | 5 << 16};
+static __constant__ int kProdSched2[5] = {0 | 0 << 4 | 0 << 8 | 2 << 12,            1 << 4 | 1 << 8 | 2 << 12,
+                                    1 | 0 << 4 | 0 << 8 | 2 << 12 | 0 << 16,  1 | 0 << 4 | 1 << 8 | 2 << 12 | 1 << 16,
+                                    1 | 1 << 4 | 1 << 8 | 2 << 12 | 2 << 16};
+
+// Products of the velocity components (three-halves rule), one row pair per L lanes, in
+// three line buffers S0..S2 of shared memory: u_x and u_y are transformed into S0 and S1
+// (exchanging through S2) and give xx, xy, yy (exchanging through S2); u_z then goes to S2,
+// and xz, yz, zz each exchange through the buffer of a component they no longer need (S0,
+// S1, S2), which takes three line buffers per row pair instead of four. Blocks of 128 threads.
 template <typename T, int N>
 __global__ void __launch_bounds__(128)
 k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows, int Nk,
@@ -373,38 +387,40 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int l = lane % L, sub = lane / L;
-  C<T>* U = tw + wfft_tw_size(N) + (warp * LPW + sub) * 4 * SL;  // [d][SL] components, then the exchange buffer
-  C<T>* buf = U + 3 * SL;
+  C<T>* S = tw + wfft_tw_size(N) + (warp * LPW + sub) * 3 * SL;  // S0, S1, S2
   wfft_build_twiddles<T, N>(tw, twg);
   __syncthreads();
-  const int h = Nk / 2, np = d * (d + 1) / 2;
+  const int h = Nk / 2;
   const long long npairs = nrows / 2;
+  const int nst = (d == 3) ? 9 : 5;
   for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
     const long long pr = g * LPW + sub;
     const bool valid = pr < npairs;
-    for (int c = 0; c < d; ++c) {
+#pragma unroll 1
+    for (int q = 0; q < nst; ++q) {
+      const int e = (d == 3) ? kProdSched3[q] : kProdSched2[q];
+      const int kind = e & 15, sa = (e >> 4) & 15, sb = (e >> 8) & 15, x = (e >> 12) & 15, ab = e >> 16;
+      C<T>* X = S + x * SL;
       C<T> v[M];
-      const C<T>* base = in + ((long long)c * nrows + 2 * pr) * h;
-      wfft_load_packed<T, N>(v, base, base + h, l, h, valid);
-      wfft<T, true, N>(v, buf, l, tw);
+      if (kind == 0) {
+        const C<T>* base = in + ((long long)sa * nrows + 2 * pr) * h;
+        wfft_load_packed<T, N>(v, base, base + h, l, h, valid);
+        wfft<T, true, N>(v, X, l, tw);
 #pragma unroll
-      for (int i = 0; i < M; ++i) U[c * SL + wfft_out_index<N>(l, i)] = v[i];
-    }
-    __syncwarp();
-    // products: the real part holds row 2p, the imaginary part row 2p+1
-    for (int ab = 0; ab < np; ++ab) {
-      int ca, cb;
-      if (d == 3) { ca = (ab < 3) ? 0 : (ab < 5 ? 1 : 2); cb = (ab < 3) ? ab : (ab < 5 ? ab - 2 : 2); }
-      else { ca = (ab < 2) ? 0 : 1; cb = (ab < 2) ? ab : 1; }
-      C<T> v[M];
+        for (int i = 0; i < M; ++i) S[sb * SL + wfft_out_index<N>(l, i)] = v[i];
+        __syncwarp();
+      } else {
+        // the real part holds row 2p, the imaginary part row 2p+1
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
-        const C<T> ua = U[ca * SL + l + L * i], ub = U[cb * SL + l + L * i];
-        v[i] = mk<T>(ua.x * ub.x, ua.y * ub.y);
+        for (int i = 0; i < M; ++i) {
+          const C<T> ua = S[sa * SL + l + L * i], ub = S[sb * SL + l + L * i];
+          v[i] = mk<T>(ua.x * ub.x, ua.y * ub.y);
+        }
+        __syncwarp();  // the exchange slot may hold a factor
+        wfft<T, false, N>(v, X, l, tw);
+        C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
+        wfft_untangle<T, N>(v, X, l, valid, h, ob, ob + h);
       }
-      wfft<T, false, N>(v, buf, l, tw);
-      C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
-      wfft_untangle<T, N>(v, buf, l, valid, h, ob, ob + h);
     }
   }
 }
@@ -652,10 +668,11 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
     constexpr int NC = decltype(nc)::value;
     if constexpr (wfft_has(NC)) {
       constexpr int LPW = 32 / wfft_L(NC);
-      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 4 * LPW * 4 * wfft_stride(NC, (int)sizeof(C<T>)));
+      constexpr int PT = 128;
+      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + (PT / 32) * LPW * 3 * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_product<T, NC>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
-      k<<<wrows_grid(k, 128, ws, (npairs + LPW - 1) / LPW), 128, ws, st>>>(in, out, d, nrows, Nk, tw + fl.tw_off);
+      k<<<wrows_grid(k, PT, ws, (npairs + LPW - 1) / LPW), PT, ws, st>>>(in, out, d, nrows, Nk, tw + fl.tw_off);
       return;
     }
     auto k = k_rows_product<T, decltype(nc)::value>;
