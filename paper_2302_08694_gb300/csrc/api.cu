@@ -24,6 +24,7 @@ struct fsib_plan {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaStream_t side = nullptr;                        // second branch of a Navier-Stokes step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
+  cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
   std::string err;
   bool ready = false;  // workspaces allocated for the current plan
   // per-launch-site profiler
@@ -627,16 +628,32 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     do_force(h, ws.Xh, ws.cw, st);                               // F^{m+1/2}
     do_spread<TI, TA>(h, ws.Xh, ws.cw, nullptr, fhat, st);       // type-1 NUFFT
     if (fork) cudaStreamWaitEvent(st, h->ev_join, 0);
-    do_fluid<TI, TA>(h, fhat, uhat, uh, st, P0);                 // Eqs. spatial_2, spatial_3
-    // The type-2 prep of u^{m+1} depends only on the fluid update: it runs on the second
-    // stream (scratch S3/S4, second fine grid) beside the U^{m+1/2} interp and the re-sort.
+    // Eqs. spatial_2, spatial_3. The type-2 prep of u^{m+1/2} needs only the half step: it runs
+    // on the second stream (scratch S3/S4, fine grid) beside the second nonlinear term and the
+    // full step; the type-2 prep of u^{m+1} follows it there (second fine grid), beside the
+    // U^{m+1/2} interp and the re-sort.
+    const double ub = (double)ws.spec_bytes / p.d * (p.d * (p.d + 1) / 2 + 3 * p.d);
+    { Prof pr(h, "ns_update", ub, 0.0, st);
+      launch_ns_update<TA>(p, P0, fhat, uhat, uh, true, st); }
+    if (fork) {
+      cudaEventRecord(h->ev_fork3, st);
+      cudaStreamWaitEvent(h->side, h->ev_fork3, 0);
+    }
+    inverse_fine<TI, TA>(h, uh, (TI*)ws.grid, sb, ws.s3, ws.s4);
+    if (fork) cudaEventRecord(h->ev_join3, h->side);
+    const C<TA>* P1 = products<TI, TA>(h, uh, st, ws.s1, ws.s2);
+    { Prof pr(h, "ns_update", ub, 0.0, st);
+      launch_ns_update<TA>(p, P1, fhat, uhat, uhat, false, st); }
     if (fork) {
       cudaEventRecord(h->ev_fork2, st);
       cudaStreamWaitEvent(h->side, h->ev_fork2, 0);
     }
     inverse_fine<TI, TA>(h, uhat, (TI*)ws.grid2, sb, ws.s3, ws.s4);
-    if (fork) cudaEventRecord(h->ev_join2, h->side);
-    do_interp_sorted<TI, TA>(h, uh, ws.Uh, st);                  // U^{m+1/2} at X^{m+1/2}
+    if (fork) {
+      cudaEventRecord(h->ev_join2, h->side);
+      cudaStreamWaitEvent(st, h->ev_join3, 0);
+    }
+    interp_points<TI>(h, (const TI*)ws.grid, ws.Uh, st);         // U^{m+1/2} at X^{m+1/2}
     do_axpy(h, X, X, ws.Uh, p.dt, st);                           // Eq. spatial_4
     do_bin(h, X, st);
     if (fork) cudaStreamWaitEvent(st, h->ev_join2, 0);
@@ -776,7 +793,9 @@ int fsib_create(fsib_t* out, int N, int d, int M, double mu, double rho, double 
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     g_create_err = "CUDA stream/event creation failed (no device?)";
     delete h;
@@ -807,6 +826,8 @@ int fsib_destroy(fsib_t h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_fork2) cudaEventDestroy(h->ev_fork2);
   if (h->ev_join2) cudaEventDestroy(h->ev_join2);
+  if (h->ev_fork3) cudaEventDestroy(h->ev_fork3);
+  if (h->ev_join3) cudaEventDestroy(h->ev_join3);
   if (h->own) cudaStreamDestroy(h->own);
   if (h->side) cudaStreamDestroy(h->side);
   delete h;
