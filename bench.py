@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-mixed workload block")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload block")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable workload block")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the NUFFT point-count sweep")
     ap.add_argument("--workload", choices=["ns3d_fp64", "ns3d_mixed"], default="ns3d_fp64",
                     help="workload of the main line (profiling runs use ns3d_mixed for the FP32 kernels)")
     return ap.parse_args()
@@ -388,6 +389,48 @@ def batched_block(fsib, torch, dev, flush, steps, warmup):
     return out
 
 
+def nufft_sweep(fsib, torch, dev, flush, sizes=(10**4, 10**5, 10**6, 10**7, 10**8), reps=3):
+    """NUFFT pts/s against M: uniform random points in the unit cube, N = 128^3, FP32-mixed,
+    tol 1e-6 (the point-dominated regime). Each transform: sort + spread + FFT passes +
+    deconvolution (type 1), or deconvolution + FFT passes + sort + interp (type 2)."""
+    stream = torch.cuda.current_stream()
+    out = []
+    gen = torch.Generator(device=dev)
+    for M in sizes:
+        gen.manual_seed(8000 + len(out))
+        try:
+            pb = fsib.Problem(128, 3, M, 1.0, 0.0, 1e-4, 1e-6, precision="mixed")
+            X = torch.rand((3, M), generator=gen, device=dev, dtype=torch.float64)
+            c = torch.randn((3, M), generator=gen, device=dev, dtype=torch.float64)
+            fh = pb.new_spec(device=dev)
+            uh = (torch.randn(pb.spec_shape, generator=gen, device=dev, dtype=torch.float32)
+                  + 1j * torch.randn(pb.spec_shape, generator=gen, device=dev, dtype=torch.float32)) * 1e-2
+            U = torch.empty_like(X)
+        except Exception as e:  # noqa: BLE001 - report and go on with the other sizes
+            out.append({"M": M, "skipped": str(e)[:200]})
+            continue
+        t = {1: 0.0, 2: 0.0}
+        for r in range(reps + 2):
+            for kind in (1, 2):
+                flush.zero_()
+                a, b = _events(torch)
+                a.record(stream)
+                if kind == 1:
+                    pb.spread(X, c, None, out=fh)
+                else:
+                    pb.interp(uh, X, out=U)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if r >= 2:
+                    t[kind] += a.elapsed_time(b)
+        out.append({"M": M, "type1_pts_per_s": M / (t[1] / reps * 1e-3), "type2_pts_per_s": M / (t[2] / reps * 1e-3),
+                    "type1_ms": t[1] / reps, "type2_ms": t[2] / reps})
+        pb.close()
+        del X, c, fh, uh, U
+        torch.cuda.empty_cache()
+    return {"workload": "uniform random points, N = 128^3, mixed, tol 1e-6", "points": out}
+
+
 def adjoint_block(fsib, torch, dev, reps=2):
     """Differentiable 3D Stokes (N = 96^3, M = 20002, K = 50, checkpoints every 10): gradient of
     sum_j (|X_j^K - c| - R)^2 w.r.t. X^0 and sigma by the FP32-mixed adjoint, checked against
@@ -523,6 +566,10 @@ def run_ours(args):
     if not args.no_adjoint:
         adjoint = adjoint_block(fsib, torch, dev)
 
+    sweep = None
+    if not args.no_sweep:
+        sweep = nufft_sweep(fsib, torch, dev, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and prec == "fp64":
         k = 2
@@ -544,7 +591,7 @@ def run_ours(args):
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": m["clocks"],
                 "gpu_launches": m["launches"] * args.steps, "launches_per_step": m["launches"],
                 "launch_shapes": m["launch_shapes"],
-                "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched,
+                "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched, "nufft_sweep": sweep,
                 "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:

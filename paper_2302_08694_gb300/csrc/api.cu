@@ -332,11 +332,13 @@ static int alloc_ws(fsib_plan* h) {
   rc |= dmalloc(&ws.box_so, sizeof(int) * (size_t)(p.nbins + 1), tot);
   rc |= dmalloc(&ws.box_po, sizeof(int) * (size_t)(p.nbins + 1), tot);
   // slices: at most one per non-empty box plus one per kMinSlice candidates (<= 27 M candidates)
-  rc |= dmalloc(&ws.box_item, sizeof(int) * (size_t)(p.nbins + 27 * (long long)p.M / kMinSlice + 64), tot);
+  rc |= dmalloc(&ws.box_item, sizeof(int) * (size_t)std::min<long long>(p.nbins + 27 * (long long)p.M / kMinSlice + 64,
+                                                                      17LL * p.nbins), tot);
   rc |= dmalloc(&ws.box_work, sizeof(int) * 4, tot);
   rc |= dmalloc(&ws.box_done, sizeof(int) * (size_t)p.nbins, tot);
   // partial slots: boxes with K > 1 hold K slots, K <= 2 cand/256; sum cand <= 27 M
-  ws.part_slots = (d == 3) ? (size_t)(2 * 27 * (long long)p.M / kMinSlice + 64) : 1;
+  // (and at most 16 per box: dense point sets get larger slices)
+  ws.part_slots = (d == 3) ? (size_t)std::min<long long>(2 * 27 * (long long)p.M / kMinSlice + 64, 16LL * p.nbins) : 1;
   rc |= dmalloc(&ws.part, sizeof(double) * 3 * 512 * ws.part_slots, tot);
   if (rc != FSIB_OK) { free_ws(ws); h->err = "device allocation failed"; return FSIB_ENOMEM; }
   g_ws_bytes = tot;

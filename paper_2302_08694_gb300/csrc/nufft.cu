@@ -567,8 +567,8 @@ __device__ __forceinline__ void fma_acc(dd& acc, dd a, dd b) { dd_fma_acc(acc, a
 __device__ __forceinline__ float acc_norm(float a) { return a; }
 __device__ __forceinline__ dd acc_norm(dd a) { return dd_norm(a); }
 
-// Work list of the 3D gather: box b is split into K_b = max(1, ceil(cand_b / kSliceCand))
-// slices of at most g.slice candidates (cand_b = points in its neighbouring bins).
+// Work list of the 3D gather: box b is split into K_b = ceil(cand_b / slice_size) slices
+// (cand_b = points in its neighbouring bins; K_b = 0 for a box that no window reaches).
 
 __device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int Bx, int By, int Bz, int lane,
                                        int* bin) {
@@ -587,6 +587,14 @@ __device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int
   return nnb;
 }
 
+// Candidates per slice of a box with c candidates: the plan's slice size, or more when that
+// would cut the box into more than kMaxSlices slices (dense point sets), so that the
+// partial boxes never exceed kMaxSlices per box.
+constexpr int kMaxSlices = 16;
+__device__ __forceinline__ int slice_size(const PointGeom& g, int c) {
+  return max(g.slice, (c + kMaxSlices - 1) / kMaxSlices);
+}
+
 // One warp per box: number of slices of the box.
 __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
                              int* __restrict__ nslice, int* __restrict__ npart, int* __restrict__ done) {
@@ -599,7 +607,8 @@ __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restric
   int c = (lane < nnb) ? offsets[bin + 1] - offsets[bin] : 0;
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   if (lane == 0) {
-    const int K = (c + g.slice - 1) / g.slice;  // 0 for a box that no window reaches
+    const int sz = slice_size(g, c);
+    const int K = (c + sz - 1) / sz;  // 0 for a box that no window reaches; at most kMaxSlices
     nslice[warp] = K;
     npart[warp] = (K > 1) ? K : 0;
     done[warp] = 0;
@@ -773,7 +782,8 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
     __syncthreads();
     const int nr = sNr;
     // this slice takes candidates [ks * slice, (ks + 1) * slice) of the concatenated ranges
-    const int f0 = ks * g.slice, f1 = min(sPre[nr], f0 + g.slice);
+    const int sz = slice_size(g, sPre[nr]);
+    const int f0 = ks * sz, f1 = min(sPre[nr], f0 + sz);
     // stage candidates [fa, fb) into buffer bb: one thread per (candidate, axis)
     auto stage = [&](int fa, int fb, int bb) {
       for (int i = threadIdx.x; i < (fb - fa) * 3; i += blockDim.x) {
@@ -902,7 +912,8 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
     }
     __syncthreads();
     const int nr = sNr;
-    const int f0 = ks * g.slice, f1 = min(sPre[nr], f0 + g.slice);
+    const int sz = slice_size(g, sPre[nr]);
+    const int f0 = ks * sz, f1 = min(sPre[nr], f0 + sz);
     // stage candidates [fa, fb) into buffer bb: eight threads per candidate, t = offset
     auto stage = [&](int fa, int fb, int bb) {
       const int c = threadIdx.x >> 3, t = threadIdx.x & 7;

@@ -77,6 +77,26 @@ def test_spread_matches_oracle(lib, torch_mod, prec, d, N, M):
     assert relmax(got, ref) <= 10 * TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_spread_dense_points_many_slices(lib, torch_mod, prec):
+    """Uniform points dense enough that a gather box would need more than 16 slices of 128
+    candidates: the slices grow instead, and split boxes are summed from their partials."""
+    torch = torch_mod
+    rng = np.random.default_rng(321)
+    d, N, M = 3, 16, 20000
+    X = rng.uniform(0.0, 1.0, (d, M))
+    F = rng.standard_normal((d, M))
+    pb = make(lib, N, d, M, prec)
+    pb.set_option("spread_slice", 128)
+    for _ in range(2):  # twice: the work counters and partial counts start from zero each call
+        fh = pb.spread(cuda(X, torch), cuda(F, torch))
+        torch.cuda.synchronize()
+        ref = sp.full_to_half(sp.spread_direct(X, F, N), N)
+        got = to_np(fh)
+        assert rel2(got, ref) <= TOL[prec]
+        assert relmax(got, ref) <= 10 * TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
 @pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1),
                                    (3, 72, 211)])
