@@ -42,6 +42,17 @@ def enclosed_area(X: np.ndarray) -> float:
 # Triangulated membrane with cot-weight springs (Sec. 6.2.3)
 # ---------------------------------------------------------------------------
 
+def target_force(X: np.ndarray, Xt: np.ndarray, K: float) -> np.ndarray:
+    """Target-point springs F_i = K (X~_i - X_i) that hold wall markers near fixed
+    targets (Poiseuille channel, Sec. 5.2.2)."""
+    return K * (Xt - X)
+
+
+def target_energy(X: np.ndarray, Xt: np.ndarray, K: float, omega: float) -> float:
+    """E_p = (omega K / 2) sum_i |X~_i - X_i|^2, so that omega F_i = -dE_p/dX_i."""
+    return float(0.5 * omega * K * np.sum((Xt - X) ** 2))
+
+
 def _edge_lengths_sq(X, tri):
     A, B, C = X[:, tri[:, 0]], X[:, tri[:, 1]], X[:, tri[:, 2]]
     a2 = np.sum((B - C) ** 2, axis=0)  # opposite A

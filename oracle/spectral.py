@@ -337,6 +337,29 @@ def ns_substeps(fhat: np.ndarray, uhat: np.ndarray, N: int, mu: float, rho: floa
 # Spectral diagnostics (Sec. 4)
 # ---------------------------------------------------------------------------
 
+def band_flux(uhat: np.ndarray, N: int, comp: int, axis: int, y0: float, y1: float,
+              L: float = 1.0) -> float:
+    """Flux of velocity component `comp` through the band y0 <= x_axis <= y1.
+
+    Phi = int_{y0}^{y1} ubar(y) dy, where ubar is u_comp averaged over the other
+    axes (the channel flux of Eq. poiseuille_flux for a laminar flow). Only the
+    modes m e_axis survive the average: ubar(y) = sum_m u-hat(m e_axis) e^{i k_m y}.
+    """
+    d = uhat.shape[0]
+    m = mode_ints(N).astype(np.float64)
+    k = TWO_PI / L * m
+    idx = [0] * d
+    acc = 0.0 + 0.0j
+    for i in range(N):
+        idx[d - 1 - axis] = i
+        if k[i] == 0.0:
+            I = y1 - y0
+        else:
+            I = (np.exp(1j * k[i] * y1) - np.exp(1j * k[i] * y0)) / (1j * k[i])
+        acc += uhat[(comp,) + tuple(idx)] * I
+    return float(acc.real)
+
+
 def kinetic_energy(uhat: np.ndarray, N: int, rho: float, L: float = 1.0) -> float:
     """E_K = (1/2) rho L^d sum_k u-hat(k) . conj(u-hat(k)) (Sec. 4.4)."""
     d = uhat.shape[0]

@@ -29,7 +29,26 @@ def mesh_model(Xref: np.ndarray, tri: np.ndarray, sigma: float):
     return force
 
 
-def ns_step(X, uhat, U, force, N, mu, rho, dt, L=1.0, Nt=None):
+def target_model(Xt: np.ndarray, K: float, omega: float):
+    """Target-point springs (Sec. 5.2.2) weighted by omega (the Lagrangian meshwidth)."""
+    def force(X):
+        return omega * lg.target_force(X, Xt, K)
+    return force
+
+
+def add_body_force(fhat: np.ndarray, fbody) -> np.ndarray:
+    """Add a uniform body force density f0 (Sec. 5.2.2): its coefficient under
+    f-hat(k) = L^-d int f e^{-ik.x} dx is f0 at k = 0 and zero elsewhere."""
+    if fbody is None:
+        return fhat
+    out = fhat.copy()
+    d = fhat.shape[0]
+    for a in range(d):
+        out[(a,) + (0,) * d] += fbody[a]
+    return out
+
+
+def ns_step(X, uhat, U, force, N, mu, rho, dt, L=1.0, Nt=None, fbody=None):
     """One step of Algorithm 1 (Eqs. spatial_1 to spatial_4).
 
     Inputs: X^m (d, M), full-spectrum u-hat^m, and U^m = u(X^m).
@@ -37,12 +56,13 @@ def ns_step(X, uhat, U, force, N, mu, rho, dt, L=1.0, Nt=None):
     direct type-1 sum; u-hat^{m+1/2} and u-hat^{m+1} by the BE/CN substeps;
     U^{m+1/2} = u^{m+1/2}(X^{m+1/2}); X^{m+1} = X^m + dt U^{m+1/2}; and
     U^{m+1} = u^{m+1}(X^{m+1}), evaluated after the position update (the order
-    Algorithm 1 needs, since X^{m+1} must exist first).
+    Algorithm 1 needs, since X^{m+1} must exist first). A uniform body force
+    fbody (length d), if given, is added to f-hat.
     Returns (X^{m+1}, u-hat^{m+1}, U^{m+1}).
     """
     Xh = X + 0.5 * dt * U
     c = force(Xh)
-    fhat = sp.spread_direct(Xh, c, N, L)
+    fhat = add_body_force(sp.spread_direct(Xh, c, N, L), fbody)
     uh, u1 = sp.ns_substeps(fhat, uhat, N, mu, rho, dt, L, Nt)
     Uh = sp.interp_direct(uh, Xh, N, L)
     X1 = X + dt * Uh

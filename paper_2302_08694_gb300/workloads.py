@@ -211,3 +211,67 @@ def config_batched(seed: int = 4, nprob: int = 64):
             probs.append(Problem(f"b{i}_3d", 3, N, X0.shape[1], 0.01, 1.0, 1e-4, 1, 1e-6,
                                  "mixed", "mesh", X0, 1.0, tri=tri, Xref=Xref))
     return probs
+
+
+# ---------------------------------------------------------------------------
+# Two-dimensional Navier-Stokes validation workloads (Secs. 5.2.1, 5.2.2)
+# ---------------------------------------------------------------------------
+
+def sine_velocity_half(N: int) -> np.ndarray:
+    """Initial velocity u_0 = (0, sin(2 pi x / L)) in the half-spectrum layout (d = 2).
+
+    sin(2 pi x) = (e^{2 pi i x} - e^{-2 pi i x}) / (2i): the y component holds
+    -i/2 at m = (1, 0); the mode m = (-1, 0) is its mirror and is implied.
+    Shape (2, N, N//2), complex128.
+    """
+    u = np.zeros((2, N, N // 2), dtype=np.complex128)
+    u[1, 0, 1] = -0.5j
+    return u
+
+
+def config_ns2d_circle(N: int = 64, Nb: int = 202, dt: float = 1e-3, T: float = 10.0,
+                       precision: str = "fp64") -> Problem:
+    """Circle of radius L/4 at the box centre in the sine flow (Sec. 5.2.1).
+
+    N = 64, N_b = 202 (h_b close to L/N), dt = 1e-3, K = 1, rho = 1, mu = 0.01, and
+    the boundary released in u_0 = (0, sin(2 pi x/L)); T = 10 is long enough for the
+    boundary to return to a circle.
+    """
+    X0 = ellipse(Nb, 0.25 * L_BOX, 0.25 * L_BOX, (0.5 * L_BOX, 0.5 * L_BOX))
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    nsteps = int(round(T / dt))
+    return Problem(f"ns2d_circle_N{N}_Nb{Nb}_{precision}", 2, N, Nb, 0.01, 1.0, dt, nsteps, tol,
+                   precision, "curve", X0, 1.0, extra={"u0": sine_velocity_half(N), "T": T})
+
+
+def channel_targets(N: int) -> np.ndarray:
+    """Target points of the two channel walls (Sec. 5.2.2): X~_i = (i h, L/4) and
+    X~_{i+N} = (i h, 3L/4), i = 0..N-1, h = L/N; shape (2, 2N)."""
+    h = L_BOX / N
+    x = h * np.arange(N, dtype=np.float64)
+    lo = np.stack([x, np.full(N, 0.25 * L_BOX)])
+    hi = np.stack([x, np.full(N, 0.75 * L_BOX)])
+    return np.concatenate([lo, hi], axis=1)
+
+
+def config_poiseuille(N: int = 8, K: float = 1.0e4, T: float = 3.0, dt: float | None = None,
+                      precision: str = "fp64") -> Problem:
+    """Navier-Stokes flow in a channel with target-point walls (Sec. 5.2.2).
+
+    L = 1, mu = 0.1, rho = 1, body force f0 = 100 along x, walls at y = L/4 and 3L/4
+    (D = L/2) with N_b = 2N markers started on their targets, fluid at rest.
+    The paper states neither the target stiffness K nor dt: K = 1e4 and
+    dt = 1e-3 * 8/N (dt proportional to h) keep the explicit spring stable, and
+    T = 3 is about twelve decay times of the slowest channel mode
+    (rate mu (pi/D)^2 / rho = 3.95), so the flux is steady to about 1e-5.
+    """
+    if dt is None:
+        dt = 1e-3 * 8.0 / N
+    Xt = channel_targets(N)
+    h = L_BOX / N
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    nsteps = int(round(T / dt))
+    return Problem(f"poiseuille_N{N}_{precision}", 2, N, 2 * N, 0.1, 1.0, dt, nsteps, tol,
+                   precision, "target", Xt.copy(), K,
+                   extra={"Xtarget": Xt, "omega": h, "fbody": (100.0, 0.0), "band": (0.25, 0.75),
+                          "D": 0.5 * L_BOX, "f0": 100.0, "T": T})
