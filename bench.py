@@ -48,7 +48,10 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload block")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable workload block")
     ap.add_argument("--no-sweep", action="store_true", help="skip the NUFFT point-count sweep")
-    ap.add_argument("--workload", choices=["ns3d_fp64", "ns3d_mixed"], default="ns3d_fp64",
+    ap.add_argument("--no-validation", action="store_true",
+                    help="skip the 2D Navier-Stokes validation block (sine circle, Poiseuille channel)")
+    ap.add_argument("--workload", choices=["ns3d_fp64", "ns3d_mixed", "ns2d_circle", "poiseuille"],
+                    default="ns3d_fp64",
                     help="workload of the main line (profiling runs use ns3d_mixed for the FP32 kernels)")
     return ap.parse_args()
 
@@ -118,23 +121,44 @@ def make_problem(fsib, prob, precision):
         pb.set_option("native_fp64", 1)
     if prob.force == "mesh":
         pb.set_force_mesh(prob.tri, prob.Xref, prob.stiffness)
+    elif prob.force == "target":
+        pb.set_force_target(prob.extra["Xtarget"], prob.stiffness, prob.extra["omega"])
     else:
         pb.set_force_curve(prob.stiffness)
+    if "fbody" in prob.extra:
+        pb.set_body_force(prob.extra["fbody"])
     return pb
 
 
 def time_oracle_steps(prob, nsteps):
     from oracle import spectral as sp
     from oracle import stepper as st
-    force = st.mesh_model(prob.Xref, prob.tri, prob.stiffness)
-    N = prob.N
+    if prob.force == "mesh":
+        force = st.mesh_model(prob.Xref, prob.tri, prob.stiffness)
+    elif prob.force == "target":
+        force = st.target_model(prob.extra["Xtarget"], prob.stiffness, prob.extra["omega"])
+    else:
+        force = st.curve_model(prob.stiffness)
+    N, d = prob.N, prob.d
     X = prob.X0.copy()
-    u = np.zeros((3, N, N, N), dtype=complex)
+    u = np.zeros((d,) + (N,) * d, dtype=complex)
     U = np.zeros_like(X)
+    fbody = prob.extra.get("fbody")
     t0 = time.perf_counter()
     for _ in range(nsteps):
-        X, u, U = st.ns_step(X, u, U, force, N, prob.mu, prob.rho, prob.dt)
+        X, u, U = st.ns_step(X, u, U, force, N, prob.mu, prob.rho, prob.dt, fbody=fbody)
     return time.perf_counter() - t0
+
+
+def workload_of(name):
+    """(problem, precision) of a named benchmark workload."""
+    if name == "ns3d_mixed":
+        return wl.config_ns3d_mixed(), "mixed"
+    if name == "ns2d_circle":
+        return wl.config_ns2d_circle(), "fp64"
+    if name == "poiseuille":
+        return wl.config_poiseuille(N=64), "fp64"
+    return wl.config_ns3d_fp64(), "fp64"
 
 
 def cpu_threads():
@@ -148,7 +172,7 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
-    prob = wl.config_ns3d_fp64()
+    prob, _ = workload_of(args.workload if args.workload != "ns3d_mixed" else "ns3d_fp64")
     k = max(1, min(args.steps, 10))
     w = min(args.warmup, 1)
     if w:
@@ -158,7 +182,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": k, "warmup": w, "ms_per_step": 1e3 * t / k, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": prob.name, "d": 3, "N": prob.N, "M": prob.M, "nsteps_config": prob.nsteps},
+            "config": {"workload": prob.name, "d": prob.d, "N": prob.N, "M": prob.M, "nsteps_config": prob.nsteps},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": f"{k} full oracle steps (direct non-uniform sums, numpy BLAS/FFT) of the "
                                        f"workload, {w} warm-up; K capped at 10 to bound the run"},
@@ -497,6 +521,116 @@ def adjoint_block(fsib, torch, dev, reps=2):
     return out
 
 
+def _chunked_steps(torch, pb, X, u, U, total, chunk, flush, stream, probe=None):
+    """Advance `total` steps in graph-replayed chunks; device time of the chunks (L2
+    flushed between chunks, outside the events); probe(step) runs after each chunk."""
+    ms, done = 0.0, 0
+    while done < total:
+        n = min(chunk, total - done)
+        flush.zero_()
+        a, b = _events(torch)
+        a.record(stream)
+        pb.step(X, u, U, nsteps=n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        done += n
+        if probe:
+            probe(done)
+    return ms
+
+
+def validation_block(fsib, torch, dev, flush, cpu_sample=True):
+    """The paper's 2D Navier-Stokes checks, run on the library (FP64 transforms):
+    sine-velocity circle (Sec. 5.2.1: area over T = 10, temporal order at t = 0.1)
+    and the Poiseuille channel on target-point walls (Sec. 5.2.2: flux against
+    Eq. poiseuille_flux, effective boundary width against N)."""
+    from paper_2302_08694_gb300 import validation as va
+    stream = torch.cuda.current_stream()
+    out = {}
+    # -- circle in the sine flow: N = 64, N_b = 202, dt = 1e-3, T = 10
+    prob = wl.config_ns2d_circle()
+    pb = make_problem(fsib, prob, "fp64")
+    X = torch.from_numpy(prob.X0.copy()).to(dev)
+    u = torch.from_numpy(prob.extra["u0"]).to(dev)
+    U = pb.interp(u, X)
+    A0 = pb.invariants(X)["volume"]
+    area = []
+
+    def probe(step):
+        area.append(pb.invariants(X)["volume"] / A0)
+    ms = _chunked_steps(torch, pb, X, u, U, prob.nsteps, 100, flush, stream, probe)
+    Xn = X.cpu().numpy()
+    r = np.hypot(Xn[0] - Xn[0].mean(), Xn[1] - Xn[1].mean())
+    circle = {"workload": prob.name, "steps": prob.nsteps, "steps_per_s": prob.nsteps / (ms * 1e-3),
+              "ms_per_step": ms / prob.nsteps, "timing": "graph replays of 100 steps, L2 flushed between",
+              "area_ratio_min": min(area), "area_ratio_max": max(area), "area_ratio_final": area[-1],
+              "radius_rel_spread_final": float(r.std() / r.mean())}
+    if cpu_sample:
+        from oracle import spectral as osp
+        from oracle import stepper as ost
+        force = ost.curve_model(prob.stiffness)
+        Xo = prob.X0.copy()
+        uo = osp.half_to_full(prob.extra["u0"], prob.N, 2)
+        Uo = osp.interp_direct(uo, Xo, prob.N)
+        k = 20
+        t0 = time.perf_counter()
+        for _ in range(k):
+            Xo, uo, Uo = ost.ns_step(Xo, uo, Uo, force, prob.N, prob.mu, prob.rho, prob.dt)
+        circle["cpu_baseline"] = {"value": k / (time.perf_counter() - t0), "unit": "steps/s",
+                                  "cores": cpu_threads(), "kind": "oracle",
+                                  "sample": f"{k} oracle steps of the same workload"}
+    # temporal order: dt = 0.002 / 2^j against dt = 0.002 / 64 at t = 0.1 (same N, N_b)
+    sols = {}
+    for j in (0, 1, 2, 3, 4, 6):
+        dt = 0.002 / 2 ** j
+        pj = wl.config_ns2d_circle(dt=dt, T=0.1)
+        pbj = make_problem(fsib, pj, "fp64")
+        Xj = torch.from_numpy(pj.X0.copy()).to(dev)
+        uj = torch.from_numpy(pj.extra["u0"]).to(dev)
+        Uj = pbj.interp(uj, Xj)
+        pbj.step(Xj, uj, Uj, nsteps=pj.nsteps)
+        sols[dt] = uj.cpu().numpy()
+        pbj.close()
+    ref = sols[0.002 / 64]
+    errs = {f"{dt:g}": rel_err(v, ref) for dt, v in sols.items() if dt != 0.002 / 64}
+    ev = list(errs.values())
+    circle["temporal_error_at_t0.1"] = errs
+    circle["temporal_order"] = [float(np.log2(a / b)) for a, b in zip(ev[:-1], ev[1:])]
+    out["sine_circle"] = circle
+    pb.close()
+    # -- Poiseuille channel: flux history and effective wall width against N
+    chan = []
+    for N in (8, 16, 32, 64, 128):
+        pp = wl.config_poiseuille(N=N)
+        ex = pp.extra
+        pbp = make_problem(fsib, pp, "fp64")
+        Xp = torch.from_numpy(pp.X0.copy()).to(dev)
+        up = pbp.new_spec(device=dev)
+        Up = pbp.interp(up, Xp)
+        D, f0 = ex["D"], ex["f0"]
+        steady = va.poiseuille_steady_flux(f0, pp.mu, D)
+        marks = {int(round(t / pp.dt)): t for t in (0.05, 0.1, 0.2, 0.5, 1.0, 2.0, 3.0)}
+        hist = []
+
+        def probe_c(step, pbp=pbp, up=up, marks=marks, hist=hist, steady=steady):
+            if step in marks:
+                hist.append((marks[step], pbp.band_flux(up, 0, 1, *ex["band"]) / steady - 1.0))
+        chunk = max(1, min(int(round(0.05 / pp.dt)), 1000))
+        msp = _chunked_steps(torch, pbp, Xp, up, Up, pp.nsteps, chunk, flush, stream, probe_c)
+        flux = pbp.band_flux(up, 0, 1, *ex["band"])
+        h = 1.0 / N
+        ana = va.poiseuille_flux([t for t, _ in hist], f0, pp.mu, pp.rho, D) / steady - 1.0
+        chan.append({"N": N, "Nb": 2 * N, "dt": pp.dt, "steps": pp.nsteps,
+                     "steps_per_s": pp.nsteps / (msp * 1e-3),
+                     "flux_rel_history": [[t, v, float(a)] for (t, v), a in zip(hist, ana)],
+                     "effective_width_over_h": (D - va.effective_width(flux, f0, pp.mu)) / h})
+        pbp.close()
+    out["poiseuille"] = {"K": wl.config_poiseuille().stiffness, "by_N": chan,
+                         "flux_rel_history_columns": ["t", "(Phi - Phi_eq)/Phi_eq FSIB", "same, Eq. poiseuille_flux"]}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -516,10 +650,7 @@ def run_ours(args):
 
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if \
         os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
-    if args.workload == "ns3d_mixed":
-        prob, prec = wl.config_ns3d_mixed(), "mixed"
-    else:
-        prob, prec = wl.config_ns3d_fp64(), "fp64"
+    prob, prec = workload_of(args.workload)
     m = measure(fsib, torch, prob, prec, args.steps, args.warmup, dev, flush, world, barrier, gpu_index)
     pb = m["pb"]
     ms_max = max_over_ranks(m["ms"], world, dev)
@@ -570,9 +701,13 @@ def run_ours(args):
     if not args.no_sweep:
         sweep = nufft_sweep(fsib, torch, dev, flush)
 
+    validation = None
+    if not args.no_validation and rank == 0 and world == 1:
+        validation = validation_block(fsib, torch, dev, flush, cpu_sample=not args.no_cpu_baseline)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and prec == "fp64":
-        k = 2
+        k = 2 if prob.d == 3 else 20
         t = time_oracle_steps(prob, k)
         cpu = {"value": k / t, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": f"{k} full oracle steps of the same workload (direct non-uniform sums, numpy BLAS/FFT)"}
@@ -582,7 +717,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
                 "data": "synthetic",
-                "config": {"workload": prob.name, "d": 3, "N": prob.N, "M": prob.M,
+                "config": {"workload": prob.name, "d": prob.d, "N": prob.N, "M": prob.M,
                            **{k: int(v) for k, v in m["info"].items()}, "tol": prob.tol,
                            "arithmetic": ("double-float transforms (FP64-accurate), FP64 positions/forces"
                                           if prec == "fp64" else "FP32 transforms, FP64 positions/forces"),
@@ -592,7 +727,7 @@ def run_ours(args):
                 "gpu_launches": m["launches"] * args.steps, "launches_per_step": m["launches"],
                 "launch_shapes": m["launch_shapes"],
                 "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched, "nufft_sweep": sweep,
-                "adjoint": adjoint}
+                "adjoint": adjoint, "validation_2d": validation}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -107,6 +107,21 @@ int fsib_set_force_curve(fsib_t h, double K);
 int fsib_set_force_mesh(fsib_t h, const int* tri, int ntri, const double* Xref,
                         double sigma);
 
+/* Target-point springs, any d (Sec. 5.2.2, the Poiseuille channel walls):
+ * F_i = K (X~_i - X_i) with weight omega (the Lagrangian meshwidth), so
+ * c_i = omega K (X~_i - X_i). Xtarget: [d][M] double, host or device, copied.
+ * Points need not form a closed curve; fsib_invariants then reports area or
+ * volume 0 (unless a mesh was set in 3D) and E_p = (omega K/2) sum |X~ - X|^2.
+ * Returns FSIB_EINVAL for a non-finite K or omega <= 0. fsib_step_adjoint
+ * rejects this model (FSIB_EUNSUPPORTED). */
+int fsib_set_force_target(fsib_t h, const double* Xtarget, double K, double omega);
+
+/* Uniform body force density f0 (host array of d doubles; Sec. 5.2.2), added
+ * to the Fourier coefficient f-hat(0) in every Navier-Stokes substep
+ * (fsib_step and fsib_fluid_step). Zero by default. FSIB_EUNSUPPORTED for a
+ * quasi-static Stokes handle (rho <= 0), FSIB_EINVAL for non-finite entries. */
+int fsib_set_body_force(fsib_t h, const double* f);
+
 /* Weighted force c_j = omega_j F_j of the current force model at X ([d][M]),
  * written to c ([d][M] double). */
 int fsib_force(fsib_t h, const double* X, double* c);
@@ -171,6 +186,16 @@ int fsib_step_adjoint(fsib_t h, const double* X0, int K, int ckpt_every, const d
  * out[5] dissipation mu L^d sum |k|^2 |u-hat|^2. uhat may be NULL (out[2..5] = 0).
  * Returns FSIB_ENONFINITE if X or uhat holds NaN/Inf. */
 int fsib_invariants(fsib_t h, const double* X, const void* uhat, double out[6]);
+
+/* Channel flux (Eq. poiseuille_flux), synchronous: the velocity component
+ * `comp` averaged over the axes other than `axis`, integrated over the band
+ * y0 <= x_axis <= y1: *flux = int_{y0}^{y1} ubar(y) dy, computed from the
+ * modes m e_axis of uhat (half spectrum) with the exact integral of each
+ * exponential. comp, axis in [0, d); flux is a host pointer. Returns
+ * FSIB_EINVAL for bad indices or non-finite limits, FSIB_ENONFINITE for a
+ * non-finite result. */
+int fsib_band_flux(fsib_t h, const void* uhat, int comp, int axis, double y0, double y1,
+                   double* flux);
 
 /* Launch-shape options, exact reorderings that leave results unchanged to
  * rounding: "fft_tile" (4, 8, 16: lines per strided-pass tile), "fft_rows"

@@ -821,6 +821,7 @@ int fsib_destroy(fsib_t h) {
   for (auto e : h->pool) cudaEventDestroy(e);
   free_ws(h->ws);
   free_mesh(h->ws);
+  if (h->ws.target) cudaFree(h->ws.target);
   if (h->side) cudaStreamSynchronize(h->side);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -980,6 +981,57 @@ int fsib_set_force_mesh(fsib_t h, const int* tri, int ntri, const double* Xref, 
   return finish(h, true);
 }
 
+int fsib_set_force_target(fsib_t h, const double* Xtarget, double K, double omega) {
+  if (!h || !Xtarget) return FSIB_EINVAL;
+  if (!std::isfinite(K) || !std::isfinite(omega) || !(omega > 0.0))
+    return fail(h, FSIB_EINVAL, "K must be finite and omega finite and > 0");
+  Workspace& ws = h->ws;
+  const size_t bytes = pts_bytes(h);
+  if (!ws.target) {
+    size_t tot = 0;
+    if (dmalloc(&ws.target, bytes, tot) != FSIB_OK) return fail(h, FSIB_ENOMEM, "target allocation failed");
+  }
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  const cudaMemcpyKind kind = is_device_ptr(Xtarget) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(ws.target, Xtarget, bytes, kind, h->own) != cudaSuccess)
+    return fail(h, FSIB_ECUDA, "copy of the target points failed");
+  ws.force_kind = 3;
+  ws.target_wK = omega * K;
+  ws.stiffness = K;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return finish(h, true);
+}
+
+int fsib_set_body_force(fsib_t h, const double* f) {
+  if (!h || !f) return FSIB_EINVAL;
+  if (h->p.stokes) return fail(h, FSIB_EUNSUPPORTED, "a body force needs the Navier-Stokes stepper (rho > 0)");
+  for (int a = 0; a < h->p.d; ++a)
+    if (!std::isfinite(f[a])) return fail(h, FSIB_EINVAL, "body force must be finite");
+  for (int a = 0; a < 3; ++a) h->p.fbody[a] = (a < h->p.d) ? f[a] : 0.0;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return FSIB_OK;
+}
+
+int fsib_band_flux(fsib_t h, const void* uhat, int comp, int axis, double y0, double y1, double* flux) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!uhat || !flux) return fail(h, FSIB_EINVAL, "NULL array");
+  if (comp < 0 || comp >= h->p.d || axis < 0 || axis >= h->p.d)
+    return fail(h, FSIB_EINVAL, "comp and axis must lie in [0, d)");
+  if (!std::isfinite(y0) || !std::isfinite(y1)) return fail(h, FSIB_EINVAL, "band limits must be finite");
+  Arg au;
+  if ((rc = stage(h, 3, uhat, spec_bytes(h), true, au)) != FSIB_OK) return rc;
+  if (h->p.prec == FSIB_FP64)
+    rc = run_band_flux<double>(h->p, h->ws, (const C<double>*)au.dev, comp, axis, y0, y1, flux, h->own);
+  else
+    rc = run_band_flux<float>(h->p, h->ws, (const C<float>*)au.dev, comp, axis, y0, y1, flux, h->own);
+  const int rc2 = finish(h, true);
+  if (rc == FSIB_ENONFINITE) return fail(h, rc, "non-finite flux");
+  if (rc != FSIB_OK) return fail(h, rc, "flux reduction failed");
+  return rc2;
+}
+
 int fsib_force(fsib_t h, const double* X, double* c) {
   int rc = begin(h);
   if (rc != FSIB_OK) return rc;
@@ -1117,7 +1169,8 @@ int fsib_invariants(fsib_t h, const double* X, const void* uhat, double out[6]) 
   int rc = begin(h);
   if (rc != FSIB_OK) return rc;
   if (!X || !out) return fail(h, FSIB_EINVAL, "NULL array");
-  if (h->p.d == 3 && !h->ws.tri) return fail(h, FSIB_ESTATE, "3D invariants need the mesh (fsib_set_force_mesh)");
+  if (h->p.d == 3 && h->ws.force_kind != 3 && !h->ws.tri)
+    return fail(h, FSIB_ESTATE, "3D invariants need the mesh (fsib_set_force_mesh)");
   Arg ax, au;
   if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
   if ((rc = stage(h, 3, uhat, spec_bytes(h), true, au)) != FSIB_OK) return rc;
@@ -1758,6 +1811,7 @@ int fsib_step_adjoint(fsib_t h, const double* X0, int K, int ckpt_every, const d
   if (!X0 || !dLdXK || !dLdX0 || !dLdsigma) return fail(h, FSIB_EINVAL, "NULL array");
   if (!h->p.stokes) return fail(h, FSIB_EUNSUPPORTED, "the adjoint covers the quasi-static Stokes stepper");
   if (!h->ws.force_kind) return fail(h, FSIB_ESTATE, "no force model set");
+  if (h->ws.force_kind == 3) return fail(h, FSIB_EUNSUPPORTED, "the adjoint covers the curve and mesh force laws");
   if (K < 1 || ckpt_every < 1) return fail(h, FSIB_EINVAL, "K and ckpt_every must be >= 1");
   if (ckpt_every > K) ckpt_every = K;
   if ((rc = ensure_adjoint(h, K, ckpt_every)) != FSIB_OK) return fail(h, rc, "adjoint workspace allocation failed");

@@ -62,8 +62,11 @@ __global__ void k_stokeslet(SpecGeom g, T inv_mu, const C<T>* __restrict__ f, C<
 //   s_a = sum_b i k_b p_ab (divergence form of the dealiased nonlinear term),
 //   P = f/rho - s, Q = P - k (k.P)/|k|^2 (|k|^2 := 1 at k = 0), lam = mu dt |k|^2 / rho,
 //   half: out = (dt/2 Q + base)/(1 + lam/2); full: out = (dt Q + (1 - lam/2) base)/(1 + lam/2).
+// A uniform body force density fb (Sec. 5.2.2) is the coefficient at k = 0 and is added there.
+struct Body { double f[3]; };
+
 template <typename T>
-__global__ void k_ns_update(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool half,
+__global__ void k_ns_update(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool half, Body fb,
                             const C<T>* __restrict__ prod, const C<T>* __restrict__ f,
                             const C<T>* __restrict__ base, C<T>* __restrict__ out) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
@@ -81,7 +84,9 @@ __global__ void k_ns_update(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool 
         s = cadd<T>(s, cscale<T>(prod[ab * g.nspec + idx], k[b]));
       }
       s = cmul_i<T>(s);
-      P[a] = csub<T>(cscale<T>(f[a * g.nspec + idx], inv_rho), s);
+      C<T> fa = f[a * g.nspec + idx];
+      if (idx == 0) fa.x += (T)fb.f[a];
+      P[a] = csub<T>(cscale<T>(fa, inv_rho), s);
     }
     C<T> kP = mk<T>(T(0), T(0));
     for (int a = 0; a < d; ++a) kP = cadd<T>(kP, cscale<T>(P[a], k[a]));
@@ -133,8 +138,9 @@ template <typename T>
 void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
                       C<T>* out, bool half, cudaStream_t st) {
   const SpecGeom g = sgeom(p);
+  const Body fb = {{p.fbody[0], p.fbody[1], p.fbody[2]}};
   k_ns_update<T><<<grid_for(g.nspec), 256, 0, st>>>(g, (T)(1.0 / p.rho), (T)(p.mu * p.dt / p.rho),
-                                                     (T)p.dt, half, prod, fhat, ubase, out);
+                                                     (T)p.dt, half, fb, prod, fhat, ubase, out);
 }
 
 template <typename T>

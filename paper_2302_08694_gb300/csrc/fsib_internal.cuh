@@ -85,6 +85,7 @@ struct Plan {
   int width_opt = 0, bin_opt = 0;
   int use_graph = 1, check_finite = 0;
   int native_fp64 = 0;  // FP64 mode: 0 = double-float transforms, 1 = native FP64 arithmetic
+  double fbody[3] = {0.0, 0.0, 0.0};  // uniform body force density, added to f-hat(0) (Navier-Stokes)
   // launch-shape tunables (chosen by fsib_autotune)
   int fft_p = 8, fft_q = 4, slice = 256;
 
@@ -128,8 +129,10 @@ struct Workspace {
   double* Uh = nullptr;       // [d][M]
   double* omega_ones = nullptr;
   // force models
-  int force_kind = 0;         // 0 none, 1 curve, 2 mesh
+  int force_kind = 0;         // 0 none, 1 curve, 2 mesh, 3 target points
   double curve_K = 0.0;
+  double* target = nullptr;   // [d][M] target points (force kind 3)
+  double target_wK = 0.0;     // omega K of the target springs
   double stiffness = 1.0;     // K (curve) or sigma (mesh): the force is linear in it
   int* csr_ptr = nullptr; int* csr_col = nullptr; double* csr_k = nullptr; int nnz = 0;
   int* tri = nullptr; int ntri = 0;
@@ -204,6 +207,9 @@ void launch_mesh_stiffness(const double* Xref, const int* tri, int ntri, int M, 
 template <typename T>
 int run_invariants(const Plan& p, Workspace& ws, const double* X, const C<T>* uhat,
                    double* out, cudaStream_t st);
+template <typename T>
+int run_band_flux(const Plan& p, Workspace& ws, const C<T>* uhat, int comp, int axis, double y0, double y1,
+                  double* flux, cudaStream_t st);
 
 template <typename T>
 void launch_mul_ik(const Plan& p, int b, const C<T>* in, C<T>* out, cudaStream_t st);

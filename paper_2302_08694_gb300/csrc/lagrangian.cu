@@ -1,6 +1,9 @@
 // Lagrangian side in double precision: position updates (Eqs. spatial_1, spatial_4),
-// force laws (Eq. elstic_force_2d; cot-weight springs of Sec. 6.2.3) and the
-// invariants of Sec. 4 (enclosed area/volume, energies, zero mode, divergence).
+// force laws (Eq. elstic_force_2d; cot-weight springs of Sec. 6.2.3; target-point
+// springs of the Poiseuille channel, Sec. 5.2.2), the invariants of Sec. 4 (enclosed
+// area/volume, energies, zero mode, divergence) and the channel flux of Eq. poiseuille_flux.
+#include <cmath>
+
 #include "fsib_internal.cuh"
 
 namespace fsib {
@@ -68,10 +71,20 @@ __global__ void k_force_mesh(const double* __restrict__ X, double* __restrict__ 
   }
 }
 
+// Target points: c = omega K (X~ - X) over all d*M entries (Sec. 5.2.2).
+__global__ void k_force_target(const double* __restrict__ X, const double* __restrict__ Xt,
+                               double* __restrict__ c, long long n, double wK) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c[i] = wK * (Xt[i] - X[i]);
+}
+
 void launch_force(const Plan& p, const Workspace& ws, const double* X, double* c, cudaStream_t st) {
   if (ws.force_kind == 1) {
     const double dth = 2.0 * 3.14159265358979323846 / p.M;
     k_force_curve<<<blocks_for(p.M), 256, 0, st>>>(X, c, p.M, ws.curve_K / dth);
+  } else if (ws.force_kind == 3) {
+    const long long n = (long long)p.d * p.M;
+    k_force_target<<<blocks_for(n), 256, 0, st>>>(X, ws.target, c, n, ws.target_wK);
   } else {
     k_force_mesh<<<blocks_for(8LL * p.M), 256, 0, st>>>(X, c, p.M, ws.csr_ptr, ws.csr_col, ws.csr_k);
   }
@@ -208,13 +221,13 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 struct InvGeom {
   int d, M, force_kind, ntri, N, h;
   long long nspec;
-  double kunit, curve_K;
+  double kunit, curve_K, target_wK;
 };
 
 __global__ void __launch_bounds__(kRedThreads)
 k_inv_points(InvGeom g, const double* __restrict__ X, const int* __restrict__ tri,
              const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ kv,
-             double* __restrict__ part) {
+             const double* __restrict__ Xt, double* __restrict__ part) {
   __shared__ double sh[32];
   double vol = 0, ep = 0, bad = 0;
   const int M = g.M;
@@ -225,7 +238,7 @@ k_inv_points(InvGeom g, const double* __restrict__ X, const int* __restrict__ tr
     for (long long i = t0; i < M; i += stride) {
       const long long ip = (i + 1 == M) ? 0 : i + 1;
       const double x = X[i], y = X[M + i], xp = X[ip], yp = X[M + ip];
-      vol += 0.5 * (x * yp - xp * y);
+      if (g.force_kind != 3) vol += 0.5 * (x * yp - xp * y);  // open walls enclose no area
       if (g.force_kind == 1) ep += 0.5 * g.curve_K / dth * ((xp - x) * (xp - x) + (yp - y) * (yp - y));
       if (!isfinite(x) || !isfinite(y)) bad += 1;
     }
@@ -247,6 +260,12 @@ k_inv_points(InvGeom g, const double* __restrict__ X, const int* __restrict__ tr
           ep += 0.25 * kv[e] * (d0 * d0 + d1 * d1 + d2 * d2);  // each edge seen twice
         }
       }
+    }
+  }
+  if (g.force_kind == 3) {  // E_p = (omega K / 2) sum |X~ - X|^2
+    for (long long i = t0; i < (long long)g.d * M; i += stride) {
+      const double e = Xt[i] - X[i];
+      ep += 0.5 * g.target_wK * e * e;
     }
   }
   const double r0 = block_sum(vol, sh);
@@ -335,11 +354,12 @@ int run_invariants(const Plan& p, Workspace& ws, const double* X, const C<T>* uh
   g.nspec = (long long)g.h * p.N * (p.d == 3 ? p.N : 1);
   g.kunit = 2.0 * 3.14159265358979323846 / p.L;
   g.curve_K = ws.curve_K;
+  g.target_wK = ws.target_wK;
   const int nblk = ws.red_blocks;
   double* part = ws.red;
   double* res = ws.red + (size_t)nblk * kRedSlots;
   cudaMemsetAsync(part, 0, sizeof(double) * ((size_t)nblk * kRedSlots + kRedSlots), st);
-  k_inv_points<<<nblk, kRedThreads, 0, st>>>(g, X, ws.tri, ws.csr_ptr, ws.csr_col, ws.csr_k, part);
+  k_inv_points<<<nblk, kRedThreads, 0, st>>>(g, X, ws.tri, ws.csr_ptr, ws.csr_col, ws.csr_k, ws.target, part);
   if (uhat) k_inv_spectrum<T><<<nblk, kRedThreads, 0, st>>>(g, uhat, part);
   k_inv_final<<<1, 32, 0, st>>>(part, nblk, res);
   double h[kRedSlots];
@@ -355,6 +375,54 @@ int run_invariants(const Plan& p, Workspace& ws, const double* X, const C<T>* uh
   out[5] = uhat ? p.mu * Ld * h[8] : 0.0;
   return h[9] > 0 ? FSIB_ENONFINITE : FSIB_OK;
 }
+
+// Channel flux (Eq. poiseuille_flux): Phi = int_{y0}^{y1} ubar(y) dy with ubar the average of
+// u_comp over the axes other than `axis`. Only the modes m e_axis survive the average, so
+// Phi = Re sum_m u-hat(m e_axis) I(m) with I(0) = y1 - y0 and
+// I(m) = (e^{i k y1} - e^{i k y0}) / (i k), k = 2 pi m / L. Along x the half spectrum
+// holds m >= 0 and each m > 0 stands for m and -m (twice the real part). One block.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+k_band_flux(const C<T>* __restrict__ u, int N, long long nspec, int comp, int axis, double kunit,
+            double y0, double y1, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int h = N / 2;
+  const int nm = (axis == 0) ? h : N;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    if (axis != 0 && i == h) continue;  // unpaired mode -N/2 (zero)
+    const int m = (axis == 0 || i < h) ? i : i - N;
+    const long long idx = (axis == 0) ? i : (axis == 1 ? (long long)i * h : (long long)i * N * h);
+    double Ir = y1 - y0, Ii = 0.0;
+    if (m != 0) {
+      const double k = kunit * m;
+      double s1, c1, s0, c0;
+      sincos(k * y1, &s1, &c1);
+      sincos(k * y0, &s0, &c0);
+      Ir = (s1 - s0) / k;
+      Ii = (c0 - c1) / k;
+    }
+    const C<T> v = u[comp * nspec + idx];
+    const double re = (double)v.x * Ir - (double)v.y * Ii;
+    acc += (axis == 0 && m > 0) ? 2.0 * re : re;
+  }
+  const double r = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = r;
+}
+
+template <typename T>
+int run_band_flux(const Plan& p, Workspace& ws, const C<T>* uhat, int comp, int axis, double y0, double y1,
+                  double* flux, cudaStream_t st) {
+  const long long nspec = (long long)(p.N / 2) * p.N * (p.d == 3 ? p.N : 1);
+  k_band_flux<T><<<1, kRedThreads, 0, st>>>(uhat, p.N, nspec, comp, axis, 2.0 * 3.14159265358979323846 / p.L,
+                                            y0, y1, ws.red);
+  if (cudaMemcpyAsync(flux, ws.red, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FSIB_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FSIB_ECUDA;
+  return std::isfinite(*flux) ? FSIB_OK : FSIB_ENONFINITE;
+}
+
+template int run_band_flux<float>(const Plan&, Workspace&, const C<float>*, int, int, double, double, double*, cudaStream_t);
+template int run_band_flux<double>(const Plan&, Workspace&, const C<double>*, int, int, double, double, double*, cudaStream_t);
 
 template int run_invariants<float>(const Plan&, Workspace&, const double*, const C<float>*, double*, cudaStream_t);
 template int run_invariants<double>(const Plan&, Workspace&, const double*, const C<double>*, double*, cudaStream_t);

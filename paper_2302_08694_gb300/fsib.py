@@ -29,7 +29,8 @@ EXPORTS = ["fsib_create", "fsib_destroy", "fsib_set_stream", "fsib_set_option", 
            "fsib_measure_peak", "fsib_spread_static", "fsib_static_last_error", "fsib_autotune",
            "fsib_batch_create", "fsib_batch_member", "fsib_batch_set_stream", "fsib_batch_autotune",
            "fsib_batch_step", "fsib_batch_info", "fsib_batch_last_error", "fsib_batch_destroy",
-           "fsib_interp_grad", "fsib_step_adjoint"]
+           "fsib_interp_grad", "fsib_step_adjoint", "fsib_set_force_target", "fsib_set_body_force",
+           "fsib_band_flux"]
 
 _lib = None
 
@@ -86,6 +87,9 @@ def load(path: str | None = None):
         "fsib_batch_destroy": ([vp], i_),
         "fsib_interp_grad": ([vp, vp, vp, vp], i_),
         "fsib_step_adjoint": ([vp, vp, i_, i_, vp, vp, vp], i_),
+        "fsib_set_force_target": ([vp, vp, d_, d_], i_),
+        "fsib_set_body_force": ([vp, dp], i_),
+        "fsib_band_flux": ([vp, vp, i_, i_, d_, d_, dp], i_),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -189,6 +193,24 @@ class Problem:
     def set_force_mesh(self, tri, Xref, sigma):
         tri = np.ascontiguousarray(tri, dtype=np.int32) if isinstance(tri, np.ndarray) else tri
         self._call("fsib_set_force_mesh", _ptr(tri), int(tri.shape[0]), _ptr(Xref), float(sigma))
+
+    def set_force_target(self, Xtarget, K, omega):
+        """Target-point springs c = omega K (X~ - X); Xtarget [d][M] float64 (host or device)."""
+        if isinstance(Xtarget, np.ndarray):
+            Xtarget = np.ascontiguousarray(Xtarget, dtype=np.float64)
+        self._call("fsib_set_force_target", _ptr(Xtarget), float(K), float(omega))
+
+    def set_body_force(self, f):
+        """Uniform body force density (d values), added to f-hat(0) in the Navier-Stokes update."""
+        vals = [float(v) for v in f] + [0.0, 0.0, 0.0]
+        arr = (ctypes.c_double * 3)(*vals[:3])
+        self._call("fsib_set_body_force", arr)
+
+    def band_flux(self, uhat, comp, axis, y0, y1):
+        """Flux of u_comp averaged over the other axes through y0 <= x_axis <= y1."""
+        v = ctypes.c_double()
+        self._call("fsib_band_flux", _ptr(uhat), int(comp), int(axis), float(y0), float(y1), ctypes.byref(v))
+        return v.value
 
     def new_spec(self, device="cuda"):
         import torch
