@@ -116,6 +116,28 @@ def membrane_energy(X: np.ndarray, Xref: np.ndarray, tri: np.ndarray, sigma: flo
     return float(0.5 * sigma * np.sum(s / (8.0 * S0)))
 
 
+def surface_area(X: np.ndarray, tri: np.ndarray) -> float:
+    """Area of the triangulated surface: the sum of its triangles' areas (Sec. 6.2.4)."""
+    return float(np.sum(triangle_areas(X, tri)))
+
+
+def surface_tension_force(X: np.ndarray, tri: np.ndarray, gamma: float) -> np.ndarray:
+    """Surface tension E = gamma S (Sec. 6.2.4): at node i,
+    F_i = -(gamma/2) sum over the triangles (i, j, k) containing i of (X_j - X_k) x n_ijk,
+    each triangle's vertices taken in its counter-clockwise order starting at i and
+    n_ijk its unit normal by the right-hand rule of (X_i, X_j, X_k). Nodal forces, omega = 1."""
+    F = np.zeros_like(X)
+    for r in range(3):
+        i, j, k = tri[:, r], tri[:, (r + 1) % 3], tri[:, (r + 2) % 3]
+        Xi, Xj, Xk = X[:, i].T, X[:, j].T, X[:, k].T
+        n = np.cross(Xj - Xi, Xk - Xi)
+        n /= np.linalg.norm(n, axis=1)[:, None]
+        f = -0.5 * gamma * np.cross(Xj - Xk, n)
+        for a in range(3):
+            np.add.at(F[a], i, f[:, a])
+    return F
+
+
 def enclosed_volume(X: np.ndarray, tri: np.ndarray) -> float:
     """V = (1/6) sum over ccw triangles (i,j,k) of X_i . (X_j x X_k).
 

@@ -29,6 +29,13 @@ def mesh_model(Xref: np.ndarray, tri: np.ndarray, sigma: float):
     return force
 
 
+def tension_model(tri: np.ndarray, gamma: float):
+    """Surface tension E = gamma S on a triangulated surface (Sec. 6.2.4); nodal forces."""
+    def force(X):
+        return lg.surface_tension_force(X, tri, gamma)
+    return force
+
+
 def target_model(Xt: np.ndarray, K: float, omega: float):
     """Target-point springs (Sec. 5.2.2) weighted by omega (the Lagrangian meshwidth)."""
     def force(X):

@@ -71,6 +71,49 @@ def latlong_sphere(n_r: int, n_phi: int, radius: float, center):
     return X, np.asarray(tris, dtype=np.int32)
 
 
+def icosphere(level: int, radius: float, center):
+    """Refined icosahedron on a sphere (Sec. 6.2.3).
+
+    Start from the regular icosahedron (12 vertices, 20 triangles); each refinement
+    splits every triangle into four through its edge midpoints and projects the new
+    vertices onto the sphere, so M = 10 * 4^level + 2 (2562 at level 4, 10242 at 5,
+    40962 at 6). Triangles are counter-clockwise seen from outside.
+
+    Returns (X (3, M) float64, tri (ntri, 3) int32).
+    """
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    V = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    P = [np.asarray(v, dtype=np.float64) / np.linalg.norm(v) for v in V]
+    F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5),
+         (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        mid = {}
+
+        def midpoint(a, b):
+            key = (a, b) if a < b else (b, a)
+            if key not in mid:
+                m = P[a] + P[b]
+                P.append(m / np.linalg.norm(m))
+                mid[key] = len(P) - 1
+            return mid[key]
+        G = []
+        for a, b, c in F:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            G += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        F = G
+    X = np.asarray(center, dtype=np.float64)[:, None] + radius * np.stack(P, axis=1)
+    tri = np.asarray(F, dtype=np.int32)
+    # orient counter-clockwise from outside: the normal must point away from the centre
+    A, B, C = X[:, tri[:, 0]], X[:, tri[:, 1]], X[:, tri[:, 2]]
+    n = np.cross((B - A).T, (C - A).T)
+    out = np.sum(n * (A - np.asarray(center, dtype=np.float64)[:, None]).T, axis=1)
+    flip = out < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    return X, tri
+
+
 def mesh_edges(tri: np.ndarray) -> np.ndarray:
     """Unique undirected edges (E, 2) int32 of a triangle list, sorted (i < j)."""
     e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]], axis=0)
@@ -275,3 +318,38 @@ def config_poiseuille(N: int = 8, K: float = 1.0e4, T: float = 3.0, dt: float | 
                    precision, "target", Xt.copy(), K,
                    extra={"Xtarget": Xt, "omega": h, "fbody": (100.0, 0.0), "band": (0.25, 0.75),
                           "D": 0.5 * L_BOX, "f0": 100.0, "T": T})
+
+
+# ---------------------------------------------------------------------------
+# Three-dimensional sphere problems of Secs. 6.2.3 (elastic) and 6.2.4 (surface tension)
+# ---------------------------------------------------------------------------
+
+def sine_velocity_half_3d(N: int) -> np.ndarray:
+    """Initial velocity u_0 = (sin(2 pi z/L), 0, sin(2 pi y/L)) in the half-spectrum layout.
+
+    Both sines live on the plane m_x = 0, which stores every (m_y, m_z): the x component
+    holds -i/2 at m_z = 1 and +i/2 at m_z = -1, the z component the same along m_y.
+    Shape (3, N, N, N//2), complex128, indexed [component, iz, iy, ix].
+    """
+    u = np.zeros((3, N, N, N // 2), dtype=np.complex128)
+    u[0, 1, 0, 0], u[0, N - 1, 0, 0] = -0.5j, 0.5j
+    u[2, 0, 1, 0], u[2, 0, N - 1, 0] = -0.5j, 0.5j
+    return u
+
+
+def config_ns3d_sphere(model: str = "elastic", level: int = 4, N: int = 32, dt: float = 1e-3,
+                       T: float = 1.0, precision: str = "fp64") -> Problem:
+    """Sphere of radius L/3 at the box centre in the sine flow u_0 = (sin 2 pi z, 0, sin 2 pi y).
+
+    model "elastic": cot-weight springs with sigma = 1 from the initial sphere (Sec. 6.2.3);
+    model "tension": surface tension gamma = 1 (Sec. 6.2.4). L = 1, rho = 1, mu = 0.01,
+    N = 32 with four refinements of the icosahedron (M = 2562) so that the Lagrangian
+    meshwidth matches the Fourier resolution, dt = 1e-3, T = 1.
+    """
+    X0, tri = icosphere(level, L_BOX / 3.0, (0.5, 0.5, 0.5))
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    nsteps = int(round(T / dt))
+    force = "mesh" if model == "elastic" else "tension"
+    return Problem(f"ns3d_sphere_{model}_L{level}_N{N}_{precision}", 3, N, X0.shape[1], 0.01, 1.0, dt,
+                   nsteps, tol, precision, force, X0.copy(), 1.0, tri=tri, Xref=X0.copy(),
+                   extra={"u0": sine_velocity_half_3d(N), "T": T, "level": level})
