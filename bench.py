@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable workload block")
     ap.add_argument("--no-sweep", action="store_true", help="skip the NUFFT point-count sweep")
     ap.add_argument("--no-validation", action="store_true",
-                    help="skip the 2D Navier-Stokes validation block (sine circle, Poiseuille channel)")
-    ap.add_argument("--workload", choices=["ns3d_fp64", "ns3d_mixed", "ns2d_circle", "poiseuille"],
+                    help="skip the validation blocks (2D sine circle and Poiseuille channel, 3D spheres)")
+    ap.add_argument("--workload", choices=["ns3d_fp64", "ns3d_mixed", "ns2d_circle", "poiseuille",
+                                           "sphere_elastic", "sphere_tension"],
                     default="ns3d_fp64",
                     help="workload of the main line (profiling runs use ns3d_mixed for the FP32 kernels)")
     return ap.parse_args()
@@ -123,6 +124,8 @@ def make_problem(fsib, prob, precision):
         pb.set_force_mesh(prob.tri, prob.Xref, prob.stiffness)
     elif prob.force == "target":
         pb.set_force_target(prob.extra["Xtarget"], prob.stiffness, prob.extra["omega"])
+    elif prob.force == "tension":
+        pb.set_force_tension(prob.tri, prob.stiffness)
     else:
         pb.set_force_curve(prob.stiffness)
     if "fbody" in prob.extra:
@@ -137,6 +140,8 @@ def time_oracle_steps(prob, nsteps):
         force = st.mesh_model(prob.Xref, prob.tri, prob.stiffness)
     elif prob.force == "target":
         force = st.target_model(prob.extra["Xtarget"], prob.stiffness, prob.extra["omega"])
+    elif prob.force == "tension":
+        force = st.tension_model(prob.tri, prob.stiffness)
     else:
         force = st.curve_model(prob.stiffness)
     N, d = prob.N, prob.d
@@ -158,6 +163,8 @@ def workload_of(name):
         return wl.config_ns2d_circle(), "fp64"
     if name == "poiseuille":
         return wl.config_poiseuille(N=64), "fp64"
+    if name in ("sphere_elastic", "sphere_tension"):
+        return wl.config_ns3d_sphere(name.split("_")[1]), "fp64"
     return wl.config_ns3d_fp64(), "fp64"
 
 
@@ -631,6 +638,59 @@ def validation_block(fsib, torch, dev, flush, cpu_sample=True):
     return out
 
 
+def validation_3d_block(fsib, torch, dev, flush, max_refine=5):
+    """The paper's 3D sphere checks on the library (FP64 transforms): a sphere of radius L/3 in
+    the sine flow, elastic (Sec. 6.2.3) and surface tension (Sec. 6.2.4). Paper configuration
+    (N = 32, four refinements, dt = 1e-3, T = 1): volume over the run; convergence study
+    (N = 4 * 2^r, r + 1 refinements, dt = 0.004 / 2^r, T = 0.2): successive relative L2
+    differences of the velocity field and their orders."""
+    from paper_2302_08694_gb300 import validation as va
+    stream = torch.cuda.current_stream()
+    out = {}
+    for model in ("elastic", "tension"):
+        prob = wl.config_ns3d_sphere(model)
+        pb = make_problem(fsib, prob, "fp64")
+        X = torch.from_numpy(prob.X0.copy()).to(dev)
+        u = torch.from_numpy(prob.extra["u0"]).to(dev)
+        U = pb.interp(u, X)
+        V0 = pb.invariants(X)["volume"]
+        vol = []
+
+        def probe(step):
+            vol.append(pb.invariants(X)["volume"] / V0)
+        ms = _chunked_steps(torch, pb, X, u, U, prob.nsteps, 100, flush, stream, probe)
+        Xn = X.cpu().numpy()
+        r = np.linalg.norm(Xn - Xn.mean(axis=1, keepdims=True), axis=0)
+        res = {"workload": prob.name, "M": prob.M, "steps": prob.nsteps, "steps_per_s": prob.nsteps / (ms * 1e-3),
+               "ms_per_step": ms / prob.nsteps, "volume_ratio_min": min(vol), "volume_ratio_max": max(vol),
+               "volume_ratio_final": vol[-1], "radius_rel_spread_final": float(r.std() / r.mean())}
+        pb.close()
+        spectra, rows = [], []
+        for rr in range(max_refine + 1):
+            N, level, dt = 4 * 2 ** rr, 1 + rr, 0.004 / 2 ** rr
+            pr = wl.config_ns3d_sphere(model, level=level, N=N, dt=dt, T=0.2)
+            pbr = make_problem(fsib, pr, "fp64")
+            Xr = torch.from_numpy(pr.X0.copy()).to(dev)
+            ur = torch.from_numpy(pr.extra["u0"]).to(dev)
+            Ur = pbr.interp(ur, Xr)
+            V0r = pbr.invariants(Xr)["volume"]
+            a, b = _events(torch)
+            a.record(stream)
+            pbr.step(Xr, ur, Ur, nsteps=pr.nsteps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            rows.append({"N": N, "M": pr.M, "dt": dt, "steps": pr.nsteps,
+                         "ms_per_step": a.elapsed_time(b) / pr.nsteps,
+                         "volume_ratio_final": pbr.invariants(Xr)["volume"] / V0r})
+            spectra.append(ur.cpu().numpy())
+            pbr.close()
+        errs = va.successive_errors(spectra)
+        res["convergence"] = {"runs": rows, "successive_rel_l2": errs,
+                              "orders": [float(np.log2(x / y)) for x, y in zip(errs[:-1], errs[1:])]}
+        out[model] = res
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -701,9 +761,10 @@ def run_ours(args):
     if not args.no_sweep:
         sweep = nufft_sweep(fsib, torch, dev, flush)
 
-    validation = None
+    validation = validation_3d = None
     if not args.no_validation and rank == 0 and world == 1:
         validation = validation_block(fsib, torch, dev, flush, cpu_sample=not args.no_cpu_baseline)
+        validation_3d = validation_3d_block(fsib, torch, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and prec == "fp64":
@@ -727,7 +788,8 @@ def run_ours(args):
                 "gpu_launches": m["launches"] * args.steps, "launches_per_step": m["launches"],
                 "launch_shapes": m["launch_shapes"],
                 "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched, "nufft_sweep": sweep,
-                "adjoint": adjoint, "validation_2d": validation}
+                "adjoint": adjoint, "validation_2d": validation,
+                "validation_3d": validation_3d}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -107,6 +107,15 @@ int fsib_set_force_curve(fsib_t h, double K);
 int fsib_set_force_mesh(fsib_t h, const int* tri, int ntri, const double* Xref,
                         double sigma);
 
+/* Surface tension, d = 3 (Sec. 6.2.4): energy gamma S with S the summed triangle
+ * areas, so F_i = -(gamma/2) sum over the triangles (i, j, k) at node i of
+ * (X_j - X_k) x n_ijk, n_ijk the unit normal of (X_i, X_j, X_k); omega = 1 (nodal
+ * forces). tri: [ntri][3] int32, counter-clockwise seen from outside (also used
+ * for the enclosed volume); host or device, copied. fsib_invariants reports
+ * E_p = gamma S. FSIB_EINVAL for d != 3, bad or repeated indices in a triangle,
+ * or a non-finite gamma; fsib_step_adjoint rejects this model (FSIB_EUNSUPPORTED). */
+int fsib_set_force_tension(fsib_t h, const int* tri, int ntri, double gamma);
+
 /* Target-point springs, any d (Sec. 5.2.2, the Poiseuille channel walls):
  * F_i = K (X~_i - X_i) with weight omega (the Lagrangian meshwidth), so
  * c_i = omega K (X~_i - X_i). Xtarget: [d][M] double, host or device, copied.

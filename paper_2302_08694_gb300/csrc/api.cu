@@ -257,7 +257,9 @@ static void free_mesh(Workspace& ws) {
   if (ws.csr_col) cudaFree(ws.csr_col);
   if (ws.csr_k) cudaFree(ws.csr_k);
   if (ws.tri) cudaFree(ws.tri);
+  if (ws.inc_jk) cudaFree(ws.inc_jk);
   ws.csr_ptr = ws.csr_col = nullptr; ws.csr_k = nullptr; ws.tri = nullptr; ws.nnz = ws.ntri = 0;
+  ws.inc_jk = nullptr;
 }
 
 template <typename P>
@@ -979,6 +981,56 @@ int fsib_set_force_mesh(fsib_t h, const int* tri, int ntri, const double* Xref, 
   ws.stiffness = sigma;
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   return finish(h, true);
+}
+
+int fsib_set_force_tension(fsib_t h, const int* tri, int ntri, double gamma) {
+  if (!h || !tri || ntri < 1) return FSIB_EINVAL;
+  if (h->p.d != 3) return fail(h, FSIB_EINVAL, "surface tension needs d = 3");
+  if (!std::isfinite(gamma)) return fail(h, FSIB_EINVAL, "gamma must be finite");
+  const int M = h->p.M;
+  std::vector<int> t(3 * (size_t)ntri);
+  if (is_device_ptr(tri)) {
+    if (cudaMemcpy(t.data(), tri, t.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(h, FSIB_ECUDA, "copy of tri failed");
+  } else {
+    std::memcpy(t.data(), tri, t.size() * sizeof(int));
+  }
+  // incidence (integer work on the host): for node i, the other two vertices of each of its
+  // triangles in the triangle's counter-clockwise order starting at i
+  std::vector<int> ptr(M + 1, 0);
+  for (size_t q = 0; q < t.size(); ++q) {
+    const int a = t[q];
+    if (a < 0 || a >= M) return fail(h, FSIB_EINVAL, "bad triangle index");
+    ptr[a + 1]++;
+  }
+  for (int q = 0; q < ntri; ++q)
+    if (t[3 * q] == t[3 * q + 1] || t[3 * q + 1] == t[3 * q + 2] || t[3 * q] == t[3 * q + 2])
+      return fail(h, FSIB_EINVAL, "degenerate triangle");
+  for (int i = 0; i < M; ++i) ptr[i + 1] += ptr[i];
+  std::vector<int2> inc(3 * (size_t)ntri);
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (int q = 0; q < ntri; ++q)
+    for (int r = 0; r < 3; ++r) {
+      const int i = t[3 * q + r], j = t[3 * q + (r + 1) % 3], k = t[3 * q + (r + 2) % 3];
+      inc[fill[i]++] = make_int2(j, k);
+    }
+  Workspace& ws = h->ws;
+  free_mesh(ws);
+  size_t tot = 0;
+  int rc = FSIB_OK;
+  ws.ntri = ntri;
+  rc |= dmalloc(&ws.csr_ptr, sizeof(int) * (M + 1), tot);
+  rc |= dmalloc(&ws.inc_jk, sizeof(int2) * inc.size(), tot);
+  rc |= dmalloc(&ws.tri, sizeof(int) * t.size(), tot);
+  if (rc != FSIB_OK) { free_mesh(ws); return fail(h, FSIB_ENOMEM, "mesh allocation failed"); }
+  if (cudaMemcpy(ws.csr_ptr, ptr.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ws.inc_jk, inc.data(), sizeof(int2) * inc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ws.tri, t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(h, FSIB_ECUDA, "copy of the incidence failed");
+  ws.force_kind = 4;
+  ws.stiffness = gamma;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return FSIB_OK;
 }
 
 int fsib_set_force_target(fsib_t h, const double* Xtarget, double K, double omega) {
@@ -1811,7 +1863,7 @@ int fsib_step_adjoint(fsib_t h, const double* X0, int K, int ckpt_every, const d
   if (!X0 || !dLdXK || !dLdX0 || !dLdsigma) return fail(h, FSIB_EINVAL, "NULL array");
   if (!h->p.stokes) return fail(h, FSIB_EUNSUPPORTED, "the adjoint covers the quasi-static Stokes stepper");
   if (!h->ws.force_kind) return fail(h, FSIB_ESTATE, "no force model set");
-  if (h->ws.force_kind == 3) return fail(h, FSIB_EUNSUPPORTED, "the adjoint covers the curve and mesh force laws");
+  if (h->ws.force_kind >= 3) return fail(h, FSIB_EUNSUPPORTED, "the adjoint covers the curve and mesh force laws");
   if (K < 1 || ckpt_every < 1) return fail(h, FSIB_EINVAL, "K and ckpt_every must be >= 1");
   if (ckpt_every > K) ckpt_every = K;
   if ((rc = ensure_adjoint(h, K, ckpt_every)) != FSIB_OK) return fail(h, rc, "adjoint workspace allocation failed");

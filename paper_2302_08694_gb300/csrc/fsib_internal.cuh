@@ -129,13 +129,14 @@ struct Workspace {
   double* Uh = nullptr;       // [d][M]
   double* omega_ones = nullptr;
   // force models
-  int force_kind = 0;         // 0 none, 1 curve, 2 mesh, 3 target points
+  int force_kind = 0;         // 0 none, 1 curve, 2 mesh, 3 target points, 4 surface tension
   double curve_K = 0.0;
   double* target = nullptr;   // [d][M] target points (force kind 3)
   double target_wK = 0.0;     // omega K of the target springs
   double stiffness = 1.0;     // K (curve) or sigma (mesh): the force is linear in it
   int* csr_ptr = nullptr; int* csr_col = nullptr; double* csr_k = nullptr; int nnz = 0;
   int* tri = nullptr; int ntri = 0;
+  int2* inc_jk = nullptr;     // surface tension: (j, k) of each triangle at a node, CSR rows csr_ptr
   // reductions
   double* red = nullptr;      // partial sums
   int red_blocks = 0;

@@ -78,6 +78,43 @@ __global__ void k_force_target(const double* __restrict__ X, const double* __res
     c[i] = wK * (Xt[i] - X[i]);
 }
 
+// Surface tension E = gamma S (Sec. 6.2.4): F_i = -(gamma/2) sum over the triangles (i, j, k)
+// at node i of (X_j - X_k) x n_ijk, n_ijk the unit normal of (X_i, X_j, X_k) (omega = 1).
+// inc[e] = (j, k) lists each triangle at node i in its counter-clockwise order from i
+// (CSR rows ptr). Eight lanes per vertex as in k_force_mesh.
+__global__ void k_force_tension(const double* __restrict__ X, double* __restrict__ c, int M,
+                                const int* __restrict__ ptr, const int2* __restrict__ inc, double half_gamma) {
+  const int sl = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3;
+  for (long long w0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; w0 < M;
+       w0 += (((long long)gridDim.x * blockDim.x) >> 5) * 4) {
+    const int i = (int)(w0 + sub);
+    const bool ok = i < M;
+    double f0 = 0, f1 = 0, f2 = 0;
+    if (ok) {
+      const double x0 = X[i], x1 = X[M + i], x2 = X[2LL * M + i];
+      for (int e = ptr[i] + sl; e < ptr[i + 1]; e += 8) {
+        const int2 jk = inc[e];
+        const double a0 = X[jk.x] - x0, a1 = X[M + jk.x] - x1, a2 = X[2LL * M + jk.x] - x2;
+        const double b0 = X[jk.y] - x0, b1 = X[M + jk.y] - x1, b2 = X[2LL * M + jk.y] - x2;
+        double n0 = a1 * b2 - a2 * b1, n1 = a2 * b0 - a0 * b2, n2 = a0 * b1 - a1 * b0;
+        const double inv = 1.0 / sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+        n0 *= inv; n1 *= inv; n2 *= inv;
+        const double e0 = a0 - b0, e1 = a1 - b1, e2 = a2 - b2;  // X_j - X_k
+        f0 -= half_gamma * (e1 * n2 - e2 * n1);
+        f1 -= half_gamma * (e2 * n0 - e0 * n2);
+        f2 -= half_gamma * (e0 * n1 - e1 * n0);
+      }
+    }
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+      f0 += __shfl_xor_sync(0xffffffffu, f0, off, 8);
+      f1 += __shfl_xor_sync(0xffffffffu, f1, off, 8);
+      f2 += __shfl_xor_sync(0xffffffffu, f2, off, 8);
+    }
+    if (ok && sl == 0) { c[i] = f0; c[M + i] = f1; c[2LL * M + i] = f2; }
+  }
+}
+
 void launch_force(const Plan& p, const Workspace& ws, const double* X, double* c, cudaStream_t st) {
   if (ws.force_kind == 1) {
     const double dth = 2.0 * 3.14159265358979323846 / p.M;
@@ -85,6 +122,8 @@ void launch_force(const Plan& p, const Workspace& ws, const double* X, double* c
   } else if (ws.force_kind == 3) {
     const long long n = (long long)p.d * p.M;
     k_force_target<<<blocks_for(n), 256, 0, st>>>(X, ws.target, c, n, ws.target_wK);
+  } else if (ws.force_kind == 4) {
+    k_force_tension<<<blocks_for(8LL * p.M), 256, 0, st>>>(X, c, p.M, ws.csr_ptr, ws.inc_jk, 0.5 * ws.stiffness);
   } else {
     k_force_mesh<<<blocks_for(8LL * p.M), 256, 0, st>>>(X, c, p.M, ws.csr_ptr, ws.csr_col, ws.csr_k);
   }
@@ -221,7 +260,7 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 struct InvGeom {
   int d, M, force_kind, ntri, N, h;
   long long nspec;
-  double kunit, curve_K, target_wK;
+  double kunit, curve_K, target_wK, gamma;
 };
 
 __global__ void __launch_bounds__(kRedThreads)
@@ -249,6 +288,11 @@ k_inv_points(InvGeom g, const double* __restrict__ X, const int* __restrict__ tr
       const double bx = X[b], by = X[M + b], bz = X[2LL * M + b];
       const double cx = X[c], cy = X[M + c], cz = X[2LL * M + c];
       vol += (ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx)) / 6.0;
+      if (g.force_kind == 4) {  // E_p = gamma S
+        const double u0 = bx - ax, u1 = by - ay, u2 = bz - az, v0 = cx - ax, v1 = cy - ay, v2 = cz - az;
+        const double n0 = u1 * v2 - u2 * v1, n1 = u2 * v0 - u0 * v2, n2 = u0 * v1 - u1 * v0;
+        ep += 0.5 * g.gamma * sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+      }
     }
     for (long long i = t0; i < M; i += stride) {
       const double x0 = X[i], x1 = X[M + i], x2 = X[2LL * M + i];
@@ -355,6 +399,7 @@ int run_invariants(const Plan& p, Workspace& ws, const double* X, const C<T>* uh
   g.kunit = 2.0 * 3.14159265358979323846 / p.L;
   g.curve_K = ws.curve_K;
   g.target_wK = ws.target_wK;
+  g.gamma = ws.stiffness;
   const int nblk = ws.red_blocks;
   double* part = ws.red;
   double* res = ws.red + (size_t)nblk * kRedSlots;

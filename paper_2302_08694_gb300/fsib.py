@@ -30,7 +30,7 @@ EXPORTS = ["fsib_create", "fsib_destroy", "fsib_set_stream", "fsib_set_option", 
            "fsib_batch_create", "fsib_batch_member", "fsib_batch_set_stream", "fsib_batch_autotune",
            "fsib_batch_step", "fsib_batch_info", "fsib_batch_last_error", "fsib_batch_destroy",
            "fsib_interp_grad", "fsib_step_adjoint", "fsib_set_force_target", "fsib_set_body_force",
-           "fsib_band_flux"]
+           "fsib_band_flux", "fsib_set_force_tension"]
 
 _lib = None
 
@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "fsib_set_force_target": ([vp, vp, d_, d_], i_),
         "fsib_set_body_force": ([vp, dp], i_),
         "fsib_band_flux": ([vp, vp, i_, i_, d_, d_, dp], i_),
+        "fsib_set_force_tension": ([vp, vp, i_, d_], i_),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -193,6 +194,11 @@ class Problem:
     def set_force_mesh(self, tri, Xref, sigma):
         tri = np.ascontiguousarray(tri, dtype=np.int32) if isinstance(tri, np.ndarray) else tri
         self._call("fsib_set_force_mesh", _ptr(tri), int(tri.shape[0]), _ptr(Xref), float(sigma))
+
+    def set_force_tension(self, tri, gamma):
+        """Surface tension gamma S on the triangulated surface tri ([ntri][3] int32, ccw from outside)."""
+        tri = np.ascontiguousarray(tri, dtype=np.int32) if isinstance(tri, np.ndarray) else tri
+        self._call("fsib_set_force_tension", _ptr(tri), int(tri.shape[0]), float(gamma))
 
     def set_force_target(self, Xtarget, K, omega):
         """Target-point springs c = omega K (X~ - X); Xtarget [d][M] float64 (host or device)."""

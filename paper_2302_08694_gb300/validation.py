@@ -36,3 +36,33 @@ def poiseuille_steady_flux(f0: float, mu: float, D: float) -> float:
 def effective_width(flux: float, f0: float, mu: float) -> float:
     """Width D_e of the ideal channel that carries `flux` at equilibrium."""
     return (12.0 * mu * flux / f0) ** (1.0 / 3.0)
+
+
+def embed_half_spectrum(H: np.ndarray, N2: int) -> np.ndarray:
+    """Zero-pad a half spectrum (d, (N,) N, N//2) to N2 >= N modes per axis, keeping each
+    integer mode m at its place (FFT order on the full axes, m_x = 0..N/2-1 on the last)."""
+    d, N = H.shape[0], H.shape[1]
+    out = np.zeros((d,) + (N2,) * (H.ndim - 2) + (N2 // 2,), dtype=H.dtype)
+    i = np.arange(N)
+    m = np.where(i < N // 2, i, i - N) % N2
+    idx = np.ix_(*([np.arange(d)] + [m] * (H.ndim - 2) + [np.arange(N // 2)]))
+    out[idx] = H
+    return out
+
+
+def half_spectrum_norm(H: np.ndarray) -> float:
+    """L2 norm of the real field a half spectrum represents, up to the factor L^(d/2)
+    (Parseval): entries with m_x > 0 stand for m and -m."""
+    w = np.full(H.shape[-1], 2.0)
+    w[0] = 1.0
+    return float(np.sqrt(np.sum(w * np.abs(H) ** 2)))
+
+
+def successive_errors(spectra) -> list:
+    """Relative L2 difference of each solution from the next finer one (spectra listed
+    from coarse to fine, each padded to the finer mode set)."""
+    out = []
+    for a, b in zip(spectra[:-1], spectra[1:]):
+        N2 = b.shape[1]
+        out.append(half_spectrum_norm(embed_half_spectrum(a, N2) - b) / half_spectrum_norm(b))
+    return out

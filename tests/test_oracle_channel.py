@@ -171,3 +171,25 @@ def test_poiseuille_series_limits():
     assert va.effective_width(steady, f0, mu) == pytest.approx(D, rel=1e-14)
     ts = np.linspace(0.0, 3.0, 31)
     assert np.all(np.diff(va.poiseuille_flux(ts, f0, mu, rho, D)) > 0)
+
+
+def test_half_spectrum_norm_and_embedding_follow_parseval():
+    """The half-spectrum L2 norm equals the field's RMS over a uniform grid (Parseval),
+    and embedding in more modes changes neither the field nor its norm."""
+    from oracle import spectral as sp
+    rng = np.random.default_rng(21)
+    for d, N in ((2, 8), (3, 6)):
+        H = wl.random_half_spectrum(rng, d, N)
+        full = sp.half_to_full(H, N, d)
+        H = sp.full_to_half(full, N)           # a consistent (Hermitian, Nyquist-free) half spectrum
+        n = 2 * N
+        g = np.meshgrid(*([np.arange(n) / n] * d), indexing="ij")
+        P = np.stack([gi.ravel() for gi in g[::-1]])
+        U = sp.interp_direct(full, P, N)
+        rms = math.sqrt(np.mean(np.sum(U * U, axis=0)))
+        assert va.half_spectrum_norm(H) == pytest.approx(rms, rel=1e-12)
+        E = va.embed_half_spectrum(H, N + 4)
+        assert va.half_spectrum_norm(E) == pytest.approx(va.half_spectrum_norm(H), rel=1e-14)
+        U2 = sp.interp_direct(sp.half_to_full(E, N + 4, d), P, N + 4)
+        assert np.max(np.abs(U2 - U)) <= 1e-12 * np.max(np.abs(U))
+    assert va.successive_errors([H, H]) == [0.0]
