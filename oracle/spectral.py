@@ -337,6 +337,20 @@ def ns_substeps(fhat: np.ndarray, uhat: np.ndarray, N: int, mu: float, rho: floa
 # Spectral diagnostics (Sec. 4)
 # ---------------------------------------------------------------------------
 
+def pressure(fhat: np.ndarray, uhat, N: int, rho: float, L: float = 1.0,
+             Nt: int | None = None) -> np.ndarray:
+    """Pressure p-hat = -i k.(f-hat - rho s-hat(u-hat)) / |k|^2 with p-hat(0) = 0
+    (Eq. pressure_poisson_k; the constant is free and chosen so that p has mean zero).
+    uhat None drops the nonlinear term (Stokes). Returns one full-spectrum component."""
+    d = fhat.shape[0]
+    P = fhat if uhat is None else fhat - rho * nonlinear(uhat, N, L, Nt)
+    ks = wavevectors(N, d, L)
+    kP = sum(ks[a] * P[a] for a in range(d))
+    k2 = ksq(N, d, L)
+    p = np.where(k2 > 0, -1j * kP / np.where(k2 > 0, k2, 1.0), 0.0)
+    return zero_nyquist(p[None], N, d)[0]
+
+
 def band_flux(uhat: np.ndarray, N: int, comp: int, axis: int, y0: float, y1: float,
               L: float = 1.0) -> float:
     """Flux of velocity component `comp` through the band y0 <= x_axis <= y1.
