@@ -635,6 +635,28 @@ def validation_block(fsib, torch, dev, flush, cpu_sample=True):
         pbp.close()
     out["poiseuille"] = {"K": wl.config_poiseuille().stiffness, "by_N": chan,
                          "flux_rel_history_columns": ["t", "(Phi - Phi_eq)/Phi_eq FSIB", "same, Eq. poiseuille_flux"]}
+    # -- normal-force circle (Sec. 6.1): u = 0 and a pressure jump F/r across the circle
+    r, Nb = 0.25, 1024
+    th = 2 * np.pi * np.arange(Nb) / Nb
+    Xc = torch.from_numpy(np.stack([0.5 + r * np.cos(th), 0.5 + r * np.sin(th)])).to(dev)
+    Fc = torch.from_numpy(np.stack([np.cos(th), np.sin(th)])).to(dev)
+    wc = torch.full((Nb,), 2 * np.pi / Nb, dtype=torch.float64, device=dev)
+    p_in, p_out = -(1 - np.pi * r * r) / r, np.pi * r
+    Y = torch.tensor([[0.5, 0.0], [0.5, 0.0]], dtype=torch.float64, device=dev)
+    rows = []
+    for N in (32, 64, 128, 256):
+        pbc = fsib.Problem(N, 2, Nb, 1.0, 0.0, 1e-3, 1e-12)
+        fh = pbc.spread(Xc, Fc, wc)
+        uc = pbc.new_spec(device=dev)
+        pbc.fluid_step(fh, uc)
+        P = pbc.pressure_at(pbc.pressure(fh), Y).cpu().numpy()
+        rows.append({"N": N, "p_centre": float(P[0]), "p_corner": float(P[1]),
+                     "rel_err_centre": float(abs(P[0] - p_in) / abs(p_in)),
+                     "rel_err_corner": float(abs(P[1] - p_out) / p_out),
+                     "max_abs_u_hat": float(uc.abs().max())})
+        pbc.close()
+    out["normal_circle_pressure"] = {"r": r, "Nb": Nb, "F": 1.0, "p_inside_exact": p_in, "p_outside_exact": p_out,
+                                     "by_N": rows}
     return out
 
 

@@ -196,6 +196,15 @@ int fsib_step_adjoint(fsib_t h, const double* X0, int K, int ckpt_every, const d
  * Returns FSIB_ENONFINITE if X or uhat holds NaN/Inf. */
 int fsib_invariants(fsib_t h, const double* X, const void* uhat, double out[6]);
 
+/* Pressure (Eq. pressure_poisson_k): p-hat = -i k.(f-hat - rho s-hat(u-hat))/|k|^2,
+ * p-hat(0) = 0 (mean-free pressure), unpaired modes -N/2 zero. fhat, uhat: half
+ * spectra of the plan ([d][...]); phat: one half-spectrum component
+ * ([(N)][N][N/2]). s-hat is the dealiased nonlinear term of the Navier-Stokes
+ * update; it is dropped for a Stokes handle or uhat == NULL (rho s-hat = 0).
+ * The pressure at points follows from fsib_interp of a spectrum whose first
+ * component is phat. */
+int fsib_pressure(fsib_t h, const void* fhat, const void* uhat, void* phat);
+
 /* Channel flux (Eq. poiseuille_flux), synchronous: the velocity component
  * `comp` averaged over the axes other than `axis`, integrated over the band
  * y0 <= x_axis <= y1: *flux = int_{y0}^{y1} ubar(y) dy, computed from the

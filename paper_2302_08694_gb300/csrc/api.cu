@@ -596,6 +596,12 @@ static void do_fluid(fsib_plan* h, const C<TA>* fhat, C<TA>* u, C<TA>* uhalf, cu
     launch_ns_update<TA>(h->p, P, fhat, u, u, false, st); }
 }
 
+template <typename TI, typename TA>
+static void do_pressure(fsib_plan* h, const C<TA>* fhat, const C<TA>* u, C<TA>* phat, cudaStream_t st) {
+  const C<TA>* P = (!h->p.stokes && u) ? products<TI, TA>(h, u, st, h->ws.s1, h->ws.s2) : nullptr;
+  launch_pressure<TA>(h->p, P, fhat, phat, st);
+}
+
 static void do_axpy(fsib_plan* h, double* y, const double* x, const double* v, double a, cudaStream_t st) {
   const long long dm = (long long)h->p.d * h->p.M;
   Prof pr(h, "positions", 24.0 * dm, 0.0, st);
@@ -1145,6 +1151,21 @@ int fsib_fluid_step(fsib_t h, const void* fhat, void* uhat, void* uhat_half) {
   if ((rc = unstage(h, au)) != FSIB_OK) return rc;
   if (!h->p.stokes && (rc = unstage(h, ah)) != FSIB_OK) return rc;
   return finish(h, au.host != nullptr || ah.host != nullptr);
+}
+
+int fsib_pressure(fsib_t h, const void* fhat, const void* uhat, void* phat) {
+  int rc = begin(h);
+  if (rc != FSIB_OK) return rc;
+  if (!fhat || !phat) return fail(h, FSIB_EINVAL, "NULL array");
+  Arg af, au, ap;
+  if ((rc = stage(h, 0, fhat, spec_bytes(h), true, af)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 1, uhat, spec_bytes(h), true, au)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 2, phat, spec_bytes(h) / h->p.d, false, ap)) != FSIB_OK) return rc;
+  FSIB_DISPATCH(h, (do_pressure<float, float>(h, (const C<float>*)af.dev, (const C<float>*)au.dev, (C<float>*)ap.dev, h->own)),
+                (do_pressure<dd, double>(h, (const C<double>*)af.dev, (const C<double>*)au.dev, (C<double>*)ap.dev, h->own)),
+                (do_pressure<double, double>(h, (const C<double>*)af.dev, (const C<double>*)au.dev, (C<double>*)ap.dev, h->own)));
+  if ((rc = unstage(h, ap)) != FSIB_OK) return rc;
+  return finish(h, ap.host != nullptr);
 }
 
 static int count_kernel_nodes(cudaGraph_t g) {

@@ -106,6 +106,39 @@ __global__ void k_ns_update(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool 
   }
 }
 
+// Pressure (Eq. pressure_poisson_k): p = -i k.(f - rho s)/|k|^2 with p(0) = 0 (mean-free).
+// With the divergence form s_a = i sum_b k_b P_ab of the dealiased products P_ab = (u_a u_b)^,
+// k.s = i sum_ab k_a k_b P_ab, so p = (-i k.f - rho sum_ab k_a k_b P_ab)/|k|^2.
+// prod == nullptr drops the nonlinear term (Stokes). One output component.
+template <typename T>
+__global__ void k_pressure(SpecGeom g, T rho, const C<T>* __restrict__ prod, const C<T>* __restrict__ f,
+                           C<T>* __restrict__ out) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
+       idx += (long long)gridDim.x * blockDim.x) {
+    T k[3];
+    const bool ok = decode_mode<T>(g, idx, k);
+    const int d = g.d;
+    const T k2 = k[0] * k[0] + k[1] * k[1] + (d == 3 ? k[2] * k[2] : T(0));
+    C<T> v = mk<T>(T(0), T(0));
+    if (ok && k2 > T(0)) {
+      C<T> kf = mk<T>(T(0), T(0));
+      for (int a = 0; a < d; ++a) kf = cadd<T>(kf, cscale<T>(f[a * g.nspec + idx], k[a]));
+      v = mk<T>(kf.y, -kf.x);  // -i k.f
+      if (prod) {
+        C<T> kk = mk<T>(T(0), T(0));
+        for (int a = 0; a < d; ++a)
+          for (int b = a; b < d; ++b) {
+            const int ab = (d == 3) ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (a + b);
+            kk = cadd<T>(kk, cscale<T>(prod[ab * g.nspec + idx], (a == b ? T(1) : T(2)) * k[a] * k[b]));
+          }
+        v = csub<T>(v, cscale<T>(kk, rho));
+      }
+      v = cscale<T>(v, T(1) / k2);
+    }
+    out[idx] = v;
+  }
+}
+
 // out_a = i k_b in_a on the half spectrum (the unpaired mode -N/2 set to zero)
 template <typename T>
 __global__ void k_mul_ik(SpecGeom g, int b, const C<T>* __restrict__ in, C<T>* __restrict__ out) {
@@ -135,6 +168,12 @@ void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t 
 }
 
 template <typename T>
+void launch_pressure(const Plan& p, const C<T>* prod, const C<T>* fhat, C<T>* phat, cudaStream_t st) {
+  const SpecGeom g = sgeom(p);
+  k_pressure<T><<<grid_for(g.nspec), 256, 0, st>>>(g, (T)p.rho, prod, fhat, phat);
+}
+
+template <typename T>
 void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
                       C<T>* out, bool half, cudaStream_t st) {
   const SpecGeom g = sgeom(p);
@@ -153,6 +192,8 @@ template void launch_mul_ik<double>(const Plan&, int, const C<double>*, C<double
 
 template void launch_stokeslet<float>(const Plan&, const C<float>*, C<float>*, cudaStream_t);
 template void launch_stokeslet<double>(const Plan&, const C<double>*, C<double>*, cudaStream_t);
+template void launch_pressure<float>(const Plan&, const C<float>*, const C<float>*, C<float>*, cudaStream_t);
+template void launch_pressure<double>(const Plan&, const C<double>*, const C<double>*, C<double>*, cudaStream_t);
 template void launch_ns_update<float>(const Plan&, const C<float>*, const C<float>*, const C<float>*,
                                       C<float>*, bool, cudaStream_t);
 template void launch_ns_update<double>(const Plan&, const C<double>*, const C<double>*, const C<double>*,

@@ -198,6 +198,8 @@ void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, 
 template <typename T>
 void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t st);
 template <typename T>
+void launch_pressure(const Plan& p, const C<T>* prod, const C<T>* fhat, C<T>* phat, cudaStream_t st);
+template <typename T>
 void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
                       C<T>* out, bool half, cudaStream_t st);
 

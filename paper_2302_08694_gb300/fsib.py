@@ -30,7 +30,7 @@ EXPORTS = ["fsib_create", "fsib_destroy", "fsib_set_stream", "fsib_set_option", 
            "fsib_batch_create", "fsib_batch_member", "fsib_batch_set_stream", "fsib_batch_autotune",
            "fsib_batch_step", "fsib_batch_info", "fsib_batch_last_error", "fsib_batch_destroy",
            "fsib_interp_grad", "fsib_step_adjoint", "fsib_set_force_target", "fsib_set_body_force",
-           "fsib_band_flux", "fsib_set_force_tension"]
+           "fsib_band_flux", "fsib_set_force_tension", "fsib_pressure"]
 
 _lib = None
 
@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "fsib_set_body_force": ([vp, dp], i_),
         "fsib_band_flux": ([vp, vp, i_, i_, d_, d_, dp], i_),
         "fsib_set_force_tension": ([vp, vp, i_, d_], i_),
+        "fsib_pressure": ([vp, vp, vp, vp], i_),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -211,6 +212,26 @@ class Problem:
         vals = [float(v) for v in f] + [0.0, 0.0, 0.0]
         arr = (ctypes.c_double * 3)(*vals[:3])
         self._call("fsib_set_body_force", arr)
+
+    def pressure(self, fhat, uhat=None, out=None):
+        """p-hat = -i k.(f-hat - rho s-hat(u-hat))/|k|^2 (one half-spectrum component)."""
+        if out is None:
+            import torch
+            dev = fhat.device if hasattr(fhat, "device") else "cpu"
+            out = torch.zeros(self.spec_shape[1:], dtype=self.spec_dtype, device=dev)
+        self._call("fsib_pressure", _ptr(fhat), _ptr(uhat), _ptr(out))
+        return out
+
+    def pressure_at(self, phat, Y):
+        """Pressure at the points Y ([d][n] float64) by the type-2 transform of phat."""
+        n = Y.shape[1]
+        probe = Problem(self.N, self.d, n, self.mu, self.rho if self.rho > 0 else 0.0, self.dt, self.tol,
+                        precision=self.precision)
+        spec = probe.new_spec(device=phat.device)
+        spec[0] = phat
+        U = probe.interp(spec, Y)
+        probe.close()
+        return U[0]
 
     def band_flux(self, uhat, comp, axis, y0, y1):
         """Flux of u_comp averaged over the other axes through y0 <= x_axis <= y1."""

@@ -1,0 +1,122 @@
+"""Diagnostics through the C ABI against the oracle: the pressure (Eq. pressure_poisson_k)
+and the equivalent 'sinc' kernel of Sec. 3.2 realised by the library's spread and interp.
+
+Pressure: FP64 mode to 1e-10 relative, mixed to 1e-5. Kernel: spreading a unit source
+and interpolating gives L^-d sum_{k in K_N} e^{ik.(x - X0)}; with the unpaired modes -N/2
+zero this is the product over the axes of the odd-order Dirichlet kernel
+delta_{L,N-1}(s) = sin((N-1) pi s/L) / (L sin(pi s/L)) (Eq. FSIB_kern_odd), whose discrete
+identities (zeroth moment, value 1/h at 0) the library must reproduce to its tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import spectral as sp
+from paper_2302_08694_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+NTOL = {"fp64": 1e-12, "mixed": 1e-6}
+CDT = {"fp64": np.complex128, "mixed": np.complex64}
+
+
+def rel2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def cuda(a, torch):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("d,N,rho", [(2, 16, 0.0), (2, 24, 1.5), (3, 8, 0.0), (3, 12, 2.0), (3, 48, 1.0)])
+def test_pressure_matches_oracle(lib, torch_mod, prec, d, N, rho):
+    torch = torch_mod
+    rng = np.random.default_rng(300 + 10 * d + N)
+    f = sp.half_to_full(wl.random_half_spectrum(rng, d, N), N, d)
+    u = 0.1 * sp.leray(sp.half_to_full(wl.random_half_spectrum(rng, d, N), N, d), N)
+    cd = CDT[prec]
+    fh, uh = sp.full_to_half(f, N).astype(cd), sp.full_to_half(u, N).astype(cd)
+    f_in = sp.half_to_full(fh.astype(np.complex128), N, d)
+    u_in = sp.half_to_full(uh.astype(np.complex128), N, d)
+    pb = lib.Problem(N, d, 4, 0.1, rho, 1e-3, NTOL[prec], precision=prec)
+    got = to_np(pb.pressure(cuda(fh, torch), cuda(uh, torch) if rho > 0 else None))
+    got = sp.half_to_full(got[None].astype(np.complex128), N, d)[0]
+    want = sp.pressure(f_in, u_in if rho > 0 else None, N, max(rho, 1.0))
+    assert rel2(got, want) <= TOL[prec]
+
+
+def test_normal_circle_pressure_through_the_library(lib, torch_mod):
+    """Sec. 6.1 normal case at N = 128, N_b = 512: zero velocity, and the pressure at the
+    centre and the corner equal the oracle's (which approach the paper's closed form)."""
+    torch = torch_mod
+    N, Nb, r = 128, 512, 0.25
+    th = 2 * math.pi * np.arange(Nb) / Nb
+    X = np.stack([0.5 + r * np.cos(th), 0.5 + r * np.sin(th)])
+    F = np.stack([np.cos(th), np.sin(th)])
+    omega = np.full(Nb, 2 * math.pi / Nb)
+    pb = lib.Problem(N, 2, Nb, 1.0, 0.0, 1e-3, 1e-12)
+    fh = pb.spread(cuda(X, torch), cuda(F, torch), cuda(omega, torch))
+    u = pb.new_spec()
+    pb.fluid_step(fh, u)
+    ph = pb.pressure(fh)
+    Y = cuda(np.array([[0.5, 0.0, 0.2], [0.5, 0.0, 0.9]]), torch)
+    P = to_np(pb.pressure_at(ph, Y))
+    torch.cuda.synchronize()
+    assert np.max(np.abs(to_np(u))) <= 1e-10 * np.max(np.abs(to_np(fh))) / (4 * math.pi ** 2)
+    ref = sp.interp_direct(sp.pressure(sp.spread_direct(X, F * omega, N), None, N, 1.0)[None],
+                           to_np(Y), N)[0]
+    assert rel2(P, ref) <= 1e-10
+    assert abs(P[0] + (1 - math.pi * r * r) / r) < 0.02 * (1 - math.pi * r * r) / r
+
+
+def dirichlet_odd(s, n, L=1.0):
+    """Odd-order Dirichlet kernel sin(n pi s/L) / (L sin(pi s/L)), value n/L at s = 0 (mod L)."""
+    s = np.asarray(s, dtype=np.float64)
+    den = np.sin(math.pi * s / L)
+    small = np.abs(den) < 1e-12
+    return np.where(small, n / L, np.sin(n * math.pi * s / L) / (L * np.where(small, 1.0, den)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("d,N", [(2, 16), (3, 12)])
+def test_equivalent_kernel_identities(lib, torch_mod, prec, d, N):
+    torch = torch_mod
+    rng = np.random.default_rng(50 + N)
+    X0 = rng.uniform(0, 1, (d, 1))
+    n = N - 1                     # modes |m| <= N/2 - 1 survive: an odd-order kernel
+    h = 1.0 / n
+    # points: the grid x_j = X0 + j h along axis 0 (zeroth moment) plus random points
+    M = n + 40
+    Y = np.repeat(X0, M, axis=1)
+    Y[0, :n] = X0[0, 0] + h * np.arange(n)
+    Y[:, n:] = rng.uniform(0, 1, (d, 40))
+    pb = lib.Problem(N, d, M, 1.0, 0.0, 1e-3, NTOL[prec], precision=prec)
+    src = lib.Problem(N, d, 1, 1.0, 0.0, 1e-3, NTOL[prec], precision=prec)
+    e = np.zeros((d, 1))
+    e[0, 0] = 1.0
+    fh = src.spread(cuda(X0, torch), cuda(e, torch))     # unit source in component 0
+    U = to_np(pb.interp(fh, cuda(Y, torch)))[0]
+    torch.cuda.synchronize()
+    want = np.ones(M)
+    for a in range(d):
+        want *= dirichlet_odd(Y[a] - X0[a, 0], n)
+    tol = 10 * TOL[prec]
+    assert np.max(np.abs(U - want)) <= tol * n ** d
+    assert U[0] == pytest.approx(n ** d, rel=tol)                        # delta(0) = 1/h^d
+    # zeroth moment along the grid line: sum_j delta(x_j - X0) h = delta_{N-1} in the other axes at 0
+    assert np.sum(U[:n]) * h == pytest.approx(n ** (d - 1), rel=tol)
