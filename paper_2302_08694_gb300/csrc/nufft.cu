@@ -869,11 +869,12 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
                  const int* __restrict__ box_item, const int* __restrict__ part_off, dd* __restrict__ part,
                  dd* __restrict__ grid, int* __restrict__ work, int* __restrict__ done) {
   // dynamic shared memory (above the 48 KB static limit): two buffers of
-  //   [c][y][x] w_x w_y (stride kXYStride), [c][a][z] C_a w_z, [c][z] w_z (high part)
+  //   [c][y][x] w_x w_y (stride kXYStride), [c][a][z] C_a w_z, [c] mask of the z planes the
+  //   candidate reaches (0 when its window misses the box along x or y)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd (*sXY)[kBoxChunkDD * kXYStride] = reinterpret_cast<dd (*)[kBoxChunkDD * kXYStride]>(smem_raw);
   dd (*sCz)[kBoxChunkDD * 24] = reinterpret_cast<dd (*)[kBoxChunkDD * 24]>(sXY + 2);
-  float (*sWz)[kBoxChunkDD * 8] = reinterpret_cast<float (*)[kBoxChunkDD * 8]>(sCz + 2);
+  unsigned (*sMask)[kBoxChunkDD] = reinterpret_cast<unsigned (*)[kBoxChunkDD]>(sCz + 2);
   __shared__ int sStart[32], sPre[33];
   __shared__ int sNr;
   const int w = g.w, nf = g.nf, M = g.M;
@@ -950,7 +951,12 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
         const float cl = __shfl_sync(0xffffffffu, cv.lo, (lane & ~7) | a);
         if (on) sCz[bb][c * 24 + a * 8 + t] = dd(ch, cl) * wa[2];
       }
-      if (on) sWz[bb][c * 8 + t] = wa[2].hi;
+      // which offsets carry weight, per axis, for the eight lanes of this candidate
+      const int gs = lane & ~7;
+      const unsigned bx = (__ballot_sync(0xffffffffu, on && wa[0].hi != 0.0f) >> gs) & 0xffu;
+      const unsigned by = (__ballot_sync(0xffffffffu, on && wa[1].hi != 0.0f) >> gs) & 0xffu;
+      const unsigned bz = (__ballot_sync(0xffffffffu, on && wa[2].hi != 0.0f) >> gs) & 0xffu;
+      if (on && t == 0) sMask[bb][c] = (bx && by) ? bz : 0u;
     };
     dd acc[2][3];
 #pragma unroll
@@ -965,9 +971,9 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
       if (c0 + kBoxChunkDD < f1) stage(c0 + kBoxChunkDD, min(f1, c0 + 2 * kBoxChunkDD), bb ^ 1);
       const dd* XY = sXY[bb];
       const dd* CZ = sCz[bb];
-      const float* WZ = sWz[bb];
+      const unsigned* MK = sMask[bb];
       for (int c = 0; c < nc; ++c) {
-        if (WZ[c * 8 + warp] == 0.0f) continue;  // uniform across the warp
+        if (!((MK[c] >> warp) & 1u)) continue;  // uniform across the warp
         const dd t0 = XY[c * kXYStride + ly * 8 + lx], t1 = XY[c * kXYStride + (ly + 4) * 8 + lx];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -1153,7 +1159,7 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
     k_scan2<<<2, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
     k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item, ws.box_work);
     if constexpr (std::is_same<T, dd>::value) {
-      constexpr size_t smem = 2 * sizeof(dd) * kBoxChunkDD * (kXYStride + 24) + 2 * sizeof(float) * kBoxChunkDD * 8;
+      constexpr size_t smem = 2 * sizeof(dd) * kBoxChunkDD * (kXYStride + 24) + 2 * sizeof(unsigned) * kBoxChunkDD;
       static const int per_sm = [] {
         raise_smem_limit(reinterpret_cast<const void*>(k_spread_box3_dd));
         int n = 0;
