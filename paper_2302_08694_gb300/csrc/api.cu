@@ -230,7 +230,8 @@ static void free_ws(Workspace& ws) {
   void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.grid2, ws.s1, ws.s2, ws.s3, ws.s4, ws.fhat, ws.uhalf, ws.bin_of,
                   ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
                   ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.wts, ws.cwp,
-                  ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.box_item, ws.box_work, ws.box_done, ws.part};
+                  ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.box_item, ws.box_sched, ws.box_work, ws.box_done,
+                  ws.part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   ws.tw = ws.dline = ws.dplane = ws.grid = ws.grid2 = ws.s1 = ws.s2 = ws.s3 = ws.s4 = ws.fhat = ws.uhalf = nullptr;
@@ -239,7 +240,7 @@ static void free_ws(Workspace& ws) {
   ws.Xh = ws.cw = ws.Uh = ws.omega_ones = ws.red = nullptr;
   ws.flag = nullptr;
   ws.wts = ws.cwp = nullptr;
-  ws.box_ns = ws.box_np = ws.box_so = ws.box_po = ws.box_item = ws.box_work = ws.box_done = nullptr;
+  ws.box_ns = ws.box_np = ws.box_so = ws.box_po = ws.box_item = ws.box_sched = ws.box_work = ws.box_done = nullptr;
   ws.part = nullptr;
   void* adj[] = {ws.adj_spec, ws.adj_pts, ws.adj_ckpt, ws.adj_part, ws.adj_sig};
   for (void* q : adj)
@@ -334,8 +335,9 @@ static int alloc_ws(fsib_plan* h) {
   rc |= dmalloc(&ws.box_so, sizeof(int) * (size_t)(p.nbins + 1), tot);
   rc |= dmalloc(&ws.box_po, sizeof(int) * (size_t)(p.nbins + 1), tot);
   // slices: at most one per non-empty box plus one per kMinSlice candidates (<= 27 M candidates)
-  rc |= dmalloc(&ws.box_item, sizeof(int) * (size_t)std::min<long long>(p.nbins + 27 * (long long)p.M / kMinSlice + 64,
-                                                                      17LL * p.nbins), tot);
+  const size_t nslice_cap = (size_t)std::min<long long>(p.nbins + 27 * (long long)p.M / kMinSlice + 64, 17LL * p.nbins);
+  rc |= dmalloc(&ws.box_item, sizeof(int) * nslice_cap, tot);
+  rc |= dmalloc(&ws.box_sched, sizeof(int) * nslice_cap, tot);
   rc |= dmalloc(&ws.box_work, sizeof(int) * 4, tot);
   rc |= dmalloc(&ws.box_done, sizeof(int) * (size_t)p.nbins, tot);
   // partial slots: boxes with K > 1 hold K slots, K <= 2 cand/256; sum cand <= 27 M

@@ -148,6 +148,7 @@ struct Workspace {
   int* box_so = nullptr;             // [nbins + 1] slice offsets
   int* box_po = nullptr;             // [nbins + 1] partial-slot offsets
   int* box_item = nullptr;           // [slices] box of each slice (non-empty boxes only)
+  int* box_sched = nullptr;          // [slices] order in which the gather takes the slices
   int* box_work = nullptr;           // [2] gather work counters: next slice, next run of empty boxes
   int* box_done = nullptr;           // [nbins] slices of a split box finished (the last one adds the partials)
   void* part = nullptr;              // T[slots][3][512] partial boxes

@@ -615,13 +615,23 @@ __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restric
   }
 }
 
-// Box of every slice: box_item[slice_off[b] + k] = b for k < K_b.
+// Box of every slice: box_item[slice_off[b] + k] = b for k < K_b; and the order in which
+// the gather takes them: the slices of split boxes (K_b > 1, the densest, whose slices
+// are the longest) first, then the single-slice boxes, so that the work left at the end of
+// the launch is short. part_off (prefix of K_b over split boxes) numbers the first group;
+// slice_off[b] - part_off[b] counts the single-slice boxes before b.
 // Also resets the gather's work counters for the launch that follows.
-__global__ void k_slice_boxes(int nbox, const int* __restrict__ slice_off, int* __restrict__ box_item,
-                              int* __restrict__ work) {
+__global__ void k_slice_boxes(int nbox, const int* __restrict__ slice_off, const int* __restrict__ part_off,
+                              int* __restrict__ box_item, int* __restrict__ sched, int* __restrict__ work) {
   if (blockIdx.x == 0 && threadIdx.x < 2) work[threadIdx.x] = 0;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x)
-    for (int k = slice_off[b]; k < slice_off[b + 1]; ++k) box_item[k] = b;
+  const int nsplit = part_off[nbox];
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+    const int s0 = slice_off[b], K = slice_off[b + 1] - s0;
+    for (int k = 0; k < K; ++k) {
+      box_item[s0 + k] = b;
+      sched[(K > 1) ? part_off[b] + k : nsplit + (s0 - part_off[b])] = s0 + k;
+    }
+  }
 }
 
 // Next work of the calling block (dynamic scheduling, so that heavy and light slices spread
@@ -739,7 +749,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
               const T* __restrict__ W, const T* __restrict__ Cw, const int* __restrict__ slice_off,
-              const int* __restrict__ box_item, const int* __restrict__ part_off, T* __restrict__ part,
+              const int* __restrict__ box_item, const int* __restrict__ sched, const int* __restrict__ part_off,
+              T* __restrict__ part,
               T* __restrict__ grid, int* __restrict__ work, int* __restrict__ done) {
   __shared__ T sB[2][kBoxChunk * 24];  // [c][axis][8] box-relative weights
   __shared__ T sC[2][kBoxChunk * 3];
@@ -753,9 +764,10 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
   __shared__ int s_item[2], s_flag;
   for (;;) {
     int run;
-    const int sl = next_slice(work, s_item, &run);
+    const int it = next_slice(work, s_item, &run);
     if (run < (nbox + 31) / 32) zero_run_block(g, slice_off, nbox, grid, run);
-    if (sl >= nslices) break;
+    if (it >= nslices) break;
+    const int sl = sched[it];
     const int box = box_item[sl], ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
     const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
     const int o[3] = {Bx * 8, By * 8, Bz * 8};
@@ -866,7 +878,8 @@ constexpr int kXYStride = 72;     // per-candidate stride of the x-y table (64 +
 __global__ void __launch_bounds__(256)
 k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
                  const dd* __restrict__ W, const dd* __restrict__ Cw, const int* __restrict__ slice_off,
-                 const int* __restrict__ box_item, const int* __restrict__ part_off, dd* __restrict__ part,
+                 const int* __restrict__ box_item, const int* __restrict__ sched, const int* __restrict__ part_off,
+                 dd* __restrict__ part,
                  dd* __restrict__ grid, int* __restrict__ work, int* __restrict__ done) {
   // dynamic shared memory (above the 48 KB static limit): two buffers of
   //   [c][y][x] w_x w_y (stride kXYStride), [c][a][z] C_a w_z, [c] mask of the z planes the
@@ -885,9 +898,10 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
   __shared__ int s_item[2], s_flag;
   for (;;) {
     int run;
-    const int sl = next_slice(work, s_item, &run);
+    const int it = next_slice(work, s_item, &run);
     if (run < (nbox + 31) / 32) zero_run_block(g, slice_off, nbox, grid, run);
-    if (sl >= nslices) break;
+    if (it >= nslices) break;
+    const int sl = sched[it];
     const int box = box_item[sl], ks = sl - slice_off[box], K = slice_off[box + 1] - slice_off[box];
     const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = box / (g.nb[0] * g.nb[1]);
     const int o[3] = {Bx * 8, By * 8, Bz * 8};
@@ -1157,7 +1171,8 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
     k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np,
                                                            ws.box_done);
     k_scan2<<<2, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
-    k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_item, ws.box_work);
+    k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_po, ws.box_item, ws.box_sched,
+                                                       ws.box_work);
     if constexpr (std::is_same<T, dd>::value) {
       constexpr size_t smem = 2 * sizeof(dd) * kBoxChunkDD * (kXYStride + 24) + 2 * sizeof(unsigned) * kBoxChunkDD;
       static const int per_sm = [] {
@@ -1167,7 +1182,7 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
         return n;
       }();
       k_spread_box3_dd<<<per_sm * num_sms(), 256, smem, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const dd*)ws.wts,
-                                                           (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
+                                                           (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_sched, ws.box_po,
                                                            (dd*)ws.part, grid, ws.box_work, ws.box_done);
     } else {
       static const int per_sm = [] {
@@ -1176,7 +1191,7 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
         return n;
       }();
       k_spread_box3<T><<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
-                                                      (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_po,
+                                                      (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_sched, ws.box_po,
                                                       (T*)ws.part, grid, ws.box_work, ws.box_done);
     }
   } else
