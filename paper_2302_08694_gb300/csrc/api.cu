@@ -154,7 +154,16 @@ static int plan_sizes(Plan& p, std::string& err) {
   int b = p.bin_opt;
   const bool gather = !(p.prec == FSIB_FP64 && p.native_fp64);
   if (gather) {
-    b = (p.d == 2) ? (b > 0 ? b : 32) : 8;  // 3D gather boxes are 8^3 (one run of 8 cells per task)
+    if (p.d == 2 && b <= 0) {
+      // 2D boxes: the largest side (32, 16, 8) that still gives one box per SM, so that a
+      // small grid spreads over the whole GPU (one block per box)
+      int dev = 0, sms = 1;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); sms = 1; }
+      b = 32;
+      while (b > 8 && (long long)(p.nf / b) * (p.nf / b) < sms) b /= 2;
+    }
+    b = (p.d == 2) ? b : 8;  // 3D gather boxes are 8^3 (one run of 8 cells per task)
     if (p.d == 2) { b = std::max(8, std::min(32, b)); b = (b / 8) * 8; }
   } else if (b <= 0) {
     if (p.d == 2) b = 32;

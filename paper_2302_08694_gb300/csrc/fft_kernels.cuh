@@ -551,6 +551,23 @@ static unsigned wrows_grid(K kern, int threads, size_t smem, long long groups) {
   return (unsigned)std::max<long long>(1, std::min<long long>(need, (long long)per * sms));
 }
 
+// A warp-level row pass runs one chain of transforms per warp. With fewer warps than this
+// (small 2D grids) most of the GPU idles on that chain, and the block-level kernels, which
+// spread each row pair over a whole block, finish first; they then take one row pair per
+// block when the pairs do not fill the SMs twice.
+constexpr long long kWarpRowsMin = 128;
+static FftLen small_rows(const FftLen& fl, long long npairs) {
+  static const int sms = [] {
+    int dev = 0, n = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+  }();
+  FftLen f = fl;
+  if (npairs < 2LL * sms * f.rows_q) f.rows_q = 1;
+  return f;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers: each dispatches on the FFT length (a compile-time kernel for the
 // lengths in FSIB_FFT_SIZES, the runtime-length kernel otherwise).
@@ -615,13 +632,14 @@ template <typename T>
 void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const FftLen& fl,
                          const C<T>* tw, cudaStream_t st) {
   const long long npairs = nrows / 2;
-  const int kQrows = fl.rows_q;
+  const FftLen fs = small_rows(fl, npairs);
+  const int kQrows = fs.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
   with_fft_len(fl.n, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
-    if constexpr (wfft_has(NC)) {
-      constexpr int LPW = 32 / wfft_L(NC);
+    constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;
+    if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_r2c<T, NC>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
@@ -630,7 +648,7 @@ void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const 
     }
     auto k = k_rows_r2c<T, decltype(nc)::value>;
     raise_smem_limit(reinterpret_cast<const void*>(k));
-    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
+    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fs, tw);
   });
 }
 
@@ -638,13 +656,14 @@ template <typename T>
 void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
                          const C<T>* tw, cudaStream_t st) {
   const long long npairs = nrows / 2;
-  const int kQrows = fl.rows_q;
+  const FftLen fs = small_rows(fl, npairs);
+  const int kQrows = fs.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
   with_fft_len(fl.n, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
-    if constexpr (wfft_has(NC)) {
-      constexpr int LPW = 32 / wfft_L(NC);
+    constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;
+    if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_c2r<T, NC>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
@@ -653,7 +672,7 @@ void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const 
     }
     auto k = k_rows_c2r<T, decltype(nc)::value>;
     raise_smem_limit(reinterpret_cast<const void*>(k));
-    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fl, tw);
+    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fs, tw);
   });
 }
 
@@ -661,13 +680,14 @@ template <typename T>
 void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int Nk,
                          const FftLen& fl, const C<T>* tw, cudaStream_t st) {
   const long long npairs = nrows / 2;
-  const int kQrows = fl.rows_q;
+  const FftLen fs = small_rows(fl, npairs);
+  const int kQrows = fs.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * 6 * (fl.n + 1));
   with_fft_len(fl.n, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
-    if constexpr (wfft_has(NC)) {
-      constexpr int LPW = 32 / wfft_L(NC);
+    constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;
+    if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       constexpr int PT = 128;
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + (PT / 32) * LPW * 3 * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_product<T, NC>;
@@ -677,7 +697,7 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
     }
     auto k = k_rows_product<T, decltype(nc)::value>;
     raise_smem_limit(reinterpret_cast<const void*>(k));
-    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, d, nrows, Nk, fl, tw);
+    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, d, nrows, Nk, fs, tw);
   });
 }
 

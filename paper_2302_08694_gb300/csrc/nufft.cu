@@ -1194,8 +1194,13 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
                                                       (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_sched, ws.box_po,
                                                       (T*)ws.part, grid, ws.box_work, ws.box_done);
     }
-  } else
-    k_spread_gather<T, 2><<<nbox, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
+  } else {
+    // one thread per (component, row, run of kSeg cells) of the box
+    const int ntask = 2 * p.bins[1] * (p.bins[0] / kSeg);
+    const int threads = std::min(256, std::max(32, (ntask + 31) / 32 * 32));
+    k_spread_gather<T, 2><<<nbox, threads, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp,
+                                                     grid);
+  }
 }
 
 template <typename T>
