@@ -442,8 +442,10 @@ constexpr int s2_R1(int n) {
 }
 constexpr int s2_P(int E) { return E == 8 ? 16 : 8; }  // lines per tile: 128-byte rows
 
+// FP32 tiles ask for three resident blocks per SM (at most 80 registers a thread): the
+// strided passes wait on memory, and the third block hides more of it.
 template <typename T, bool INV, typename Tin, typename Tout, int N>
-__global__ void __launch_bounds__(16 * s2_P((int)sizeof(C<T>)))
+__global__ void __launch_bounds__(16 * s2_P((int)sizeof(C<T>)), sizeof(C<T>) == 8 ? 3 : 1)
 k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
          Mult<T> mult, const C<T>* __restrict__ twg) {
   constexpr int P = s2_P((int)sizeof(C<T>)), R1 = s2_R1(N), R2 = N / R1, NT = 16 * P;
