@@ -604,6 +604,20 @@ def validation_block(fsib, torch, dev, flush, cpu_sample=True):
     ev = list(errs.values())
     circle["temporal_error_at_t0.1"] = errs
     circle["temporal_order"] = [float(np.log2(a / b)) for a, b in zip(ev[:-1], ev[1:])]
+    # space and time together (Fig. spatial_conv): N = 8 * 2^r, N_b = 26 * 2^r, dt = 0.001 / 2^r, T = 0.1
+    spectra = []
+    for rr in range(6):
+        pj = wl.config_ns2d_circle(N=8 * 2 ** rr, Nb=26 * 2 ** rr, dt=0.001 / 2 ** rr, T=0.1)
+        pbj = make_problem(fsib, pj, "fp64")
+        Xj = torch.from_numpy(pj.X0.copy()).to(dev)
+        uj = torch.from_numpy(pj.extra["u0"]).to(dev)
+        Uj = pbj.interp(uj, Xj)
+        pbj.step(Xj, uj, Uj, nsteps=pj.nsteps)
+        spectra.append(uj.cpu().numpy())
+        pbj.close()
+    se = va.successive_errors(spectra)
+    circle["space_time_convergence"] = {"N": [8 * 2 ** rr for rr in range(6)], "successive_rel_l2": se,
+                                        "orders": [float(np.log2(a / b)) for a, b in zip(se[:-1], se[1:])]}
     out["sine_circle"] = circle
     pb.close()
     # -- Poiseuille channel: flux history and effective wall width against N
