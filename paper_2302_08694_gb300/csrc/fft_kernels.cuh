@@ -442,12 +442,9 @@ constexpr int s2_R1(int n) {
 }
 constexpr int s2_P(int E) { return E == 8 ? 16 : 8; }  // lines per tile: 128-byte rows
 
-// FP32 tiles ask for three resident blocks per SM (at most 80 registers a thread): the
-// strided passes wait on memory, and the third block hides more of it.
 template <typename T, bool INV, typename Tin, typename Tout, int N>
-__global__ void __launch_bounds__(16 * s2_P((int)sizeof(C<T>)), sizeof(C<T>) == 8 ? 3 : 1)
-k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
-         Mult<T> mult, const C<T>* __restrict__ twg) {
+__device__ __forceinline__ void fft_s2_body(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner,
+                                            int Nk, int ntile, Mult<T> mult, const C<T>* __restrict__ twg) {
   constexpr int P = s2_P((int)sizeof(C<T>)), R1 = s2_R1(N), R2 = N / R1, NT = 16 * P;
   constexpr int RM = R1 > R2 ? R1 : R2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -541,6 +538,27 @@ k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, in
   }
 }
 
+// FP32 tiles ask for three resident blocks per SM (at most 80 registers a thread): the
+// strided passes wait on memory, and the third block hides more of it. Double-float tiles
+// keep the compiler's own register choice (a minimum-blocks hint of one raises it).
+template <typename T, bool INV, typename Tin, typename Tout, int N>
+__global__ void __launch_bounds__(16 * s2_P(8), 3)
+k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
+         Mult<T> mult, const C<T>* __restrict__ twg) {
+  fft_s2_body<T, INV, Tin, Tout, N>(in, out, inner, Nk, ntile, mult, twg);
+}
+template <typename T, bool INV, typename Tin, typename Tout, int N>
+__global__ void __launch_bounds__(16 * s2_P(16))
+k_fft_s2_dd(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
+            Mult<T> mult, const C<T>* __restrict__ twg) {
+  fft_s2_body<T, INV, Tin, Tout, N>(in, out, inner, Nk, ntile, mult, twg);
+}
+template <typename T, bool INV, typename Tin, typename Tout, int N>
+inline auto fft_s2_kernel() {
+  if constexpr (sizeof(C<T>) == 8) return k_fft_s2<T, INV, Tin, Tout, N>;
+  else return k_fft_s2_dd<T, INV, Tin, Tout, N>;
+}
+
 // Persistent grid of a warp-transform kernel: resident blocks per SM times the SMs,
 // or fewer when there is less work.
 template <typename K>
@@ -606,13 +624,13 @@ void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, in
       const long long blocks2 = (long long)ncomp * outer * nt2;
       const size_t smem2 = sizeof(C<T>) * (size_t)(NC + NC * P2);
       if (inverse && !fwd_only) {
-        auto k = k_fft_s2<T, true, Tin, Tout, NC>;
+        auto k = fft_s2_kernel<T, true, Tin, Tout, NC>();
         raise_smem_limit(reinterpret_cast<const void*>(k));
         k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off);
         return;
       }
       if (!inverse && !inv_only) {
-        auto k = k_fft_s2<T, false, Tin, Tout, NC>;
+        auto k = fft_s2_kernel<T, false, Tin, Tout, NC>();
         raise_smem_limit(reinterpret_cast<const void*>(k));
         k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off);
         return;

@@ -1,4 +1,6 @@
 // Fourier-space fluid solves on the half spectrum (Secs. 3.1-3.3, 6.1).
+#include <type_traits>
+
 #include "fsib_internal.cuh"
 
 namespace fsib {
@@ -139,6 +141,99 @@ __global__ void k_pressure(SpecGeom g, T rho, const C<T>* __restrict__ prod, con
   }
 }
 
+// The same update for FP64 mode in double-float arithmetic: GB300 executes FP64 at a small
+// fraction of its FP32 rate, and this kernel is arithmetic-bound in FP64. Inputs and outputs
+// stay double; each value is split exactly into hi + lo floats on load and rejoined on store.
+// Reciprocals take one Newton step from the float reciprocal (error about 2^-46).
+__device__ __forceinline__ dd dd_rcp(dd a) {
+  const dd r(__frcp_rn(a.hi));
+  return r + r * (dd(1.0f) - a * r);
+}
+// Exact-enough split of a double into hi + lo floats with integer operations (the FP64
+// conversions run at the FP64 rate): hi keeps the top 24 significant bits (truncated), lo is
+// the remaining 29 bits rounded to a float and scaled by 2^(E - 52). Values below 2^-100
+// (far under any tolerance here) become zero; Inf, NaN and values beyond the float range
+// take the slow conversion so that they stay visible.
+__device__ __forceinline__ dd split_double(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((u >> 52) & 0x7ffULL) - 1023;
+  if (e < -100) return dd(0.0f, 0.0f);
+  if (e > 127) return dd(__double2float_rn(v), 0.0f);  // Inf, NaN or out of float range: keep it visible
+  const unsigned sgn = (unsigned)(u >> 32) & 0x80000000u;
+  const unsigned long long m = u & 0xfffffffffffffULL;
+  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+  float lo = __uint2float_rn((unsigned)(m & 0x1fffffffULL));          // low 29 bits, exact up to 2^24 rounding
+  lo *= __uint_as_float((unsigned)(e - 52 + 127) << 23);               // 2^(e - 52), a normal float for e >= -74
+  if (e < -74) lo = 0.0f;
+  return dd(hi, sgn ? -lo : lo);
+}
+// hi + lo as a double: both floats widened by integer operations, one FP64 addition.
+__device__ __forceinline__ double widen_float(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ex = (b >> 23) & 0xffu;
+  if (ex == 0) return 0.0;  // zero (float subnormals do not occur in these values)
+  if (ex == 255) return (double)f;  // Inf or NaN
+  const unsigned long long r = ((unsigned long long)(b & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex - 127 + 1023) << 52) |
+                               ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)r);
+}
+__device__ __forceinline__ double join_dd(dd a) { return widen_float(a.hi) + widen_float(a.lo); }
+
+struct DDc { dd x, y; };
+__device__ __forceinline__ DDc ddc(double2 v) { return {split_double(v.x), split_double(v.y)}; }
+
+__global__ void k_ns_update_dd(SpecGeom g, dd kunit, dd inv_rho, dd mu_dt_over_rho, dd dt, bool half, Body fb,
+                               const double2* __restrict__ prod, const double2* __restrict__ f,
+                               const double2* __restrict__ base, double2* __restrict__ out) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(idx % g.h);
+    const long long r = idx / g.h;
+    const int iy = (int)(r % g.N), iz = (g.d == 3) ? (int)(r / g.N) : 0;
+    const bool ok = !(iy == g.N / 2 || (g.d == 3 && iz == g.N / 2));
+    const int my = iy < g.N / 2 ? iy : iy - g.N, mz = iz < g.N / 2 ? iz : iz - g.N;
+    const int d = g.d;
+    const dd k[3] = {kunit * dd((float)ix), kunit * dd((float)my), kunit * dd((float)mz)};
+    dd k2 = k[0] * k[0] + k[1] * k[1];
+    if (d == 3) k2 = k2 + k[2] * k[2];
+    DDc P[3];
+    for (int a = 0; a < d; ++a) {
+      dd sx(0.0f), sy(0.0f);
+      for (int b = 0; b < d; ++b) {
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        const int ab = (d == 3) ? (lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)) : (lo + hi);
+        const DDc pv = ddc(prod[ab * g.nspec + idx]);
+        sx = sx + pv.x * k[b];
+        sy = sy + pv.y * k[b];
+      }
+      double2 fv = f[a * g.nspec + idx];
+      if (idx == 0) fv.x += fb.f[a];
+      const DDc fa = ddc(fv);
+      P[a] = {fa.x * inv_rho + sy, fa.y * inv_rho - sx};  // f/rho - i s
+    }
+    dd kPx(0.0f), kPy(0.0f);
+    for (int a = 0; a < d; ++a) { kPx = kPx + P[a].x * k[a]; kPy = kPy + P[a].y * k[a]; }
+    const dd ik2 = (k2.hi > 0.0f) ? dd_rcp(k2) : dd(1.0f);
+    const dd lam = mu_dt_over_rho * k2;
+    const dd den = dd_rcp(dd(1.0f) + dd(0.5f) * lam);
+    const dd cx = kPx * ik2, cy = kPy * ik2;
+    const dd hdt = dd(0.5f) * dt, keep = dd(1.0f) - dd(0.5f) * lam;
+    for (int a = 0; a < d; ++a) {
+      double2 v = make_double2(0.0, 0.0);
+      if (ok) {
+        const dd qx = P[a].x - k[a] * cx, qy = P[a].y - k[a] * cy;
+        const DDc bv = ddc(base[a * g.nspec + idx]);
+        dd vx, vy;
+        if (half) { vx = (qx * hdt + bv.x) * den; vy = (qy * hdt + bv.y) * den; }
+        else { vx = (qx * dt + bv.x * keep) * den; vy = (qy * dt + bv.y * keep) * den; }
+        v = make_double2(join_dd(vx), join_dd(vy));
+      }
+      out[a * g.nspec + idx] = v;
+    }
+  }
+}
+
 // out_a = i k_b in_a on the half spectrum (the unpaired mode -N/2 set to zero)
 template <typename T>
 __global__ void k_mul_ik(SpecGeom g, int b, const C<T>* __restrict__ in, C<T>* __restrict__ out) {
@@ -178,6 +273,13 @@ void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C
                       C<T>* out, bool half, cudaStream_t st) {
   const SpecGeom g = sgeom(p);
   const Body fb = {{p.fbody[0], p.fbody[1], p.fbody[2]}};
+  if constexpr (std::is_same<T, double>::value) {
+    if (!p.native_fp64) {
+      k_ns_update_dd<<<grid_for(g.nspec), 256, 0, st>>>(g, dd(g.kunit), dd(1.0 / p.rho), dd(p.mu * p.dt / p.rho),
+                                                         dd(p.dt), half, fb, prod, fhat, ubase, out);
+      return;
+    }
+  }
   k_ns_update<T><<<grid_for(g.nspec), 256, 0, st>>>(g, (T)(1.0 / p.rho), (T)(p.mu * p.dt / p.rho),
                                                      (T)p.dt, half, fb, prod, fhat, ubase, out);
 }
