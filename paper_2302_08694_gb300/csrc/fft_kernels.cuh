@@ -402,13 +402,13 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
       const int kind = e & 15, sa = (e >> 4) & 15, sb = (e >> 8) & 15, x = (e >> 12) & 15, ab = e >> 16;
       C<T>* X = S + x * SL;
       C<T> v[M];
+      // One forward transform serves both directions (the inverse is conj(F(conj(x)))), so
+      // the loop holds a single copy of the transform code.
       if (kind == 0) {
         const C<T>* base = in + ((long long)sa * nrows + 2 * pr) * h;
         wfft_load_packed<T, N>(v, base, base + h, l, h, valid);
-        wfft<T, true, N>(v, X, l, tw);
 #pragma unroll
-        for (int i = 0; i < M; ++i) S[sb * SL + wfft_out_index<N>(l, i)] = v[i];
-        __syncwarp();
+        for (int i = 0; i < M; ++i) v[i] = cconj<T>(v[i]);
       } else {
         // the real part holds row 2p, the imaginary part row 2p+1
 #pragma unroll
@@ -417,7 +417,13 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
           v[i] = mk<T>(ua.x * ub.x, ua.y * ub.y);
         }
         __syncwarp();  // the exchange slot may hold a factor
-        wfft<T, false, N>(v, X, l, tw);
+      }
+      wfft<T, false, N>(v, X, l, tw);
+      if (kind == 0) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) S[sb * SL + wfft_out_index<N>(l, i)] = cconj<T>(v[i]);
+        __syncwarp();
+      } else {
         C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
         wfft_untangle<T, N>(v, X, l, valid, h, ob, ob + h);
       }
