@@ -17,7 +17,7 @@ constexpr int kMaxW = 16;
 
 struct PointGeom {
   int d, M, nf, w;
-  double L;
+  double L, invL, scale;  // scale = nf / L (reciprocals: FP64 division is slow on this GPU)
   int b[3], nb[3];
   int slice;  // candidates per slice of a 3D gather box
 };
@@ -25,17 +25,18 @@ struct PointGeom {
 static PointGeom geom(const Plan& p) {
   PointGeom g;
   g.d = p.d; g.M = p.M; g.nf = p.nf; g.w = p.w; g.L = p.L;
+  g.invL = 1.0 / p.L; g.scale = (double)p.nf / p.L;
   for (int a = 0; a < 3; ++a) { g.b[a] = p.bins[a]; g.nb[a] = p.nbin[a]; }
   g.slice = p.slice;
   return g;
 }
 
 // Fine-grid coordinate t in [0, nf) of a coordinate x (periodic wrap of the unwrapped position).
-__device__ __forceinline__ double grid_coord(double x, double L, int nf) {
-  double xm = x - L * floor(x / L);
-  double t = xm * (double)nf / L;
-  if (t >= (double)nf) t -= (double)nf;
-  if (!(t >= 0.0 && t < (double)nf)) t = 0.0;  // also maps a non-finite position to a valid cell
+__device__ __forceinline__ double grid_coord(double x, const PointGeom& g) {
+  const double xm = fma(-g.L, floor(x * g.invL), x);
+  double t = xm * g.scale;
+  if (t >= (double)g.nf) t -= (double)g.nf;
+  if (!(t >= 0.0 && t < (double)g.nf)) t = 0.0;  // rounding just below 0, or a non-finite position
   return t;
 }
 
@@ -62,7 +63,7 @@ __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __re
     if (ok) {
       long long b = 0, mul = 1;
       for (int a = 0; a < g.d; ++a) {
-        const double t = grid_coord(X[(long long)a * g.M + j], g.L, g.nf);
+        const double t = grid_coord(X[(long long)a * g.M + j], g);
         const int B = bin_of_start(window_start(t, g.w), g.nf, g.b[a], g.nb[a]);
         b += B * mul;
         mul *= g.nb[a];
@@ -219,7 +220,7 @@ __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const i
     const int s = offsets[bin_of[j]] + rank[j];
     perm[s] = j;
     for (int a = 0; a < g.d; ++a) {
-      const double t = grid_coord(X[(long long)a * g.M + j], g.L, g.nf);
+      const double t = grid_coord(X[(long long)a * g.M + j], g);
       const int c0 = window_start(t, g.w);
       i0[(long long)a * g.M + s] = c0;
       delta[(long long)a * g.M + s] = (T)((double)c0 - t);  // in [-w/2, -w/2 + 1)
