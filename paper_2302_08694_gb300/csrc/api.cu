@@ -526,7 +526,7 @@ static void do_bin(fsib_plan* h, const double* X, cudaStream_t st, const double*
   const double rs = (p.prec == FSIB_FP64) ? 8.0 : 4.0;
   {
     Prof pr(h, "sort", 2.0 * p.d * p.M * 8.0 + 4.0 * p.M * 8.0 + p.d * p.M * (4.0 + rs) + 12.0 * p.nbins, 0.0, st);
-    launch_bin_points(p, h->ws, X, st);
+    launch_bin_points(p, h->ws, X, st, !uses_prep(p));  // the gather needs no occupied-bin list
   }
   if (!uses_prep(p)) return;
   const double ts = (p.prec == FSIB_FP64) ? 8.0 : 4.0;

@@ -182,7 +182,8 @@ template <typename T>
 void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int Nk,
                          const FftLen& fl, const C<T>* tw, cudaStream_t st);
 
-void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st);
+// occupied: also list the occupied bins (needed by the scatter spread, launch_spread)
+void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied = true);
 template <typename T>
 void launch_spread(const Plan& p, Workspace& ws, const double* cw, const double* omega,
                    T* grid, cudaStream_t st);

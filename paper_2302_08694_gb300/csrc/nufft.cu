@@ -155,32 +155,41 @@ __device__ __forceinline__ void block_prefix(int (&v)[NV], int (&tot)[NV], int (
 }
 
 // Bin offsets (exclusive scan of the counts, total at [nbins]) and the list of occupied bins.
+// OCC: also list the occupied bins (the scatter spread walks them; the gather does not).
+template <bool OCC>
 __global__ void __launch_bounds__(kScanThreads)
 k_bin_scan(const int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
            int* __restrict__ occ, int* __restrict__ nocc) {
-  __shared__ int wsum[2][32];
+  constexpr int NV = OCC ? 2 : 1;
+  __shared__ int wsum[NV][32];
   int carry = 0, carry_o = 0;
   for (long long base = 0; base < nbins; base += (long long)kScanThreads * kScanPer) {
     const long long i0 = base + (long long)threadIdx.x * kScanPer;
     int c[kScanPer];
     scan_load(counts, i0, nbins, c);
-    int v[2] = {0, 0}, tot[2];
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) { v[0] += c[k]; v[1] += (c[k] > 0); }
-    block_prefix<2>(v, tot, wsum);
-    int run = carry + v[0], runo = carry_o + v[1];
+    int v[NV], tot[NV];
+    v[0] = 0;
+    if constexpr (OCC) v[1] = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      if (c[k] > 0) occ[runo++] = (int)(i0 + k);
+      v[0] += c[k];
+      if constexpr (OCC) v[1] += (c[k] > 0);
+    }
+    block_prefix<NV>(v, tot, wsum);
+    int run = carry + v[0], runo = 0;
+    if constexpr (OCC) runo = carry_o + v[1];
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      if constexpr (OCC) { if (c[k] > 0) occ[runo++] = (int)(i0 + k); }
       const int t = c[k];
       c[k] = run;
       run += t;
     }
     scan_store(offsets, i0, nbins, c);
     carry += tot[0];
-    carry_o += tot[1];
+    if constexpr (OCC) carry_o += tot[1];
   }
-  if (threadIdx.x == 0) { offsets[nbins] = carry; *nocc = carry_o; }
+  if (threadIdx.x == 0) { offsets[nbins] = carry; if (OCC) *nocc = carry_o; }
 }
 
 // Exclusive scans of two int arrays of length n, one per block (blockIdx.x = 0: a, 1: b);
@@ -228,12 +237,13 @@ __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const i
   }
 }
 
-void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st) {
+void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied) {
   const PointGeom g = geom(p);
   cudaMemsetAsync(ws.counts, 0, sizeof(int) * (size_t)p.nbins, st);
   const int nb = (p.M + 255) / 256;
   k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts);
-  k_bin_scan<<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc);
+  if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc);
+  else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc);
   if (p.prec == FSIB_FP64)
     k_bin_scatter<double><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
                                               (double*)ws.delta);
