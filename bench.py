@@ -201,8 +201,8 @@ def run_reference(args):
 # (k_box_slices, k_scan2, k_slice_boxes, k_spread_box3[_dd]), from one ncu capture of
 # the current kernels per workload; profiles/spread_site_traffic.txt has the command and the
 # per-kernel figures. Set an entry to None when those kernels change.
-SITE_TRAFFIC = {("ns3d_N64_M10082_fp64", "spread"): 9968640.0,
-                ("ns3d_N128_M40322_mixed", "spread"): 163269120.0}
+SITE_TRAFFIC = {("ns3d_N64_M10082_fp64", "spread"): 10024448.0,
+                ("ns3d_N128_M40322_mixed", "spread"): 163444224.0}
 
 
 def _events(torch):
