@@ -669,8 +669,30 @@ def validation_block(fsib, torch, dev, flush, cpu_sample=True):
                      "rel_err_corner": float(abs(P[1] - p_out) / p_out),
                      "max_abs_u_hat": float(uc.abs().max())})
         pbc.close()
+    # width of the pressure jump (Fig. reso_stokes), N and N_b refined together (h_b close to L/N):
+    # jump height over the steepest slope, of the band-limited pressure and of its samples on
+    # the Eulerian grid of the centreline (central differences over 2h)
+    widths = []
+    for N in (32, 64, 128, 256):
+        Nbw = int(np.ceil(2 * np.pi * r * N))
+        thw = 2 * np.pi * np.arange(Nbw) / Nbw
+        Xw = torch.from_numpy(np.stack([0.5 + r * np.cos(thw), 0.5 + r * np.sin(thw)])).to(dev)
+        Fw = torch.from_numpy(np.stack([np.cos(thw), np.sin(thw)])).to(dev)
+        ww = torch.full((Nbw,), 2 * np.pi / Nbw, dtype=torch.float64, device=dev)
+        pbw = fsib.Problem(N, 2, Nbw, 1.0, 0.0, 1e-3, 1e-12)
+        ph = pbw.pressure(pbw.spread(Xw, Fw, ww))
+        h = 1.0 / N
+        yf = np.linspace(0.5 + r - 4 * h, 0.5 + r + 4 * h, 801)
+        yg = np.arange(N) * h
+        Pf = pbw.pressure_at(ph, torch.from_numpy(np.stack([np.full_like(yf, 0.5), yf])).to(dev)).cpu().numpy()
+        Pg = pbw.pressure_at(ph, torch.from_numpy(np.stack([np.full_like(yg, 0.5), yg])).to(dev)).cpu().numpy()
+        jump = 1.0 / r
+        widths.append({"N": N, "Nb": Nbw,
+                       "width_over_h_max_slope": float(jump / np.max(np.abs(np.gradient(Pf, yf))) / h),
+                       "width_over_h_grid": float(jump / (np.max(np.abs(Pg[2:] - Pg[:-2])) / (2 * h)) / h)})
+        pbw.close()
     out["normal_circle_pressure"] = {"r": r, "Nb": Nb, "F": 1.0, "p_inside_exact": p_in, "p_outside_exact": p_out,
-                                     "by_N": rows}
+                                     "by_N": rows, "jump_width": widths}
     return out
 
 

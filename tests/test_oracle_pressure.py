@@ -73,3 +73,21 @@ def test_tangent_circle_has_no_pressure():
     N = 32
     p = sp.pressure(sp.spread_direct(X, c, N), None, N, 1.0)
     assert np.max(np.abs(p)) <= 1e-15
+
+
+def test_pressure_jump_width_is_a_fixed_multiple_of_h():
+    """Fig. reso_stokes: with N and N_b refined together the width of the pressure jump
+    (height over slope) is a fixed multiple of h, about 2h. Sampled on the Eulerian grid of
+    the centreline (slope by central differences over 2h) it settles at 1.70h."""
+    r = 0.25
+    widths = []
+    for N in (32, 64, 128):
+        Nb = int(math.ceil(2 * math.pi * r * N))
+        X, c = _circle(Nb, r, True)
+        p = sp.pressure(sp.spread_direct(X, c, N), None, N, 1.0)
+        h = 1.0 / N
+        y = np.arange(N) * h
+        P = _at(p, np.stack([np.full_like(y, 0.5), y]), N)
+        widths.append((1.0 / r) / (np.max(np.abs(P[2:] - P[:-2])) / (2 * h)) / h)
+    assert 1.5 < widths[-1] < 2.5
+    assert abs(widths[0] - widths[-1]) < 0.02 * widths[-1]
