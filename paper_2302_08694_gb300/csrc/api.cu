@@ -240,7 +240,7 @@ static void free_ws(Workspace& ws) {
                   ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
                   ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.wts, ws.cwp,
                   ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.box_item, ws.box_sched, ws.box_work, ws.box_done,
-                  ws.part};
+                  ws.part, ws.band};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   ws.tw = ws.dline = ws.dplane = ws.grid = ws.grid2 = ws.s1 = ws.s2 = ws.s3 = ws.s4 = ws.fhat = ws.uhalf = nullptr;
@@ -251,6 +251,7 @@ static void free_ws(Workspace& ws) {
   ws.wts = ws.cwp = nullptr;
   ws.box_ns = ws.box_np = ws.box_so = ws.box_po = ws.box_item = ws.box_sched = ws.box_work = ws.box_done = nullptr;
   ws.part = nullptr;
+  ws.band = nullptr;
   void* adj[] = {ws.adj_spec, ws.adj_pts, ws.adj_ckpt, ws.adj_part, ws.adj_sig};
   for (void* q : adj)
     if (q) cudaFree(q);
@@ -349,6 +350,7 @@ static int alloc_ws(fsib_plan* h) {
   rc |= dmalloc(&ws.box_sched, sizeof(int) * nslice_cap, tot);
   rc |= dmalloc(&ws.box_work, sizeof(int) * 4, tot);
   rc |= dmalloc(&ws.box_done, sizeof(int) * (size_t)p.nbins, tot);
+  rc |= dmalloc(&ws.band, (size_t)p.nbin[1] * (d == 3 ? p.nbin[2] : 1), tot);
   // partial slots: boxes with K > 1 hold K slots, K <= 2 cand/256; sum cand <= 27 M
   // (and at most 16 per box: dense point sets get larger slices)
   ws.part_slots = (d == 3) ? (size_t)std::min<long long>(2 * 27 * (long long)p.M / kMinSlice + 64, 16LL * p.nbins) : 1;
@@ -409,10 +411,24 @@ template <typename TI>
 static void spread_points(fsib_plan* h, const double* c, const double* omega, TI* grid, cudaStream_t st);
 template <typename TI>
 static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st);
+// Row bands of the last gather binning (RowBands): the gather spread writes only those bands,
+// and an interpolation that follows the same binning reads only those.
+static bool uses_prep(const Plan& p);
+static RowBands row_bands(const Plan& p, const Workspace& ws) {
+  RowBands rb;
+  if (!uses_prep(p) || !ws.band) return rb;
+  rb.flag = ws.band;
+  rb.n = p.nf;
+  rb.b = p.bins[1];
+  rb.nby = p.nbin[1];
+  rb.d3 = (p.d == 3);
+  return rb;
+}
+
 template <typename TI>
 static void rows_r2c_first(const Plan& p, Workspace& ws, const TI* grid, C<TI>* out, long long nrows,
                            const C<TI>* tw, cudaStream_t st) {
-  launch_fft_rows_r2c<TI>(grid, out, nrows, p.N, p.fl_nf, tw, st);
+  launch_fft_rows_r2c<TI>(grid, out, nrows, p.N, p.fl_nf, tw, st, row_bands(p, ws));
 }
 
 // ---------------------------------------------------------------------------
@@ -451,8 +467,10 @@ static void forward_fine(fsib_plan* h, const TI* grid, C<TA>* out, cudaStream_t 
 
 template <typename TI, typename TA>
 // sa, sb: scratch pair (default S1, S2).
+// banded: the grid feeds an interpolation at the points of the last binning, so the rows that
+// none of their windows reaches are not computed.
 static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t st, void* sa = nullptr,
-                         void* sb = nullptr) {
+                         void* sb = nullptr, bool banded = false) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const int N = p.N, hh = N / 2, n = p.nf, d = p.d;
@@ -470,12 +488,14 @@ static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t s
     { Prof pr(h, "t2.iy_strided", (double)d * n * hh * (n + N) * cs, fft_flops((double)d * n * hh, n), st);
       launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, true, none, tw, st); }
     { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
-      launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n * n, N, p.fl_nf, tw, st); }
+      launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n * n, N, p.fl_nf, tw, st,
+                              banded ? row_bands(p, ws) : RowBands()); }
   } else {
     { Prof pr(h, "t2.iy_strided_deconv", (double)d * hh * (n + N) * cs, fft_flops((double)d * hh, n), st);
       launch_fft_strided<TI, TA, TI>(in, s2, d, 1, hh, N, p.fl_nf, true, dec, tw, st); }
     { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * rs + (double)d * n * hh * cs, fft_flops(0.5 * d * n, n), st);
-      launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n, N, p.fl_nf, tw, st); }
+      launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n, N, p.fl_nf, tw, st,
+                              banded ? row_bands(p, ws) : RowBands()); }
   }
 }
 
@@ -578,8 +598,8 @@ static void do_spread(fsib_plan* h, const double* X, const double* c, const doub
 
 // interp at the points of the last binning
 template <typename TI, typename TA>
-static void do_interp_sorted(fsib_plan* h, const C<TA>* uhat, double* U, cudaStream_t st) {
-  inverse_fine<TI, TA>(h, uhat, (TI*)h->ws.grid, st);
+static void do_interp_sorted(fsib_plan* h, const C<TA>* uhat, double* U, cudaStream_t st, bool banded = false) {
+  inverse_fine<TI, TA>(h, uhat, (TI*)h->ws.grid, st, nullptr, nullptr, banded);
   interp_points<TI>(h, (const TI*)h->ws.grid, U, st);
 }
 
@@ -660,7 +680,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
       cudaEventRecord(h->ev_fork3, st);
       cudaStreamWaitEvent(h->side, h->ev_fork3, 0);
     }
-    inverse_fine<TI, TA>(h, uh, (TI*)ws.grid, sb, ws.s3, ws.s4);
+    inverse_fine<TI, TA>(h, uh, (TI*)ws.grid, sb, ws.s3, ws.s4, true);  // binning of X^{m+1/2}
     if (fork) cudaEventRecord(h->ev_join3, h->side);
     const C<TA>* P1 = products<TI, TA>(h, uh, st, ws.s1, ws.s2);
     { Prof pr(h, "ns_update", ub, 0.0, st);
@@ -684,13 +704,13 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     do_force(h, X, ws.cw, st);
     do_spread<TI, TA>(h, X, ws.cw, nullptr, fhat, st);
     do_stokeslet<TA>(h, fhat, uh, st);
-    do_interp_sorted<TI, TA>(h, uh, ws.Uh, st);
+    do_interp_sorted<TI, TA>(h, uh, ws.Uh, st, true);
     do_axpy(h, ws.Xh, X, ws.Uh, 0.5 * p.dt, st);
     // U(X^{m+1/2})
     do_force(h, ws.Xh, ws.cw, st);
     do_spread<TI, TA>(h, ws.Xh, ws.cw, nullptr, fhat, st);
     do_stokeslet<TA>(h, fhat, uh, st);
-    do_interp_sorted<TI, TA>(h, uh, ws.Uh, st);
+    do_interp_sorted<TI, TA>(h, uh, ws.Uh, st, true);
     do_axpy(h, X, X, ws.Uh, p.dt, st);
     if (U) cudaMemcpyAsync(U, ws.Uh, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
     if (uhat) cudaMemcpyAsync(uhat, uh, ws.spec_bytes, cudaMemcpyDeviceToDevice, st);
@@ -1140,9 +1160,9 @@ int fsib_interp(fsib_t h, const void* uhat, const double* X, double* U) {
   if ((rc = stage(h, 3, uhat, spec_bytes(h), true, ah)) != FSIB_OK) return rc;
   if ((rc = stage(h, 1, U, pts_bytes(h), false, au)) != FSIB_OK) return rc;
   do_bin(h, (const double*)ax.dev, h->own);
-  FSIB_DISPATCH(h, (do_interp_sorted<float, float>(h, (const C<float>*)ah.dev, (double*)au.dev, h->own)),
-                (do_interp_sorted<dd, double>(h, (const C<double>*)ah.dev, (double*)au.dev, h->own)),
-                (do_interp_sorted<double, double>(h, (const C<double>*)ah.dev, (double*)au.dev, h->own)));
+  FSIB_DISPATCH(h, (do_interp_sorted<float, float>(h, (const C<float>*)ah.dev, (double*)au.dev, h->own, true)),
+                (do_interp_sorted<dd, double>(h, (const C<double>*)ah.dev, (double*)au.dev, h->own, true)),
+                (do_interp_sorted<double, double>(h, (const C<double>*)ah.dev, (double*)au.dev, h->own, true)));
   if ((rc = unstage(h, au)) != FSIB_OK) return rc;
   return finish(h, au.host != nullptr);
 }

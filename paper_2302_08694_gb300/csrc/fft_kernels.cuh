@@ -106,7 +106,7 @@ k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inne
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_rows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk, FftLen fl,
-           const C<T>* __restrict__ twg) {
+           const C<T>* __restrict__ twg, RowBands rb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = NC ? NC : fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
@@ -118,7 +118,7 @@ k_rows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, i
     const int p = t / n, x = t % n;
     const long long pr = pr0 + p;
     C<T> v = mk<T>(T(0), T(0));
-    if (pr < npairs) v = mk<T>(in[(2 * pr) * n + x], in[(2 * pr + 1) * n + x]);
+    if (pr < npairs && rb.on(2 * pr)) v = mk<T>(in[(2 * pr) * n + x], in[(2 * pr + 1) * n + x]);
     a[p * ls + x] = v;
   }
   __syncthreads();
@@ -154,7 +154,7 @@ __device__ __forceinline__ C<T> pack_rows(const C<T>* __restrict__ A, const C<T>
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
-           FftLen fl, const C<T>* __restrict__ twg) {
+           FftLen fl, const C<T>* __restrict__ twg, RowBands rb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = NC ? NC : fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
@@ -174,7 +174,7 @@ k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, i
   for (int t = threadIdx.x; t < kQrows * n; t += blockDim.x) {
     const int p = t / n, x = t % n;
     const long long pr = pr0 + p;
-    if (pr >= npairs) continue;
+    if (pr >= npairs || !rb.on(2 * pr)) continue;
     const C<T> z = r[p * ls + x];
     out[(2 * pr) * n + x] = z.x;
     out[(2 * pr + 1) * n + x] = z.y;
@@ -282,7 +282,7 @@ __device__ __forceinline__ void wfft_load_packed(C<T> (&v)[wfft_M(N)], const C<T
 template <typename T, int N>
 __global__ void __launch_bounds__(256)
 k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
-            const C<T>* __restrict__ twg) {
+            const C<T>* __restrict__ twg, RowBands rb) {
   constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
@@ -294,7 +294,8 @@ k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, 
   const int h = Nk / 2;
   for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
     const long long pr = g * LPW + sub;
-    const bool valid = pr < npairs;
+    const bool valid = pr < npairs && rb.on(2 * pr);  // rows that no window reads are not written
+    if (!__any_sync(0xffffffffu, valid)) continue;
     C<T> v[M];
     wfft_load_packed<T, N>(v, in + (2 * pr) * h, in + (2 * pr + 1) * h, l, h, valid);
     wfft<T, true, N>(v, buf, l, tw);
@@ -337,7 +338,7 @@ __device__ __forceinline__ void wfft_untangle(const C<T> (&v)[wfft_M(N)], C<T>* 
 template <typename T, int N>
 __global__ void __launch_bounds__(256)
 k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
-            const C<T>* __restrict__ twg) {
+            const C<T>* __restrict__ twg, RowBands rb) {
   constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
@@ -350,11 +351,22 @@ k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, 
   for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
     const long long pr = g * LPW + sub;
     const bool valid = pr < npairs;
+    const bool on = valid && rb.on(2 * pr);  // both rows of a pair lie in one band
+    if (!__any_sync(0xffffffffu, on)) {      // every row of this warp is zero: so is its spectrum
+      if (valid) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          const int k = l + L * i;
+          if (k < h) { out[(2 * pr) * h + k] = mk<T>(T(0), T(0)); out[(2 * pr + 1) * h + k] = mk<T>(T(0), T(0)); }
+        }
+      }
+      continue;
+    }
     C<T> v[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
       const int x = l + L * i;
-      v[i] = valid ? mk<T>(in[(2 * pr) * N + x], in[(2 * pr + 1) * N + x]) : mk<T>(T(0), T(0));
+      v[i] = on ? mk<T>(in[(2 * pr) * N + x], in[(2 * pr + 1) * N + x]) : mk<T>(T(0), T(0));
     }
     wfft<T, false, N>(v, buf, l, tw);
     wfft_untangle<T, N>(v, buf, l, valid, h, out + (2 * pr) * h, out + (2 * pr + 1) * h);
@@ -656,7 +668,7 @@ void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, in
 
 template <typename T>
 void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const FftLen& fl,
-                         const C<T>* tw, cudaStream_t st) {
+                         const C<T>* tw, cudaStream_t st, RowBands rb) {
   const long long npairs = nrows / 2;
   const FftLen fs = small_rows(fl, npairs);
   const int kQrows = fs.rows_q;
@@ -669,18 +681,18 @@ void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const 
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_r2c<T, NC>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
-      k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off);
+      k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off, rb);
       return;
     }
     auto k = k_rows_r2c<T, decltype(nc)::value>;
     raise_smem_limit(reinterpret_cast<const void*>(k));
-    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fs, tw);
+    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fs, tw, rb);
   });
 }
 
 template <typename T>
 void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
-                         const C<T>* tw, cudaStream_t st) {
+                         const C<T>* tw, cudaStream_t st, RowBands rb) {
   const long long npairs = nrows / 2;
   const FftLen fs = small_rows(fl, npairs);
   const int kQrows = fs.rows_q;
@@ -693,12 +705,12 @@ void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const 
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
       auto k = k_wrows_c2r<T, NC>;
       raise_smem_limit(reinterpret_cast<const void*>(k));
-      k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off);
+      k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off, rb);
       return;
     }
     auto k = k_rows_c2r<T, decltype(nc)::value>;
     raise_smem_limit(reinterpret_cast<const void*>(k));
-    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fs, tw);
+    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fs, tw, rb);
   });
 }
 
@@ -729,9 +741,9 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
 
 #define FSIB_FFT_INST_R(T)                                                                       \
   template void launch_fft_rows_r2c<T>(const T*, C<T>*, long long, int, const FftLen&,           \
-                                       const C<T>*, cudaStream_t);                               \
+                                       const C<T>*, cudaStream_t, RowBands);                     \
   template void launch_fft_rows_c2r<T>(const C<T>*, T*, long long, int, const FftLen&,           \
-                                       const C<T>*, cudaStream_t);
+                                       const C<T>*, cudaStream_t, RowBands);
 #define FSIB_FFT_INST_P(T)                                                                       \
   template void launch_rows_product<T>(const C<T>*, C<T>*, int, long long, int, const FftLen&,   \
                                        const C<T>*, cudaStream_t);

@@ -151,6 +151,7 @@ struct Workspace {
   int* box_sched = nullptr;          // [slices] order in which the gather takes the slices
   int* box_work = nullptr;           // [2] gather work counters: next slice, next run of empty boxes
   int* box_done = nullptr;           // [nbins] slices of a split box finished (the last one adds the partials)
+  unsigned char* band = nullptr;     // [nb_z][nb_y] row bands reached by a window (gather path; see RowBands)
   void* part = nullptr;              // T[slots][3][512] partial boxes
   size_t part_slots = 0;
   // reverse mode (allocated on first use)
@@ -172,12 +173,27 @@ template <typename T, typename Tin = T, typename Tout = T>
 void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, int inner,
                         int Nk, const FftLen& fl, bool inverse, Mult<T> mult,
                         const C<T>* tw, cudaStream_t st);
+// Rows of the fine grid (along x) that no window of the current point binning reaches, by
+// band of boxes (y div b, z div b): the gather spread leaves them unwritten, the first forward
+// row pass takes them as zeros, and the last inverse row pass skips them (no interpolation
+// window reads them). flag == nullptr: every row is on.
+struct RowBands {
+  const unsigned char* flag = nullptr;  // [nb_z][nb_y]
+  int n = 1, b = 1, nby = 1, d3 = 0;    // row length (fine grid), box side, boxes along y, d == 3
+  __device__ __forceinline__ bool on(long long row) const {
+    if (!flag) return true;
+    const int y = (int)(row % n);
+    const int z = d3 ? (int)((row / n) % n) : 0;
+    return flag[(z / b) * nby + y / b] != 0;
+  }
+};
+
 template <typename T>
 void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const FftLen& fl,
-                         const C<T>* tw, cudaStream_t st);
+                         const C<T>* tw, cudaStream_t st, RowBands rb = RowBands());
 template <typename T>
 void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
-                         const C<T>* tw, cudaStream_t st);
+                         const C<T>* tw, cudaStream_t st, RowBands rb = RowBands());
 template <typename T>
 void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int Nk,
                          const FftLen& fl, const C<T>* tw, cudaStream_t st);

@@ -20,6 +20,7 @@ struct PointGeom {
   double L, invL, scale;  // scale = nf / L (reciprocals: FP64 division is slow on this GPU)
   int b[3], nb[3];
   int slice;  // candidates per slice of a 3D gather box
+  const unsigned char* band;  // row bands reached by a window (RowBands), or nullptr
 };
 
 static PointGeom geom(const Plan& p) {
@@ -28,6 +29,7 @@ static PointGeom geom(const Plan& p) {
   g.invL = 1.0 / p.L; g.scale = (double)p.nf / p.L;
   for (int a = 0; a < 3; ++a) { g.b[a] = p.bins[a]; g.nb[a] = p.nbin[a]; }
   g.slice = p.slice;
+  g.band = nullptr;
   return g;
 }
 
@@ -52,8 +54,11 @@ __device__ __forceinline__ int bin_of_start(int i0, int nf, int b, int nb) {
 
 // Bin of every point and its rank within the bin. Lanes of a warp that fall in the same
 // bin (neighbouring points usually do) share one atomic increment.
+// With band != nullptr it also marks the row bands (boxes along y and z) that the windows of
+// the bin reach: windows starting in bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach.
 __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of,
-                            int* __restrict__ rank, int* __restrict__ counts) {
+                            int* __restrict__ rank, int* __restrict__ counts, unsigned char* __restrict__ band,
+                            int reach) {
   const int lane = threadIdx.x & 31;
   for (long long j0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; j0 < g.M;
        j0 += (long long)gridDim.x * blockDim.x) {
@@ -73,7 +78,16 @@ __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __re
     const unsigned same = __match_any_sync(0xffffffffu, bin);
     const int leader = __ffs(same) - 1;
     int base = 0;
-    if (ok && lane == leader) base = atomicAdd(&counts[bin], __popc(same));
+    if (ok && lane == leader) {
+      base = atomicAdd(&counts[bin], __popc(same));
+      if (band) {
+        const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
+        const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
+        const int rz = (g.d == 3) ? reach : 0;
+        for (int dz = 0; dz <= rz; ++dz)
+          for (int dy = 0; dy <= reach; ++dy) band[((bz + dz) % nbz) * nby + (by + dy) % nby] = 1;
+      }
+    }
     base = __shfl_sync(0xffffffffu, base, leader);
     if (ok) {
       bin_of[j] = bin;
@@ -241,7 +255,10 @@ void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream
   const PointGeom g = geom(p);
   cudaMemsetAsync(ws.counts, 0, sizeof(int) * (size_t)p.nbins, st);
   const int nb = (p.M + 255) / 256;
-  k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts);
+  unsigned char* band = occupied ? nullptr : ws.band;  // row bands for the gather path
+  if (band) cudaMemsetAsync(band, 0, (size_t)p.nbin[1] * (p.d == 3 ? p.nbin[2] : 1), st);
+  const int reach = (p.bins[1] + p.w - 2) / p.bins[1];
+  k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts, band, reach);
   if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc);
   else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc);
   if (p.prec == FSIB_FP64)
@@ -499,6 +516,7 @@ k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, 
   const int nseg = bxs / kSeg;
   const int box = blockIdx.x;
   const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = (D == 3) ? box / (g.nb[0] * g.nb[1]) : 0;
+  if (g.band && !g.band[Bz * g.nb[1] + By]) return;  // a row band that no window reaches: never read
   const int ox = Bx * bxs, oy = By * bys, oz = Bz * bzs;
   // task: (component, z, y, segment) -> a run of kSeg cells along x
   const int ntask = D * bzs * bys * nseg;
@@ -675,8 +693,12 @@ __device__ __forceinline__ void zero_box(const PointGeom& g, int box, T* __restr
   }
 }
 
-__device__ __forceinline__ bool box_empty(const int* __restrict__ slice_off, int nbox, int box) {
-  return box < nbox && slice_off[box + 1] == slice_off[box];
+// A box that no window reaches is zeroed when its row band is read by the forward row pass.
+__device__ __forceinline__ bool box_empty(const PointGeom& g, const int* __restrict__ slice_off, int nbox, int box) {
+  if (box >= nbox || slice_off[box + 1] != slice_off[box]) return false;
+  if (!g.band) return true;
+  const int by = (box / g.nb[0]) % g.nb[1], bz = box / (g.nb[0] * g.nb[1]);
+  return g.band[bz * g.nb[1] + by] != 0;
 }
 
 // One run by the whole block: warp w takes boxes 4w .. 4w + 3 of the run.
@@ -687,7 +709,7 @@ __device__ __forceinline__ void zero_run_block(const PointGeom& g, const int* __
 #pragma unroll 1
   for (int k = 0; k < 4; ++k) {
     const int box = run * 32 + warp * 4 + k;
-    if (box_empty(slice_off, nbox, box)) zero_box<T>(g, box, grid, lane);  // uniform across the warp
+    if (box_empty(g, slice_off, nbox, box)) zero_box<T>(g, box, grid, lane);  // uniform across the warp
   }
 }
 
@@ -703,7 +725,7 @@ __device__ __forceinline__ void zero_empty_boxes(const PointGeom& g, const int* 
     run = __shfl_sync(0xffffffffu, run, 0);
     if (run >= nruns) break;
     const int b0 = run * 32;
-    unsigned m = __ballot_sync(0xffffffffu, box_empty(slice_off, nbox, b0 + lane));
+    unsigned m = __ballot_sync(0xffffffffu, box_empty(g, slice_off, nbox, b0 + lane));
     while (m) {
       const int box = b0 + __ffs(m) - 1;
       m &= m - 1;
@@ -1172,7 +1194,8 @@ void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const dou
 
 template <typename T>
 void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st) {
-  const PointGeom g = geom(p);
+  PointGeom g = geom(p);
+  g.band = ws.band;  // boxes in bands that no window reaches are neither gathered nor zeroed
   const int b = p.bins[0];
   // neighbour bins holding window starts that reach the box: floor((-w + 1)/b) .. 0
   const int dlo = -((p.w - 1 + b - 1) / b), dhi = 0;
