@@ -54,11 +54,8 @@ __device__ __forceinline__ int bin_of_start(int i0, int nf, int b, int nb) {
 
 // Bin of every point and its rank within the bin. Lanes of a warp that fall in the same
 // bin (neighbouring points usually do) share one atomic increment.
-// With band != nullptr it also marks the row bands (boxes along y and z) that the windows of
-// the bin reach: windows starting in bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach.
 __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of,
-                            int* __restrict__ rank, int* __restrict__ counts, unsigned char* __restrict__ band,
-                            int reach) {
+                            int* __restrict__ rank, int* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
   for (long long j0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; j0 < g.M;
        j0 += (long long)gridDim.x * blockDim.x) {
@@ -78,16 +75,7 @@ __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __re
     const unsigned same = __match_any_sync(0xffffffffu, bin);
     const int leader = __ffs(same) - 1;
     int base = 0;
-    if (ok && lane == leader) {
-      base = atomicAdd(&counts[bin], __popc(same));
-      if (band) {
-        const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
-        const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
-        const int rz = (g.d == 3) ? reach : 0;
-        for (int dz = 0; dz <= rz; ++dz)
-          for (int dy = 0; dy <= reach; ++dy) band[((bz + dz) % nbz) * nby + (by + dy) % nby] = 1;
-      }
-    }
+    if (ok && lane == leader) base = atomicAdd(&counts[bin], __popc(same));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (ok) {
       bin_of[j] = bin;
@@ -170,13 +158,16 @@ __device__ __forceinline__ void block_prefix(int (&v)[NV], int (&tot)[NV], int (
 
 // Bin offsets (exclusive scan of the counts, total at [nbins]) and the list of occupied bins.
 // OCC: also list the occupied bins (the scatter spread walks them; the gather does not).
+// It also clears the row-band flags (nband bytes) that the scatter then marks.
 template <bool OCC>
 __global__ void __launch_bounds__(kScanThreads)
 k_bin_scan(const int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
-           int* __restrict__ occ, int* __restrict__ nocc) {
+           int* __restrict__ occ, int* __restrict__ nocc, unsigned char* __restrict__ band, int nband) {
   constexpr int NV = OCC ? 2 : 1;
   __shared__ int wsum[NV][32];
   int carry = 0, carry_o = 0;
+  if (band)
+    for (int i = threadIdx.x; i < nband; i += blockDim.x) band[i] = 0;
   for (long long base = 0; base < nbins; base += (long long)kScanThreads * kScanPer) {
     const long long i0 = base + (long long)threadIdx.x * kScanPer;
     int c[kScanPer];
@@ -238,9 +229,26 @@ k_scan2(const int* __restrict__ a, const int* __restrict__ b, int n, int* __rest
 template <typename T>
 __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const int* __restrict__ bin_of,
                               const int* __restrict__ rank, const int* __restrict__ offsets,
-                              int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.M; j += gridDim.x * blockDim.x) {
-    const int s = offsets[bin_of[j]] + rank[j];
+                              int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta,
+                              unsigned char* __restrict__ band, int reach) {
+  const int lane = threadIdx.x & 31;
+  for (int j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; j0 < g.M; j0 += gridDim.x * blockDim.x) {
+    const int j = j0 + lane;
+    const int bin = (j < g.M) ? bin_of[j] : -1;
+    if (band) {
+      // row bands (boxes along y and z) that windows of this bin reach: windows starting in
+      // bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach; one lane per bin
+      const unsigned same = __match_any_sync(0xffffffffu, bin);
+      if (bin >= 0 && lane == __ffs(same) - 1) {
+        const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
+        const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
+        const int rz = (g.d == 3) ? reach : 0;
+        for (int dz = 0; dz <= rz; ++dz)
+          for (int dy = 0; dy <= reach; ++dy) band[((bz + dz) % nbz) * nby + (by + dy) % nby] = 1;
+      }
+    }
+    if (j >= g.M) continue;
+    const int s = offsets[bin] + rank[j];
     perm[s] = j;
     for (int a = 0; a < g.d; ++a) {
       const double t = grid_coord(X[(long long)a * g.M + j], g);
@@ -256,17 +264,17 @@ void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream
   cudaMemsetAsync(ws.counts, 0, sizeof(int) * (size_t)p.nbins, st);
   const int nb = (p.M + 255) / 256;
   unsigned char* band = occupied ? nullptr : ws.band;  // row bands for the gather path
-  if (band) cudaMemsetAsync(band, 0, (size_t)p.nbin[1] * (p.d == 3 ? p.nbin[2] : 1), st);
+  const int nband = p.nbin[1] * (p.d == 3 ? p.nbin[2] : 1);
   const int reach = (p.bins[1] + p.w - 2) / p.bins[1];
-  k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts, band, reach);
-  if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc);
-  else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc);
+  k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts);
+  if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, nband);
+  else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, nband);
   if (p.prec == FSIB_FP64)
     k_bin_scatter<double><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
-                                              (double*)ws.delta);
+                                              (double*)ws.delta, band, reach);
   else
     k_bin_scatter<float><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
-                                             (float*)ws.delta);
+                                             (float*)ws.delta, band, reach);
 }
 
 // ---------------------------------------------------------------------------
