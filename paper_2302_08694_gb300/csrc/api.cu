@@ -326,6 +326,7 @@ static int alloc_ws(fsib_plan* h) {
   rc |= dmalloc(&ws.bin_of, sizeof(int) * p.M, tot);
   rc |= dmalloc(&ws.rank, sizeof(int) * p.M, tot);
   rc |= dmalloc(&ws.counts, sizeof(int) * (size_t)p.nbins, tot);
+  if (ws.counts && cudaMemset(ws.counts, 0, sizeof(int) * (size_t)p.nbins) != cudaSuccess) rc |= FSIB_ECUDA;
   rc |= dmalloc(&ws.offsets, sizeof(int) * (size_t)(p.nbins + 1), tot);
   rc |= dmalloc(&ws.occ, sizeof(int) * (size_t)p.nbins, tot);
   rc |= dmalloc(&ws.nocc, sizeof(int), tot);
@@ -1454,8 +1455,9 @@ static int spread_static_impl(const Plan& p, const double* X, const double* F, c
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws.dline, D.data(), D.size() * sizeof(T), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws.dplane, Dp.data(), Dp.size() * sizeof(T), cudaMemcpyHostToDevice, st);
   // The scratch keeps the previous call's contents: zero what must start at zero
-  // (the grid accumulates spread contributions; launch_bin_points clears the bin counts).
+  // (the grid accumulates spread contributions; the bin counts start at zero).
   if (e == cudaSuccess) e = cudaMemsetAsync(ws.grid, 0, ws.grid_bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.counts, 0, sizeof(int) * (size_t)p.nbins, st);  // the binning counts into it
   if (e != cudaSuccess) {
     cudaGetLastError();
     g_static_err = std::string("table upload: ") + cudaGetErrorString(e);

@@ -158,10 +158,11 @@ __device__ __forceinline__ void block_prefix(int (&v)[NV], int (&tot)[NV], int (
 
 // Bin offsets (exclusive scan of the counts, total at [nbins]) and the list of occupied bins.
 // OCC: also list the occupied bins (the scatter spread walks them; the gather does not).
-// It also clears the row-band flags (nband bytes) that the scatter then marks.
+// It also clears the row-band flags (nband bytes) that the scatter then marks, and leaves the
+// counts at zero for the next binning (no memset node in the step graph).
 template <bool OCC>
 __global__ void __launch_bounds__(kScanThreads)
-k_bin_scan(const int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
+k_bin_scan(int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
            int* __restrict__ occ, int* __restrict__ nocc, unsigned char* __restrict__ band, int nband) {
   constexpr int NV = OCC ? 2 : 1;
   __shared__ int wsum[NV][32];
@@ -172,6 +173,12 @@ k_bin_scan(const int* __restrict__ counts, long long nbins, int* __restrict__ of
     const long long i0 = base + (long long)threadIdx.x * kScanPer;
     int c[kScanPer];
     scan_load(counts, i0, nbins, c);
+    {
+      int z[kScanPer];
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) z[k] = 0;
+      scan_store(counts, i0, nbins, z);
+    }
     int v[NV], tot[NV];
     v[0] = 0;
     if constexpr (OCC) v[1] = 0;
@@ -261,7 +268,7 @@ __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const i
 
 void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied) {
   const PointGeom g = geom(p);
-  cudaMemsetAsync(ws.counts, 0, sizeof(int) * (size_t)p.nbins, st);
+  // counts are zero here: the workspace starts zeroed and every scan clears them after use
   const int nb = (p.M + 255) / 256;
   unsigned char* band = occupied ? nullptr : ws.band;  // row bands for the gather path
   const int nband = p.nbin[1] * (p.d == 3 ? p.nbin[2] : 1);
