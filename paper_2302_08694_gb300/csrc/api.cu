@@ -240,7 +240,7 @@ static void free_ws(Workspace& ws) {
                   ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
                   ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.wts, ws.cwp,
                   ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.box_item, ws.box_sched, ws.box_work, ws.box_done,
-                  ws.part, ws.band};
+                  ws.part, ws.band, ws.band_dil};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   ws.tw = ws.dline = ws.dplane = ws.grid = ws.grid2 = ws.s1 = ws.s2 = ws.s3 = ws.s4 = ws.fhat = ws.uhalf = nullptr;
@@ -251,7 +251,7 @@ static void free_ws(Workspace& ws) {
   ws.wts = ws.cwp = nullptr;
   ws.box_ns = ws.box_np = ws.box_so = ws.box_po = ws.box_item = ws.box_sched = ws.box_work = ws.box_done = nullptr;
   ws.part = nullptr;
-  ws.band = nullptr;
+  ws.band = ws.band_dil = nullptr;
   void* adj[] = {ws.adj_spec, ws.adj_pts, ws.adj_ckpt, ws.adj_part, ws.adj_sig};
   for (void* q : adj)
     if (q) cudaFree(q);
@@ -352,6 +352,7 @@ static int alloc_ws(fsib_plan* h) {
   rc |= dmalloc(&ws.box_work, sizeof(int) * 4, tot);
   rc |= dmalloc(&ws.box_done, sizeof(int) * (size_t)p.nbins, tot);
   rc |= dmalloc(&ws.band, (size_t)p.nbin[1] * (d == 3 ? p.nbin[2] : 1), tot);
+  rc |= dmalloc(&ws.band_dil, (size_t)p.nbin[1] * (d == 3 ? p.nbin[2] : 1), tot);
   // partial slots: boxes with K > 1 hold K slots, K <= 2 cand/256; sum cand <= 27 M
   // (and at most 16 per box: dense point sets get larger slices)
   ws.part_slots = (d == 3) ? (size_t)std::min<long long>(2 * 27 * (long long)p.M / kMinSlice + 64, 16LL * p.nbins) : 1;
@@ -411,14 +412,14 @@ static int alloc_ws(fsib_plan* h) {
 template <typename TI>
 static void spread_points(fsib_plan* h, const double* c, const double* omega, TI* grid, cudaStream_t st);
 template <typename TI>
-static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st);
+static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st, bool guarded = false);
 // Row bands of the last gather binning (RowBands): the gather spread writes only those bands,
 // and an interpolation that follows the same binning reads only those.
 static bool uses_prep(const Plan& p);
-static RowBands row_bands(const Plan& p, const Workspace& ws) {
+static RowBands row_bands(const Plan& p, const Workspace& ws, bool dilated = false) {
   RowBands rb;
-  if (!uses_prep(p) || !ws.band) return rb;
-  rb.flag = ws.band;
+  if (!uses_prep(p) || !ws.band || !ws.band_dil) return rb;
+  rb.flag = dilated ? ws.band_dil : ws.band;
   rb.n = p.nf;
   rb.b = p.bins[1];
   rb.nby = p.nbin[1];
@@ -469,9 +470,10 @@ static void forward_fine(fsib_plan* h, const TI* grid, C<TA>* out, cudaStream_t 
 template <typename TI, typename TA>
 // sa, sb: scratch pair (default S1, S2).
 // banded: the grid feeds an interpolation at the points of the last binning, so the rows that
-// none of their windows reaches are not computed.
+// none of their windows reaches are not computed (1: those bands; 2: the widened bands of the
+// last binning that recorded them, for points that have moved by less than a box since).
 static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t st, void* sa = nullptr,
-                         void* sb = nullptr, bool banded = false) {
+                         void* sb = nullptr, int banded = 0) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const int N = p.N, hh = N / 2, n = p.nf, d = p.d;
@@ -490,13 +492,13 @@ static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t s
       launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, true, none, tw, st); }
     { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
       launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n * n, N, p.fl_nf, tw, st,
-                              banded ? row_bands(p, ws) : RowBands()); }
+                              banded ? row_bands(p, ws, banded == 2) : RowBands()); }
   } else {
     { Prof pr(h, "t2.iy_strided_deconv", (double)d * hh * (n + N) * cs, fft_flops((double)d * hh, n), st);
       launch_fft_strided<TI, TA, TI>(in, s2, d, 1, hh, N, p.fl_nf, true, dec, tw, st); }
     { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * rs + (double)d * n * hh * cs, fft_flops(0.5 * d * n, n), st);
       launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n, N, p.fl_nf, tw, st,
-                              banded ? row_bands(p, ws) : RowBands()); }
+                              banded ? row_bands(p, ws, banded == 2) : RowBands()); }
   }
 }
 
@@ -542,12 +544,12 @@ static bool uses_prep(const Plan& p) { return !(p.prec == FSIB_FP64 && p.native_
 // Sort the points into bins; for the gather kernels also evaluate their kernel weights
 // (and, when c is given, their weighted forces) once per sort.
 static void do_bin(fsib_plan* h, const double* X, cudaStream_t st, const double* c = nullptr,
-                   const double* omega = nullptr) {
+                   const double* omega = nullptr, bool dilate = false) {
   const Plan& p = h->p;
   const double rs = (p.prec == FSIB_FP64) ? 8.0 : 4.0;
   {
     Prof pr(h, "sort", 2.0 * p.d * p.M * 8.0 + 4.0 * p.M * 8.0 + p.d * p.M * (4.0 + rs) + 12.0 * p.nbins, 0.0, st);
-    launch_bin_points(p, h->ws, X, st, !uses_prep(p));  // the gather needs no occupied-bin list
+    launch_bin_points(p, h->ws, X, st, !uses_prep(p), dilate);  // the gather needs no occupied-bin list
   }
   if (!uses_prep(p)) return;
   const double ts = (p.prec == FSIB_FP64) ? 8.0 : 4.0;
@@ -578,21 +580,23 @@ void spread_points<double>(fsib_plan* h, const double* c, const double* omega, d
   Prof pr(h, "spread", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
   launch_spread<double>(h->p, h->ws, c, omega, grid, st);
 }
+// guarded: the grid holds only the widened bands of an earlier binning (inverse_fine mode 2);
+// a point whose window leaves them gets NaN, which the non-finite checks report.
 template <typename TI>
-static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st) {
+static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st, bool guarded) {
   Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
-  launch_interp_warp<TI>(h->p, h->ws, grid, U, st);
+  launch_interp_warp<TI>(h->p, h->ws, grid, U, st, guarded ? h->ws.band_dil : nullptr);
 }
 template <>
-void interp_points<double>(fsib_plan* h, const double* grid, double* U, cudaStream_t st) {
+void interp_points<double>(fsib_plan* h, const double* grid, double* U, cudaStream_t st, bool) {
   Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
   launch_interp<double>(h->p, h->ws, grid, U, st);
 }
 
 template <typename TI, typename TA>
 static void do_spread(fsib_plan* h, const double* X, const double* c, const double* omega, C<TA>* fhat,
-                      cudaStream_t st) {
-  do_bin(h, X, st, c, omega);
+                      cudaStream_t st, bool dilate = false) {
+  do_bin(h, X, st, c, omega, dilate);
   spread_points<TI>(h, c, omega, (TI*)h->ws.grid, st);
   forward_fine<TI, TA>(h, (const TI*)h->ws.grid, fhat, st);
 }
@@ -600,7 +604,7 @@ static void do_spread(fsib_plan* h, const double* X, const double* c, const doub
 // interp at the points of the last binning
 template <typename TI, typename TA>
 static void do_interp_sorted(fsib_plan* h, const C<TA>* uhat, double* U, cudaStream_t st, bool banded = false) {
-  inverse_fine<TI, TA>(h, uhat, (TI*)h->ws.grid, st, nullptr, nullptr, banded);
+  inverse_fine<TI, TA>(h, uhat, (TI*)h->ws.grid, st, nullptr, nullptr, banded ? 1 : 0);
   interp_points<TI>(h, (const TI*)h->ws.grid, U, st);
 }
 
@@ -668,7 +672,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     if (fork) cudaEventRecord(h->ev_join, h->side);
     do_axpy(h, ws.Xh, X, U, 0.5 * p.dt, st);                    // Eq. spatial_1
     do_force(h, ws.Xh, ws.cw, st);                               // F^{m+1/2}
-    do_spread<TI, TA>(h, ws.Xh, ws.cw, nullptr, fhat, st);       // type-1 NUFFT
+    do_spread<TI, TA>(h, ws.Xh, ws.cw, nullptr, fhat, st, true); // type-1 NUFFT; widened bands for U^{m+1}
     if (fork) cudaStreamWaitEvent(st, h->ev_join, 0);
     // Eqs. spatial_2, spatial_3. The type-2 prep of u^{m+1/2} needs only the half step: it runs
     // on the second stream (scratch S3/S4, fine grid) beside the second nonlinear term and the
@@ -681,7 +685,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
       cudaEventRecord(h->ev_fork3, st);
       cudaStreamWaitEvent(h->side, h->ev_fork3, 0);
     }
-    inverse_fine<TI, TA>(h, uh, (TI*)ws.grid, sb, ws.s3, ws.s4, true);  // binning of X^{m+1/2}
+    inverse_fine<TI, TA>(h, uh, (TI*)ws.grid, sb, ws.s3, ws.s4, 1);  // binning of X^{m+1/2}
     if (fork) cudaEventRecord(h->ev_join3, h->side);
     const C<TA>* P1 = products<TI, TA>(h, uh, st, ws.s1, ws.s2);
     { Prof pr(h, "ns_update", ub, 0.0, st);
@@ -690,7 +694,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
       cudaEventRecord(h->ev_fork2, st);
       cudaStreamWaitEvent(h->side, h->ev_fork2, 0);
     }
-    inverse_fine<TI, TA>(h, uhat, (TI*)ws.grid2, sb, ws.s3, ws.s4);
+    inverse_fine<TI, TA>(h, uhat, (TI*)ws.grid2, sb, ws.s3, ws.s4, 2);  // widened bands of X^{m+1/2}
     if (fork) {
       cudaEventRecord(h->ev_join2, h->side);
       cudaStreamWaitEvent(st, h->ev_join3, 0);
@@ -699,7 +703,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     do_axpy(h, X, X, ws.Uh, p.dt, st);                           // Eq. spatial_4
     do_bin(h, X, st);
     if (fork) cudaStreamWaitEvent(st, h->ev_join2, 0);
-    interp_points<TI>(h, (const TI*)ws.grid2, U, st);            // U^{m+1} at X^{m+1}
+    interp_points<TI>(h, (const TI*)ws.grid2, U, st, true);      // U^{m+1} at X^{m+1}
   } else {
     // U(X^m)
     do_force(h, X, ws.cw, st);

@@ -152,6 +152,7 @@ struct Workspace {
   int* box_work = nullptr;           // [2] gather work counters: next slice, next run of empty boxes
   int* box_done = nullptr;           // [nbins] slices of a split box finished (the last one adds the partials)
   unsigned char* band = nullptr;     // [nb_z][nb_y] row bands reached by a window (gather path; see RowBands)
+  unsigned char* band_dil = nullptr; // the same, widened by one box each way (kept from the X^{m+1/2} binning)
   void* part = nullptr;              // T[slots][3][512] partial boxes
   size_t part_slots = 0;
   // reverse mode (allocated on first use)
@@ -198,8 +199,10 @@ template <typename T>
 void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int Nk,
                          const FftLen& fl, const C<T>* tw, cudaStream_t st);
 
-// occupied: also list the occupied bins (needed by the scatter spread, launch_spread)
-void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied = true);
+// occupied: also list the occupied bins (needed by the scatter spread, launch_spread). Otherwise
+// the row bands are marked; dilate: also the widened bands (ws.band_dil).
+void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied = true,
+                       bool dilate = false);
 template <typename T>
 void launch_spread(const Plan& p, Workspace& ws, const double* cw, const double* omega,
                    T* grid, cudaStream_t st);
@@ -210,8 +213,10 @@ template <typename T>
 void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const double* omega, cudaStream_t st);
 template <typename T>
 void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st);
+// guard: row bands the grid holds (RowBands flags); a point whose window leaves them gets NaN.
 template <typename T>
-void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st);
+void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st,
+                        const unsigned char* guard = nullptr);
 
 template <typename T>
 void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t st);

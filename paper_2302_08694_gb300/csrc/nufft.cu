@@ -163,12 +163,15 @@ __device__ __forceinline__ void block_prefix(int (&v)[NV], int (&tot)[NV], int (
 template <bool OCC>
 __global__ void __launch_bounds__(kScanThreads)
 k_bin_scan(int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
-           int* __restrict__ occ, int* __restrict__ nocc, unsigned char* __restrict__ band, int nband) {
+           int* __restrict__ occ, int* __restrict__ nocc, unsigned char* __restrict__ band,
+           unsigned char* __restrict__ band_dil, int nband) {
   constexpr int NV = OCC ? 2 : 1;
   __shared__ int wsum[NV][32];
   int carry = 0, carry_o = 0;
   if (band)
     for (int i = threadIdx.x; i < nband; i += blockDim.x) band[i] = 0;
+  if (band_dil)
+    for (int i = threadIdx.x; i < nband; i += blockDim.x) band_dil[i] = 0;
   for (long long base = 0; base < nbins; base += (long long)kScanThreads * kScanPer) {
     const long long i0 = base + (long long)threadIdx.x * kScanPer;
     int c[kScanPer];
@@ -237,7 +240,7 @@ template <typename T>
 __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const int* __restrict__ bin_of,
                               const int* __restrict__ rank, const int* __restrict__ offsets,
                               int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta,
-                              unsigned char* __restrict__ band, int reach) {
+                              unsigned char* __restrict__ band, unsigned char* __restrict__ band_dil, int reach) {
   const int lane = threadIdx.x & 31;
   for (int j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; j0 < g.M; j0 += gridDim.x * blockDim.x) {
     const int j = j0 + lane;
@@ -252,6 +255,12 @@ __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const i
         const int rz = (g.d == 3) ? reach : 0;
         for (int dz = 0; dz <= rz; ++dz)
           for (int dy = 0; dy <= reach; ++dy) band[((bz + dz) % nbz) * nby + (by + dy) % nby] = 1;
+        if (band_dil) {  // one more box each way: the bands still hold the windows after a move of under a box
+          const int z0 = (g.d == 3) ? -1 : 0;
+          for (int dz = z0; dz <= rz - z0; ++dz)
+            for (int dy = -1; dy <= reach + 1; ++dy)
+              band_dil[((bz + dz + nbz) % nbz) * nby + (by + dy + nby) % nby] = 1;
+        }
       }
     }
     if (j >= g.M) continue;
@@ -266,22 +275,24 @@ __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const i
   }
 }
 
-void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied) {
+void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied,
+                       bool dilate) {
   const PointGeom g = geom(p);
   // counts are zero here: the workspace starts zeroed and every scan clears them after use
   const int nb = (p.M + 255) / 256;
   unsigned char* band = occupied ? nullptr : ws.band;  // row bands for the gather path
+  unsigned char* band_dil = (occupied || !dilate) ? nullptr : ws.band_dil;
   const int nband = p.nbin[1] * (p.d == 3 ? p.nbin[2] : 1);
   const int reach = (p.bins[1] + p.w - 2) / p.bins[1];
   k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts);
-  if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, nband);
-  else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, nband);
+  if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
+  else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
   if (p.prec == FSIB_FP64)
     k_bin_scatter<double><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
-                                              (double*)ws.delta, band, reach);
+                                              (double*)ws.delta, band, band_dil, reach);
   else
     k_bin_scatter<float><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
-                                             (float*)ws.delta, band, reach);
+                                             (float*)ws.delta, band, band_dil, reach);
 }
 
 // ---------------------------------------------------------------------------
@@ -1071,7 +1082,7 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
 template <typename T, int D>
 __global__ void __launch_bounds__(256)
 k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__ i0s, const T* __restrict__ W,
-              const T* __restrict__ grid, double* __restrict__ U) {
+              const T* __restrict__ grid, double* __restrict__ U, const unsigned char* __restrict__ guard) {
   // per warp: the window's rows (y, z) as grid offsets and their weight products w_y w_z
   constexpr int kRows = (D == 3) ? kMaxW * kMaxW : kMaxW;
   __shared__ int sOff[8][kRows];
@@ -1089,11 +1100,13 @@ k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__
     const T* ws = W + s * D * w;
     const int bx = i0s[s], by = i0s[(long long)M + s], bz = (D == 3) ? i0s[2LL * M + s] : 0;
     __syncwarp();
+    bool miss = false;  // a window row outside the bands the grid holds
     for (int r = lane; r < nrow; r += 32) {
       const int qz = (D == 3) ? r / w : 0, qy = r - qz * w;
       int gy = by + qy, gz = bz + qz;
       gy += (gy < 0) ? nf : 0; gy -= (gy >= nf) ? nf : 0;
       if (D == 3) { gz += (gz < 0) ? nf : 0; gz -= (gz >= nf) ? nf : 0; }
+      if (guard && !guard[(D == 3 ? gz / g.b[2] : 0) * g.nb[1] + gy / g.b[1]]) miss = true;
       off[r] = (D == 3) ? (gz * nf + gy) * nf : gy * nf;
       T v = ws[w + qy];
       if (D == 3) v = v * ws[2 * w + qz];
@@ -1135,10 +1148,12 @@ k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] = warp_sum(acc[a]);
+    const bool bad = __any_sync(0xffffffffu, miss);
     if (lane == 0) {
       const int j = perm[s];
 #pragma unroll
-      for (int a = 0; a < D; ++a) U[(long long)a * M + j] = to_double_val(acc[a]);
+      for (int a = 0; a < D; ++a) U[(long long)a * M + j] = bad ? __longlong_as_double(0x7ff8000000000000LL)
+                                                                 : to_double_val(acc[a]);
     }
   }
 }
@@ -1253,22 +1268,24 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
 }
 
 template <typename T>
-void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st) {
+void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st,
+                        const unsigned char* guard) {
   const PointGeom g = geom(p);
   long long blocks = (p.M + 7) / 8;
   if (blocks > 32LL * num_sms()) blocks = 32LL * num_sms();
   if (p.d == 3)
-    k_interp_warp<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U);
+    k_interp_warp<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard);
   else
-    k_interp_warp<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U);
+    k_interp_warp<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard);
 }
 
 template void launch_point_prep<float>(const Plan&, Workspace&, const double*, const double*, cudaStream_t);
 template void launch_point_prep<dd>(const Plan&, Workspace&, const double*, const double*, cudaStream_t);
 template void launch_spread_gather<float>(const Plan&, Workspace&, float*, cudaStream_t);
 template void launch_spread_gather<dd>(const Plan&, Workspace&, dd*, cudaStream_t);
-template void launch_interp_warp<float>(const Plan&, Workspace&, const float*, double*, cudaStream_t);
-template void launch_interp_warp<dd>(const Plan&, Workspace&, const dd*, double*, cudaStream_t);
+template void launch_interp_warp<float>(const Plan&, Workspace&, const float*, double*, cudaStream_t,
+                                        const unsigned char*);
+template void launch_interp_warp<dd>(const Plan&, Workspace&, const dd*, double*, cudaStream_t, const unsigned char*);
 
 
 template void launch_spread<float>(const Plan&, Workspace&, const double*, const double*, float*, cudaStream_t);

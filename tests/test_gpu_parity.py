@@ -301,3 +301,30 @@ def test_bad_arguments_rejected(lib, torch_mod):
     with pytest.raises(lib.FsibError) as ei:
         pb.step(np.zeros((2, 10)), pb.new_spec(), np.zeros((2, 10)))  # no force model
     assert ei.value.code == -7
+
+
+def test_velocity_guard_after_a_move_beyond_the_widened_bands(lib, torch_mod):
+    """The inverse transform behind U^{m+1} computes only the rows within one box of the
+    windows at X^{m+1/2}. A uniform flow that carries a cluster of points several boxes in a
+    half step (far beyond any stable time step) must give NaN there, never a value read from
+    rows that were not computed; at a normal step size the same setup gives the flow speed."""
+    torch = torch_mod
+    N, d, M = 64, 3, 40          # fine grid 128^3: 16 boxes of 8 cells per axis
+    rng = np.random.default_rng(77)
+    X0 = rng.uniform(0.45, 0.55, (d, M))
+    for dt, expect_nan in ((0.5, True), (1e-3, False)):
+        pb = lib.Problem(N, d, M, 0.1, 1.0, dt, 1e-12)
+        pb.set_force_target(X0, 0.0, 1.0)              # no boundary force
+        u = np.zeros((d, N, N, N), dtype=np.complex128)
+        u[1, 0, 0, 0] = 1.0                              # uniform flow u = (0, 1, 0)
+        uh = cuda(sp.full_to_half(u, N), torch)
+        Xt = cuda(X0, torch)
+        Ut = pb.interp(uh, Xt)
+        pb.step(Xt, uh, Ut, nsteps=1)
+        torch.cuda.synchronize()
+        got = to_np(Ut)
+        if expect_nan:
+            assert np.isnan(got).all()
+        else:
+            assert np.allclose(got[1], 1.0, rtol=0, atol=1e-10)
+            assert np.allclose(got[[0, 2]], 0.0, atol=1e-10)
