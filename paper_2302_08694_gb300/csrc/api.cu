@@ -427,6 +427,19 @@ static RowBands row_bands(const Plan& p, const Workspace& ws, bool dilated = fal
   return rb;
 }
 
+// The y passes of a 3D grid skip the z-slabs that no window reaches (see ZSkip).
+static ZSkip z_skip(const Plan& p, const Workspace& ws, bool dilated, bool zero) {
+  ZSkip zs;
+  const RowBands rb = row_bands(p, ws, dilated);
+  if (!rb.flag || p.d != 3) return zs;
+  zs.flag = rb.flag;
+  zs.outer = p.nf;
+  zs.b = p.bins[2];
+  zs.nby = p.nbin[1];
+  zs.zero = zero;
+  return zs;
+}
+
 template <typename TI>
 static void rows_r2c_first(const Plan& p, Workspace& ws, const TI* grid, C<TI>* out, long long nrows,
                            const C<TI>* tw, cudaStream_t st) {
@@ -456,7 +469,7 @@ static void forward_fine(fsib_plan* h, const TI* grid, C<TA>* out, cudaStream_t 
     { Prof pr(h, "t1.rows_r2c", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
       rows_r2c_first<TI>(p, ws, grid, s1, (long long)d * n * n, tw, st); }
     { Prof pr(h, "t1.fy_strided", (double)d * n * hh * (n + N) * cs, fft_flops((double)d * n * hh, n), st);
-      launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, false, none, tw, st); }
+      launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, false, none, tw, st, z_skip(p, ws, false, true)); }
     { Prof pr(h, "t1.fz_strided_deconv", (double)d * N * hh * (n + N) * cs, fft_flops((double)d * N * hh, n), st);
       launch_fft_strided<TI, TI, TA>(s2, out, d, 1, N * hh, N, p.fl_nf, false, dec, tw, st); }
   } else {
@@ -489,7 +502,8 @@ static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t s
     { Prof pr(h, "t2.iz_strided_deconv", (double)d * N * hh * (n + N) * cs, fft_flops((double)d * N * hh, n), st);
       launch_fft_strided<TI, TA, TI>(in, s1, d, 1, N * hh, N, p.fl_nf, true, dec, tw, st); }
     { Prof pr(h, "t2.iy_strided", (double)d * n * hh * (n + N) * cs, fft_flops((double)d * n * hh, n), st);
-      launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, true, none, tw, st); }
+      launch_fft_strided<TI>(s1, s2, d, n, hh, N, p.fl_nf, true, none, tw, st,
+                             banded ? z_skip(p, ws, banded == 2, false) : ZSkip()); }
     { Prof pr(h, "t2.ix_rows_c2r", (double)d * n * n * n * rs + (double)d * n * n * hh * cs, fft_flops(0.5 * d * n * n, n), st);
       launch_fft_rows_c2r<TI>(s2, grid, (long long)d * n * n, N, p.fl_nf, tw, st,
                               banded ? row_bands(p, ws, banded == 2) : RowBands()); }

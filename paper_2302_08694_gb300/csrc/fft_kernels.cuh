@@ -462,7 +462,8 @@ constexpr int s2_P(int E) { return E == 8 ? 16 : 8; }  // lines per tile: 128-by
 
 template <typename T, bool INV, typename Tin, typename Tout, int N>
 __device__ __forceinline__ void fft_s2_body(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner,
-                                            int Nk, int ntile, Mult<T> mult, const C<T>* __restrict__ twg) {
+                                            int Nk, int ntile, Mult<T> mult, const C<T>* __restrict__ twg,
+                                            ZSkip zs) {
   constexpr int P = s2_P((int)sizeof(C<T>)), R1 = s2_R1(N), R2 = N / R1, NT = 16 * P;
   constexpr int RM = R1 > R2 ? R1 : R2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -474,6 +475,19 @@ __device__ __forceinline__ void fft_s2_body(const C<Tin>* __restrict__ in, C<Tou
   const int h = Nk / 2;
   const C<Tin>* src = in + co * (long long)Lin * inner;
   C<Tout>* dst = out + co * (long long)Lout * inner;
+  if (zs.flag) {  // a z-slab that no window reaches (uniform across the block)
+    const int bz = (int)(co % zs.outer) / zs.b;
+    bool any = false;
+    for (int by = 0; by < zs.nby; ++by) any |= zs.flag[bz * zs.nby + by] != 0;
+    if (!any) {
+      if (zs.zero)
+        for (int t = threadIdx.x; t < Lout * P; t += NT) {
+          const int i = t / P, q = q0 + t % P;
+          if (q < inner) dst[(long long)i * inner + q] = C<Tout>{};
+        }
+      return;
+    }
+  }
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
   {
     // every load of this thread is issued before the first shared-memory store
@@ -562,14 +576,14 @@ __device__ __forceinline__ void fft_s2_body(const C<Tin>* __restrict__ in, C<Tou
 template <typename T, bool INV, typename Tin, typename Tout, int N>
 __global__ void __launch_bounds__(16 * s2_P(8), 3)
 k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
-         Mult<T> mult, const C<T>* __restrict__ twg) {
-  fft_s2_body<T, INV, Tin, Tout, N>(in, out, inner, Nk, ntile, mult, twg);
+         Mult<T> mult, const C<T>* __restrict__ twg, ZSkip zs) {
+  fft_s2_body<T, INV, Tin, Tout, N>(in, out, inner, Nk, ntile, mult, twg, zs);
 }
 template <typename T, bool INV, typename Tin, typename Tout, int N>
 __global__ void __launch_bounds__(16 * s2_P(16))
 k_fft_s2_dd(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
-            Mult<T> mult, const C<T>* __restrict__ twg) {
-  fft_s2_body<T, INV, Tin, Tout, N>(in, out, inner, Nk, ntile, mult, twg);
+            Mult<T> mult, const C<T>* __restrict__ twg, ZSkip zs) {
+  fft_s2_body<T, INV, Tin, Tout, N>(in, out, inner, Nk, ntile, mult, twg, zs);
 }
 template <typename T, bool INV, typename Tin, typename Tout, int N>
 inline auto fft_s2_kernel() {
@@ -624,7 +638,7 @@ static void with_fft_len(int n, F&& f) {
 template <typename T, typename Tin, typename Tout>
 void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, int inner, int Nk,
                         const FftLen& fl, bool inverse, Mult<T> mult, const C<T>* tw,
-                        cudaStream_t st) {
+                        cudaStream_t st, ZSkip zs) {
   const int kP = fl.tile_p;
   const int ntile = (inner + kP - 1) / kP;
   const long long blocks = (long long)ncomp * outer * ntile;
@@ -644,13 +658,13 @@ void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, in
       if (inverse && !fwd_only) {
         auto k = fft_s2_kernel<T, true, Tin, Tout, NC>();
         raise_smem_limit(reinterpret_cast<const void*>(k));
-        k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off);
+        k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off, zs);
         return;
       }
       if (!inverse && !inv_only) {
         auto k = fft_s2_kernel<T, false, Tin, Tout, NC>();
         raise_smem_limit(reinterpret_cast<const void*>(k));
-        k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off);
+        k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off, zs);
         return;
       }
     }
@@ -751,6 +765,6 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
 #define FSIB_FFT_INST_S(T, Ti, To)                                                               \
   template void launch_fft_strided<T, Ti, To>(const C<Ti>*, C<To>*, int, int, int, int,          \
                                               const FftLen&, bool, Mult<T>, const C<T>*,         \
-                                              cudaStream_t);
+                                              cudaStream_t, ZSkip);
 
 }  // namespace fsib

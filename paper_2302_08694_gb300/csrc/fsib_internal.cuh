@@ -170,10 +170,17 @@ struct Workspace {
 // ---------------------------------------------------------------------------
 // Launchers (implemented in the .cu files). All enqueue on `st`.
 // ---------------------------------------------------------------------------
+// Strided passes along y of a 3D grid [comp][z][y][x] (outer = z): the z-slabs of boxes whose
+// row bands are all off (RowBands flags) are skipped; zero: write zeros there instead (their
+// input column is zero). The two-stage kernels honour it; other lengths compute every line.
+struct ZSkip {
+  const unsigned char* flag = nullptr;  // [nb_z][nb_y]
+  int outer = 1, b = 1, nby = 1, zero = 0;
+};
 template <typename T, typename Tin = T, typename Tout = T>
 void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, int inner,
                         int Nk, const FftLen& fl, bool inverse, Mult<T> mult,
-                        const C<T>* tw, cudaStream_t st);
+                        const C<T>* tw, cudaStream_t st, ZSkip zs = ZSkip());
 // Rows of the fine grid (along x) that no window of the current point binning reaches, by
 // band of boxes (y div b, z div b): the gather spread leaves them unwritten, the first forward
 // row pass takes them as zeros, and the last inverse row pass skips them (no interpolation
