@@ -197,12 +197,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the spread site
-# (k_box_slices, k_scan2, k_slice_boxes, k_spread_box3[_dd]), from one ncu capture of
-# the current kernels per workload; profiles/spread_site_traffic.txt has the command and the
-# per-kernel figures. Set an entry to None when those kernels change.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a site, from one
+# ncu capture of the current kernels per workload: the spread site (k_box_slices, k_scan2,
+# k_slice_boxes, k_spread_box3[_dd]; profiles/spread_site_traffic.txt has the command and the
+# per-kernel figures) and the mixed product pass (k_wrows_product<float, 192>;
+# profiles/kernels_ns3d_N128_M40322_mixed.txt). Set an entry to None when those kernels change.
 SITE_TRAFFIC = {("ns3d_N64_M10082_fp64", "spread"): 10024448.0,
-                ("ns3d_N128_M40322_mixed", "spread"): 163444224.0}
+                ("ns3d_N128_M40322_mixed", "spread"): 163444224.0,
+                ("ns3d_N128_M40322_mixed", "nl.rows_product"): 112261376.0}
 
 
 def _events(torch):

@@ -239,32 +239,9 @@ k_scan2(const int* __restrict__ a, const int* __restrict__ b, int n, int* __rest
 template <typename T>
 __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const int* __restrict__ bin_of,
                               const int* __restrict__ rank, const int* __restrict__ offsets,
-                              int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta,
-                              unsigned char* __restrict__ band, unsigned char* __restrict__ band_dil, int reach) {
-  const int lane = threadIdx.x & 31;
-  for (int j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; j0 < g.M; j0 += gridDim.x * blockDim.x) {
-    const int j = j0 + lane;
-    const int bin = (j < g.M) ? bin_of[j] : -1;
-    if (band) {
-      // row bands (boxes along y and z) that windows of this bin reach: windows starting in
-      // bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach; one lane per bin
-      const unsigned same = __match_any_sync(0xffffffffu, bin);
-      if (bin >= 0 && lane == __ffs(same) - 1) {
-        const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
-        const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
-        const int rz = (g.d == 3) ? reach : 0;
-        for (int dz = 0; dz <= rz; ++dz)
-          for (int dy = 0; dy <= reach; ++dy) band[((bz + dz) % nbz) * nby + (by + dy) % nby] = 1;
-        if (band_dil) {  // one more box each way: the bands still hold the windows after a move of under a box
-          const int z0 = (g.d == 3) ? -1 : 0;
-          for (int dz = z0; dz <= rz - z0; ++dz)
-            for (int dy = -1; dy <= reach + 1; ++dy)
-              band_dil[((bz + dz + nbz) % nbz) * nby + (by + dy + nby) % nby] = 1;
-        }
-      }
-    }
-    if (j >= g.M) continue;
-    const int s = offsets[bin] + rank[j];
+                              int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.M; j += gridDim.x * blockDim.x) {
+    const int s = offsets[bin_of[j]] + rank[j];
     perm[s] = j;
     for (int a = 0; a < g.d; ++a) {
       const double t = grid_coord(X[(long long)a * g.M + j], g);
@@ -272,6 +249,34 @@ __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const i
       i0[(long long)a * g.M + s] = c0;
       delta[(long long)a * g.M + s] = (T)((double)c0 - t);  // in [-w/2, -w/2 + 1)
     }
+  }
+}
+
+static int num_sms();
+
+// Row bands (boxes along y and z) that the windows of each occupied bin reach: windows
+// starting in bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach per axis; band_dil
+// one box more each way (the bands still hold the windows after a move of under a box). One
+// thread per bin, after the scan has cleared the flags; a flag already set is not stored again.
+__global__ void k_band_mark(PointGeom g, const int* __restrict__ offsets, unsigned char* __restrict__ band,
+                            unsigned char* __restrict__ band_dil, int reach) {
+  const int nbins = g.nb[0] * g.nb[1] * (g.d == 3 ? g.nb[2] : 1);
+  const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
+  const int rz = (g.d == 3) ? reach : 0, z0 = (g.d == 3) ? -1 : 0;
+  for (int bin = blockIdx.x * blockDim.x + threadIdx.x; bin < nbins; bin += gridDim.x * blockDim.x) {
+    if (offsets[bin + 1] == offsets[bin]) continue;
+    const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
+    for (int dz = 0; dz <= rz; ++dz)
+      for (int dy = 0; dy <= reach; ++dy) {
+        unsigned char* f = &band[((bz + dz) % nbz) * nby + (by + dy) % nby];
+        if (!*f) *f = 1;
+      }
+    if (band_dil)
+      for (int dz = z0; dz <= rz - z0; ++dz)
+        for (int dy = -1; dy <= reach + 1; ++dy) {
+          unsigned char* f = &band_dil[((bz + dz + nbz) % nbz) * nby + (by + dy + nby) % nby];
+          if (!*f) *f = 1;
+        }
   }
 }
 
@@ -287,12 +292,16 @@ void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream
   k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts);
   if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
   else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
+  if (band) {
+    const long long nbb = std::min<long long>((p.nbins + 255) / 256, 4LL * num_sms());
+    k_band_mark<<<(unsigned)std::max<long long>(1, nbb), 256, 0, st>>>(g, ws.offsets, band, band_dil, reach);
+  }
   if (p.prec == FSIB_FP64)
     k_bin_scatter<double><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
-                                              (double*)ws.delta, band, band_dil, reach);
+                                              (double*)ws.delta);
   else
     k_bin_scatter<float><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
-                                             (float*)ws.delta, band, band_dil, reach);
+                                             (float*)ws.delta);
 }
 
 // ---------------------------------------------------------------------------
