@@ -226,6 +226,32 @@ def replica_value(steps, ms_max, world):
     return world * steps / (ms_max * 1e-3)
 
 
+def step_bytes(prob, prec, nf, Nt):
+    """Algorithmic bytes of one whole step (every fine and dealiasing grid written once and read
+    once, spectra read and written once per use, points read once): type-1 and type-2
+    2 d G s + d K c + M d (8 + s) each; the nonlinear term 2 d K c + 2 d D s + d(d+1) D s + d K c;
+    an update 3 d K c; Navier-Stokes = t1 + 2 t2 + 2 V + 2 updates, Stokes = 2 t1 + 2 t2 + 2
+    Stokeslets (2 d K c each). G = nf^d, K = N^d, D = Nt^d; s, c = bytes per real, complex."""
+    d, N, M = prob.d, prob.N, prob.M
+    s = 4.0 if prec == "mixed" else 8.0
+    c = 2.0 * s
+    G, K, D = float(nf) ** d, float(N) ** d, float(Nt) ** d
+    t = 2 * d * G * s + d * K * c + M * d * (8 + s)
+    if prob.rho > 0:
+        V = 2 * d * K * c + 2 * d * D * s + d * (d + 1) * D * s + d * K * c
+        return t + 2 * t + 2 * V + 2 * 3 * d * K * c
+    return 2 * t + 2 * t + 2 * 2 * d * K * c
+
+
+def step_roofline(prob, prec, nf, Nt, ms_per_step, pk):
+    """Whole-step HBM fraction from the algorithmic bytes (the step skips rows no window
+    reaches, so it moves fewer bytes than this model counts); pk: the measured peaks."""
+    b = step_bytes(prob, prec, nf, Nt)
+    gbs = b / (ms_per_step * 1e-3) / 1e9
+    hbm = float(pk["hbm_gbs"])
+    return {"algorithmic_bytes_per_step": b, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm}
+
+
 def roofline_of(site, prec, pk, pk_src, fp64_peak, fp32_peak):
     """Binding roofline of one launch site: HBM (algorithmic bytes) or ALU (algorithmic flops).
 
@@ -370,6 +396,7 @@ def mixed_block(fsib, torch, dev, flush, pk, pk_src, fp64_peak, fp32_peak, steps
             "error_vs_fp64_run": errs, "launch_shapes": m["launch_shapes"],
             "roofline": dict(roofline_of(top, "mixed", pk, pk_src, fp64_peak, fp32_peak),
                              traffic=SITE_TRAFFIC.get((prob.name, top["name"]))),
+            "step_roofline": step_roofline(prob, "mixed", m["info"]["nf"], m["info"]["Nt"], m["ms"] / steps, pk),
             "breakdown": breakdown_of(m["sites"], m["nprof"], 8)}
 
 
@@ -412,12 +439,17 @@ def batched_block(fsib, torch, dev, flush, steps, warmup):
         k = f"{p.d}d_N{p.N}"
         tuned.setdefault(k, {kk: int(m.info(kk)) for kk in ("fft_tile", "fft_rows", "spread_slice")})
     mtot = sum(p.M for p in probs)
+    bytes_step = sum(step_bytes(p, "mixed", int(m.info("nf")), int(m.info("Nt"))) for p, m in zip(probs, B.members))
+    hbm = float(peaks()[0]["hbm_gbs"])
+    gbs = bytes_step / (ms / steps * 1e-3) / 1e9
     out = {"workload": f"batched{n}_mixed", "problems": n, "value": n * steps / (ms * 1e-3),
            "unit": "problem-steps/s", "batch_steps_per_s": steps / (ms * 1e-3), "ms_per_batch_step": ms / steps,
            "boundary_points_per_s": mtot * steps / (ms * 1e-3), "total_points": mtot,
            "launches_per_batch_step": int(B.info("launches_per_step")), "autotune_seconds": tune_s,
            "finite": ok, "n_2d": sum(p.d == 2 for p in probs), "n_3d": sum(p.d == 3 for p in probs),
-           "tuned_shapes": tuned}
+           "tuned_shapes": tuned,
+           "step_roofline": {"algorithmic_bytes_per_batch_step": bytes_step, "achieved_gbs": gbs, "peak_gbs": hbm,
+                             "frac": gbs / hbm}}
     B.close()
     return out
 
@@ -845,6 +877,7 @@ def run_ours(args):
                            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{world}"},
                 "nufft_pts_per_s": {"type1": world * m["pts1"], "type2": world * m["pts2"]},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": m["clocks"],
+                "step_roofline": step_roofline(prob, prec, m["info"]["nf"], m["info"]["Nt"], ms_max / args.steps, pk),
                 "gpu_launches": m["launches"] * args.steps, "launches_per_step": m["launches"],
                 "launch_shapes": m["launch_shapes"],
                 "breakdown": breakdown_of(m["sites"], m["nprof"]), "mixed": mixed, "batched": batched, "nufft_sweep": sweep,
