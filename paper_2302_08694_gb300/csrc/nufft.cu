@@ -710,7 +710,8 @@ __device__ __forceinline__ int next_slice(int* __restrict__ work, int* s_item, i
   return s_item[0];
 }
 
-// Zeroing of the boxes that no window reaches, in runs of 32 boxes claimed from a counter
+// Zeroing of the boxes that no window reaches but whose row band another box's windows reach
+// (the forward row pass reads those rows whole), in runs of 32 boxes claimed from a counter
 // (work[1]): 16-byte stores along x.
 template <typename T>
 __device__ __forceinline__ void zero_box(const PointGeom& g, int box, T* __restrict__ grid, int lane) {
