@@ -158,8 +158,8 @@ __device__ __forceinline__ void block_prefix(int (&v)[NV], int (&tot)[NV], int (
 
 // Bin offsets (exclusive scan of the counts, total at [nbins]) and the list of occupied bins.
 // OCC: also list the occupied bins (the scatter spread walks them; the gather does not).
-// It also clears the row-band flags (nband bytes) that the scatter then marks, and leaves the
-// counts at zero for the next binning (no memset node in the step graph).
+// It also clears the row-band flags (nband bytes) that k_band_mark then marks, and, without
+// them, leaves the counts at zero for the next binning (no memset node in the step graph).
 template <bool OCC>
 __global__ void __launch_bounds__(kScanThreads)
 k_bin_scan(int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
@@ -176,7 +176,7 @@ k_bin_scan(int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
     const long long i0 = base + (long long)threadIdx.x * kScanPer;
     int c[kScanPer];
     scan_load(counts, i0, nbins, c);
-    {
+    if (!band) {  // with row bands, k_band_mark clears the counts (a parallel pass over the bins)
       int z[kScanPer];
 #pragma unroll
       for (int k = 0; k < kScanPer; ++k) z[k] = 0;
@@ -258,12 +258,14 @@ static int num_sms();
 // starting in bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach per axis; band_dil
 // one box more each way (the bands still hold the windows after a move of under a box). One
 // thread per bin, after the scan has cleared the flags; a flag already set is not stored again.
-__global__ void k_band_mark(PointGeom g, const int* __restrict__ offsets, unsigned char* __restrict__ band,
-                            unsigned char* __restrict__ band_dil, int reach) {
+// It also returns the bin counts to zero.
+__global__ void k_band_mark(PointGeom g, const int* __restrict__ offsets, int* __restrict__ counts,
+                            unsigned char* __restrict__ band, unsigned char* __restrict__ band_dil, int reach) {
   const int nbins = g.nb[0] * g.nb[1] * (g.d == 3 ? g.nb[2] : 1);
   const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
   const int rz = (g.d == 3) ? reach : 0, z0 = (g.d == 3) ? -1 : 0;
   for (int bin = blockIdx.x * blockDim.x + threadIdx.x; bin < nbins; bin += gridDim.x * blockDim.x) {
+    counts[bin] = 0;  // zero again for the next binning (the scan has consumed them)
     if (offsets[bin + 1] == offsets[bin]) continue;
     const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
     for (int dz = 0; dz <= rz; ++dz)
@@ -294,7 +296,8 @@ void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream
   else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
   if (band) {
     const long long nbb = std::min<long long>((p.nbins + 255) / 256, 4LL * num_sms());
-    k_band_mark<<<(unsigned)std::max<long long>(1, nbb), 256, 0, st>>>(g, ws.offsets, band, band_dil, reach);
+    k_band_mark<<<(unsigned)std::max<long long>(1, nbb), 256, 0, st>>>(g, ws.offsets, ws.counts, band, band_dil,
+                                                                         reach);
   }
   if (p.prec == FSIB_FP64)
     k_bin_scatter<double><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
