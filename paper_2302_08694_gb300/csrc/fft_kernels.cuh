@@ -280,9 +280,8 @@ __device__ __forceinline__ void wfft_load_packed(C<T> (&v)[wfft_M(N)], const C<T
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(256)
-k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
-            const C<T>* __restrict__ twg, RowBands rb) {
+__device__ __forceinline__ void wrows_c2r_body(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs,
+                                               int Nk, const C<T>* __restrict__ twg, RowBands rb) {
   constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
@@ -308,6 +307,27 @@ k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, 
       }
     }
   }
+}
+
+// FP32 lines ask for three resident blocks per SM (the pass is bound by the transforms' latency
+// once the row bands cut its traffic); double-float lines keep the compiler's register choice
+// (a minimum-blocks hint of one raises it).
+template <typename T, int N>
+__global__ void __launch_bounds__(256, 3)
+k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
+            const C<T>* __restrict__ twg, RowBands rb) {
+  wrows_c2r_body<T, N>(in, out, npairs, Nk, twg, rb);
+}
+template <typename T, int N>
+__global__ void __launch_bounds__(256)
+k_wrows_c2r_dd(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
+               const C<T>* __restrict__ twg, RowBands rb) {
+  wrows_c2r_body<T, N>(in, out, npairs, Nk, twg, rb);
+}
+template <typename T, int N>
+inline auto wrows_c2r_kernel() {
+  if constexpr (sizeof(C<T>) == 8) return k_wrows_c2r<T, N>;
+  else return k_wrows_c2r_dd<T, N>;
 }
 
 // Untangle the spectra of two real rows packed as Z = A + iB: A[k] = (Z[k] + conj Z[N-k]) / 2,
@@ -717,7 +737,7 @@ void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const 
     constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;
     if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
-      auto k = k_wrows_c2r<T, NC>;
+      auto k = wrows_c2r_kernel<T, NC>();
       raise_smem_limit(reinterpret_cast<const void*>(k));
       k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off, rb);
       return;
