@@ -356,9 +356,8 @@ __device__ __forceinline__ void wfft_untangle(const C<T> (&v)[wfft_M(N)], C<T>* 
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(256)
-k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
-            const C<T>* __restrict__ twg, RowBands rb) {
+__device__ __forceinline__ void wrows_r2c_body(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs,
+                                               int Nk, const C<T>* __restrict__ twg, RowBands rb) {
   constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
@@ -391,6 +390,26 @@ k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, 
     wfft<T, false, N>(v, buf, l, tw);
     wfft_untangle<T, N>(v, buf, l, valid, h, out + (2 * pr) * h, out + (2 * pr + 1) * h);
   }
+}
+
+// FP32 lines: three resident blocks per SM, as for the c2r pass; double-float lines keep the
+// compiler's register choice.
+template <typename T, int N>
+__global__ void __launch_bounds__(256, 3)
+k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
+            const C<T>* __restrict__ twg, RowBands rb) {
+  wrows_r2c_body<T, N>(in, out, npairs, Nk, twg, rb);
+}
+template <typename T, int N>
+__global__ void __launch_bounds__(256)
+k_wrows_r2c_dd(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
+               const C<T>* __restrict__ twg, RowBands rb) {
+  wrows_r2c_body<T, N>(in, out, npairs, Nk, twg, rb);
+}
+template <typename T, int N>
+inline auto wrows_r2c_kernel() {
+  if constexpr (sizeof(C<T>) == 8) return k_wrows_r2c<T, N>;
+  else return k_wrows_r2c_dd<T, N>;
 }
 
 // Schedule of the product pass (see k_wrows_product): kind 0 = inverse transform of
@@ -713,7 +732,7 @@ void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const 
     constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;
     if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
-      auto k = k_wrows_r2c<T, NC>;
+      auto k = wrows_r2c_kernel<T, NC>();
       raise_smem_limit(reinterpret_cast<const void*>(k));
       k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off, rb);
       return;
