@@ -162,7 +162,10 @@ int fsib_fluid_step(fsib_t h, const void* fhat, void* uhat, void* uhat_half);
  * Navier-Stokes: state (X^m, u-hat^m, U^m) -> (X^{m+n}, u-hat^{m+n}, U^{m+n}) by
  *   Algorithm 1, where U^m must equal the interpolated velocity u^m(X^m)
  *   (fsib_interp gives U^0). U^{m+1} is interpolated at X^{m+1} after the
- *   position update.
+ *   position update, from a fine grid computed only near the windows at
+ *   X^{m+1/2} (within one box of 8 fine cells): a point that moves farther in
+ *   half a step (far beyond a stable dt) gets NaN in U^{m+1}, which the
+ *   "check_finite" option reports on the next step.
  * Stokes: X^{m+1} = X^m + dt U(X^{m+1/2}), X^{m+1/2} = X^m + dt/2 U(X^m),
  *   U(X) = interp(Stokeslet(spread(F(X), X)), X); uhat and U may be NULL
  *   (when given, U receives U(X^{m+1/2}) of the last step).
