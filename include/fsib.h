@@ -47,7 +47,7 @@ extern "C" {
 #define FSIB_ECUDA        -3  /* a CUDA call or kernel launch failed */
 #define FSIB_ENONFINITE   -4  /* non-finite positions or velocities detected */
 #define FSIB_ETIMEOUT     -5  /* a bounded device wait ran out */
-#define FSIB_EUNSUPPORTED -6  /* valid request this build does not support */
+#define FSIB_EUNSUPPORTED -6  /* valid request the library does not support */
 #define FSIB_ESTATE       -7  /* call out of order (e.g. no force model set) */
 
 #define FSIB_FP64  0          /* transforms and fluid solve in double */
