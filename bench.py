@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-validation", action="store_true",
                     help="skip the validation blocks (2D sine circle and Poiseuille channel, 3D spheres)")
     ap.add_argument("--workload", choices=["ns3d_fp64", "ns3d_mixed", "ns2d_circle", "poiseuille",
-                                           "sphere_elastic", "sphere_tension"],
+                                           "sphere_elastic", "sphere_tension", "stokes2d"],
                     default="ns3d_fp64",
                     help="workload of the main line (profiling runs use ns3d_mixed for the FP32 kernels)")
     return ap.parse_args()
@@ -151,7 +151,10 @@ def time_oracle_steps(prob, nsteps):
     fbody = prob.extra.get("fbody")
     t0 = time.perf_counter()
     for _ in range(nsteps):
-        X, u, U = st.ns_step(X, u, U, force, N, prob.mu, prob.rho, prob.dt, fbody=fbody)
+        if prob.rho > 0:
+            X, u, U = st.ns_step(X, u, U, force, N, prob.mu, prob.rho, prob.dt, fbody=fbody)
+        else:
+            X = st.stokes_step(X, force, N, prob.mu, prob.dt)
     return time.perf_counter() - t0
 
 
@@ -165,6 +168,8 @@ def workload_of(name):
         return wl.config_poiseuille(N=64), "fp64"
     if name in ("sphere_elastic", "sphere_tension"):
         return wl.config_ns3d_sphere(name.split("_")[1]), "fp64"
+    if name == "stokes2d":
+        return wl.config_stokes2d(), "fp64"
     return wl.config_ns3d_fp64(), "fp64"
 
 
