@@ -542,6 +542,10 @@ __global__ void k_point_prep(PointGeom g, double beta, const typename DeltaT<T>:
 
 constexpr int kChunk = 32;  // candidates staged per round
 
+// Neighbouring bins whose window starts can reach box (Bx, By, Bz) (defined below).
+__device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int Bx, int By, int Bz, int lane,
+                                       int* bin);
+
 template <typename T, int D>
 __global__ void __launch_bounds__(256)
 k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
@@ -567,30 +571,54 @@ k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, 
 #pragma unroll
   for (int i = 0; i < kSeg; ++i) acc[i] = T(0);
   const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
-  // neighbour bins per axis: B + dlo .. B + dhi (mod nb), or every bin once if that span covers the axis
-  const int span = dhi - dlo + 1;
-  const int sx = min(span, g.nb[0]), sy = min(span, g.nb[1]), sz = (D == 3) ? min(span, g.nb[2]) : 1;
-  const int bx0 = (span >= g.nb[0]) ? 0 : Bx + dlo, by0 = (span >= g.nb[1]) ? 0 : By + dlo;
-  const int bz0 = (D == 3) ? ((span >= g.nb[2]) ? 0 : Bz + dlo) : 0;
-  const int nnb = sx * sy * sz;
-  for (int nb = 0; nb < nnb; ++nb) {
-    int nbx = bx0 + nb % sx, nby = by0 + (nb / sx) % sy, nbz = (D == 3) ? bz0 + nb / (sx * sy) : 0;
-    nbx = (nbx % g.nb[0] + g.nb[0]) % g.nb[0];
-    nby = (nby % g.nb[1] + g.nb[1]) % g.nb[1];
-    if (D == 3) nbz = (nbz % g.nb[2] + g.nb[2]) % g.nb[2];
-    const int bin = (nbz * g.nb[1] + nby) * g.nb[0] + nbx;
-    const int p0 = offsets[bin], p1 = offsets[bin + 1];
-    for (int c0 = p0; c0 < p1; c0 += kChunk) {
-      const int nc = min(kChunk, p1 - c0);
+  // candidates: the points of the neighbouring bins (B + dlo .. B + dhi per axis, mod nb), as
+  // one list of ranges (first point, prefix of lengths) built by warp 0, staged kChunk at a time
+  __shared__ int sStart[32], sPre[33], sSp[kChunk];
+  __shared__ int sNr;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int bin = 0;
+    const int nnb = nb_list(g, dlo, dhi, Bx, By, Bz, lane, &bin);
+    int p0 = 0, len = 0;
+    if (lane < nnb) { p0 = offsets[bin]; len = offsets[bin + 1] - p0; }
+    int incl = len;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += t;
+    }
+    const unsigned nonempty = __ballot_sync(0xffffffffu, len > 0);
+    if (len > 0) {
+      const int slot = __popc(nonempty & ((1u << lane) - 1u));
+      sStart[slot] = p0;
+      sPre[slot] = incl - len;
+    }
+    if (lane == 31) { sNr = __popc(nonempty); sPre[__popc(nonempty)] = incl; }
+  }
+  __syncthreads();
+  const int nr = sNr, total = sPre[nr];
+  {
+    for (int c0 = 0; c0 < total; c0 += kChunk) {
+      const int nc = min(kChunk, total - c0);
+      __syncthreads();
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int f = c0 + c;
+        int lo = 0, hi = nr - 1;  // last range with sPre <= f
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sPre[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const int sp = sStart[lo] + (f - sPre[lo]);
+        sSp[c] = sp;
+        for (int a = 0; a < D; ++a) {
+          sI[c * 3 + a] = i0s[(long long)a * M + sp];
+          sC[c * D + a] = Cw[(long long)sp * D + a];
+        }
+      }
       __syncthreads();
       for (int i = threadIdx.x; i < nc * D * w; i += blockDim.x) {
         const int c = i / (D * w), r = i % (D * w);
-        sW[c * D * kMaxW + r] = W[(long long)(c0 + c) * D * w + r];
-      }
-      for (int i = threadIdx.x; i < nc * D; i += blockDim.x) sC[i] = Cw[(long long)c0 * D + i];
-      for (int i = threadIdx.x; i < nc * D; i += blockDim.x) {
-        const int c = i / D, a = i % D;
-        sI[c * 3 + a] = i0s[(long long)a * M + c0 + c];
+        sW[c * D * kMaxW + r] = W[(long long)sSp[c] * D * w + r];
       }
       __syncthreads();
       if (!active) continue;
