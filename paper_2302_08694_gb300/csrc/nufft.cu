@@ -282,6 +282,78 @@ __global__ void k_band_mark(PointGeom g, const int* __restrict__ offsets, int* _
   }
 }
 
+// The whole binning of a small problem in one block (one launch instead of four): bins and
+// ranks with shared-memory atomics, the exclusive scan of the bin counts in shared memory, the
+// row bands and the scatter. Used when the points are few (the positions' FP64 grid
+// coordinates, computed twice per point, run on one SM) and the bins fit in shared memory.
+constexpr int kSmallBins = 8192;
+constexpr int kSmallM = 2048;
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_bin_small(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of, int* __restrict__ rank,
+            int* __restrict__ offsets, int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta,
+            unsigned char* __restrict__ band, unsigned char* __restrict__ band_dil, int nband, int reach) {
+  __shared__ int sc[kSmallBins];
+  __shared__ int wsum[1][32];
+  const int nbins = g.nb[0] * g.nb[1] * (g.d == 3 ? g.nb[2] : 1);
+  const int M = g.M;
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x) sc[i] = 0;
+  for (int i = threadIdx.x; band && i < nband; i += blockDim.x) band[i] = 0;
+  for (int i = threadIdx.x; band_dil && i < nband; i += blockDim.x) band_dil[i] = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    int b = 0, mul = 1;
+    for (int a = 0; a < g.d; ++a) {
+      const double t = grid_coord(X[(long long)a * M + j], g);
+      b += bin_of_start(window_start(t, g.w), g.nf, g.b[a], g.nb[a]) * mul;
+      mul *= g.nb[a];
+    }
+    bin_of[j] = b;
+    rank[j] = atomicAdd(&sc[b], 1);
+  }
+  __syncthreads();
+  // exclusive scan: thread t owns the bins [t per, (t + 1) per)
+  const int per = (nbins + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b0 = threadIdx.x * per;
+  int loc = 0;
+  for (int k = 0; k < per; ++k)
+    if (b0 + k < nbins) loc += sc[b0 + k];
+  int v[1] = {loc}, tot[1];
+  block_prefix<1>(v, tot, wsum);
+  int run = v[0];
+  const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
+  const int rz = (g.d == 3) ? reach : 0, z0 = (g.d == 3) ? -1 : 0;
+  for (int k = 0; k < per; ++k) {
+    const int bin = b0 + k;
+    if (bin >= nbins) break;
+    const int c = sc[bin];
+    sc[bin] = run;
+    offsets[bin] = run;
+    run += c;
+    if (c > 0 && band) {  // row bands of this bin's windows (see k_band_mark)
+      const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
+      for (int dz = 0; dz <= rz; ++dz)
+        for (int dy = 0; dy <= reach; ++dy) band[((bz + dz) % nbz) * nby + (by + dy) % nby] = 1;
+      if (band_dil)
+        for (int dz = z0; dz <= rz - z0; ++dz)
+          for (int dy = -1; dy <= reach + 1; ++dy) band_dil[((bz + dz + nbz) % nbz) * nby + (by + dy + nby) % nby] = 1;
+    }
+  }
+  if (threadIdx.x == 0) offsets[nbins] = tot[0];
+  __syncthreads();
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    const int s = sc[bin_of[j]] + rank[j];
+    perm[s] = j;
+    for (int a = 0; a < g.d; ++a) {
+      const double t = grid_coord(X[(long long)a * M + j], g);
+      const int c0 = window_start(t, g.w);
+      i0[(long long)a * M + s] = c0;
+      delta[(long long)a * M + s] = (T)((double)c0 - t);
+    }
+  }
+}
+
 void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied,
                        bool dilate) {
   const PointGeom g = geom(p);
@@ -291,6 +363,15 @@ void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream
   unsigned char* band_dil = (occupied || !dilate) ? nullptr : ws.band_dil;
   const int nband = p.nbin[1] * (p.d == 3 ? p.nbin[2] : 1);
   const int reach = (p.bins[1] + p.w - 2) / p.bins[1];
+  if (!occupied && p.M <= kSmallM && p.nbins <= kSmallBins) {  // gather path, small problem
+    if (p.prec == FSIB_FP64)
+      k_bin_small<double><<<1, 1024, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
+                                             (double*)ws.delta, band, band_dil, nband, reach);
+    else
+      k_bin_small<float><<<1, 1024, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
+                                            (float*)ws.delta, band, band_dil, nband, reach);
+    return;
+  }
   k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts);
   if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
   else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);

@@ -63,7 +63,8 @@ def test_batch_matches_individual_handles(lib, torch_mod, prec):
     for s, X, u, U in singles:
         s.step(X, u, U, nsteps=3)
     torch.cuda.synchronize()
-    assert B.info("launches_per_step") > 30 * n
+    # the batch graph holds every member's step: as many kernels as the members' own graphs
+    assert B.info("launches_per_step") == sum(s.info("launches_per_step") for s, _, _, _ in singles)
     t = 1e-12 if prec == "fp64" else 1e-5
     for i, (p, (s, X, u, U)) in enumerate(zip(probs, singles)):
         x0 = p["X0"]
