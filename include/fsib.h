@@ -57,7 +57,12 @@ extern "C" {
 typedef struct fsib_plan* fsib_t;
 
 /* Create a handle for one problem.
- * N: modes per axis (even, 4..512). d: 2 or 3. M: number of boundary points (>= 1).
+ * N: modes per axis (even, 4..1024). d: 2 or 3. M: number of boundary points (>= 1).
+ * The fine grid (sigma N points per axis, rounded up to a multiple of 8 with no prime
+ * factor above 3) and the dealiasing grid (3N/2, rounded up to an even length with no
+ * prime factor above 3) must each fit
+ * the longest transform, 2048 points in 2D and 512 in 3D: at sigma = 2 that is
+ * N <= 1024 in 2D and N <= 256 in 3D. A larger grid returns FSIB_EUNSUPPORTED.
  * mu: dynamic viscosity (> 0). rho: density; rho > 0 selects Navier-Stokes
  * (Algorithm 1, Eqs. spatial_1-4), rho <= 0 the quasi-static Stokes stepper
  * (Eq. stokeslet, same midpoint rule in time). dt: time step (> 0).

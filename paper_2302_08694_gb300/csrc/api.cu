@@ -50,17 +50,25 @@ int check_last(const char* where) {
   return e == cudaSuccess ? FSIB_OK : FSIB_ECUDA;
 }
 
+size_t smem_optin() {
+  static const int optin = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaGetLastError();
+      v = 48 * 1024;
+    }
+    return v;
+  }();
+  return (size_t)optin;
+}
+
 void raise_smem_limit(const void* kernel) {
   static std::mutex mu;
   static std::unordered_set<const void*> done;
-  static int optin = -1;
   std::lock_guard<std::mutex> lk(mu);
   if (done.count(kernel)) return;
-  if (optin < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 48 * 1024;
-  }
+  const int optin = (int)smem_optin();
   // the opt-in limit covers static and dynamic shared memory together
   cudaFuncAttributes fa;
   size_t stat = 0;
@@ -147,8 +155,10 @@ static int plan_sizes(Plan& p, std::string& err) {
   p.nf = smooth_even_at_least(std::max((int)std::ceil(p.sigma * p.N - 1e-9), 2 * w));
   while (p.nf % 8) p.nf = smooth_even_at_least(p.nf + 1);  // boxes of 8 cells tile the grid
   p.Nt = smooth_even_at_least((3 * p.N + 1) / 2);
-  if (p.nf > kMaxFFT || p.Nt > kMaxFFT) {
-    err = "fine or dealiasing grid exceeds the supported FFT length 512";
+  const int maxfft = (p.d == 2) ? kMaxFFT2 : kMaxFFT3;
+  if (p.nf > maxfft || p.Nt > maxfft) {
+    err = "fine or dealiasing grid exceeds the supported FFT length " + std::to_string(maxfft) + " (" +
+          std::to_string(p.d) + "D)";
     return FSIB_EUNSUPPORTED;
   }
   int b = p.bin_opt;
@@ -833,7 +843,7 @@ int fsib_create(fsib_t* out, int N, int d, int M, double mu, double rho, double 
   if (!out) { g_create_err = "out is NULL"; return FSIB_EINVAL; }
   *out = nullptr;
   if (d != 2 && d != 3) { g_create_err = "d must be 2 or 3"; return FSIB_EINVAL; }
-  if (N < 4 || N > 512 || (N % 2)) { g_create_err = "N must be even, 4 <= N <= 512"; return FSIB_EINVAL; }
+  if (N < 4 || N > 1024 || (N % 2)) { g_create_err = "N must be even, 4 <= N <= 1024"; return FSIB_EINVAL; }
   if (M < 1) { g_create_err = "M must be >= 1"; return FSIB_EINVAL; }
   if (!(mu > 0) || !(dt > 0) || !std::isfinite(mu) || !std::isfinite(dt) || !std::isfinite(rho)) {
     g_create_err = "mu and dt must be positive and finite";
@@ -1512,7 +1522,7 @@ extern "C" {
 int fsib_spread_static(int N, int d, int M, double tol, int precision, const double* X, const double* F,
                        const double* omega, void* fhat, void* stream) {
   g_static_err.clear();
-  if ((d != 2 && d != 3) || N < 4 || N > 512 || (N % 2) || M < 1 || !(tol >= 1e-14 && tol <= 1e-2) ||
+  if ((d != 2 && d != 3) || N < 4 || N > 1024 || (N % 2) || M < 1 || !(tol >= 1e-14 && tol <= 1e-2) ||
       (precision != FSIB_FP64 && precision != FSIB_MIXED)) {
     g_static_err = "bad N, d, M, tol or precision";
     return FSIB_EINVAL;

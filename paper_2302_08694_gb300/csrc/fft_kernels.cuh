@@ -197,7 +197,7 @@ k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long 
   const long long npairs = nrows / 2;
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* a = tw + n;
-  C<T>* b = a + kQrows * 6 * ls;
+  C<T>* b = a + kQrows * np * ls;  // np >= d lines per row pair in each buffer
   const long long pr0 = (long long)blockIdx.x * kQrows;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[fl.tw_off + i];
   for (int t = threadIdx.x; t < kQrows * d * n; t += blockDim.x) {
@@ -674,10 +674,24 @@ static void with_fft_len(int n, F&& f) {
   }
 }
 
+// Shared memory of the block-level kernels: the twiddles (n) and two buffers of `lines` lines
+// of `ls` elements. Long lines take fewer lines per block, down to the fewest that fit the
+// opt-in limit (a power of two for the strided tiles); every length up to the largest
+// transform of a plan fits with one line pair per block.
+template <typename T>
+static int fit_lines(int want, int n, int lines_per_unit, int ls, bool pow2) {
+  int q = std::max(1, want);
+  while (q > 1 && sizeof(C<T>) * ((size_t)n + 2 * (size_t)q * lines_per_unit * ls) > smem_optin())
+    q = pow2 ? q / 2 : q - 1;
+  return q;
+}
+
 template <typename T, typename Tin, typename Tout>
 void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, int inner, int Nk,
-                        const FftLen& fl, bool inverse, Mult<T> mult, const C<T>* tw,
+                        const FftLen& flr, bool inverse, Mult<T> mult, const C<T>* tw,
                         cudaStream_t st, ZSkip zs) {
+  FftLen fl = flr;
+  fl.tile_p = fit_lines<T>(fl.tile_p, fl.n, 1, fl.n, true);
   const int kP = fl.tile_p;
   const int ntile = (inner + kP - 1) / kP;
   const long long blocks = (long long)ncomp * outer * ntile;
@@ -723,7 +737,8 @@ template <typename T>
 void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const FftLen& fl,
                          const C<T>* tw, cudaStream_t st, RowBands rb) {
   const long long npairs = nrows / 2;
-  const FftLen fs = small_rows(fl, npairs);
+  FftLen fs = small_rows(fl, npairs);
+  fs.rows_q = fit_lines<T>(fs.rows_q, fl.n, 1, fl.n + 1, false);
   const int kQrows = fs.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
@@ -747,7 +762,8 @@ template <typename T>
 void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const FftLen& fl,
                          const C<T>* tw, cudaStream_t st, RowBands rb) {
   const long long npairs = nrows / 2;
-  const FftLen fs = small_rows(fl, npairs);
+  FftLen fs = small_rows(fl, npairs);
+  fs.rows_q = fit_lines<T>(fs.rows_q, fl.n, 1, fl.n + 1, false);
   const int kQrows = fs.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * (fl.n + 1));
@@ -771,10 +787,12 @@ template <typename T>
 void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int Nk,
                          const FftLen& fl, const C<T>* tw, cudaStream_t st) {
   const long long npairs = nrows / 2;
-  const FftLen fs = small_rows(fl, npairs);
+  const int lp = (d == 3) ? 6 : 3;  // lines per row pair: max(d, d(d+1)/2)
+  FftLen fs = small_rows(fl, npairs);
+  fs.rows_q = fit_lines<T>(fs.rows_q, fl.n, lp, fl.n + 1, false);
   const int kQrows = fs.rows_q;
   const long long blocks = (npairs + kQrows - 1) / kQrows;
-  const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * 6 * (fl.n + 1));
+  const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * lp * (fl.n + 1));
   with_fft_len(fl.n, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
     constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;

@@ -53,7 +53,10 @@ __device__ __forceinline__ C<To> ccvt(const C<From>& i) {
 // 1-D FFT plan of one length n = 2^a 3^b (radix stages of 4, 2 and 3).
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 12;
-constexpr int kMaxFFT = 512;
+// Longest transform per axis: 2048 in 2D (N up to 1024 at sigma = 2); 512 in 3D, where a
+// fine grid of 512^3 cells per component keeps every element index within 32 bits.
+constexpr int kMaxFFT2 = 2048;
+constexpr int kMaxFFT3 = 512;
 
 struct FftLen {
   int n = 0;
@@ -252,5 +255,8 @@ void launch_vjp_combine(int d, int M, double s, double sigma, const double* Gu, 
 
 int check_last(const char* where);
 void raise_smem_limit(const void* kernel);
+// Dynamic shared memory a block of a kernel without static shared memory may request
+// (the device's opt-in limit per block).
+size_t smem_optin();
 
 }  // namespace fsib
