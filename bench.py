@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable workload block")
     ap.add_argument("--no-sweep", action="store_true", help="skip the NUFFT point-count sweep")
     ap.add_argument("--no-validation", action="store_true",
-                    help="skip the validation blocks (2D sine circle and Poiseuille channel, 3D spheres)")
+                    help="skip the validation blocks (2D sine circle, Poiseuille channel and Stokes circle, "
+                         "3D spheres)")
     ap.add_argument("--workload", choices=["ns3d_fp64", "ns3d_mixed", "ns2d_circle", "poiseuille",
                                            "sphere_elastic", "sphere_tension", "stokes2d"],
                     default="ns3d_fp64",
@@ -587,10 +588,11 @@ def _chunked_steps(torch, pb, X, u, U, total, chunk, flush, stream, probe=None):
 
 
 def validation_block(fsib, torch, dev, flush, cpu_sample=True):
-    """The paper's 2D Navier-Stokes checks, run on the library (FP64 transforms):
-    sine-velocity circle (Sec. 5.2.1: area over T = 10, temporal order at t = 0.1)
-    and the Poiseuille channel on target-point walls (Sec. 5.2.2: flux against
-    Eq. poiseuille_flux, effective boundary width against N)."""
+    """The paper's 2D checks, run on the library (FP64 transforms): sine-velocity circle
+    (Sec. 5.2.1: area over T = 10, temporal order at t = 0.1), the Poiseuille channel on
+    target-point walls (Sec. 5.2.2: flux against Eq. poiseuille_flux, effective boundary width
+    against N), and the Stokes circle with normal and tangent forces (Sec. 6.1: pressure jump,
+    convergence studies up to N = 1024, jump widths)."""
     from paper_2302_08694_gb300 import validation as va
     stream = torch.cuda.current_stream()
     out = {}
@@ -732,6 +734,130 @@ def validation_block(fsib, torch, dev, flush, cpu_sample=True):
         pbw.close()
     out["normal_circle_pressure"] = {"r": r, "Nb": Nb, "F": 1.0, "p_inside_exact": p_in, "p_outside_exact": p_out,
                                      "by_N": rows, "jump_width": widths}
+    out["stokes_circle"] = stokes_circle_block(fsib, torch, dev)
+    return out
+
+
+def stokes_circle_block(fsib, torch, dev):
+    """The paper's 2D Stokes circle studies (Sec. 6.1) on the library (FP64 transforms, Stokes,
+    mu = 1): a circle of radius r = L/4 at the centre carries N_b points with a unit force per
+    unit theta (weights 2 pi / N_b), either along the outward normal ('normal': u = 0, pressure
+    jump F/r) or along the clockwise tangent ('tangent': p constant, a circulating flow).
+    Reported: the coupling study at fixed N_b = 64 with N = 4 .. 1024, the first-order study with
+    N and N_b refined together (N = 8 .. 1024), the exponential convergence in N_b at N = 128,
+    and the width of the jump of du_x/dy across the circle on the vertical centreline."""
+    r = 0.25
+
+    def circle(Nb, kind):
+        th = 2 * np.pi * np.arange(Nb) / Nb
+        X = np.stack([0.5 + r * np.cos(th), 0.5 + r * np.sin(th)])
+        F = np.stack([np.cos(th), np.sin(th)]) if kind == "normal" else np.stack([np.sin(th), -np.cos(th)])
+        w = np.full(Nb, 2 * np.pi / Nb)
+        return [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (X, F, w)]
+
+    def solve(N, Nb, kind):
+        """(problem, f-hat, u-hat, U at the points) of one Stokes solve."""
+        X, F, w = circle(Nb, kind)
+        pb = fsib.Problem(N, 2, Nb, 1.0, 0.0, 1e-3, 1e-12)
+        fh = pb.spread(X, F, w)
+        uh = pb.new_spec(device=dev)
+        pb.fluid_step(fh, uh)
+        return pb, fh, uh, pb.interp(uh, X)
+
+    def at(N, spec, Y):
+        """Both components of a half spectrum at the points Y ([2][n])."""
+        probe = fsib.Problem(N, 2, Y.shape[1], 1.0, 0.0, 1e-3, 1e-12)
+        V = probe.interp(spec, torch.from_numpy(np.ascontiguousarray(Y)).to(dev)).cpu().numpy()
+        probe.close()
+        return V
+
+    def grid_points(N):
+        g = np.arange(N) / N
+        gy, gx = np.meshgrid(g, g, indexing="ij")
+        return np.stack([gx.ravel(), gy.ravel()])
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    p_in, p_out = -(1 - np.pi * r * r) / r, np.pi * r
+    out = {"r": r, "mu": 1.0, "F": 1.0}
+    # -- coupling of L/N and h_b: N_b = 64, N = 4 .. 1024 (Fig. circle:error_Nh)
+    Nb, Ns = 64, [2 ** k for k in range(2, 11)]
+    Nfine = Ns[-1]
+    _, _, ut_fine, Ut_fine = solve(Nfine, Nb, "tangent")
+    Ut_fine = Ut_fine.cpu().numpy()
+    rows = []
+    for N in Ns:
+        Yg = grid_points(N)
+        inside = np.hypot(Yg[0] - 0.5, Yg[1] - 0.5) < r
+        pbn, fhn, uhn, _ = solve(N, Nb, "normal")
+        P = at(N, torch.stack([pbn.pressure(fhn), torch.zeros_like(uhn[1])]), Yg)[0]
+        pex = np.where(inside, p_in, p_out)
+        pbt, fht, uht, Ut = solve(N, Nb, "tangent")
+        row = {"N": N, "h_b_over_h": 2 * np.pi * r / Nb * N,
+               "normal_p_grid_rel_err": rel(P, pex),
+               "normal_u_hat_max": float(uhn.abs().max()),
+               "tangent_p_hat_max": float(pbt.pressure(fht).abs().max())}
+        if N < Nfine:
+            row["tangent_U_points_rel_diff_vs_N1024"] = rel(Ut.cpu().numpy(), Ut_fine)
+            row["tangent_u_grid_rel_diff_vs_N1024"] = rel(at(N, uht, Yg), at(Nfine, ut_fine, Yg))
+        rows.append(row)
+        pbn.close()
+        pbt.close()
+    out["coupling_Nb64"] = rows
+    # -- N and N_b refined together, tangent case (Fig. u_Nh_h_comp): successive differences of U
+    # at the coarse points (theta_j of N_b is theta_2j of 2 N_b)
+    Us, diffs = [], []
+    for k in range(8):
+        N, Nbk = 8 * 2 ** k, 4 * 2 ** k
+        pbk, _, _, Uk = solve(N, Nbk, "tangent")
+        Us.append(Uk.cpu().numpy())
+        pbk.close()
+    for k in range(7):
+        diffs.append(rel(Us[k], Us[k + 1][:, ::2]))
+    out["tangent_refined_together"] = {
+        "N": [8 * 2 ** k for k in range(8)], "Nb": [4 * 2 ** k for k in range(8)],
+        "successive_rel_diff": diffs,
+        "orders": [float(np.log2(diffs[k] / diffs[k + 1])) for k in range(6)]}
+    # -- exponential convergence in N_b at N = 128 (Fig. err_2_N): centreline x = L/2, grid y
+    N = 128
+    Yc = np.stack([np.full(N, 0.5), np.arange(N) / N])
+    pexc = np.where(np.abs(Yc[1] - 0.5) < r, p_in, p_out)
+    perr, udiff, uprev, un, pt = [], [], None, [], []
+    for Nbk in (4, 8, 16, 32, 64):
+        pbn, fhn, uhn, _ = solve(N, Nbk, "normal")
+        perr.append(rel(at(N, torch.stack([pbn.pressure(fhn), torch.zeros_like(uhn[1])]), Yc)[0], pexc))
+        un.append(float(np.max(np.abs(at(N, uhn, Yc)))))
+        pbt, fht, uht, _ = solve(N, Nbk, "tangent")
+        ux = at(N, uht, Yc)[0]
+        pt.append(float(np.max(np.abs(at(N, torch.stack([pbt.pressure(fht), torch.zeros_like(uht[1])]), Yc)[0]))))
+        if uprev is not None:
+            udiff.append(rel(uprev, ux))
+        uprev = ux
+        pbn.close()
+        pbt.close()
+    out["Nb_convergence_N128"] = {"Nb": [4, 8, 16, 32, 64], "normal_p_centreline_rel_err": perr,
+                                  "normal_u_centreline_max": un, "tangent_p_centreline_max": pt,
+                                  "tangent_ux_centreline_successive_rel_diff": udiff}
+    # -- width of the jump of du_x/dy (Fig. reso_stokes, tangent case): the jump (F/(mu r)) over
+    # the steepest slope of du_x/dy on a fine probe line across the top of the circle
+    widths = []
+    for N in (32, 64, 128, 256):
+        Nbw = int(np.ceil(2 * np.pi * r * N))
+        pbw, _, uhw, _ = solve(N, Nbw, "tangent")
+        h = 1.0 / N
+        yf = np.linspace(0.5 + r - 4 * h, 0.5 + r + 4 * h, 801)
+        ux = at(N, uhw, np.stack([np.full_like(yf, 0.5), yf]))[0]
+        d1 = np.gradient(ux, yf)
+        yg = np.arange(N) * h
+        ug = at(N, uhw, np.stack([np.full_like(yg, 0.5), yg]))[0]
+        dg = (ug[2:] - ug[:-2]) / (2 * h)            # du_x/dy on the grid, central differences
+        widths.append({"N": N, "Nb": Nbw,
+                       "width_over_h_max_slope": float((1.0 / r) / np.max(np.abs(np.gradient(d1, yf))) / h),
+                       "width_over_h_grid": float((1.0 / r) / (np.max(np.abs(dg[2:] - dg[:-2])) / (2 * h)) / h),
+                       "dux_dy_change_over_8h": float(d1[-1] - d1[0])})
+        pbw.close()
+    out["tangent_dux_dy_jump_width"] = widths
     return out
 
 

@@ -48,7 +48,7 @@ def test_create_calls_reject_bad_arguments_before_any_device_work():
         (16, 3, -5, 1.0, 1.0, 1e-3, 1e-6, "M must be"),
         (7, 3, 10, 1.0, 1.0, 1e-3, 1e-6, "N must be"),          # odd N
         (2, 2, 10, 1.0, 1.0, 1e-3, 1e-6, "N must be"),          # below the smallest grid
-        (1024, 2, 10, 1.0, 1.0, 1e-3, 1e-6, "N must be"),       # above the largest grid
+        (1026, 2, 10, 1.0, 1.0, 1e-3, 1e-6, "N must be"),       # above the largest grid
         (16, 1, 10, 1.0, 1.0, 1e-3, 1e-6, "d must be"),
         (16, 4, 10, 1.0, 1.0, 1e-3, 1e-6, "d must be"),
         (16, 3, 10, 0.0, 1.0, 1e-3, 1e-6, "mu and dt"),         # viscosity must be positive
