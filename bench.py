@@ -735,6 +735,7 @@ def validation_block(fsib, torch, dev, flush, cpu_sample=True):
     out["normal_circle_pressure"] = {"r": r, "Nb": Nb, "F": 1.0, "p_inside_exact": p_in, "p_outside_exact": p_out,
                                      "by_N": rows, "jump_width": widths}
     out["stokes_circle"] = stokes_circle_block(fsib, torch, dev)
+    out["steady_poiseuille"] = steady_channel_block(fsib, torch, dev)
     return out
 
 
@@ -859,6 +860,48 @@ def stokes_circle_block(fsib, torch, dev):
         pbw.close()
     out["tangent_dux_dy_jump_width"] = widths
     return out
+
+
+def steady_channel_block(fsib, torch, dev):
+    """The paper's steady Poiseuille convergence study (Sec. 5.2.2): a channel of width D = L
+    bounded by one wall at y = 0 (periodic in y), mu = 0.1, f0 = 100, N = N_b = 8 .. 512, on the
+    library's Stokes path (FP64 transforms). At equilibrium the wall carries the force that
+    balances the body force, the same on every marker (the markers X_i = (i h, 0) are
+    equispaced), so it is spread with omega = h; the Stokeslet drops the k = 0 mode, so the
+    uniform body force acts only through the mean flow, which the no-slip condition fixes:
+    u = u_S - U_S(X_wall). Errors: relative 2-norm on the Eulerian grid of the line x = L/2
+    against Eq. steady_poiseuille_velo, with D and with the effective width D_e of the computed
+    flux (walls moved by (D - D_e)/2 into the fluid)."""
+    mu, f0, L = 0.1, 100.0, 1.0
+    rows = []
+    for k in range(7):
+        N = 8 * 2 ** k
+        h = L / N
+        X = np.stack([np.arange(N) * h, np.zeros(N)])
+        F = np.stack([np.full(N, -f0 * L * L / (N * h)), np.zeros(N)])   # sum_i omega F_i = -f0 L^2
+        Xt, Ft, wt = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (X, F, np.full(N, h))]
+        pb = fsib.Problem(N, 2, N, mu, 0.0, 1e-3, 1e-12)
+        uh = pb.new_spec(device=dev)
+        pb.fluid_step(pb.spread(Xt, Ft, wt), uh)
+        ubar = -float(pb.interp(uh, Xt)[0].mean())
+        pb.close()
+        yg = np.arange(N) * h
+        probe = fsib.Problem(N, 2, N, mu, 0.0, 1e-3, 1e-12)
+        ug = probe.interp(uh, torch.from_numpy(np.stack([np.full(N, 0.5), yg])).to(dev))[0].cpu().numpy() + ubar
+        probe.close()
+        flux = ubar * L   # the non-zero y modes integrate to zero over a period
+        De = (12.0 * mu * flux / f0) ** (1.0 / 3.0)
+        dlt = 0.5 * (L - De)
+        u_ex = f0 / (2 * mu) * yg * (L - yg)
+        u_e = np.where((yg > dlt) & (yg < L - dlt), f0 / (2 * mu) * (yg - dlt) * (L - dlt - yg), 0.0)
+        rows.append({"N": N, "Nb": N, "rel_err": float(np.linalg.norm(ug - u_ex) / np.linalg.norm(u_ex)),
+                     "rel_err_effective_width": float(np.linalg.norm(ug - u_e) / np.linalg.norm(u_e)),
+                     "effective_width_over_h": (L - De) / h})
+    e = [r["rel_err"] for r in rows]
+    ee = [r["rel_err_effective_width"] for r in rows]
+    return {"mu": mu, "f0": f0, "D": L, "by_N": rows,
+            "orders": [float(np.log2(e[i] / e[i + 1])) for i in range(len(e) - 1)],
+            "orders_effective_width": [float(np.log2(ee[i] / ee[i + 1])) for i in range(len(ee) - 1)]}
 
 
 def validation_3d_block(fsib, torch, dev, flush, max_refine=5):

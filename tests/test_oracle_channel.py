@@ -193,3 +193,35 @@ def test_half_spectrum_norm_and_embedding_follow_parseval():
         U2 = sp.interp_direct(sp.half_to_full(E, N + 4, d), P, N + 4)
         assert np.max(np.abs(U2 - U)) <= 1e-12 * np.max(np.abs(U))
     assert va.successive_errors([H, H]) == [0.0]
+
+
+def test_steady_channel_orders_follow_the_paper():
+    """Steady Poiseuille flow with one wall at y = 0 and D = L (Sec. 5.2.2): the wall force that
+    balances f0 L^2 is spread from N equispaced markers (omega = h), the Stokeslet gives the
+    flow without its mean, and no-slip at the wall fixes the mean. Against
+    Eq. steady_poiseuille_velo the error on the grid of the line x = L/2 is first order; with
+    the effective width D_e of the computed flux it converges faster, towards the paper's
+    order 3/2; Delta_e = D - D_e approaches the 0.4h of Fig. effective_width."""
+    mu, f0, L = 0.1, 100.0, 1.0
+    e, ee, width = [], [], []
+    for N in (16, 32, 64, 128, 256):
+        h = L / N
+        X = np.stack([np.arange(N) * h, np.zeros(N)])
+        F = np.stack([np.full(N, -f0 * L * L / (N * h)), np.zeros(N)])
+        u = sp.stokeslet(sp.spread_direct(X, F * h, N), N, mu)
+        ubar = -sp.interp_direct(u, X, N)[0].mean()
+        yg = np.arange(N) * h
+        ug = sp.interp_direct(u, np.stack([np.full(N, 0.5), yg]), N)[0] + ubar
+        De = va.effective_width(ubar * L, f0, mu)
+        dl = 0.5 * (L - De)
+        u_ex = f0 / (2 * mu) * yg * (L - yg)
+        u_e = np.where((yg > dl) & (yg < L - dl), f0 / (2 * mu) * (yg - dl) * (L - dl - yg), 0.0)
+        e.append(np.linalg.norm(ug - u_ex) / np.linalg.norm(u_ex))
+        ee.append(np.linalg.norm(ug - u_e) / np.linalg.norm(u_e))
+        width.append((L - De) / h)
+        assert abs(ug[0]) <= 1e-9 * np.max(np.abs(ug))    # no slip at the wall
+    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    orders_e = np.log2(np.array(ee[:-1]) / np.array(ee[1:]))
+    assert np.all(np.abs(orders - 1.0) < 0.1)
+    assert np.all(orders_e > 1.5) and np.all(np.diff(orders_e) < 0)   # decreasing towards 3/2
+    assert 0.40 < width[-1] < 0.42 and np.all(np.diff(width) < 0)
