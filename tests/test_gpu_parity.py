@@ -113,6 +113,39 @@ def test_interp_matches_oracle(lib, torch_mod, prec, d, N, M):
     assert rel2(to_np(U), ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("d", [2, 3])
+def test_points_on_the_period_boundary_and_on_grid_nodes(lib, torch_mod, prec, d):
+    """Coordinates that sit exactly on the period boundary (0, L, -L, 2L, one rounding step
+    either side of them), on fine-grid nodes k L / n_f and half-way between nodes, where the
+    periodic wrap and the window start round: both transforms still match the direct sums."""
+    torch = torch_mod
+    N = 16
+    nf = 2 * N   # fine grid at sigma = 2 (a multiple of 8 above 2w at both tolerances)
+    edge = [0.0, 1.0, -1.0, 2.0, np.nextafter(1.0, 0.0), np.nextafter(0.0, -1.0), np.nextafter(1.0, 2.0),
+            -1e-300, 3.0 / nf, 17.0 / nf, (nf - 1.0) / nf, 0.5 / nf, 5.5 / nf, 0.5, -0.5 / nf]
+    rng = np.random.default_rng(4242)
+    M = 60
+    X = np.empty((d, M))
+    for a in range(d):
+        X[a] = rng.choice(edge, M)
+    X[:, 0] = 0.0
+    X[:, 1] = np.nextafter(1.0, 0.0)
+    F = rng.standard_normal((d, M))
+    H = half_random(rng, d, N)
+    pb = make(lib, N, d, M, prec)
+    fh = pb.spread(cuda(X, torch), cuda(F, torch))
+    Hc = H.astype(CDT[prec])
+    U = pb.interp(cuda(Hc, torch), cuda(X, torch))
+    torch.cuda.synchronize()
+    ref = sp.full_to_half(sp.spread_direct(X, F, N), N)
+    got = to_np(fh)
+    assert rel2(got, ref) <= TOL[prec]
+    assert relmax(got, ref) <= 10 * TOL[prec]
+    Uref = sp.interp_direct(sp.half_to_full(Hc.astype(np.complex128), N, d), X, N)
+    assert rel2(to_np(U), Uref) <= TOL[prec]
+
+
 def test_spread_interp_host_pointers_match_device(lib, torch_mod):
     torch = torch_mod
     rng = np.random.default_rng(7)
