@@ -71,8 +71,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms; stop(t0, t1) keeps the
+    samples taken inside the timed region [t0, t1] (host wall clock), or all of them when
+    none falls inside (a region shorter than the sampling interval)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -81,12 +83,20 @@ class ClockSampler:
         self.proc = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                          "-i", str(gpu_index), "-lms", "20"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def _when(stamp):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except Exception:
+            return None
+
+    def stop(self, t0=None, t1=None):
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -98,19 +108,23 @@ class ClockSampler:
         rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
         self.f.close()
         os.unlink(self.f.name)
+        inside = [r for r in rows if t0 is not None and t1 is not None
+                  and (lambda w: w is not None and t0 <= w <= t1)(self._when(r[0]))]
+        use = inside or rows
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        for r in use:
             try:
-                sm.append(float(r[1]))
-                smax = max(smax, float(r[2]))
-                for k, v in zip(names, r[5:9]):
+                sm.append(float(r[2]))
+                smax = max(smax, float(r[3]))
+                for k, v in zip(names, r[6:10]):
                     if v.strip().lower() == "active":
                         reasons.add(k)
             except Exception:
                 continue
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "timed region" if inside else "whole sampling run"}
 
 
 NATIVE_FP64 = False
@@ -305,6 +319,8 @@ def measure(fsib, torch, prob, prec, steps, warmup, dev, flush, world=1, barrier
     ev = [_events(torch) for _ in range(steps)]
     if barrier:
         barrier()
+    torch.cuda.synchronize()
+    t_begin = time.time()
     for s in range(steps):
         flush.zero_()  # L2 flush between timed iterations (outside the events)
         ev[s][0].record(stream)
@@ -313,7 +329,7 @@ def measure(fsib, torch, prob, prec, steps, warmup, dev, flush, world=1, barrier
     if barrier:
         barrier()
     torch.cuda.synchronize()
-    clocks = sampler.stop() if sampler else None
+    clocks = sampler.stop(t_begin, time.time()) if sampler else None
     ms = sum(a.elapsed_time(b) for a, b in ev)
     launches = int(pb.info("launches_per_step"))
     # NUFFT throughput, type-1 and type-2 separately
