@@ -146,6 +146,31 @@ def test_points_on_the_period_boundary_and_on_grid_nodes(lib, torch_mod, prec, d
     assert rel2(to_np(U), Uref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("d", [2, 3])
+def test_all_points_at_one_place(lib, torch_mod, prec, d):
+    """The densest input the binning can meet: every point at the same position (one bin holds
+    them all, so the gather splits the boxes it reaches into the most slices), and a second
+    case with the points spread over one fine cell. Both transforms against the direct sums."""
+    torch = torch_mod
+    N, M = 16, 4000
+    rng = np.random.default_rng(99)
+    for X in (np.tile(rng.uniform(0, 1, (d, 1)), (1, M)), 0.3 + rng.uniform(0, 1.0 / 32, (d, M))):
+        F = rng.standard_normal((d, M))
+        H = half_random(rng, d, N)
+        pb = make(lib, N, d, M, prec)
+        fh = pb.spread(cuda(X, torch), cuda(F, torch))
+        Hc = H.astype(CDT[prec])
+        U = pb.interp(cuda(Hc, torch), cuda(X, torch))
+        torch.cuda.synchronize()
+        ref = sp.full_to_half(sp.spread_direct(X, F, N), N)
+        got = to_np(fh)
+        assert rel2(got, ref) <= TOL[prec]
+        assert relmax(got, ref) <= 10 * TOL[prec]
+        Uref = sp.interp_direct(sp.half_to_full(Hc.astype(np.complex128), N, d), X, N)
+        assert rel2(to_np(U), Uref) <= TOL[prec]
+
+
 def test_spread_interp_host_pointers_match_device(lib, torch_mod):
     torch = torch_mod
     rng = np.random.default_rng(7)
