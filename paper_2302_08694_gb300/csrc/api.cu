@@ -868,7 +868,7 @@ int fsib_create(fsib_t* out, int N, int d, int M, double mu, double rho, double 
       cudaEventCreateWithFlags(&h->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     g_create_err = "CUDA stream/event creation failed (no device?)";
-    delete h;
+    fsib_destroy(h);  // releases the streams and events created before the failure
     return FSIB_ECUDA;
   }
   rc = alloc_ws(h);

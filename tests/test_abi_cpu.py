@@ -81,3 +81,20 @@ def test_create_calls_reject_bad_arguments_before_any_device_work():
         assert "bad N, d, M, tol or precision" in lib.fsib_static_last_error().decode()
     assert lib.fsib_spread_static(16, 3, 8, 1e-6, 0, None, None, None, None, None) == -1
     assert "NULL array" in lib.fsib_static_last_error().decode()
+
+
+def test_create_without_a_device_fails_cleanly():
+    """With valid arguments and no GPU, fsib_create returns FSIB_ECUDA (-3) and a message, and
+    leaves the handle NULL (what it had created is released); no CPU fallback exists."""
+    import ctypes
+
+    import torch
+    if torch.cuda.is_available():
+        import pytest
+        pytest.skip("a GPU is present")
+    fbuild.build()
+    lib = fsib.load()
+    h = ctypes.c_void_p()
+    assert lib.fsib_create(ctypes.byref(h), 16, 3, 10, 1.0, 1.0, 1e-3, 1e-6) == -3
+    assert h.value is None
+    assert "no device" in lib.fsib_last_error(None).decode()
