@@ -25,6 +25,7 @@ struct fsib_plan {
   cudaStream_t side = nullptr;                        // second branch of a Navier-Stokes step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
   cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
+  cudaEvent_t ev_copy = nullptr;  // end of the copy of u-hat to host inside a step
   std::string err;
   bool ready = false;  // workspaces allocated for the current plan
   // per-launch-site profiler
@@ -36,7 +37,7 @@ struct fsib_plan {
   std::vector<cudaEvent_t> pool;
   // captured step graph
   cudaGraphExec_t gexec = nullptr;
-  const void* gkey[3] = {nullptr, nullptr, nullptr};
+  const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
   int graph_kernels = 0;
 };
 
@@ -675,8 +676,12 @@ static void do_force(fsib_plan* h, const double* X, double* c, cudaStream_t st) 
 }
 
 // One time step on device arrays (Algorithm 1, or the quasi-static Stokes midpoint rule).
+// u_in / u_out (Navier-Stokes, pinned host memory, or NULL): u-hat^m is copied in from u_in
+// at the head of the second stream's branch, so the copy overlaps the force, sort and type-1
+// NUFFT, and u-hat^{m+1} is copied out to u_out on the second stream beside the interps.
 template <typename TI, typename TA>
-static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_t st) {
+static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_t st,
+                    const void* u_in = nullptr, void* u_out = nullptr) {
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const long long dm = (long long)p.d * p.M;
@@ -692,6 +697,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
       cudaEventRecord(h->ev_fork, st);
       cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     }
+    if (u_in) cudaMemcpyAsync(uhat, u_in, ws.spec_bytes, cudaMemcpyHostToDevice, sb);
     const C<TA>* P0 = products<TI, TA>(h, uhat, sb, ws.s3, ws.s4);
     if (fork) cudaEventRecord(h->ev_join, h->side);
     do_axpy(h, ws.Xh, X, U, 0.5 * p.dt, st);                    // Eq. spatial_1
@@ -723,11 +729,16 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
       cudaEventRecord(h->ev_join2, h->side);
       cudaStreamWaitEvent(st, h->ev_join3, 0);
     }
+    if (u_out) {  // after the join point: the final interp does not wait for the copy
+      cudaMemcpyAsync(u_out, uhat, ws.spec_bytes, cudaMemcpyDeviceToHost, sb);
+      if (fork) cudaEventRecord(h->ev_copy, h->side);
+    }
     interp_points<TI>(h, (const TI*)ws.grid, ws.Uh, st);         // U^{m+1/2} at X^{m+1/2}
     do_axpy(h, X, X, ws.Uh, p.dt, st);                           // Eq. spatial_4
     do_bin(h, X, st);
     if (fork) cudaStreamWaitEvent(st, h->ev_join2, 0);
     interp_points<TI>(h, (const TI*)ws.grid2, U, st, true);      // U^{m+1} at X^{m+1}
+    if (u_out && fork) cudaStreamWaitEvent(st, h->ev_copy, 0);
   } else {
     // U(X^m)
     do_force(h, X, ws.cw, st);
@@ -760,6 +771,12 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
 static int fail(fsib_plan* h, int code, const std::string& msg) {
   if (h) h->err = msg;
   return code;
+}
+
+static bool is_pinned_host(const void* q) {
+  cudaPointerAttributes a;
+  if (!q || cudaPointerGetAttributes(&a, q) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeHost;
 }
 
 static bool is_device_ptr(const void* q) {
@@ -865,7 +882,8 @@ int fsib_create(fsib_t* out, int N, int d, int M, double mu, double rho, double 
       cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join3, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     g_create_err = "CUDA stream/event creation failed (no device?)";
     fsib_destroy(h);  // releases the streams and events created before the failure
@@ -899,6 +917,7 @@ int fsib_destroy(fsib_t h) {
   if (h->ev_join2) cudaEventDestroy(h->ev_join2);
   if (h->ev_fork3) cudaEventDestroy(h->ev_fork3);
   if (h->ev_join3) cudaEventDestroy(h->ev_join3);
+  if (h->ev_copy) cudaEventDestroy(h->ev_copy);
   if (h->own) cudaStreamDestroy(h->own);
   if (h->side) cudaStreamDestroy(h->side);
   delete h;
@@ -1249,19 +1268,24 @@ int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps) {
   if (!h->ws.force_kind) return fail(h, FSIB_ESTATE, "no force model set");
   const bool ns = !h->p.stokes;
   if (ns && (!uhat || !U)) return fail(h, FSIB_EINVAL, "Navier-Stokes step needs uhat and U");
+  // A single Navier-Stokes step on a pinned host u-hat copies it inside the step (see do_step),
+  // overlapped with work that does not read it; otherwise host arrays are staged around it.
+  const bool u_inside = ns && nsteps == 1 && !is_device_ptr(uhat) && is_pinned_host(uhat);
   Arg ax, au, aU;
   if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
-  if ((rc = stage(h, 3, uhat, spec_bytes(h), ns, au)) != FSIB_OK) return rc;
+  if ((rc = stage(h, 3, uhat, spec_bytes(h), ns && !u_inside, au)) != FSIB_OK) return rc;
   if ((rc = stage(h, 1, U, pts_bytes(h), ns, aU)) != FSIB_OK) return rc;
+  const void* u_in = u_inside ? au.host : nullptr;
+  void* u_out = u_inside ? au.host : nullptr;
   const bool f64 = h->p.prec == FSIB_FP64;
   auto enqueue = [&](cudaStream_t st) {
-    FSIB_DISPATCH(h, (do_step<float, float>(h, (double*)ax.dev, (C<float>*)au.dev, (double*)aU.dev, st)),
-                  (do_step<dd, double>(h, (double*)ax.dev, (C<double>*)au.dev, (double*)aU.dev, st)),
-                  (do_step<double, double>(h, (double*)ax.dev, (C<double>*)au.dev, (double*)aU.dev, st)));
+    FSIB_DISPATCH(h, (do_step<float, float>(h, (double*)ax.dev, (C<float>*)au.dev, (double*)aU.dev, st, u_in, u_out)),
+                  (do_step<dd, double>(h, (double*)ax.dev, (C<double>*)au.dev, (double*)aU.dev, st, u_in, u_out)),
+                  (do_step<double, double>(h, (double*)ax.dev, (C<double>*)au.dev, (double*)aU.dev, st, u_in, u_out)));
   };
   if (nsteps > 0) {
     if (h->p.use_graph && !h->prof_on) {
-      const void* key[3] = {ax.dev, au.dev, aU.dev};
+      const void* key[4] = {ax.dev, au.dev, aU.dev, u_in};
       if (!h->gexec || std::memcmp(key, h->gkey, sizeof(key)) != 0) {
         if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
         cudaGraph_t g = nullptr;
@@ -1283,7 +1307,7 @@ int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps) {
     }
   }
   if ((rc = unstage(h, ax)) != FSIB_OK) return rc;
-  if ((rc = unstage(h, au)) != FSIB_OK) return rc;
+  if (!u_inside && (rc = unstage(h, au)) != FSIB_OK) return rc;
   if ((rc = unstage(h, aU)) != FSIB_OK) return rc;
   const bool host = ax.host || au.host || aU.host;
   rc = finish(h, host || h->p.check_finite);

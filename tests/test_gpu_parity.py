@@ -294,6 +294,48 @@ def test_ns3d_steps_match_oracle(lib, torch_mod, prec):
     assert rel2(to_np(Ut), U) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_steps_on_host_buffers_match_device_buffers(lib, torch_mod, prec):
+    """fsib_step on host arrays: a single step on a pinned u-hat copies it inside the step
+    (beside work that does not read it), pageable arrays and multi-step calls are staged
+    around it, and the profiling mode runs the same copies in line. Every form gives the
+    device-array result (to rounding: the order of points within a bin is not fixed)."""
+    torch = torch_mod
+    N, dt, mu, rho = 12, 2e-3, 0.01, 1.0
+    Xref, tri = wl.latlong_sphere(6, 12, 0.25, (0.52, 0.47, 0.5))
+    X0 = 0.5 + (Xref - 0.5) * np.array([[1.15], [0.9], [1.0]])
+    M = X0.shape[1]
+    rng = np.random.default_rng(55)
+    u0 = sp.full_to_half(0.1 * sp.leray(sp.half_to_full(half_random(rng, 3, N), N, 3), N), N).astype(CDT[prec])
+    pb = make(lib, N, 3, M, prec, mu=mu, rho=rho, dt=dt)
+    pb.set_force_mesh(tri, cuda(Xref, torch), 1.0)
+    U0 = to_np(pb.interp(cuda(u0, torch), cuda(X0, torch)))
+
+    def run(kind, nsteps, profile=False):
+        if kind == "device":
+            X, u, U = cuda(X0, torch), cuda(u0, torch), cuda(U0, torch)
+        elif kind == "pinned":
+            X, u, U = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (X0, u0, U0))
+        else:
+            X, u, U = X0.copy(), u0.copy(), U0.copy()
+        pb.profile(profile)
+        for _ in range(2):   # twice: the second call replays the captured graph
+            pb.step(X, u, U, nsteps=nsteps)
+        pb.profile(False)
+        torch.cuda.synchronize()
+        return [a.detach().cpu().numpy() if hasattr(a, "detach") else a for a in (X, u, U)]
+
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for nsteps in (1, 2):
+        ref = run("device", nsteps)
+        for kind, prof in (("pinned", False), ("pageable", False), ("pinned", True)):
+            got = run(kind, nsteps, prof)
+            assert rel2(got[0] - X0, ref[0] - X0) <= tol, (kind, nsteps, prof)
+            assert rel2(got[1], ref[1]) <= tol, (kind, nsteps, prof)
+            assert rel2(got[2], ref[2]) <= tol, (kind, nsteps, prof)
+            assert np.max(np.abs(got[1] - u0)) > 0      # the host u-hat was written back
+
+
 def test_step_graph_and_direct_agree(lib, torch_mod):
     torch = torch_mod
     N, M = 16, 64
