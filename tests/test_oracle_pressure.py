@@ -91,3 +91,20 @@ def test_pressure_jump_width_is_a_fixed_multiple_of_h():
         widths.append((1.0 / r) / (np.max(np.abs(P[2:] - P[:-2])) / (2 * h)) / h)
     assert 1.5 < widths[-1] < 2.5
     assert abs(widths[0] - widths[-1]) < 0.02 * widths[-1]
+
+
+def test_trivial_solutions_vanish_below_the_transition():
+    """Sec. 6.1, coupling of L/N and h_b (Fig. circle:error_Nh): with N_b = 64 markers on the
+    circle r = L/4 the solutions that should vanish (the normal case's velocity, the tangent
+    case's pressure) are at rounding level while the marker spacing h_b = 2 pi r / N_b is
+    below the grid spacing h = L/N (N < 41), and are not once it is above it."""
+    r, Nb = 0.25, 64
+    Xn, cn = _circle(Nb, r, True)
+    Xt, ct = _circle(Nb, r, False)
+    for N in (8, 16, 32, 48, 64):
+        un = np.max(np.abs(sp.stokeslet(sp.spread_direct(Xn, cn, N), N, 1.0)))
+        pt = np.max(np.abs(sp.pressure(sp.spread_direct(Xt, ct, N), None, N, 1.0)))
+        if 2 * math.pi * r / Nb < 1.0 / N:
+            assert un <= 1e-15 and pt <= 1e-13, (N, un, pt)
+        else:
+            assert un >= 1e-9 and pt >= 1e-7, (N, un, pt)
