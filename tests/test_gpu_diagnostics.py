@@ -84,6 +84,33 @@ def test_normal_circle_pressure_through_the_library(lib, torch_mod):
     assert abs(P[0] + (1 - math.pi * r * r) / r) < 0.02 * (1 - math.pi * r * r) / r
 
 
+def test_circle_trivial_solutions_vanish_below_the_transition(lib, torch_mod):
+    """Sec. 6.1 coupling study (Fig. circle:error_Nh), FP64 through the library: N_b = 64
+    markers on the circle r = L/4; while h_b < h (N < 41) the normal case's velocity and the
+    tangent case's pressure are at the NUFFT tolerance, beyond it they are not."""
+    torch = torch_mod
+    r, Nb = 0.25, 64
+    th = 2 * math.pi * np.arange(Nb) / Nb
+    X = cuda(np.stack([0.5 + r * np.cos(th), 0.5 + r * np.sin(th)]), torch)
+    w = cuda(np.full(Nb, 2 * math.pi / Nb), torch)
+    Fn = cuda(np.stack([np.cos(th), np.sin(th)]), torch)
+    Ft = cuda(np.stack([np.sin(th), -np.cos(th)]), torch)
+    for N in (16, 32, 64):
+        pb = lib.Problem(N, 2, Nb, 1.0, 0.0, 1e-3, 1e-12)
+        fn = pb.spread(X, Fn, w)
+        un = pb.new_spec()
+        pb.fluid_step(fn, un)
+        pt = pb.pressure(pb.spread(X, Ft, w))
+        torch.cuda.synchronize()
+        scale = float(torch.abs(fn).max())
+        a, b = float(torch.abs(un).max()) / scale, float(torch.abs(pt).max()) / scale
+        if 2 * math.pi * r / Nb < 1.0 / N:
+            assert a <= 1e-12 and b <= 1e-12, (N, a, b)
+        else:
+            assert a >= 1e-8 and b >= 1e-5, (N, a, b)
+        pb.close()
+
+
 def dirichlet_odd(s, n, L=1.0):
     """Odd-order Dirichlet kernel sin(n pi s/L) / (L sin(pi s/L)), value n/L at s = 0 (mod L)."""
     s = np.asarray(s, dtype=np.float64)
