@@ -108,3 +108,19 @@ def test_trivial_solutions_vanish_below_the_transition():
             assert un <= 1e-15 and pt <= 1e-13, (N, un, pt)
         else:
             assert un >= 1e-9 and pt >= 1e-7, (N, un, pt)
+
+
+def test_tangent_circle_is_first_order_when_refined_together():
+    """Sec. 6.1 (Fig. u_Nh_h_comp): with N and N_b doubled together (N = 8 N_b / 4 ... here
+    N = 64 .. 512, N_b = N / 2) the velocity of the tangent case at the markers converges at
+    first order: successive differences at the common markers halve at each refinement."""
+    r = 0.25
+
+    def velocity(N, Nb):
+        X, c = _circle(Nb, r, False)
+        return sp.interp_direct(sp.stokeslet(sp.spread_direct(X, c, N), N, 1.0), X, N)
+
+    U = [velocity(N, N // 2) for N in (64, 128, 256, 512)]
+    d = [np.linalg.norm(U[k] - U[k + 1][:, ::2]) / np.linalg.norm(U[k + 1][:, ::2]) for k in range(3)]
+    orders = [math.log2(d[k] / d[k + 1]) for k in range(2)]
+    assert all(0.9 < q < 1.3 for q in orders), orders
