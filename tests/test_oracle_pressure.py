@@ -111,9 +111,10 @@ def test_trivial_solutions_vanish_below_the_transition():
 
 
 def test_tangent_circle_is_first_order_when_refined_together():
-    """Sec. 6.1 (Fig. u_Nh_h_comp): with N and N_b doubled together (N = 8 N_b / 4 ... here
-    N = 64 .. 512, N_b = N / 2) the velocity of the tangent case at the markers converges at
-    first order: successive differences at the common markers halve at each refinement."""
+    """Sec. 6.1 (Fig. u_Nh_h_comp): with N and N_b doubled together (N_b = N / 2, from the
+    paper's N = 8, N_b = 4; here the asymptotic range N = 64 .. 512) the velocity of the
+    tangent case at the markers converges at first order: successive differences at the
+    common markers halve at each refinement."""
     r = 0.25
 
     def velocity(N, Nb):
