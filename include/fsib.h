@@ -174,6 +174,12 @@ int fsib_fluid_step(fsib_t h, const void* fhat, void* uhat, void* uhat_half);
  * Stokes: X^{m+1} = X^m + dt U(X^{m+1/2}), X^{m+1/2} = X^m + dt/2 U(X^m),
  *   U(X) = interp(Stokeslet(spread(F(X), X)), X); uhat and U may be NULL
  *   (when given, U receives U(X^{m+1/2}) of the last step).
+ * Host arrays are copied to device buffers before the steps and back after them.
+ * For one Navier-Stokes step (nsteps = 1) on a page-locked host uhat, uhat is
+ * copied inside the step instead, beside work that does not read it (the
+ * force, the sort and the type-1 NUFFT; the final interpolations), so the
+ * copies cost less than their transfer time. Synchronous when any array is
+ * on the host.
  * Needs a force model. */
 int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps);
 
