@@ -180,3 +180,44 @@ def test_3d_membrane_ns_step_small():
     assert sp.max_divergence(u1, N) <= 1e-14
     assert np.max(np.abs(u1[:, 0, 0, 0])) <= 1e-17
     assert abs(lg.enclosed_volume(X1, tri) / V0 - 1) < 1e-6
+
+
+# P14 for the quasi-static Stokes stepper (reading C12) ----------------------------------------
+
+def test_stokes_midpoint_step_is_second_order_against_an_ode_solver():
+    """The quasi-static Stokes stepper advances dX/dt = U(X), U = interp(Stokeslet(spread(F(X)))),
+    by the midpoint rule of Eqs. spatial_1 and spatial_4 (X^{m+1/2} = X^m + dt/2 U(X^m),
+    X^{m+1} = X^m + dt U(X^{m+1/2})). Against an independent high-accuracy solution of the same
+    ODE (scipy's DOP853 at rtol 1e-13) its error falls by 4 when dt halves. A forward-Euler step,
+    a second stage evaluated at X^m, or an average of the two stage velocities would each fall
+    by 2, and fail."""
+    integrate = pytest.importorskip("scipy.integrate")
+    N, M, mu, T = 8, 16, 1.0, 0.05
+    X0 = wl.ellipse(M, 0.3, 0.15, (0.47, 0.52))
+    force = st.curve_model(1.0)
+
+    def rhs(t, y):
+        return st.stokes_velocity(y.reshape(2, M), force, N, mu).ravel()
+
+    ref = integrate.solve_ivp(rhs, (0.0, T), X0.ravel(), method="DOP853", rtol=1e-13,
+                              atol=1e-15).y[:, -1].reshape(2, M)
+    assert np.linalg.norm(ref - X0) > 1e-3  # the boundary moves well above the errors measured
+
+    def run(step, n):
+        X = X0.copy()
+        for _ in range(n):
+            X = step(X, T / n)
+        return X
+
+    def ratios(step):
+        e = [np.linalg.norm(run(step, n) - ref) for n in (4, 8, 16, 32)]
+        return [e[i] / e[i + 1] for i in range(3)]
+
+    midpoint = ratios(lambda X, dt: st.stokes_step(X, force, N, mu, dt))
+    assert all(3.8 < r < 4.2 for r in midpoint), midpoint
+    # plausible mistakes, written here, are first order
+    euler = ratios(lambda X, dt: X + dt * st.stokes_velocity(X, force, N, mu))
+    averaged = ratios(lambda X, dt: X + 0.5 * dt * (st.stokes_velocity(X, force, N, mu) + st.stokes_velocity(
+        X + 0.5 * dt * st.stokes_velocity(X, force, N, mu), force, N, mu)))
+    for r in (euler, averaged):
+        assert all(1.8 < q < 2.2 for q in r), r
