@@ -9,8 +9,9 @@ no-slip walls, viscosity mu, density rho:
   D_e     = (12 mu Phi / f0)^(1/3), the channel width that carries flux Phi, and the
             effective boundary width Delta_e = D - D_e.
 
-These are host-side formulas for reporting; the flux of a computed velocity comes
-from the library (fsib_band_flux).
+The oracle's channel pins (test_oracle_channel.py) check the oracle against these
+formulas; they are written from the paper's equations and share nothing with the
+oracle or the library.
 """
 from __future__ import annotations
 

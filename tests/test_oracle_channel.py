@@ -13,7 +13,7 @@ import pytest
 from oracle import lagrangian as lg
 from oracle import spectral as sp
 from oracle import stepper as st
-from paper_2302_08694_gb300 import validation as va
+import closed_forms as va
 from paper_2302_08694_gb300 import workloads as wl
 
 
