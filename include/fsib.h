@@ -91,6 +91,11 @@ int fsib_set_stream(fsib_t h, void* stream);
  *  "fft_tile", "fft_rows", "spread_slice": launch shapes, see fsib_autotune
  *  "check_finite" 1 = fsib_step checks positions for NaN/Inf at the end
  *               (adds a synchronisation), 0 = no check (default)
+ *  "spread_sum" FSIB_MIXED gather spreads (appendix A.1, Eq. type1_conv): how each
+ *               fine-grid cell sums its terms in FP32. 0 = plain FMAs; 1 = every
+ *               term into a compensated (TwoSum) sum; 2 = the terms of each staged
+ *               chunk of candidate points with FMAs, the chunk sums into a
+ *               compensated sum (default). FSIB_FP64 mode ignores it.
  * Returns FSIB_EINVAL for an unknown key or out-of-range value. */
 int fsib_set_option(fsib_t h, const char* key, double value);
 
@@ -169,8 +174,11 @@ int fsib_fluid_step(fsib_t h, const void* fhat, void* uhat, void* uhat_half);
  *   (fsib_interp gives U^0). U^{m+1} is interpolated at X^{m+1} after the
  *   position update, from a fine grid computed only near the windows at
  *   X^{m+1/2} (within one box of 8 fine cells): a point that moves farther in
- *   half a step (far beyond a stable dt) gets NaN in U^{m+1}, which the
- *   "check_finite" option reports on the next step.
+ *   half a step (far beyond a stable dt) gets NaN in U^{m+1} and the handle
+ *   records it. The first fsib_step, fsib_interp or fsib_invariants call that
+ *   starts after the GPU has finished that step returns FSIB_ENONFINITE (and
+ *   clears the record) without running; a synchronous step (host arrays, or
+ *   "check_finite" set) returns it at once.
  * Stokes: X^{m+1} = X^m + dt U(X^{m+1/2}), X^{m+1/2} = X^m + dt/2 U(X^m),
  *   U(X) = interp(Stokeslet(spread(F(X), X)), X); uhat and U may be NULL
  *   (when given, U receives U(X^{m+1/2}) of the last step).
@@ -298,9 +306,18 @@ int fsib_measure_peak(int kind, double* gflops);
  * mixed N > 64 at moderate M) or an argument is invalid.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. All calls share the one array, which keeps the previous
- * call's contents (the call clears what must start at zero): calls that overlap
- * on the GPU, from several streams or host threads, race on it. */
+ * any stream capture. Every later call made outside stream capture looks the
+ * address up again (after a device reset the array is new and empty).
+ * The twiddle and deconvolution tables are built on the host and copied into the
+ * array by the first call for a given (device, N, d, tol, precision), which waits
+ * for that copy (a stream synchronisation); later calls with the same values
+ * reuse them and enqueue kernels and memsets only. Under stream capture a call
+ * whose tables are not there returns FSIB_EINVAL without enqueueing anything:
+ * make one call with the same values outside capture first.
+ * All calls share the one array, which keeps the previous call's contents (the
+ * call clears what must start at zero; a call with other sizes replaces the
+ * tables): calls that overlap on the GPU, from several streams or host threads,
+ * race on it. */
 int fsib_spread_static(int N, int d, int M, double tol, int precision, const double* X,
                        const double* F, const double* omega, void* fhat, void* stream);
 

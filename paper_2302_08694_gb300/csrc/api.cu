@@ -272,6 +272,8 @@ static void free_ws(Workspace& ws) {
     if (ws.stage[i]) cudaFree(ws.stage[i]);
     ws.stage[i] = nullptr; ws.stage_bytes[i] = 0;
   }
+  if (ws.miss_host) cudaFreeHost(ws.miss_host);
+  ws.miss_host = ws.miss_dev = nullptr;
 }
 
 static void free_mesh(Workspace& ws) {
@@ -368,6 +370,17 @@ static int alloc_ws(fsib_plan* h) {
   // (and at most 16 per box: dense point sets get larger slices)
   ws.part_slots = (d == 3) ? (size_t)std::min<long long>(2 * 27 * (long long)p.M / kMinSlice + 64, 16LL * p.nbins) : 1;
   rc |= dmalloc(&ws.part, sizeof(double) * 3 * 512 * ws.part_slots, tot);
+  if (cudaHostAlloc((void**)&ws.miss_host, sizeof(unsigned int), cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    ws.miss_host = nullptr;
+    rc |= FSIB_ENOMEM;
+  } else {
+    *ws.miss_host = 0u;
+    if (cudaHostGetDevicePointer((void**)&ws.miss_dev, ws.miss_host, 0) != cudaSuccess) {
+      cudaGetLastError();
+      rc |= FSIB_ENOMEM;
+    }
+  }
   if (rc != FSIB_OK) { free_ws(ws); h->err = "device allocation failed"; return FSIB_ENOMEM; }
   g_ws_bytes = tot;
 
@@ -606,11 +619,13 @@ void spread_points<double>(fsib_plan* h, const double* c, const double* omega, d
   launch_spread<double>(h->p, h->ws, c, omega, grid, st);
 }
 // guarded: the grid holds only the widened bands of an earlier binning (inverse_fine mode 2);
-// a point whose window leaves them gets NaN, which the non-finite checks report.
+// a point whose window leaves them gets NaN and raises the handle's miss flag, which the next
+// fsib_step, fsib_interp or fsib_invariants turns into FSIB_ENONFINITE (take_miss).
 template <typename TI>
 static void interp_points(fsib_plan* h, const TI* grid, double* U, cudaStream_t st, bool guarded) {
   Prof pr(h, "interp", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
-  launch_interp_warp<TI>(h->p, h->ws, grid, U, st, guarded ? h->ws.band_dil : nullptr);
+  launch_interp_warp<TI>(h->p, h->ws, grid, U, st, guarded ? h->ws.band_dil : nullptr,
+                         guarded ? h->ws.miss_dev : nullptr);
 }
 template <>
 void interp_points<double>(fsib_plan* h, const double* grid, double* U, cudaStream_t st, bool) {
@@ -796,6 +811,19 @@ static int begin(fsib_plan* h) {
   return FSIB_OK;
 }
 
+// Report (once) a velocity that a finished step could not interpolate: a point moved more than
+// one box of the fine grid in half a step, beyond the rows computed for U^{m+1}. The flag lives
+// in mapped host memory, so this reads it without a synchronisation; a step still running on
+// the GPU is reported by a later call.
+static int take_miss(fsib_plan* h) {
+  volatile unsigned int* f = h->ws.miss_host;
+  if (!f || *f == 0u) return FSIB_OK;
+  *f = 0u;
+  return fail(h, FSIB_ENONFINITE,
+              "U^{m+1} is NaN at points that moved more than one box (8 fine cells) in half a step; "
+              "the time step is far beyond a stable one");
+}
+
 static int finish(fsib_plan* h, bool sync) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(h, FSIB_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));
@@ -963,6 +991,11 @@ int fsib_set_option(fsib_t h, const char* key, double v) {
     h->p.slice = (int)v;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     return FSIB_OK;
+  } else if (k == "spread_sum") {
+    if (!(v == 0 || v == 1 || v == 2)) return fail(h, FSIB_EINVAL, "spread_sum must be 0, 1 or 2");
+    h->p.spread_sum = (int)v;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    return FSIB_OK;
   } else if (k == "native_fp64") {
     q.native_fp64 = (v != 0);
   } else if (k == "graph") {
@@ -997,6 +1030,7 @@ int fsib_get_info(fsib_t h, const char* key, double* value) {
   else if (k == "fft_tile") *value = p.fft_p;
   else if (k == "fft_rows") *value = p.fft_q;
   else if (k == "spread_slice") *value = p.slice;
+  else if (k == "spread_sum") *value = p.spread_sum;
   else if (k == "workspace_bytes") *value = (double)g_ws_bytes;
   else if (k == "launches_per_step") *value = h->graph_kernels;
   else return fail(h, FSIB_EINVAL, "unknown info key: " + k);
@@ -1202,6 +1236,7 @@ int fsib_spread(fsib_t h, const double* X, const double* F, const double* omega,
 int fsib_interp(fsib_t h, const void* uhat, const double* X, double* U) {
   int rc = begin(h);
   if (rc != FSIB_OK) return rc;
+  if ((rc = take_miss(h)) != FSIB_OK) return rc;
   if (!X || !U || !uhat) return fail(h, FSIB_EINVAL, "NULL array");
   Arg ax, au, ah;
   if ((rc = stage(h, 0, X, pts_bytes(h), true, ax)) != FSIB_OK) return rc;
@@ -1263,6 +1298,7 @@ static int count_kernel_nodes(cudaGraph_t g) {
 int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps) {
   int rc = begin(h);
   if (rc != FSIB_OK) return rc;
+  if ((rc = take_miss(h)) != FSIB_OK) return rc;
   if (!X) return fail(h, FSIB_EINVAL, "X is NULL");
   if (nsteps < 0) return fail(h, FSIB_EINVAL, "nsteps < 0");
   if (!h->ws.force_kind) return fail(h, FSIB_ESTATE, "no force model set");
@@ -1312,6 +1348,9 @@ int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps) {
   const bool host = ax.host || au.host || aU.host;
   rc = finish(h, host || h->p.check_finite);
   if (rc != FSIB_OK) return rc;
+  if (host || h->p.check_finite) {
+    if ((rc = take_miss(h)) != FSIB_OK) return rc;  // the steps have finished: report at once
+  }
   if (h->p.check_finite) {
     double inv[6];
     const int r2 = f64 ? run_invariants<double>(h->p, h->ws, (const double*)ax.dev, nullptr, inv, h->own)
@@ -1325,6 +1364,7 @@ int fsib_step(fsib_t h, double* X, void* uhat, double* U, int nsteps) {
 int fsib_invariants(fsib_t h, const double* X, const void* uhat, double out[6]) {
   int rc = begin(h);
   if (rc != FSIB_OK) return rc;
+  if ((rc = take_miss(h)) != FSIB_OK) return rc;
   if (!X || !out) return fail(h, FSIB_EINVAL, "NULL array");
   if (h->p.d == 3 && h->ws.force_kind != 3 && !h->ws.tri)
     return fail(h, FSIB_ESTATE, "3D invariants need the mesh (fsib_set_force_mesh)");
@@ -1336,6 +1376,10 @@ int fsib_invariants(fsib_t h, const double* X, const void* uhat, double out[6]) 
   else
     rc = run_invariants<float>(h->p, h->ws, (const double*)ax.dev, (const C<float>*)au.dev, out, h->own);
   const int rc2 = finish(h, true);
+  if (rc2 == FSIB_OK && rc == FSIB_OK) {
+    const int rc3 = take_miss(h);  // a step that finished during this call
+    if (rc3 != FSIB_OK) return rc3;
+  }
   if (rc == FSIB_ENONFINITE) return fail(h, rc, "non-finite values in X or uhat");
   if (rc != FSIB_OK) return fail(h, rc, "invariant reduction failed");
   return rc2;
@@ -1399,11 +1443,24 @@ static __device__ __align__(256) unsigned char g_static_scratch[FSIB_STATIC_SCRA
 
 // Device address of g_static_scratch per device. In host code the symbol name is
 // only a host-side stand-in, so the address must come from cudaGetSymbolAddress
-// with the device current.
+// with the device current. The address is looked up again on every call made
+// outside stream capture: after a device reset the module is loaded anew and the
+// array may sit elsewhere (its contents, the cached tables included, are gone).
 static std::mutex g_static_mu;
 static void* g_static_addr[64] = {nullptr};
 
-static int static_scratch_base(void** out, std::string& err) {
+// Twiddle and deconvolution tables last uploaded into each device's scratch, by the
+// sizes that fix them. A call with the same sizes uploads nothing, so it can run under
+// stream capture; the tables sit at the start of the scratch, at offsets fixed by
+// (n_f, N, precision) alone.
+struct StaticTables {
+  void* base = nullptr;
+  int N = 0, d = 0, nf = 0, w = 0, prec = -1;
+  double beta = 0.0;
+};
+static StaticTables g_static_tab[64];
+
+static int static_scratch_base(void** out, int* dev_out, bool capturing, std::string& err) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
@@ -1411,7 +1468,12 @@ static int static_scratch_base(void** out, std::string& err) {
     return FSIB_ECUDA;
   }
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_addr[dev]) {
+  if (capturing) {
+    if (!g_static_addr[dev]) {
+      err = "the first fsib_spread_static call on a device must come before any stream capture";
+      return FSIB_EINVAL;
+    }
+  } else {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || !p) {
@@ -1419,9 +1481,11 @@ static int static_scratch_base(void** out, std::string& err) {
       err = std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e);
       return FSIB_ECUDA;
     }
+    if (p != g_static_addr[dev]) g_static_tab[dev] = StaticTables();  // a new module: no tables yet
     g_static_addr[dev] = p;
   }
   *out = g_static_addr[dev];
+  *dev_out = dev;
   return FSIB_OK;
 }
 
@@ -1449,11 +1513,20 @@ static int spread_static_impl(const Plan& p, const double* X, const double* F, c
   const long long s1n = (d == 3) ? d * n * n * hh : d * n * hh;
   const long long s2n = (d == 3) ? d * n * N * hh : 1;
   const long long dpn = (d == 3) ? N * hh : hh;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    g_static_err = "cudaStreamIsCapturing failed on the given stream";
+    return FSIB_ECUDA;
+  }
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
 
-  // Layout pass (base = null) to size the request, then the real carve.
+  // Layout pass (base = null) to size the request, then the real carve. The tables come
+  // first, so their offsets depend on (n_f, N, precision) only.
   Workspace ws;
   size_t need = 0;
   unsigned char* base = nullptr;
+  int dev = 0;
   for (int pass = 0; pass < 2; ++pass) {
     Carver c{base};
     ws.tw = c.take<void>((size_t)n * cs);
@@ -1480,39 +1553,64 @@ static int spread_static_impl(const Plan& p, const double* X, const double* F, c
         return FSIB_EINVAL;
       }
       void* b = nullptr;
-      const int rc = static_scratch_base(&b, g_static_err);
+      const int rc = static_scratch_base(&b, &dev, capturing, g_static_err);
       if (rc != FSIB_OK) return rc;
       base = static_cast<unsigned char*>(b);
     }
   }
 
-  // Host tables (twiddles of the fine grid, per-axis deconvolution), copied into the scratch.
-  const double pi = 3.14159265358979323846;
-  std::vector<T> tw(2 * (size_t)n), D(N), Dp(dpn);
-  for (long long j = 0; j < n; ++j) {
-    const double ang = 2.0 * pi * (double)j / (double)n;
-    tw[2 * j] = (T)std::cos(ang);
-    tw[2 * j + 1] = (T)(-std::sin(ang));
+  // Twiddles of the fine grid and per-axis deconvolution: uploaded once per device and sizes.
+  bool have;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    const StaticTables& t = g_static_tab[dev];
+    have = t.base == base && t.N == p.N && t.d == p.d && t.nf == p.nf && t.w == p.w && t.beta == p.beta &&
+           t.prec == p.prec;
   }
-  std::vector<double> zq, wq, Dd(N);
-  gauss_legendre(std::max(64, 4 * p.w + 64), zq, wq);
-  const double hf = p.L / p.nf;
-  for (long long i = 0; i < N; ++i) {
-    const long long m = (i < N / 2) ? i : i - N;
-    Dd[i] = (i == N / 2) ? 0.0 : hf / psi_hat(2.0 * pi * m / p.L, p.w, p.beta, hf, zq, wq);
-    D[i] = (T)Dd[i];
+  cudaError_t e = cudaSuccess;
+  if (!have) {
+    if (capturing) {
+      g_static_err = "the tables for these sizes are not in the static scratch: make one call with the same "
+                     "N, d, tol and precision outside stream capture first";
+      return FSIB_EINVAL;
+    }
+    const double pi = 3.14159265358979323846;
+    std::vector<T> tw(2 * (size_t)n), D(N), Dp(dpn);
+    for (long long j = 0; j < n; ++j) {
+      const double ang = 2.0 * pi * (double)j / (double)n;
+      tw[2 * j] = (T)std::cos(ang);
+      tw[2 * j + 1] = (T)(-std::sin(ang));
+    }
+    std::vector<double> zq, wq, Dd(N);
+    gauss_legendre(std::max(64, 4 * p.w + 64), zq, wq);
+    const double hf = p.L / p.nf;
+    for (long long i = 0; i < N; ++i) {
+      const long long m = (i < N / 2) ? i : i - N;
+      Dd[i] = (i == N / 2) ? 0.0 : hf / psi_hat(2.0 * pi * m / p.L, p.w, p.beta, hf, zq, wq);
+      D[i] = (T)Dd[i];
+    }
+    for (long long q = 0; q < dpn; ++q) Dp[q] = (T)((d == 3) ? Dd[q / hh] * Dd[q % hh] : Dd[q]);
+    // the host vectors die with this scope: the copies complete before it ends
+    e = cudaMemcpyAsync(ws.tw, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws.dline, D.data(), D.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws.dplane, Dp.data(), Dp.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g_static_err = std::string("table upload: ") + cudaGetErrorString(e);
+      return FSIB_ECUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    StaticTables& t = g_static_tab[dev];
+    t.base = base; t.N = p.N; t.d = p.d; t.nf = p.nf; t.w = p.w; t.beta = p.beta; t.prec = p.prec;
   }
-  for (long long q = 0; q < dpn; ++q) Dp[q] = (T)((d == 3) ? Dd[q / hh] * Dd[q % hh] : Dd[q]);
-  cudaError_t e = cudaMemcpyAsync(ws.tw, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ws.dline, D.data(), D.size() * sizeof(T), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ws.dplane, Dp.data(), Dp.size() * sizeof(T), cudaMemcpyHostToDevice, st);
   // The scratch keeps the previous call's contents: zero what must start at zero
   // (the grid accumulates spread contributions; the bin counts start at zero).
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws.grid, 0, ws.grid_bytes, st);
+  e = cudaMemsetAsync(ws.grid, 0, ws.grid_bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws.counts, 0, sizeof(int) * (size_t)p.nbins, st);  // the binning counts into it
   if (e != cudaSuccess) {
     cudaGetLastError();
-    g_static_err = std::string("table upload: ") + cudaGetErrorString(e);
+    g_static_err = std::string("scratch clear: ") + cudaGetErrorString(e);
     return FSIB_ECUDA;
   }
 

@@ -91,6 +91,9 @@ struct Plan {
   double fbody[3] = {0.0, 0.0, 0.0};  // uniform body force density, added to f-hat(0) (Navier-Stokes)
   // launch-shape tunables (chosen by fsib_autotune)
   int fft_p = 8, fft_q = 4, slice = 256;
+  // summation in the FP32 gather spreads: 0 plain FMAs, 1 compensated per term, 2 compensated
+  // per staged chunk of candidates (see kSumPlain, kSumTerm, kSumChunk)
+  int spread_sum = 2;
 
   // derived
   int nf = 0;        // fine grid per axis
@@ -156,6 +159,11 @@ struct Workspace {
   int* box_done = nullptr;           // [nbins] slices of a split box finished (the last one adds the partials)
   unsigned char* band = nullptr;     // [nb_z][nb_y] row bands reached by a window (gather path; see RowBands)
   unsigned char* band_dil = nullptr; // the same, widened by one box each way (kept from the X^{m+1/2} binning)
+  // Set to 1 by an interpolation from a grid that holds only the widened bands when a window
+  // leaves them (the point gets NaN); page-locked host memory mapped into the device, so the
+  // host reads it at the next call without a synchronisation (miss_host) and clears it.
+  unsigned int* miss_host = nullptr;
+  unsigned int* miss_dev = nullptr;
   void* part = nullptr;              // T[slots][3][512] partial boxes
   size_t part_slots = 0;
   // reverse mode (allocated on first use)
@@ -223,10 +231,11 @@ template <typename T>
 void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const double* omega, cudaStream_t st);
 template <typename T>
 void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st);
-// guard: row bands the grid holds (RowBands flags); a point whose window leaves them gets NaN.
+// guard: row bands the grid holds (RowBands flags); a point whose window leaves them gets NaN
+// and sets *miss (when miss is not null).
 template <typename T>
 void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st,
-                        const unsigned char* guard = nullptr);
+                        const unsigned char* guard = nullptr, unsigned int* miss = nullptr);
 
 template <typename T>
 void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t st);

@@ -621,13 +621,43 @@ __global__ void k_point_prep(PointGeom g, double beta, const typename DeltaT<T>:
   }
 }
 
+__device__ __forceinline__ void fma_acc(float& acc, float a, float b) { acc = __fmaf_rn(a, b, acc); }
+__device__ __forceinline__ void fma_acc(dd& acc, dd a, dd b) { dd_fma_acc(acc, a, b); }
+__device__ __forceinline__ float acc_norm(float a) { return a; }
+__device__ __forceinline__ dd acc_norm(dd a) { return dd_norm(a); }
+
+// Compensated FP32 sum (Kahan's compensation in Neumaier's form, with Knuth's TwoSum so that no
+// ordering of magnitudes is assumed): s is the rounded running sum, c the sum of the exact
+// rounding errors of the additions; the sum is s + c. The error of a compensated sum of n terms is
+// about 2u sum|x_i| + O(n u^2) sum|x_i| instead of the (n - 1) u sum|x_i| of recursive summation.
+struct cf {
+  float s, c;
+  __host__ __device__ constexpr cf(float v = 0.0f) : s(v), c(0.0f) {}
+};
+__device__ __forceinline__ void add_comp(cf& a, float x) {
+  float s, e;
+  two_sum(a.s, x, s, e);
+  a.s = s;
+  a.c = __fadd_rn(a.c, e);
+}
+__device__ __forceinline__ void fma_acc(cf& acc, float a, float b) { add_comp(acc, __fmul_rn(a, b)); }
+__device__ __forceinline__ float acc_norm(cf a) { return __fadd_rn(a.s, a.c); }
+
+// Summation of the FP32 gather spreads (option "spread_sum"): kSumPlain adds every term with an
+// FMA; kSumTerm adds every term into a compensated sum; kSumChunk adds the terms of one staged
+// chunk of candidates with FMAs and the chunk's partial sum into a compensated sum. Double-float
+// accumulators are compensated by construction and ignore the option.
+constexpr int kSumPlain = 0, kSumTerm = 1, kSumChunk = 2;
+template <typename T, int COMP> struct SumAcc { using type = T; };
+template <> struct SumAcc<float, kSumTerm> { using type = cf; };
+
 constexpr int kChunk = 32;  // candidates staged per round
 
 // Neighbouring bins whose window starts can reach box (Bx, By, Bz) (defined below).
 __device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int Bx, int By, int Bz, int lane,
                                        int* bin);
 
-template <typename T, int D>
+template <typename T, int D, int COMP>
 __global__ void __launch_bounds__(256)
 k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
                 const T* __restrict__ W, const T* __restrict__ Cw, T* __restrict__ grid) {
@@ -648,9 +678,11 @@ k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, 
   const int seg = task % nseg, ty = (task / nseg) % bys, tz = (task / (nseg * bys)) % bzs;
   const int comp = task / (nseg * bys * bzs);
   const int cx0 = ox + seg * kSeg, cy = oy + ty, cz = oz + tz;
-  T acc[kSeg];
+  using A = typename SumAcc<T, COMP>::type;
+  A acc[kSeg];
+  cf tot[kSeg];  // kSumChunk: compensated sums of the chunks' partial sums
 #pragma unroll
-  for (int i = 0; i < kSeg; ++i) acc[i] = T(0);
+  for (int i = 0; i < kSeg; ++i) { acc[i] = A(0); tot[i] = cf(0.0f); }
   const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
   // candidates: the points of the neighbouring bins (B + dlo .. B + dhi per axis, mod nb), as
   // one list of ranges (first point, prefix of lengths) built by warp 0, staged kChunk at a time
@@ -726,22 +758,28 @@ k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, 
 #pragma unroll
         for (int i = 0; i < kSeg; ++i) {
           const int qx = qx0 + i;
-          if (qx >= 0 && qx < w) acc[i] = acc[i] + t * wc[qx];
+          if (qx >= 0 && qx < w) {
+            if constexpr (COMP == kSumTerm && std::is_same<T, float>::value) fma_acc(acc[i], t, wc[qx]);
+            else acc[i] = acc[i] + t * wc[qx];
+          }
         }
+      }
+      if constexpr (COMP == kSumChunk && std::is_same<T, float>::value) {
+#pragma unroll
+        for (int i = 0; i < kSeg; ++i) { add_comp(tot[i], acc[i]); acc[i] = A(0); }
       }
     }
   }
   if (active) {
     T* out = grid + comp * gcells + ((long long)cz * nf + cy) * nf + cx0;
 #pragma unroll
-    for (int i = 0; i < kSeg; ++i) out[i] = acc[i];
+    for (int i = 0; i < kSeg; ++i) {
+      if constexpr (COMP == kSumChunk && std::is_same<T, float>::value) out[i] = acc_norm(tot[i]);
+      else out[i] = acc_norm(acc[i]);
+    }
   }
 }
 
-__device__ __forceinline__ void fma_acc(float& acc, float a, float b) { acc = __fmaf_rn(a, b, acc); }
-__device__ __forceinline__ void fma_acc(dd& acc, dd a, dd b) { dd_fma_acc(acc, a, b); }
-__device__ __forceinline__ float acc_norm(float a) { return a; }
-__device__ __forceinline__ dd acc_norm(dd a) { return dd_norm(a); }
 
 // Work list of the 3D gather: box b is split into K_b = ceil(cand_b / slice_size) slices
 // (cand_b = points in its neighbouring bins; K_b = 0 for a box that no window reaches).
@@ -926,7 +964,7 @@ constexpr int kBoxChunk = 64;
 __device__ __forceinline__ bool is_zero(float v) { return v == 0.0f; }
 __device__ __forceinline__ bool is_zero(dd v) { return v.hi == 0.0f; }
 
-template <typename T>
+template <typename T, int COMP>
 __global__ void __launch_bounds__(256)
 k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
               const T* __restrict__ W, const T* __restrict__ Cw, const int* __restrict__ slice_off,
@@ -1000,11 +1038,13 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
         sC[bb][c * 3 + a] = Cw[sp * 3 + a];
       }
     };
-    T acc[2][3];
+    using A = typename SumAcc<T, COMP>::type;
+    A acc[2][3];
+    cf tot[2][3];  // kSumChunk: compensated sums of the chunks' partial sums
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) acc[k][a] = T(0);
+      for (int a = 0; a < 3; ++a) { acc[k][a] = A(0); tot[k][a] = cf(0.0f); }
     int bb = 0;
     stage(f0, min(f1, f0 + kBoxChunk), 0);
     __syncthreads();
@@ -1025,6 +1065,12 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
           fma_acc(acc[1][a], cv, t1);
         }
       }
+      if constexpr (COMP == kSumChunk && std::is_same<T, float>::value) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) { add_comp(tot[k][a], acc[k][a]); acc[k][a] = A(0); }
+      }
       __syncthreads();
       bb ^= 1;
     }
@@ -1035,7 +1081,9 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
       const int yk = ly + 4 * k;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const T v = acc_norm(acc[k][a]);
+        T v;
+        if constexpr (COMP == kSumChunk && std::is_same<T, float>::value) v = acc_norm(tot[k][a]);
+        else v = acc_norm(acc[k][a]);
         if (K == 1) {
           grid[a * gcells + ((long long)cz * nf + (o[1] + yk)) * nf + cx] = v;
         } else {
@@ -1204,7 +1252,8 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
 template <typename T, int D>
 __global__ void __launch_bounds__(256)
 k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__ i0s, const T* __restrict__ W,
-              const T* __restrict__ grid, double* __restrict__ U, const unsigned char* __restrict__ guard) {
+              const T* __restrict__ grid, double* __restrict__ U, const unsigned char* __restrict__ guard,
+              unsigned int* miss_flag) {
   // per warp: the window's rows (y, z) as grid offsets and their weight products w_y w_z
   constexpr int kRows = (D == 3) ? kMaxW * kMaxW : kMaxW;
   __shared__ int sOff[8][kRows];
@@ -1276,6 +1325,7 @@ k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__
 #pragma unroll
       for (int a = 0; a < D; ++a) U[(long long)a * M + j] = bad ? __longlong_as_double(0x7ff8000000000000LL)
                                                                  : to_double_val(acc[a]);
+      if (bad && miss_flag) *(volatile unsigned int*)miss_flag = 1u;
     }
   }
 }
@@ -1371,34 +1421,47 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
                                                            (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_sched, ws.box_po,
                                                            (dd*)ws.part, grid, ws.box_work, ws.box_done);
     } else {
-      static const int per_sm = [] {
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spread_box3<T>, 256, 0) != cudaSuccess || n < 1) n = 4;
-        return n;
-      }();
-      k_spread_box3<T><<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts,
-                                                      (const T*)ws.cwp, ws.box_so, ws.box_item, ws.box_sched, ws.box_po,
-                                                      (T*)ws.part, grid, ws.box_work, ws.box_done);
+      auto run = [&](auto kern) {
+        static int per_sm_cache[3] = {0, 0, 0};
+        int& per_sm = per_sm_cache[p.spread_sum];
+        if (!per_sm) {
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 4;
+        }
+        kern<<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp,
+                                                 ws.box_so, ws.box_item, ws.box_sched, ws.box_po, (T*)ws.part, grid,
+                                                 ws.box_work, ws.box_done);
+      };
+      if (p.spread_sum == kSumTerm) run(k_spread_box3<T, kSumTerm>);
+      else if (p.spread_sum == kSumChunk) run(k_spread_box3<T, kSumChunk>);
+      else run(k_spread_box3<T, kSumPlain>);
     }
   } else {
     // one thread per (component, row, run of kSeg cells) of the box
     const int ntask = 2 * p.bins[1] * (p.bins[0] / kSeg);
     const int threads = std::min(256, std::max(32, (ntask + 31) / 32 * 32));
-    k_spread_gather<T, 2><<<nbox, threads, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp,
-                                                     grid);
+    const int mode = std::is_same<T, float>::value ? p.spread_sum : kSumPlain;
+    auto run = [&](auto kern) {
+      kern<<<nbox, threads, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
+    };
+    if (mode == kSumTerm) run(k_spread_gather<T, 2, kSumTerm>);
+    else if (mode == kSumChunk) run(k_spread_gather<T, 2, kSumChunk>);
+    else run(k_spread_gather<T, 2, kSumPlain>);
   }
 }
 
 template <typename T>
 void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaStream_t st,
-                        const unsigned char* guard) {
+                        const unsigned char* guard, unsigned int* miss) {
   const PointGeom g = geom(p);
   long long blocks = (p.M + 7) / 8;
   if (blocks > 32LL * num_sms()) blocks = 32LL * num_sms();
   if (p.d == 3)
-    k_interp_warp<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard);
+    k_interp_warp<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard,
+                                                          miss);
   else
-    k_interp_warp<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard);
+    k_interp_warp<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard,
+                                                          miss);
 }
 
 template void launch_point_prep<float>(const Plan&, Workspace&, const double*, const double*, cudaStream_t);
@@ -1406,8 +1469,9 @@ template void launch_point_prep<dd>(const Plan&, Workspace&, const double*, cons
 template void launch_spread_gather<float>(const Plan&, Workspace&, float*, cudaStream_t);
 template void launch_spread_gather<dd>(const Plan&, Workspace&, dd*, cudaStream_t);
 template void launch_interp_warp<float>(const Plan&, Workspace&, const float*, double*, cudaStream_t,
-                                        const unsigned char*);
-template void launch_interp_warp<dd>(const Plan&, Workspace&, const dd*, double*, cudaStream_t, const unsigned char*);
+                                        const unsigned char*, unsigned int*);
+template void launch_interp_warp<dd>(const Plan&, Workspace&, const dd*, double*, cudaStream_t, const unsigned char*,
+                                     unsigned int*);
 
 
 template void launch_spread<float>(const Plan&, Workspace&, const double*, const double*, float*, cudaStream_t);

@@ -97,6 +97,34 @@ def test_spread_dense_points_many_slices(lib, torch_mod, prec):
         assert relmax(got, ref) <= 10 * TOL[prec]
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("d,N,M", [(2, 32, 3000), (3, 16, 20000), (3, 24, 997)])
+def test_mixed_spread_summation_modes(lib, torch_mod, mode, d, N, M):
+    """The FP32 gather spread's three summations (plain FMAs, compensated per term, compensated
+    per staged chunk of candidates) all match the direct sums at the mixed tolerance, on dense
+    point sets whose cells collect hundreds of terms, and split 3D boxes into several slices."""
+    torch = torch_mod
+    rng = np.random.default_rng(500 + 7 * mode + d * N + M)
+    X = rng.uniform(0.3, 0.6, (d, M))          # clustered: many terms per cell
+    F = rng.standard_normal((d, M))
+    pb = make(lib, N, d, M, "mixed")
+    pb.set_option("spread_sum", mode)
+    assert pb.info("spread_sum") == mode
+    fh = pb.spread(cuda(X, torch), cuda(F, torch))
+    torch.cuda.synchronize()
+    ref = sp.full_to_half(sp.spread_direct(X, F, N), N)
+    got = to_np(fh)
+    assert rel2(got, ref) <= TOL["mixed"]
+    assert relmax(got, ref) <= 10 * TOL["mixed"]
+
+
+def test_spread_sum_option_is_checked(lib, torch_mod):
+    pb = make(lib, 8, 3, 10, "mixed")
+    assert pb.info("spread_sum") == 2              # compensated per chunk of candidates by default
+    with pytest.raises(lib.FsibError):
+        pb.set_option("spread_sum", 3)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp64native", "mixed"])
 @pytest.mark.parametrize("d,N,M", [(2, 16, 300), (2, 24, 37), (3, 8, 50), (3, 16, 700), (3, 12, 1),
                                    (3, 72, 211)])
@@ -407,7 +435,8 @@ def test_velocity_guard_after_a_move_beyond_the_widened_bands(lib, torch_mod):
     """The inverse transform behind U^{m+1} computes only the rows within one box of the
     windows at X^{m+1/2}. A uniform flow that carries a cluster of points several boxes in a
     half step (far beyond any stable time step) must give NaN there, never a value read from
-    rows that were not computed; at a normal step size the same setup gives the flow speed."""
+    rows that were not computed, and the next call must return FSIB_ENONFINITE; at a normal
+    step size the same setup gives the flow speed."""
     torch = torch_mod
     N, d, M = 64, 3, 40          # fine grid 128^3: 16 boxes of 8 cells per axis
     rng = np.random.default_rng(77)
@@ -425,6 +454,20 @@ def test_velocity_guard_after_a_move_beyond_the_widened_bands(lib, torch_mod):
         got = to_np(Ut)
         if expect_nan:
             assert np.isnan(got).all()
+            # the next call reports it as an error, without running, and clears the record
+            with pytest.raises(lib.FsibError) as e:
+                pb.step(Xt, uh, Ut, nsteps=1)
+            assert e.value.code == -4 and "moved more than one box" in str(e.value)
+            assert np.isnan(to_np(Ut)).all()
+            pb.interp(uh, Xt, out=Ut)                    # recovers: U^m from the spectrum
+            torch.cuda.synchronize()
+            assert np.isfinite(to_np(Ut)).all()
+            # a synchronous step (host arrays) reports it at once
+            Xh, uhh, Uh = X0.copy(), np.ascontiguousarray(sp.full_to_half(u, N)), np.empty_like(X0)
+            pb.interp(uhh, Xh, out=Uh)
+            with pytest.raises(lib.FsibError) as e:
+                pb.step(Xh, uhh, Uh, nsteps=1)
+            assert e.value.code == -4
         else:
             assert np.allclose(got[1], 1.0, rtol=0, atol=1e-10)
             assert np.allclose(got[[0, 2]], 0.0, atol=1e-10)
