@@ -250,16 +250,30 @@ int fsib_autotune(fsib_t h, const double* X, const void* uhat, const double* U);
  * fsib_batch_create makes one member handle per problem (arrays of length
  * nprob; precision FSIB_FP64 or FSIB_MIXED for all members). Set each member's
  * force model through fsib_batch_member. fsib_batch_step advances every member
- * by nsteps steps (as fsib_step) with one CUDA graph launch per step: the graph
- * holds one branch per member, forked from and joined into the batch stream, so
- * the members' kernels run concurrently. X, uhat, U: arrays of nprob device
- * pointers (uhat[i], U[i] may be NULL for Stokes members). fsib_batch_autotune
- * runs fsib_autotune on every member. Info keys: "nprob", "launches_per_step". */
+ * by nsteps steps (as fsib_step) with one CUDA graph launch per step. The graph is
+ * built from a recording of every member's step: members with the same sequence
+ * of phases (same d, flow and arithmetic) form a group, and each phase runs as
+ * one launch over the group's members (at most 16 a launch; the members'
+ * arguments travel in the launch's parameter space). Members with the same d, N,
+ * fine and dealiasing grids and step structure form a group; groups run as
+ * concurrent branches of the graph. Double-float and FP64 transforms run once
+ * per member. The graph is
+ * rebuilt when the arrays or a member's plan, launch shapes or force model
+ * change. X, uhat, U: arrays of nprob device pointers (uhat[i], U[i] may be
+ * NULL for Stokes members). fsib_batch_autotune runs fsib_autotune on every
+ * member. Info keys: "nprob", "launches_per_step" (kernel launches in one batch
+ * step), "groups", "merge". */
 typedef struct fsib_batch* fsib_batch_t;
 int fsib_batch_create(fsib_batch_t* out, int nprob, const int* N, const int* d, const int* M,
                       const double* mu, const double* rho, const double* dt, const double* tol,
                       int precision);
 int fsib_batch_member(fsib_batch_t b, int i, fsib_t* h);
+/* Batch options. "merge": 1 (default) = each phase of the members' steps runs as one launch
+ * over the members of a group that share its kernel (see fsib_batch_step); 0 = one graph
+ * branch per member holding that member's own launches. "group_max": largest group (0 = no
+ * limit, default; a larger group is split into balanced ones that run concurrently). Results
+ * agree to rounding either way. FSIB_EINVAL for an unknown key or a bad value. */
+int fsib_batch_set_option(fsib_batch_t b, const char* key, double value);
 int fsib_batch_set_stream(fsib_batch_t b, void* stream);
 int fsib_batch_autotune(fsib_batch_t b, double* const* X, void* const* uhat, double* const* U);
 int fsib_batch_step(fsib_batch_t b, double* const* X, void* const* uhat, double* const* U,

@@ -39,7 +39,14 @@ struct fsib_plan {
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
   int graph_kernels = 0;
+  unsigned long long gen = 0;  // bumped whenever the work of a step changes (batches re-record then)
 };
+
+// The step's work changed (plan, launch shapes, force model): drop the captured graph.
+static void invalidate_graph(fsib_plan* h) {
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  ++h->gen;
+}
 
 static std::string g_create_err;
 
@@ -62,6 +69,11 @@ size_t smem_optin() {
     return v;
   }();
   return (size_t)optin;
+}
+
+Recorder*& recorder() {
+  static thread_local Recorder* r = nullptr;
+  return r;
 }
 
 void raise_smem_limit(const void* kernel) {
@@ -200,7 +212,13 @@ struct Prof {
   int site = -1;
   cudaEvent_t a = nullptr, b = nullptr;
   cudaStream_t st;
+  const char* prev_site = nullptr;  // recording: the enclosing site label, restored on exit
   Prof(fsib_plan* hh, const char* name, double bytes, double flops, cudaStream_t s) : h(hh), st(s) {
+    if (Recorder* r = recorder()) {  // recording a batch member's step: label the operations
+      prev_site = r->site;
+      r->site = name;
+      return;
+    }
     if (!h->prof_on) return;
     for (size_t i = 0; i < h->sites.size(); ++i)
       if (h->sites[i].name == name) { site = (int)i; break; }
@@ -219,6 +237,10 @@ struct Prof {
     cudaEventRecord(a, st);
   }
   ~Prof() {
+    if (prev_site) {
+      if (Recorder* r = recorder()) r->site = prev_site;
+      return;
+    }
     if (site < 0) return;
     cudaEventRecord(b, st);
     h->pending.push_back({site, a, b});
@@ -304,7 +326,7 @@ static int alloc_ws(fsib_plan* h) {
   Workspace& ws = h->ws;
   free_ws(ws);
   h->ready = false;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  invalidate_graph(h);
   const bool f64 = p.prec == FSIB_FP64;
   const size_t rs = f64 ? 8 : 4, cs = 2 * rs;
   const long long N = p.N, hh = p.N / 2, n = p.nf, Nt = p.Nt, d = p.d;
@@ -614,7 +636,7 @@ static void spread_points(fsib_plan* h, const double* c, const double* omega, TI
 template <>
 void spread_points<double>(fsib_plan* h, const double* c, const double* omega, double* grid, cudaStream_t st) {
   { Prof pr(h, "zero_grid", (double)h->ws.grid_bytes, 0.0, st);
-    cudaMemsetAsync(h->ws.grid, 0, h->ws.grid_bytes, st); }
+    memset_async(h->ws.grid, 0, h->ws.grid_bytes, st); }
   Prof pr(h, "spread", point_bytes(h->p) + (double)h->ws.grid_bytes, point_flops(h->p), st);
   launch_spread<double>(h->p, h->ws, c, omega, grid, st);
 }
@@ -706,7 +728,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     // The nonlinear term of u^m does not depend on the boundary: its transforms run on a
     // second stream (own scratch s3, s4) while the force and the type-1 NUFFT run here.
     // While the profiler times launch sites, the branch runs in line so that no two sites overlap.
-    const bool fork = !h->prof_on;
+    const bool fork = !h->prof_on && !recorder();
     cudaStream_t sb = fork ? h->side : st;
     if (fork) {
       cudaEventRecord(h->ev_fork, st);
@@ -767,8 +789,8 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     do_stokeslet<TA>(h, fhat, uh, st);
     do_interp_sorted<TI, TA>(h, uh, ws.Uh, st, true);
     do_axpy(h, X, X, ws.Uh, p.dt, st);
-    if (U) cudaMemcpyAsync(U, ws.Uh, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
-    if (uhat) cudaMemcpyAsync(uhat, uh, ws.spec_bytes, cudaMemcpyDeviceToDevice, st);
+    if (U) memcpy_async(U, ws.Uh, sizeof(double) * dm, cudaMemcpyDeviceToDevice, st);
+    if (uhat) memcpy_async(uhat, uh, ws.spec_bytes, cudaMemcpyDeviceToDevice, st);
   }
 }
 
@@ -978,23 +1000,23 @@ int fsib_set_option(fsib_t h, const char* key, double v) {
     if (!(v == 4 || v == 8 || v == 16)) return fail(h, FSIB_EINVAL, "fft_tile must be 4, 8 or 16");
     h->p.fft_p = (int)v;
     h->p.fl_nf.tile_p = h->p.fl_nt.tile_p = (int)v;
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    invalidate_graph(h);
     return FSIB_OK;
   } else if (k == "fft_rows") {
     if (!(v == 2 || v == 4 || v == 8)) return fail(h, FSIB_EINVAL, "fft_rows must be 2, 4 or 8");
     h->p.fft_q = (int)v;
     h->p.fl_nf.rows_q = h->p.fl_nt.rows_q = (int)v;
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    invalidate_graph(h);
     return FSIB_OK;
   } else if (k == "spread_slice") {
     if (!(v >= kMinSlice && v <= 4096)) return fail(h, FSIB_EINVAL, "spread_slice must be in [128, 4096]");
     h->p.slice = (int)v;
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    invalidate_graph(h);
     return FSIB_OK;
   } else if (k == "spread_sum") {
     if (!(v == 0 || v == 1 || v == 2)) return fail(h, FSIB_EINVAL, "spread_sum must be 0, 1 or 2");
     h->p.spread_sum = (int)v;
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    invalidate_graph(h);
     return FSIB_OK;
   } else if (k == "native_fp64") {
     q.native_fp64 = (v != 0);
@@ -1044,7 +1066,7 @@ int fsib_set_force_curve(fsib_t h, double K) {
   h->ws.force_kind = 1;
   h->ws.curve_K = K;
   h->ws.stiffness = K;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  invalidate_graph(h);
   return FSIB_OK;
 }
 
@@ -1098,7 +1120,7 @@ int fsib_set_force_mesh(fsib_t h, const int* tri, int ntri, const double* Xref, 
                         ws.nnz, h->own);
   ws.force_kind = 2;
   ws.stiffness = sigma;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  invalidate_graph(h);
   return finish(h, true);
 }
 
@@ -1148,7 +1170,7 @@ int fsib_set_force_tension(fsib_t h, const int* tri, int ntri, double gamma) {
     return fail(h, FSIB_ECUDA, "copy of the incidence failed");
   ws.force_kind = 4;
   ws.stiffness = gamma;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  invalidate_graph(h);
   return FSIB_OK;
 }
 
@@ -1170,7 +1192,7 @@ int fsib_set_force_target(fsib_t h, const double* Xtarget, double K, double omeg
   ws.force_kind = 3;
   ws.target_wK = omega * K;
   ws.stiffness = K;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  invalidate_graph(h);
   return finish(h, true);
 }
 
@@ -1180,7 +1202,7 @@ int fsib_set_body_force(fsib_t h, const double* f) {
   for (int a = 0; a < h->p.d; ++a)
     if (!std::isfinite(f[a])) return fail(h, FSIB_EINVAL, "body force must be finite");
   for (int a = 0; a < 3; ++a) h->p.fbody[a] = (a < h->p.d) ? f[a] : 0.0;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  invalidate_graph(h);
   return FSIB_OK;
 }
 
@@ -1759,7 +1781,13 @@ struct fsib_batch {
   std::vector<cudaEvent_t> join;
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void*> gkey;
+  std::vector<unsigned long long> ggen;  // members' step generations the graph was built from
   int graph_kernels = 0;
+  int merge = 1;                     // 1: one launch per phase over the members (default); 0: branches
+  int group_max = 0;                 // largest merged group (0: no limit); larger classes are split
+  int groups = 0;                    // member groups of the merged graph (concurrent branches)
+  std::vector<cudaStream_t> gs;      // capture streams of the groups
+  std::vector<cudaEvent_t> gjoin;
   std::string err;
 };
 
@@ -1768,12 +1796,157 @@ static int bfail(fsib_batch* b, int code, const std::string& msg) {
   return code;
 }
 
+// Merged batch step (option "merge" = 1). Each member's step is recorded by the launch layer
+// (launch.cuh) in program order, its operations labelled by launch site. Members whose site
+// sequences agree (same dimension, kind of flow and arithmetic) form a group; the group's schedule
+// walks the sites in order and, inside a site, takes the r-th operation of every member at once:
+// kernels with the same functor, block and shared memory, and the same grid unless the kernel is
+// correct for any grid, become one k_multi launch over those members (blockIdx.y = member, grid
+// = the largest asked for, the members' parameters in the launch's parameter space; at most
+// kMaxMerge members a launch); other operations run per member. The groups are concurrent
+// branches of the captured graph; a group lists its members by decreasing M, so that the largest
+// problems' blocks start first.
+struct BatchItem {
+  bool merged = false;
+  std::vector<const RecOp*> ops;  // one per member taking part
+  dim3 grid;                      // merged: x = the largest grid asked for, y = members
+};
+
+static bool merges_with(const RecOp& a, const RecOp& b) {
+  return a.kind == RecOp::kKernel && b.kind == RecOp::kKernel && a.emit && a.id == b.id &&
+         a.block.x == b.block.x && a.block.y == b.block.y && a.block.z == b.block.z && a.smem == b.smem &&
+         a.grid.y == 1 && a.grid.z == 1 && b.grid.y == 1 && b.grid.z == 1 && (a.any_grid || a.grid.x == b.grid.x);
+}
+
+static int batch_capture_merged(fsib_batch* b, double* const* X, void* const* uhat, double* const* U,
+                                cudaGraph_t* graph) {
+  const size_t n = b->m.size();
+  std::vector<Recorder> rec(n);
+  for (size_t i = 0; i < n; ++i) {
+    fsib_plan* h = b->m[i];
+    void* u = uhat ? uhat[i] : nullptr;
+    double* Ui = U ? U[i] : nullptr;
+    recorder() = &rec[i];
+    FSIB_DISPATCH(h, (do_step<float, float>(h, X[i], (C<float>*)u, Ui, b->own)),
+                  (do_step<dd, double>(h, X[i], (C<double>*)u, Ui, b->own)),
+                  (do_step<double, double>(h, X[i], (C<double>*)u, Ui, b->own)));
+    recorder() = nullptr;
+  }
+  // segments: runs of operations with the same site label
+  struct Seg { std::string label; size_t lo, hi; };
+  std::vector<std::vector<Seg>> segs(n);
+  std::vector<std::string> keys(n);
+  for (size_t i = 0; i < n; ++i) {
+    const std::vector<RecOp>& ops = rec[i].ops;
+    for (size_t k = 0; k < ops.size(); ++k) {
+      if (segs[i].empty() || segs[i].back().label != ops[k].site) segs[i].push_back({ops[k].site, k, k});
+      segs[i].back().hi = k + 1;
+    }
+    // one group per grid shape: its members' operations line up one to one (they differ in M
+    // only), and the groups, each a chain of merged launches, run concurrently
+    const Plan& p = b->m[i]->p;
+    keys[i] = std::to_string(p.d) + " " + std::to_string(p.N) + " " + std::to_string(p.nf) + " " +
+              std::to_string(p.Nt) + "\n";
+    for (const Seg& sg : segs[i]) keys[i] += sg.label + "\n";
+  }
+  std::vector<std::vector<size_t>> classes;
+  std::vector<std::string> ckeys;
+  for (size_t i = 0; i < n; ++i) {
+    size_t g = 0;
+    while (g < ckeys.size() && ckeys[g] != keys[i]) ++g;
+    if (g == ckeys.size()) { ckeys.push_back(keys[i]); classes.emplace_back(); }
+    classes[g].push_back(i);
+  }
+  // A class larger than group_max is split into balanced groups (members dealt out by size), so
+  // that no single chain of launches holds most of the work.
+  std::vector<std::vector<size_t>> groups;
+  for (std::vector<size_t>& c : classes) {
+    const size_t cap = b->group_max > 0 ? (size_t)b->group_max : c.size();
+    const size_t nsub = (c.size() + cap - 1) / cap;
+    std::stable_sort(c.begin(), c.end(), [&](size_t x, size_t y) { return b->m[x]->p.M > b->m[y]->p.M; });
+    std::vector<std::vector<size_t>> sub(nsub);
+    for (size_t j = 0; j < c.size(); ++j) sub[j % nsub].push_back(c[j]);
+    for (auto& g : sub) groups.push_back(std::move(g));
+  }
+  std::vector<std::vector<BatchItem>> sched(groups.size());
+  for (size_t g = 0; g < groups.size(); ++g) {
+    const std::vector<size_t>& mem = groups[g];
+    const size_t nseg = segs[mem[0]].size();
+    for (size_t sgi = 0; sgi < nseg; ++sgi) {
+      size_t R = 0;
+      for (size_t i : mem) R = std::max(R, segs[i][sgi].hi - segs[i][sgi].lo);
+      for (size_t r = 0; r < R; ++r) {
+        std::vector<BatchItem> items;
+        for (size_t i : mem) {
+          const Seg& sg = segs[i][sgi];
+          if (sg.lo + r >= sg.hi) continue;
+          const RecOp* op = &rec[i].ops[sg.lo + r];
+          BatchItem* into = nullptr;
+          for (BatchItem& it : items)
+            if (it.ops.size() < (size_t)kMaxMerge && merges_with(*it.ops[0], *op)) { into = &it; break; }
+          if (!into) { items.emplace_back(); into = &items.back(); }
+          into->ops.push_back(op);
+        }
+        for (BatchItem& it : items) {
+          const RecOp& op0 = *it.ops[0];
+          it.merged = it.ops.size() > 1 && op0.emit != nullptr;
+          if (it.merged) {
+            unsigned gx = 1;
+            for (const RecOp* o : it.ops) gx = std::max(gx, o->grid.x);
+            it.grid = dim3(gx, (unsigned)it.ops.size(), 1);
+          }
+          sched[g].push_back(std::move(it));
+        }
+      }
+    }
+  }
+  while (b->gs.size() < groups.size()) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return bfail(b, FSIB_ECUDA, "CUDA stream/event creation failed");
+    b->gs.push_back(st);
+    b->gjoin.push_back(ev);
+  }
+  if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return bfail(b, FSIB_ECUDA, "stream capture failed to start");
+  cudaEventRecord(b->fork, b->own);
+  for (size_t g = 0; g < groups.size(); ++g) {
+    cudaStream_t st = b->gs[g];
+    cudaStreamWaitEvent(st, b->fork, 0);
+    for (const BatchItem& it : sched[g]) {
+      if (it.merged) {
+        const RecOp& o = *it.ops[0];
+        const void* packs[kMaxMerge];
+        for (size_t j = 0; j < it.ops.size(); ++j) packs[j] = it.ops[j]->pack.data();
+        o.emit(it.grid, o.block, o.smem, st, packs);
+        continue;
+      }
+      for (const RecOp* o : it.ops) {
+        if (o->kind == RecOp::kKernel) o->emit_one(o->grid, o->block, o->smem, st, o->pack.data());
+        else if (o->kind == RecOp::kMemset) cudaMemsetAsync(o->dst, o->value, o->bytes, st);
+        else cudaMemcpyAsync(o->dst, o->src, o->bytes, o->ckind, st);
+      }
+    }
+    cudaEventRecord(b->gjoin[g], st);
+    cudaStreamWaitEvent(b->own, b->gjoin[g], 0);
+  }
+  const cudaError_t e = cudaStreamEndCapture(b->own, graph);
+  if (e != cudaSuccess || !*graph) return bfail(b, FSIB_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+  b->groups = (int)groups.size();
+  return FSIB_OK;
+}
+
+
 extern "C" {
 
 int fsib_batch_destroy(fsib_batch* b) {
   if (!b) return FSIB_OK;
   if (b->own) cudaStreamSynchronize(b->own);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (auto st : b->gs) cudaStreamDestroy(st);
+  for (auto e : b->gjoin) cudaEventDestroy(e);
   for (auto* h : b->m) fsib_destroy(h);
   for (auto e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -1841,8 +2014,30 @@ int fsib_batch_info(fsib_batch* b, const char* key, double* value) {
   const std::string k(key);
   if (k == "nprob") *value = (double)b->m.size();
   else if (k == "launches_per_step") *value = b->graph_kernels;
+  else if (k == "merge") *value = b->merge;
+  else if (k == "group_max") *value = b->group_max;
+  else if (k == "groups") *value = b->groups;
   else return bfail(b, FSIB_EINVAL, "unknown info key: " + k);
   return FSIB_OK;
+}
+
+int fsib_batch_set_option(fsib_batch* b, const char* key, double value) {
+  if (!b || !key) return FSIB_EINVAL;
+  const std::string k(key);
+  if (k == "merge") {
+    if (value != 0 && value != 1) return bfail(b, FSIB_EINVAL, "merge must be 0 or 1");
+    b->merge = (int)value;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    return FSIB_OK;
+  }
+  if (k == "group_max") {
+    if (!(value >= 0 && value <= 65535) || value != (double)(int)value)
+      return bfail(b, FSIB_EINVAL, "group_max must be an integer in [0, 65535]");
+    b->group_max = (int)value;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    return FSIB_OK;
+  }
+  return bfail(b, FSIB_EINVAL, "unknown batch option key: " + k);
 }
 
 int fsib_batch_autotune(fsib_batch* b, double* const* X, void* const* uhat, double* const* U) {
@@ -1871,32 +2066,42 @@ int fsib_batch_step(fsib_batch* b, double* const* X, void* const* uhat, double* 
     if (!h->ws.force_kind) return bfail(b, FSIB_ESTATE, "member " + std::to_string(i) + " has no force model");
     key.push_back(X[i]); key.push_back(u); key.push_back(Ui);
   }
+  std::vector<unsigned long long> gen;
+  for (size_t i = 0; i < n; ++i) gen.push_back(b->m[i]->gen);
   if (cudaEventRecord(b->ev_in, b->user) != cudaSuccess || cudaStreamWaitEvent(b->own, b->ev_in, 0) != cudaSuccess)
     return bfail(b, FSIB_ECUDA, "stream ordering failed");
-  if (!b->gexec || key != b->gkey) {
+  if (!b->gexec || key != b->gkey || gen != b->ggen) {
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
     cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-      return bfail(b, FSIB_ECUDA, "stream capture failed to start");
-    cudaEventRecord(b->fork, b->own);
-    for (size_t i = 0; i < n; ++i) {
-      fsib_plan* h = b->m[i];
-      cudaStreamWaitEvent(h->own, b->fork, 0);
-      void* u = uhat ? uhat[i] : nullptr;
-      double* Ui = U ? U[i] : nullptr;
-      FSIB_DISPATCH(h, (do_step<float, float>(h, X[i], (C<float>*)u, Ui, h->own)),
-                    (do_step<dd, double>(h, X[i], (C<double>*)u, Ui, h->own)),
-                    (do_step<double, double>(h, X[i], (C<double>*)u, Ui, h->own)));
-      cudaEventRecord(b->join[i], h->own);
-      cudaStreamWaitEvent(b->own, b->join[i], 0);
+    if (b->merge) {
+      const int rc = batch_capture_merged(b, X, uhat, U, &g);
+      if (rc != FSIB_OK) return rc;
+    } else {
+      if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bfail(b, FSIB_ECUDA, "stream capture failed to start");
+      cudaEventRecord(b->fork, b->own);
+      for (size_t i = 0; i < n; ++i) {
+        fsib_plan* h = b->m[i];
+        cudaStreamWaitEvent(h->own, b->fork, 0);
+        void* u = uhat ? uhat[i] : nullptr;
+        double* Ui = U ? U[i] : nullptr;
+        FSIB_DISPATCH(h, (do_step<float, float>(h, X[i], (C<float>*)u, Ui, h->own)),
+                      (do_step<dd, double>(h, X[i], (C<double>*)u, Ui, h->own)),
+                      (do_step<double, double>(h, X[i], (C<double>*)u, Ui, h->own)));
+        cudaEventRecord(b->join[i], h->own);
+        cudaStreamWaitEvent(b->own, b->join[i], 0);
+      }
+      cudaError_t e = cudaStreamEndCapture(b->own, &g);
+      if (e != cudaSuccess || !g) return bfail(b, FSIB_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+      b->groups = (int)n;
     }
-    cudaError_t e = cudaStreamEndCapture(b->own, &g);
-    if (e != cudaSuccess || !g) return bfail(b, FSIB_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    cudaError_t e = cudaSuccess;
     b->graph_kernels = count_kernel_nodes(g);
     e = cudaGraphInstantiate(&b->gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { b->gexec = nullptr; return bfail(b, FSIB_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
     b->gkey = key;
+    b->ggen = gen;
   }
   for (int s = 0; s < nsteps; ++s)
     if (cudaGraphLaunch(b->gexec, b->own) != cudaSuccess) return bfail(b, FSIB_ECUDA, "graph launch failed");

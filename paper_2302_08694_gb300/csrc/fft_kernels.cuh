@@ -39,8 +39,11 @@ __device__ __forceinline__ C<T>* fft_lines(C<T>* a, C<T>* b, int nl, int ls, int
 // Strided pass
 // ---------------------------------------------------------------------------
 template <typename T, bool INV, typename Tin, typename Tout, int NC>
-__global__ void __launch_bounds__(kThreads)
-k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk,
+struct KFftStrided {
+  static constexpr int kThreads = fsib::kThreads, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
+  __device__ static void run(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk,
               FftLen fl, Mult<T> mult, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = NC ? NC : fl.n, kP = fl.tile_p, lgP = __ffs(kP) - 1;
@@ -99,13 +102,17 @@ k_fft_strided(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inne
     }
   }
 }
+};
 
 // ---------------------------------------------------------------------------
 // Row passes: real rows (length n) <-> half spectra (N/2 modes)
 // ---------------------------------------------------------------------------
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads)
-k_rows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk, FftLen fl,
+struct KRowsR2C {
+  static constexpr int kThreads = fsib::kThreads, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
+  __device__ static void run(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk, FftLen fl,
            const C<T>* __restrict__ twg, RowBands rb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = NC ? NC : fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
@@ -134,6 +141,7 @@ k_rows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, i
     out[(2 * pr + 1) * h + k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
   }
 }
+};
 
 // Build the packed complex spectrum Z = A + iB of two real rows from their half spectra.
 template <typename T>
@@ -152,8 +160,11 @@ __device__ __forceinline__ C<T> pack_rows(const C<T>* __restrict__ A, const C<T>
 }
 
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads)
-k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
+struct KRowsC2R {
+  static constexpr int kThreads = fsib::kThreads, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
+  __device__ static void run(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
            FftLen fl, const C<T>* __restrict__ twg, RowBands rb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = NC ? NC : fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
@@ -180,6 +191,7 @@ k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, i
     out[(2 * pr + 1) * n + x] = z.y;
   }
 }
+};
 
 // ---------------------------------------------------------------------------
 // Products of the velocity components on the dealiasing grid (three-halves rule):
@@ -188,8 +200,11 @@ k_rows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, i
 // products ordered (xx, xy, xz, yy, yz, zz) in 3D and (xx, xy, yy) in 2D.
 // ---------------------------------------------------------------------------
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads)
-k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows,
+struct KRowsProduct {
+  static constexpr int kThreads = fsib::kThreads, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
+  __device__ static void run(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows,
                int Nk, FftLen fl, const C<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = NC ? NC : fl.n, ls = n + 1, h = Nk / 2, kQrows = fl.rows_q;
@@ -241,6 +256,7 @@ k_rows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long 
     ob[h + k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
   }
 }
+};
 
 // ---------------------------------------------------------------------------
 // Row passes with the warp-level transform (lengths with a warp plan, wfft.cuh).
@@ -313,22 +329,27 @@ __device__ __forceinline__ void wrows_c2r_body(const C<T>* __restrict__ in, T* _
 // once the row bands cut its traffic); double-float lines keep the compiler's register choice
 // (a minimum-blocks hint of one raises it).
 template <typename T, int N>
-__global__ void __launch_bounds__(256, 3)
-k_wrows_c2r(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
+struct KWRowsC2R {
+  static constexpr int kThreads = 256, kMinBlocks = 3;
+  static constexpr bool kAnyGrid = true;
+  static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
+  __device__ static void run(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
             const C<T>* __restrict__ twg, RowBands rb) {
   wrows_c2r_body<T, N>(in, out, npairs, Nk, twg, rb);
 }
+};
 template <typename T, int N>
-__global__ void __launch_bounds__(256)
-k_wrows_c2r_dd(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
+struct KWRowsC2RDD {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  static constexpr bool kMerge = false;  // batches merge FP32 transforms only
+  __device__ static void run(const C<T>* __restrict__ in, T* __restrict__ out, long long npairs, int Nk,
                const C<T>* __restrict__ twg, RowBands rb) {
   wrows_c2r_body<T, N>(in, out, npairs, Nk, twg, rb);
 }
+};
 template <typename T, int N>
-inline auto wrows_c2r_kernel() {
-  if constexpr (sizeof(C<T>) == 8) return k_wrows_c2r<T, N>;
-  else return k_wrows_c2r_dd<T, N>;
-}
+using WRowsC2R = std::conditional_t<sizeof(C<T>) == 8, KWRowsC2R<T, N>, KWRowsC2RDD<T, N>>;
 
 // Untangle the spectra of two real rows packed as Z = A + iB: A[k] = (Z[k] + conj Z[N-k]) / 2,
 // B[k] = (Z[k] - conj Z[N-k]) / 2i, for the kept modes k < h. v holds Z in output order.
@@ -395,22 +416,27 @@ __device__ __forceinline__ void wrows_r2c_body(const T* __restrict__ in, C<T>* _
 // FP32 lines: three resident blocks per SM, as for the c2r pass; double-float lines keep the
 // compiler's register choice.
 template <typename T, int N>
-__global__ void __launch_bounds__(256, 3)
-k_wrows_r2c(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
+struct KWRowsR2C {
+  static constexpr int kThreads = 256, kMinBlocks = 3;
+  static constexpr bool kAnyGrid = true;
+  static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
+  __device__ static void run(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
             const C<T>* __restrict__ twg, RowBands rb) {
   wrows_r2c_body<T, N>(in, out, npairs, Nk, twg, rb);
 }
+};
 template <typename T, int N>
-__global__ void __launch_bounds__(256)
-k_wrows_r2c_dd(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
+struct KWRowsR2CDD {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  static constexpr bool kMerge = false;  // batches merge FP32 transforms only
+  __device__ static void run(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs, int Nk,
                const C<T>* __restrict__ twg, RowBands rb) {
   wrows_r2c_body<T, N>(in, out, npairs, Nk, twg, rb);
 }
+};
 template <typename T, int N>
-inline auto wrows_r2c_kernel() {
-  if constexpr (sizeof(C<T>) == 8) return k_wrows_r2c<T, N>;
-  else return k_wrows_r2c_dd<T, N>;
-}
+using WRowsR2C = std::conditional_t<sizeof(C<T>) == 8, KWRowsR2C<T, N>, KWRowsR2CDD<T, N>>;
 
 // Schedule of the product pass (see k_wrows_product): kind 0 = inverse transform of
 // component a into slot b; kind 1 = product ab of slots a and b; x = slot used for the
@@ -430,8 +456,11 @@ static __constant__ int kProdSched2[5] = {0 | 0 << 4 | 0 << 8 | 2 << 12,        
 // and xz, yz, zz each exchange through the buffer of a component they no longer need (S0,
 // S1, S2), which takes three line buffers per row pair instead of four. Blocks of 128 threads.
 template <typename T, int N>
-__global__ void __launch_bounds__(128)
-k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows, int Nk,
+struct KWRowsProduct {
+  static constexpr int kThreads = 128, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
+  __device__ static void run(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows, int Nk,
                 const C<T>* __restrict__ twg) {
   constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -481,6 +510,7 @@ k_wrows_product(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long
     }
   }
 }
+};
 
 // ---------------------------------------------------------------------------
 // Strided pass in two register stages, N = R1 x R2 (radices up to 16; the lengths below).
@@ -613,27 +643,31 @@ __device__ __forceinline__ void fft_s2_body(const C<Tin>* __restrict__ in, C<Tou
 // strided passes wait on memory, and the third block hides more of it. Double-float tiles
 // keep the compiler's own register choice (a minimum-blocks hint of one raises it).
 template <typename T, bool INV, typename Tin, typename Tout, int N>
-__global__ void __launch_bounds__(16 * s2_P(8), 3)
-k_fft_s2(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
+struct KFftS2 {
+  static constexpr int kThreads = 16 * s2_P(8), kMinBlocks = 3;
+  static constexpr bool kAnyGrid = false;
+  static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
+  __device__ static void run(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
          Mult<T> mult, const C<T>* __restrict__ twg, ZSkip zs) {
   fft_s2_body<T, INV, Tin, Tout, N>(in, out, inner, Nk, ntile, mult, twg, zs);
 }
+};
 template <typename T, bool INV, typename Tin, typename Tout, int N>
-__global__ void __launch_bounds__(16 * s2_P(16))
-k_fft_s2_dd(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
+struct KFftS2DD {
+  static constexpr int kThreads = 16 * s2_P(16), kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  static constexpr bool kMerge = false;  // batches merge FP32 transforms only
+  __device__ static void run(const C<Tin>* __restrict__ in, C<Tout>* __restrict__ out, int inner, int Nk, int ntile,
             Mult<T> mult, const C<T>* __restrict__ twg, ZSkip zs) {
   fft_s2_body<T, INV, Tin, Tout, N>(in, out, inner, Nk, ntile, mult, twg, zs);
 }
+};
 template <typename T, bool INV, typename Tin, typename Tout, int N>
-inline auto fft_s2_kernel() {
-  if constexpr (sizeof(C<T>) == 8) return k_fft_s2<T, INV, Tin, Tout, N>;
-  else return k_fft_s2_dd<T, INV, Tin, Tout, N>;
-}
+using FftS2 = std::conditional_t<sizeof(C<T>) == 8, KFftS2<T, INV, Tin, Tout, N>, KFftS2DD<T, INV, Tin, Tout, N>>;
 
 // Persistent grid of a warp-transform kernel: resident blocks per SM times the SMs,
 // or fewer when there is less work.
-template <typename K>
-static unsigned wrows_grid(K kern, int threads, size_t smem, long long groups) {
+static unsigned wrows_grid(const void* kern, int threads, size_t smem, long long groups) {
   int dev = 0, sms = 1, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -709,26 +743,26 @@ void launch_fft_strided(const C<Tin>* in, C<Tout>* out, int ncomp, int outer, in
       const long long blocks2 = (long long)ncomp * outer * nt2;
       const size_t smem2 = sizeof(C<T>) * (size_t)(NC + NC * P2);
       if (inverse && !fwd_only) {
-        auto k = fft_s2_kernel<T, true, Tin, Tout, NC>();
-        raise_smem_limit(reinterpret_cast<const void*>(k));
-        k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off, zs);
+        using K = FftS2<T, true, Tin, Tout, NC>;
+        raise_smem_limit(kernel_ptr<K>());
+        launch<K>((unsigned)blocks2, 16 * P2, smem2, st, in, out, inner, Nk, nt2, mult, tw + fl.tw_off, zs);
         return;
       }
       if (!inverse && !inv_only) {
-        auto k = fft_s2_kernel<T, false, Tin, Tout, NC>();
-        raise_smem_limit(reinterpret_cast<const void*>(k));
-        k<<<(unsigned)blocks2, 16 * P2, smem2, st>>>(in, out, inner, Nk, nt2, mult, tw + fl.tw_off, zs);
+        using K = FftS2<T, false, Tin, Tout, NC>;
+        raise_smem_limit(kernel_ptr<K>());
+        launch<K>((unsigned)blocks2, 16 * P2, smem2, st, in, out, inner, Nk, nt2, mult, tw + fl.tw_off, zs);
         return;
       }
     }
     if (inverse) {
-      auto k = k_fft_strided<T, true, Tin, Tout, NCI>;
-      raise_smem_limit(reinterpret_cast<const void*>(k));
-      k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
+      using K = KFftStrided<T, true, Tin, Tout, NCI>;
+      raise_smem_limit(kernel_ptr<K>());
+      launch<K>((unsigned)blocks, kThreads, smem, st, in, out, inner, Nk, fl, mult, tw);
     } else {
-      auto k = k_fft_strided<T, false, Tin, Tout, NCF>;
-      raise_smem_limit(reinterpret_cast<const void*>(k));
-      k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, inner, Nk, fl, mult, tw);
+      using K = KFftStrided<T, false, Tin, Tout, NCF>;
+      raise_smem_limit(kernel_ptr<K>());
+      launch<K>((unsigned)blocks, kThreads, smem, st, in, out, inner, Nk, fl, mult, tw);
     }
   });
 }
@@ -747,14 +781,15 @@ void launch_fft_rows_r2c(const T* in, C<T>* out, long long nrows, int Nk, const 
     constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;
     if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
-      auto k = wrows_r2c_kernel<T, NC>();
-      raise_smem_limit(reinterpret_cast<const void*>(k));
-      k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off, rb);
+      using K = WRowsR2C<T, NC>;
+      raise_smem_limit(kernel_ptr<K>());
+      launch<K>(wrows_grid(kernel_ptr<K>(), 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st, in, out, npairs, Nk,
+                tw + fl.tw_off, rb);
       return;
     }
-    auto k = k_rows_r2c<T, decltype(nc)::value>;
-    raise_smem_limit(reinterpret_cast<const void*>(k));
-    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fs, tw, rb);
+    using K = KRowsR2C<T, decltype(nc)::value>;
+    raise_smem_limit(kernel_ptr<K>());
+    launch<K>((unsigned)blocks, kThreads, smem, st, in, out, npairs, Nk, fs, tw, rb);
   });
 }
 
@@ -772,14 +807,15 @@ void launch_fft_rows_c2r(const C<T>* in, T* out, long long nrows, int Nk, const 
     constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;
     if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + 8 * LPW * wfft_stride(NC, (int)sizeof(C<T>)));
-      auto k = wrows_c2r_kernel<T, NC>();
-      raise_smem_limit(reinterpret_cast<const void*>(k));
-      k<<<wrows_grid(k, 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st>>>(in, out, npairs, Nk, tw + fl.tw_off, rb);
+      using K = WRowsC2R<T, NC>;
+      raise_smem_limit(kernel_ptr<K>());
+      launch<K>(wrows_grid(kernel_ptr<K>(), 256, ws, (npairs + LPW - 1) / LPW), 256, ws, st, in, out, npairs, Nk,
+                tw + fl.tw_off, rb);
       return;
     }
-    auto k = k_rows_c2r<T, decltype(nc)::value>;
-    raise_smem_limit(reinterpret_cast<const void*>(k));
-    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, npairs, Nk, fs, tw, rb);
+    using K = KRowsC2R<T, decltype(nc)::value>;
+    raise_smem_limit(kernel_ptr<K>());
+    launch<K>((unsigned)blocks, kThreads, smem, st, in, out, npairs, Nk, fs, tw, rb);
   });
 }
 
@@ -799,14 +835,15 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
     if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       constexpr int PT = 128;
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + (PT / 32) * LPW * 3 * wfft_stride(NC, (int)sizeof(C<T>)));
-      auto k = k_wrows_product<T, NC>;
-      raise_smem_limit(reinterpret_cast<const void*>(k));
-      k<<<wrows_grid(k, PT, ws, (npairs + LPW - 1) / LPW), PT, ws, st>>>(in, out, d, nrows, Nk, tw + fl.tw_off);
+      using K = KWRowsProduct<T, NC>;
+      raise_smem_limit(kernel_ptr<K>());
+      launch<K>(wrows_grid(kernel_ptr<K>(), PT, ws, (npairs + LPW - 1) / LPW), PT, ws, st, in, out, d, nrows, Nk,
+                tw + fl.tw_off);
       return;
     }
-    auto k = k_rows_product<T, decltype(nc)::value>;
-    raise_smem_limit(reinterpret_cast<const void*>(k));
-    k<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, d, nrows, Nk, fs, tw);
+    using K = KRowsProduct<T, decltype(nc)::value>;
+    raise_smem_limit(kernel_ptr<K>());
+    launch<K>((unsigned)blocks, kThreads, smem, st, in, out, d, nrows, Nk, fs, tw);
   });
 }
 

@@ -37,7 +37,10 @@ __device__ __forceinline__ bool decode_mode(const SpecGeom& g, long long idx, T*
 
 // u = mu^-1 (I/|k|^2 - k k^T/|k|^4) f, u(0) = 0 (Eq. stokeslet)
 template <typename T>
-__global__ void k_stokeslet(SpecGeom g, T inv_mu, const C<T>* __restrict__ f, C<T>* __restrict__ u) {
+struct KStokeslet {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(SpecGeom g, T inv_mu, const C<T>* __restrict__ f, C<T>* __restrict__ u) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
        idx += (long long)gridDim.x * blockDim.x) {
     T k[3];
@@ -58,7 +61,8 @@ __global__ void k_stokeslet(SpecGeom g, T inv_mu, const C<T>* __restrict__ f, C<
       u[a * g.nspec + idx] = v;
     }
   }
-}
+  }
+};
 
 // NS substep (Eqs. spatial_2, spatial_3 with V of Algorithm 2):
 //   s_a = sum_b i k_b p_ab (divergence form of the dealiased nonlinear term),
@@ -68,9 +72,12 @@ __global__ void k_stokeslet(SpecGeom g, T inv_mu, const C<T>* __restrict__ f, C<
 struct Body { double f[3]; };
 
 template <typename T>
-__global__ void k_ns_update(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool half, Body fb,
-                            const C<T>* __restrict__ prod, const C<T>* __restrict__ f,
-                            const C<T>* __restrict__ base, C<T>* __restrict__ out) {
+struct KNsUpdate {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool half, Body fb,
+                             const C<T>* __restrict__ prod, const C<T>* __restrict__ f,
+                             const C<T>* __restrict__ base, C<T>* __restrict__ out) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
        idx += (long long)gridDim.x * blockDim.x) {
     T k[3];
@@ -106,7 +113,8 @@ __global__ void k_ns_update(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool 
       out[a * g.nspec + idx] = v;
     }
   }
-}
+  }
+};
 
 // Pressure (Eq. pressure_poisson_k): p = -i k.(f - rho s)/|k|^2 with p(0) = 0 (mean-free).
 // With the divergence form s_a = i sum_b k_b P_ab of the dealiased products P_ab = (u_a u_b)^,
@@ -183,9 +191,12 @@ __device__ __forceinline__ double join_dd(dd a) { return widen_float(a.hi) + wid
 struct DDc { dd x, y; };
 __device__ __forceinline__ DDc ddc(double2 v) { return {split_double(v.x), split_double(v.y)}; }
 
-__global__ void k_ns_update_dd(SpecGeom g, dd kunit, dd inv_rho, dd mu_dt_over_rho, dd dt, bool half, Body fb,
-                               const double2* __restrict__ prod, const double2* __restrict__ f,
-                               const double2* __restrict__ base, double2* __restrict__ out) {
+struct KNsUpdateDD {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(SpecGeom g, dd kunit, dd inv_rho, dd mu_dt_over_rho, dd dt, bool half, Body fb,
+                             const double2* __restrict__ prod, const double2* __restrict__ f,
+                             const double2* __restrict__ base, double2* __restrict__ out) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
        idx += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(idx % g.h);
@@ -232,7 +243,8 @@ __global__ void k_ns_update_dd(SpecGeom g, dd kunit, dd inv_rho, dd mu_dt_over_r
       out[a * g.nspec + idx] = v;
     }
   }
-}
+  }
+};
 
 // out_a = i k_b in_a on the half spectrum (the unpaired mode -N/2 set to zero)
 template <typename T>
@@ -259,7 +271,7 @@ static unsigned grid_for(long long n) {
 template <typename T>
 void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t st) {
   const SpecGeom g = sgeom(p);
-  k_stokeslet<T><<<grid_for(g.nspec), 256, 0, st>>>(g, (T)(1.0 / p.mu), fhat, uhat);
+  launch<KStokeslet<T>>(grid_for(g.nspec), 256, 0, st, g, (T)(1.0 / p.mu), fhat, uhat);
 }
 
 template <typename T>
@@ -275,13 +287,13 @@ void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C
   const Body fb = {{p.fbody[0], p.fbody[1], p.fbody[2]}};
   if constexpr (std::is_same<T, double>::value) {
     if (!p.native_fp64) {
-      k_ns_update_dd<<<grid_for(g.nspec), 256, 0, st>>>(g, dd(g.kunit), dd(1.0 / p.rho), dd(p.mu * p.dt / p.rho),
-                                                         dd(p.dt), half, fb, prod, fhat, ubase, out);
+      launch<KNsUpdateDD>(grid_for(g.nspec), 256, 0, st, g, dd(g.kunit), dd(1.0 / p.rho), dd(p.mu * p.dt / p.rho),
+                          dd(p.dt), half, fb, prod, fhat, ubase, out);
       return;
     }
   }
-  k_ns_update<T><<<grid_for(g.nspec), 256, 0, st>>>(g, (T)(1.0 / p.rho), (T)(p.mu * p.dt / p.rho),
-                                                     (T)p.dt, half, fb, prod, fhat, ubase, out);
+  launch<KNsUpdate<T>>(grid_for(g.nspec), 256, 0, st, g, (T)(1.0 / p.rho), (T)(p.mu * p.dt / p.rho), (T)p.dt, half,
+                       fb, prod, fhat, ubase, out);
 }
 
 template <typename T>

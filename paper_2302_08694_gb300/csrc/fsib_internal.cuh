@@ -9,6 +9,7 @@
 
 #include "../../include/fsib.h"
 #include "dd.cuh"
+#include "launch.cuh"
 
 namespace fsib {
 

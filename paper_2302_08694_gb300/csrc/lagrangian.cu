@@ -16,32 +16,43 @@ static unsigned blocks_for(long long n, int bs = 256) {
 }
 
 // y = x + a v
-__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ v,
-                       double a, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = x[i] + a * v[i];
-}
+struct KAxpy {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ v,
+                             double a, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+      y[i] = x[i] + a * v[i];
+  }
+};
 
 void launch_axpy(double* y, const double* x, const double* v, double a, long long n, cudaStream_t st) {
-  k_axpy<<<blocks_for(n), 256, 0, st>>>(y, x, v, a, n);
+  launch<KAxpy>(blocks_for(n), 256, 0, st, y, x, v, a, n);
 }
 
 // Closed curve: c_j = omega F_j = K (X_{j+1} + X_{j-1} - 2 X_j)/dtheta, dtheta = 2 pi/M.
-__global__ void k_force_curve(const double* __restrict__ X, double* __restrict__ c, int M, double K_over_dth) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-    const int jp = (j + 1 == M) ? 0 : j + 1, jm = (j == 0) ? M - 1 : j - 1;
-    for (int a = 0; a < 2; ++a) {
-      const double* x = X + (long long)a * M;
-      c[(long long)a * M + j] = K_over_dth * ((x[jp] - x[j]) + (x[jm] - x[j]));
+struct KForceCurve {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(const double* __restrict__ X, double* __restrict__ c, int M, double K_over_dth) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+      const int jp = (j + 1 == M) ? 0 : j + 1, jm = (j == 0) ? M - 1 : j - 1;
+      for (int a = 0; a < 2; ++a) {
+        const double* x = X + (long long)a * M;
+        c[(long long)a * M + j] = K_over_dth * ((x[jp] - x[j]) + (x[jm] - x[j]));
+      }
     }
   }
-}
+};
 
 // Springs: c_i = sum_j K_ij (X_j - X_i), CSR adjacency (omega = 1).
 // Eight lanes per vertex: the lanes take the vertex's CSR entries in strides of eight
 // and reduce with shuffles, so that a vertex of high degree (a pole of a latitude-
 // longitude mesh joins every point of the first ring) costs few rounds.
-__global__ void k_force_mesh(const double* __restrict__ X, double* __restrict__ c, int M,
+struct KForceMesh {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(const double* __restrict__ X, double* __restrict__ c, int M,
                              const int* __restrict__ ptr, const int* __restrict__ col,
                              const double* __restrict__ kv) {
   const int sl = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3;
@@ -69,21 +80,29 @@ __global__ void k_force_mesh(const double* __restrict__ X, double* __restrict__ 
     }
     if (ok && sl == 0) { c[i] = f0; c[M + i] = f1; c[2LL * M + i] = f2; }
   }
-}
+  }
+};
 
 // Target points: c = omega K (X~ - X) over all d*M entries (Sec. 5.2.2).
-__global__ void k_force_target(const double* __restrict__ X, const double* __restrict__ Xt,
-                               double* __restrict__ c, long long n, double wK) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    c[i] = wK * (Xt[i] - X[i]);
-}
+struct KForceTarget {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(const double* __restrict__ X, const double* __restrict__ Xt,
+                             double* __restrict__ c, long long n, double wK) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+      c[i] = wK * (Xt[i] - X[i]);
+  }
+};
 
 // Surface tension E = gamma S (Sec. 6.2.4): F_i = -(gamma/2) sum over the triangles (i, j, k)
 // at node i of (X_j - X_k) x n_ijk, n_ijk the unit normal of (X_i, X_j, X_k) (omega = 1).
 // inc[e] = (j, k) lists each triangle at node i in its counter-clockwise order from i
 // (CSR rows ptr). Eight lanes per vertex as in k_force_mesh.
-__global__ void k_force_tension(const double* __restrict__ X, double* __restrict__ c, int M,
-                                const int* __restrict__ ptr, const int2* __restrict__ inc, double half_gamma) {
+struct KForceTension {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(const double* __restrict__ X, double* __restrict__ c, int M,
+                             const int* __restrict__ ptr, const int2* __restrict__ inc, double half_gamma) {
   const int sl = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3;
   for (long long w0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; w0 < M;
        w0 += (((long long)gridDim.x * blockDim.x) >> 5) * 4) {
@@ -113,19 +132,20 @@ __global__ void k_force_tension(const double* __restrict__ X, double* __restrict
     }
     if (ok && sl == 0) { c[i] = f0; c[M + i] = f1; c[2LL * M + i] = f2; }
   }
-}
+  }
+};
 
 void launch_force(const Plan& p, const Workspace& ws, const double* X, double* c, cudaStream_t st) {
   if (ws.force_kind == 1) {
     const double dth = 2.0 * 3.14159265358979323846 / p.M;
-    k_force_curve<<<blocks_for(p.M), 256, 0, st>>>(X, c, p.M, ws.curve_K / dth);
+    launch<KForceCurve>(blocks_for(p.M), 256, 0, st, X, c, p.M, ws.curve_K / dth);
   } else if (ws.force_kind == 3) {
     const long long n = (long long)p.d * p.M;
-    k_force_target<<<blocks_for(n), 256, 0, st>>>(X, ws.target, c, n, ws.target_wK);
+    launch<KForceTarget>(blocks_for(n), 256, 0, st, X, ws.target, c, n, ws.target_wK);
   } else if (ws.force_kind == 4) {
-    k_force_tension<<<blocks_for(8LL * p.M), 256, 0, st>>>(X, c, p.M, ws.csr_ptr, ws.inc_jk, 0.5 * ws.stiffness);
+    launch<KForceTension>(blocks_for(8LL * p.M), 256, 0, st, X, c, p.M, ws.csr_ptr, ws.inc_jk, 0.5 * ws.stiffness);
   } else {
-    k_force_mesh<<<blocks_for(8LL * p.M), 256, 0, st>>>(X, c, p.M, ws.csr_ptr, ws.csr_col, ws.csr_k);
+    launch<KForceMesh>(blocks_for(8LL * p.M), 256, 0, st, X, c, p.M, ws.csr_ptr, ws.csr_col, ws.csr_k);
   }
 }
 

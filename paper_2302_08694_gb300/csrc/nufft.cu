@@ -54,7 +54,10 @@ __device__ __forceinline__ int bin_of_start(int i0, int nf, int b, int nb) {
 
 // Bin of every point and its rank within the bin. Lanes of a warp that fall in the same
 // bin (neighbouring points usually do) share one atomic increment.
-__global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of,
+struct KBinCount {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of,
                             int* __restrict__ rank, int* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
   for (long long j0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; j0 < g.M;
@@ -83,6 +86,7 @@ __global__ void k_bin_count(PointGeom g, const double* __restrict__ X, int* __re
     }
   }
 }
+};
 
 // Single-block exclusive scans. A tile is kScanThreads x kScanPer consecutive entries;
 // each thread owns kScanPer of them (eight 16-byte loads when the tile is full), scans
@@ -161,8 +165,10 @@ __device__ __forceinline__ void block_prefix(int (&v)[NV], int (&tot)[NV], int (
 // It also clears the row-band flags (nband bytes) that k_band_mark then marks, and, without
 // them, leaves the counts at zero for the next binning (no memset node in the step graph).
 template <bool OCC>
-__global__ void __launch_bounds__(kScanThreads)
-k_bin_scan(int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
+struct KBinScan {
+  static constexpr int kThreads = kScanThreads, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  __device__ static void run(int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
            int* __restrict__ occ, int* __restrict__ nocc, unsigned char* __restrict__ band,
            unsigned char* __restrict__ band_dil, int nband) {
   constexpr int NV = OCC ? 2 : 1;
@@ -206,11 +212,14 @@ k_bin_scan(int* __restrict__ counts, long long nbins, int* __restrict__ offsets,
   }
   if (threadIdx.x == 0) { offsets[nbins] = carry; if (OCC) *nocc = carry_o; }
 }
+};
 
 // Exclusive scans of two int arrays of length n, one per block (blockIdx.x = 0: a, 1: b);
 // out arrays hold n + 1 entries.
-__global__ void __launch_bounds__(kScanThreads)
-k_scan2(const int* __restrict__ a, const int* __restrict__ b, int n, int* __restrict__ oa, int* __restrict__ ob) {
+struct KScan2 {
+  static constexpr int kThreads = kScanThreads, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  __device__ static void run(const int* __restrict__ a, const int* __restrict__ b, int n, int* __restrict__ oa, int* __restrict__ ob) {
   __shared__ int wsum[1][32];
   const int* in = blockIdx.x ? b : a;
   int* out = blockIdx.x ? ob : oa;
@@ -235,9 +244,13 @@ k_scan2(const int* __restrict__ a, const int* __restrict__ b, int n, int* __rest
   }
   if (threadIdx.x == 0) out[n] = carry;
 }
+};
 
 template <typename T>
-__global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const int* __restrict__ bin_of,
+struct KBinScatter {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, const double* __restrict__ X, const int* __restrict__ bin_of,
                               const int* __restrict__ rank, const int* __restrict__ offsets,
                               int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.M; j += gridDim.x * blockDim.x) {
@@ -251,6 +264,7 @@ __global__ void k_bin_scatter(PointGeom g, const double* __restrict__ X, const i
     }
   }
 }
+};
 
 static int num_sms();
 
@@ -259,7 +273,10 @@ static int num_sms();
 // one box more each way (the bands still hold the windows after a move of under a box). One
 // thread per bin, after the scan has cleared the flags; a flag already set is not stored again.
 // It also returns the bin counts to zero.
-__global__ void k_band_mark(PointGeom g, const int* __restrict__ offsets, int* __restrict__ counts,
+struct KBandMark {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, const int* __restrict__ offsets, int* __restrict__ counts,
                             unsigned char* __restrict__ band, unsigned char* __restrict__ band_dil, int reach) {
   const int nbins = g.nb[0] * g.nb[1] * (g.d == 3 ? g.nb[2] : 1);
   const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
@@ -281,6 +298,7 @@ __global__ void k_band_mark(PointGeom g, const int* __restrict__ offsets, int* _
         }
   }
 }
+};
 
 // The whole binning of a small problem in one block (one launch instead of four): bins and
 // ranks with shared-memory atomics, the exclusive scan of the bin counts in shared memory, the
@@ -290,8 +308,10 @@ constexpr int kSmallBins = 8192;
 constexpr int kSmallM = 2048;
 
 template <typename T>
-__global__ void __launch_bounds__(1024)
-k_bin_small(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of, int* __restrict__ rank,
+struct KBinSmall {
+  static constexpr int kThreads = 1024, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  __device__ static void run(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of, int* __restrict__ rank,
             int* __restrict__ offsets, int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta,
             unsigned char* __restrict__ band, unsigned char* __restrict__ band_dil, int nband, int reach) {
   __shared__ int sc[kSmallBins];
@@ -353,6 +373,7 @@ k_bin_small(PointGeom g, const double* __restrict__ X, int* __restrict__ bin_of,
     }
   }
 }
+};
 
 void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream_t st, bool occupied,
                        bool dilate) {
@@ -365,26 +386,26 @@ void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream
   const int reach = (p.bins[1] + p.w - 2) / p.bins[1];
   if (!occupied && p.M <= kSmallM && p.nbins <= kSmallBins) {  // gather path, small problem
     if (p.prec == FSIB_FP64)
-      k_bin_small<double><<<1, 1024, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
+      launch<KBinSmall<double>>(1, 1024, 0, st, g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
                                              (double*)ws.delta, band, band_dil, nband, reach);
     else
-      k_bin_small<float><<<1, 1024, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
+      launch<KBinSmall<float>>(1, 1024, 0, st, g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
                                             (float*)ws.delta, band, band_dil, nband, reach);
     return;
   }
-  k_bin_count<<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.counts);
-  if (occupied) k_bin_scan<true><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
-  else k_bin_scan<false><<<1, kScanThreads, 0, st>>>(ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
+  launch<KBinCount>(nb, 256, 0, st, g, X, ws.bin_of, ws.rank, ws.counts);
+  if (occupied) launch<KBinScan<true>>(1, kScanThreads, 0, st, ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
+  else launch<KBinScan<false>>(1, kScanThreads, 0, st, ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
   if (band) {
     const long long nbb = std::min<long long>((p.nbins + 255) / 256, 4LL * num_sms());
-    k_band_mark<<<(unsigned)std::max<long long>(1, nbb), 256, 0, st>>>(g, ws.offsets, ws.counts, band, band_dil,
+    launch<KBandMark>((unsigned)std::max<long long>(1, nbb), 256, 0, st, g, ws.offsets, ws.counts, band, band_dil,
                                                                          reach);
   }
   if (p.prec == FSIB_FP64)
-    k_bin_scatter<double><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
+    launch<KBinScatter<double>>(nb, 256, 0, st, g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
                                               (double*)ws.delta);
   else
-    k_bin_scatter<float><<<nb, 256, 0, st>>>(g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
+    launch<KBinScatter<float>>(nb, 256, 0, st, g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
                                              (float*)ws.delta);
 }
 
@@ -438,8 +459,10 @@ __device__ __forceinline__ void atomic_add_comp(float* hi, float* lo, float v) {
 // shared memory, one warp per point, flush with global atomics.
 // ---------------------------------------------------------------------------
 template <typename T, int D, bool COMP>
-__global__ void __launch_bounds__(kSpreadThreads)
-k_spread(PointGeom g, T beta, const double* __restrict__ cw, const double* __restrict__ omega,
+struct KSpreadScatter {
+  static constexpr int kThreads = kSpreadThreads, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, T beta, const double* __restrict__ cw, const double* __restrict__ omega,
          const int* __restrict__ perm, const int* __restrict__ offsets, const int* __restrict__ occ,
          const int* __restrict__ nocc, const int* __restrict__ i0s, const T* __restrict__ delta,
          T* __restrict__ grid) {
@@ -508,13 +531,16 @@ k_spread(PointGeom g, T beta, const double* __restrict__ cw, const double* __res
     __syncthreads();
   }
 }
+};
 
 // ---------------------------------------------------------------------------
 // Interp: one warp per (sorted) point, gather of the w^D window, warp reduction.
 // ---------------------------------------------------------------------------
 template <typename T, int D>
-__global__ void __launch_bounds__(kSpreadThreads)
-k_interp(PointGeom g, T beta, const int* __restrict__ perm, const int* __restrict__ i0s,
+struct KInterp {
+  static constexpr int kThreads = kSpreadThreads, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, T beta, const int* __restrict__ perm, const int* __restrict__ i0s,
          const T* __restrict__ delta, const T* __restrict__ grid, double* __restrict__ U) {
   __shared__ T wts_all[(kSpreadThreads / 32) * 3 * kMaxW];
   const int w = g.w, nf = g.nf, M = g.M;
@@ -554,6 +580,7 @@ k_interp(PointGeom g, T beta, const int* __restrict__ perm, const int* __restric
     __syncwarp();
   }
 }
+};
 
 // ---------------------------------------------------------------------------
 // Kernel weights in the transform arithmetic: float evaluates phi in FP32, dd
@@ -604,7 +631,10 @@ __device__ __forceinline__ dd weight_of<dd>(double delta, int q, int, double, dd
 constexpr int kSeg = 8;  // cells per thread run along x in the gather
 
 template <typename T, int D>
-__global__ void k_point_prep(PointGeom g, double beta, const typename DeltaT<T>::type* __restrict__ delta,
+struct KPointPrep {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, double beta, const typename DeltaT<T>::type* __restrict__ delta,
                              const int* __restrict__ perm, const double* __restrict__ cw,
                              const double* __restrict__ omega, T* __restrict__ W, T* __restrict__ Cw, dd s2w, dd bdd) {
   const int w = g.w, M = g.M;
@@ -620,6 +650,7 @@ __global__ void k_point_prep(PointGeom g, double beta, const typename DeltaT<T>:
     }
   }
 }
+};
 
 __device__ __forceinline__ void fma_acc(float& acc, float a, float b) { acc = __fmaf_rn(a, b, acc); }
 __device__ __forceinline__ void fma_acc(dd& acc, dd a, dd b) { dd_fma_acc(acc, a, b); }
@@ -658,8 +689,10 @@ __device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int
                                        int* bin);
 
 template <typename T, int D, int COMP>
-__global__ void __launch_bounds__(256)
-k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
+struct KSpreadGather {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  __device__ static void run(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
                 const T* __restrict__ W, const T* __restrict__ Cw, T* __restrict__ grid) {
   __shared__ T sW[kChunk * D * kMaxW];
   __shared__ T sC[kChunk * D];
@@ -779,6 +812,7 @@ k_spread_gather(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, 
     }
   }
 }
+};
 
 
 // Work list of the 3D gather: box b is split into K_b = ceil(cand_b / slice_size) slices
@@ -810,7 +844,10 @@ __device__ __forceinline__ int slice_size(const PointGeom& g, int c) {
 }
 
 // One warp per box: number of slices of the box.
-__global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
+struct KBoxSlices {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = false;
+  __device__ static void run(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
                              int* __restrict__ nslice, int* __restrict__ npart, int* __restrict__ done) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   const int nbox = g.nb[0] * g.nb[1] * g.nb[2];
@@ -828,6 +865,7 @@ __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restric
     done[warp] = 0;
   }
 }
+};
 
 // Box of every slice: box_item[slice_off[b] + k] = b for k < K_b; and the order in which
 // the gather takes them: the slices of split boxes (K_b > 1, the densest, whose slices
@@ -835,7 +873,10 @@ __global__ void k_box_slices(PointGeom g, int dlo, int dhi, const int* __restric
 // the launch is short. part_off (prefix of K_b over split boxes) numbers the first group;
 // slice_off[b] - part_off[b] counts the single-slice boxes before b.
 // Also resets the gather's work counters for the launch that follows.
-__global__ void k_slice_boxes(int nbox, const int* __restrict__ slice_off, const int* __restrict__ part_off,
+struct KSliceBoxes {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(int nbox, const int* __restrict__ slice_off, const int* __restrict__ part_off,
                               int* __restrict__ box_item, int* __restrict__ sched, int* __restrict__ work) {
   if (blockIdx.x == 0 && threadIdx.x < 2) work[threadIdx.x] = 0;
   const int nsplit = part_off[nbox];
@@ -847,6 +888,7 @@ __global__ void k_slice_boxes(int nbox, const int* __restrict__ slice_off, const
     }
   }
 }
+};
 
 // Next work of the calling block (dynamic scheduling, so that heavy and light slices spread
 // evenly over the SMs): a slice (work[0]) and, with it, a run of boxes to zero (work[1]), so
@@ -965,8 +1007,10 @@ __device__ __forceinline__ bool is_zero(float v) { return v == 0.0f; }
 __device__ __forceinline__ bool is_zero(dd v) { return v.hi == 0.0f; }
 
 template <typename T, int COMP>
-__global__ void __launch_bounds__(256)
-k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
+struct KSpreadBox3 {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
               const T* __restrict__ W, const T* __restrict__ Cw, const int* __restrict__ slice_off,
               const int* __restrict__ box_item, const int* __restrict__ sched, const int* __restrict__ part_off,
               T* __restrict__ part,
@@ -1096,6 +1140,7 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
   }
   zero_empty_boxes<T>(g, slice_off, nbox, grid, work);
 }
+};
 
 // Double-float variant of the 3D gather. The per-lane work is six double-float
 // multiply-adds per candidate and plane, so the weight products are formed once per block
@@ -1104,8 +1149,10 @@ k_spread_box3(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, co
 // of w_x w_y products and its d x 8 values C_a w_z (plus w_z for the plane test).
 constexpr int kBoxChunkDD = 32;   // candidates per chunk (eight threads each)
 constexpr int kXYStride = 72;     // per-candidate stride of the x-y table (64 + 8: staging stores hit all banks)
-__global__ void __launch_bounds__(256)
-k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
+struct KSpreadBox3DD {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
                  const dd* __restrict__ W, const dd* __restrict__ Cw, const int* __restrict__ slice_off,
                  const int* __restrict__ box_item, const int* __restrict__ sched, const int* __restrict__ part_off,
                  dd* __restrict__ part,
@@ -1247,11 +1294,14 @@ k_spread_box3_dd(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets,
   }
   zero_empty_boxes<dd>(g, slice_off, nbox, grid, work);
 }
+};
 
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256)
-k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__ i0s, const T* __restrict__ W,
+struct KInterpWarp {
+  static constexpr int kThreads = 256, kMinBlocks = 0;
+  static constexpr bool kAnyGrid = true;
+  __device__ static void run(PointGeom g, const int* __restrict__ perm, const int* __restrict__ i0s, const T* __restrict__ W,
               const T* __restrict__ grid, double* __restrict__ U, const unsigned char* __restrict__ guard,
               unsigned int* miss_flag) {
   // per warp: the window's rows (y, z) as grid offsets and their weight products w_y w_z
@@ -1329,6 +1379,7 @@ k_interp_warp(PointGeom g, const int* __restrict__ perm, const int* __restrict__
     }
   }
 }
+};
 
 static int num_sms() {
   static int n = 0;
@@ -1353,15 +1404,23 @@ void launch_spread(const Plan& p, Workspace& ws, const double* cw, const double*
   const int blocks = 4 * num_sms();
   const T beta = (T)p.beta;
   if (D == 3) {
-    auto kern = comp ? k_spread<T, 3, true> : k_spread<T, 3, false>;
-    raise_smem_limit(reinterpret_cast<const void*>(kern));
-    kern<<<blocks, kSpreadThreads, smem, st>>>(g, beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc,
-                                               ws.i0, (const T*)ws.delta, grid);
+    auto run = [&](auto k) {
+      using K = typename decltype(k)::type;
+      raise_smem_limit(kernel_ptr<K>());
+      launch<K>(blocks, kSpreadThreads, smem, st, g, beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
+                (const T*)ws.delta, grid);
+    };
+    if (comp) run(type_tag<KSpreadScatter<T, 3, true>>());
+    else run(type_tag<KSpreadScatter<T, 3, false>>());
   } else {
-    auto kern = comp ? k_spread<T, 2, true> : k_spread<T, 2, false>;
-    raise_smem_limit(reinterpret_cast<const void*>(kern));
-    kern<<<blocks, kSpreadThreads, smem, st>>>(g, beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc,
-                                               ws.i0, (const T*)ws.delta, grid);
+    auto run = [&](auto k) {
+      using K = typename decltype(k)::type;
+      raise_smem_limit(kernel_ptr<K>());
+      launch<K>(blocks, kSpreadThreads, smem, st, g, beta, cw, omega, ws.perm, ws.offsets, ws.occ, ws.nocc, ws.i0,
+                (const T*)ws.delta, grid);
+    };
+    if (comp) run(type_tag<KSpreadScatter<T, 2, true>>());
+    else run(type_tag<KSpreadScatter<T, 2, false>>());
   }
 }
 
@@ -1373,9 +1432,9 @@ void launch_interp(const Plan& p, Workspace& ws, const T* grid, double* U, cudaS
   if (blocks > 16LL * num_sms()) blocks = 16LL * num_sms();
   const T beta = (T)p.beta;
   if (p.d == 3)
-    k_interp<T, 3><<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, beta, ws.perm, ws.i0, (const T*)ws.delta, grid, U);
+    launch<KInterp<T, 3>>((unsigned)blocks, kSpreadThreads, 0, st, g, beta, ws.perm, ws.i0, (const T*)ws.delta, grid, U);
   else
-    k_interp<T, 2><<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, beta, ws.perm, ws.i0, (const T*)ws.delta, grid, U);
+    launch<KInterp<T, 2>>((unsigned)blocks, kSpreadThreads, 0, st, g, beta, ws.perm, ws.i0, (const T*)ws.delta, grid, U);
 }
 
 template <typename T>
@@ -1387,10 +1446,10 @@ void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const dou
   if (blocks > 64LL * num_sms()) blocks = 64LL * num_sms();
   T* Cw = cw ? (T*)ws.cwp : nullptr;
   if (p.d == 3)
-    k_point_prep<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw,
+    launch<KPointPrep<T, 3>>((unsigned)blocks, 256, 0, st, g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw,
                                                       dd(2.0 / p.w), dd(p.beta));
   else
-    k_point_prep<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw,
+    launch<KPointPrep<T, 2>>((unsigned)blocks, 256, 0, st, g, p.beta, (const Td*)ws.delta, ws.perm, cw, omega, (T*)ws.wts, Cw,
                                                       dd(2.0 / p.w), dd(p.beta));
 }
 
@@ -1404,49 +1463,52 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
   const int nbox = (int)p.nbins;
   if (p.d == 3) {
     // slices per box, their prefix sums, then the sliced gather and the partial reduction
-    k_box_slices<<<(nbox * 32 + 255) / 256, 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np,
+    launch<KBoxSlices>((nbox * 32 + 255) / 256, 256, 0, st, g, dlo, dhi, ws.offsets, ws.box_ns, ws.box_np,
                                                            ws.box_done);
-    k_scan2<<<2, 1024, 0, st>>>(ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
-    k_slice_boxes<<<(nbox + 255) / 256, 256, 0, st>>>(nbox, ws.box_so, ws.box_po, ws.box_item, ws.box_sched,
+    launch<KScan2>(2, 1024, 0, st, ws.box_ns, ws.box_np, nbox, ws.box_so, ws.box_po);
+    launch<KSliceBoxes>((nbox + 255) / 256, 256, 0, st, nbox, ws.box_so, ws.box_po, ws.box_item, ws.box_sched,
                                                        ws.box_work);
     if constexpr (std::is_same<T, dd>::value) {
       constexpr size_t smem = 2 * sizeof(dd) * kBoxChunkDD * (kXYStride + 24) + 2 * sizeof(unsigned) * kBoxChunkDD;
       static const int per_sm = [] {
-        raise_smem_limit(reinterpret_cast<const void*>(k_spread_box3_dd));
+        raise_smem_limit(kernel_ptr<KSpreadBox3DD>());
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spread_box3_dd, 256, smem) != cudaSuccess || n < 1) n = 4;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr<KSpreadBox3DD>(), 256, smem) != cudaSuccess ||
+            n < 1)
+          n = 4;
         return n;
       }();
-      k_spread_box3_dd<<<per_sm * num_sms(), 256, smem, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const dd*)ws.wts,
-                                                           (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_sched, ws.box_po,
-                                                           (dd*)ws.part, grid, ws.box_work, ws.box_done);
+      launch<KSpreadBox3DD>(per_sm * num_sms(), 256, smem, st, g, dlo, dhi, ws.offsets, ws.i0, (const dd*)ws.wts,
+                            (const dd*)ws.cwp, ws.box_so, ws.box_item, ws.box_sched, ws.box_po, (dd*)ws.part, grid,
+                            ws.box_work, ws.box_done);
     } else {
-      auto run = [&](auto kern) {
-        static int per_sm_cache[3] = {0, 0, 0};
-        int& per_sm = per_sm_cache[p.spread_sum];
+      auto run = [&](auto k) {
+        using K = typename decltype(k)::type;
+        static int per_sm = 0;
         if (!per_sm) {
-          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1)
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_ptr<K>(), 256, 0) != cudaSuccess ||
+              per_sm < 1)
             per_sm = 4;
         }
-        kern<<<per_sm * num_sms(), 256, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp,
-                                                 ws.box_so, ws.box_item, ws.box_sched, ws.box_po, (T*)ws.part, grid,
-                                                 ws.box_work, ws.box_done);
+        launch<K>(per_sm * num_sms(), 256, 0, st, g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp,
+                  ws.box_so, ws.box_item, ws.box_sched, ws.box_po, (T*)ws.part, grid, ws.box_work, ws.box_done);
       };
-      if (p.spread_sum == kSumTerm) run(k_spread_box3<T, kSumTerm>);
-      else if (p.spread_sum == kSumChunk) run(k_spread_box3<T, kSumChunk>);
-      else run(k_spread_box3<T, kSumPlain>);
+      if (p.spread_sum == kSumTerm) run(type_tag<KSpreadBox3<T, kSumTerm>>());
+      else if (p.spread_sum == kSumChunk) run(type_tag<KSpreadBox3<T, kSumChunk>>());
+      else run(type_tag<KSpreadBox3<T, kSumPlain>>());
     }
   } else {
     // one thread per (component, row, run of kSeg cells) of the box
     const int ntask = 2 * p.bins[1] * (p.bins[0] / kSeg);
     const int threads = std::min(256, std::max(32, (ntask + 31) / 32 * 32));
     const int mode = std::is_same<T, float>::value ? p.spread_sum : kSumPlain;
-    auto run = [&](auto kern) {
-      kern<<<nbox, threads, 0, st>>>(g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
+    auto run = [&](auto k) {
+      using K = typename decltype(k)::type;
+      launch<K>(nbox, threads, 0, st, g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
     };
-    if (mode == kSumTerm) run(k_spread_gather<T, 2, kSumTerm>);
-    else if (mode == kSumChunk) run(k_spread_gather<T, 2, kSumChunk>);
-    else run(k_spread_gather<T, 2, kSumPlain>);
+    if (mode == kSumTerm) run(type_tag<KSpreadGather<T, 2, kSumTerm>>());
+    else if (mode == kSumChunk) run(type_tag<KSpreadGather<T, 2, kSumChunk>>());
+    else run(type_tag<KSpreadGather<T, 2, kSumPlain>>());
   }
 }
 
@@ -1457,11 +1519,9 @@ void launch_interp_warp(const Plan& p, Workspace& ws, const T* grid, double* U, 
   long long blocks = (p.M + 7) / 8;
   if (blocks > 32LL * num_sms()) blocks = 32LL * num_sms();
   if (p.d == 3)
-    k_interp_warp<T, 3><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard,
-                                                          miss);
+    launch<KInterpWarp<T, 3>>((unsigned)blocks, 256, 0, st, g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard, miss);
   else
-    k_interp_warp<T, 2><<<(unsigned)blocks, 256, 0, st>>>(g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard,
-                                                          miss);
+    launch<KInterpWarp<T, 2>>((unsigned)blocks, 256, 0, st, g, ws.perm, ws.i0, (const T*)ws.wts, grid, U, guard, miss);
 }
 
 template void launch_point_prep<float>(const Plan&, Workspace&, const double*, const double*, cudaStream_t);

@@ -30,7 +30,7 @@ EXPORTS = ["fsib_create", "fsib_destroy", "fsib_set_stream", "fsib_set_option", 
            "fsib_batch_create", "fsib_batch_member", "fsib_batch_set_stream", "fsib_batch_autotune",
            "fsib_batch_step", "fsib_batch_info", "fsib_batch_last_error", "fsib_batch_destroy",
            "fsib_interp_grad", "fsib_step_adjoint", "fsib_set_force_target", "fsib_set_body_force",
-           "fsib_band_flux", "fsib_set_force_tension", "fsib_pressure"]
+           "fsib_band_flux", "fsib_set_force_tension", "fsib_pressure", "fsib_batch_set_option"]
 
 _lib = None
 
@@ -92,6 +92,7 @@ def load(path: str | None = None):
         "fsib_band_flux": ([vp, vp, i_, i_, d_, d_, dp], i_),
         "fsib_set_force_tension": ([vp, vp, i_, d_], i_),
         "fsib_pressure": ([vp, vp, vp, vp], i_),
+        "fsib_batch_set_option": ([vp, ctypes.c_char_p, d_], i_),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -388,6 +389,9 @@ class Batch:
 
     def autotune(self, X, uhat, U):
         self._bcall("fsib_batch_autotune", self._ptrs(X), self._ptrs(uhat), self._ptrs(U))
+
+    def set_option(self, key, value):
+        self._bcall("fsib_batch_set_option", key.encode(), float(value))
 
     def info(self, key):
         v = ctypes.c_double()
