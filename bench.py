@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--adjoint", action="store_true", help="time the differentiable workload (detail file)")
     ap.add_argument("--sweep", action="store_true", help="NUFFT point-count sweep (detail file)")
     ap.add_argument("--detail", default=None, help="write the long report (JSON) to this path")
+    ap.add_argument("--batch-size", type=int, default=64,
+                    help="problems of the batched workload taken (the first K of its 64; profiling runs)")
     ap.add_argument("--workload", choices=["ns3d_fp64", "ns3d_mixed", "ns2d_circle", "poiseuille",
                                            "sphere_elastic", "sphere_tension", "stokes2d"],
                     default="ns3d_fp64",
@@ -329,16 +331,19 @@ def roofline_of(site, arith, pk, pk_src, fp64_peak, fp32_peak, workload):
     return r
 
 
-def timed_steps(torch, pb, X, u, U, steps, flush, stream):
+def timed_steps(torch, pb, X, u, U, steps, flush, stream, label="timed"):
     """Device time (ms) of `steps` single steps, CUDA events on the launching stream around
-    each step, L2 flushed between steps (outside the events)."""
+    each step, L2 flushed between steps (outside the events). The steps sit in an NVTX range
+    named `label`, so a profiler can capture them alone (ncu --nvtx --nvtx-include label/)."""
     ev = [_events(torch) for _ in range(steps)]
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push(label)
     for s in range(steps):
         flush.zero_()
         ev[s][0].record(stream)
         pb.step(X, u, U, nsteps=1)
         ev[s][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in ev)
 
@@ -378,7 +383,7 @@ def site_profile(pb, X, u, U, flush, nprof):
 
 
 def measure(fsib, torch, prob, prec, steps, warmup, dev, flush, barrier=None, sampler_idx=None,
-            nufft_reps=20, nprof=20, native=False):
+            nufft_reps=20, nprof=20, native=False, label="timed"):
     """Time one workload: steps/s (CUDA events around each step, L2 flushed between steps),
     NUFFT pts/s for type-1 and type-2, and the per-launch-site breakdown."""
     stream = torch.cuda.current_stream()
@@ -399,7 +404,7 @@ def measure(fsib, torch, prob, prec, steps, warmup, dev, flush, barrier=None, sa
     if barrier:
         barrier()
     t_begin = time.time()
-    ms = timed_steps(torch, pb, X, u, U, steps, flush, stream)
+    ms = timed_steps(torch, pb, X, u, U, steps, flush, stream, label)
     if barrier:
         barrier()
     clocks = sampler.stop(t_begin, time.time()) if sampler else None
@@ -448,7 +453,8 @@ def error_vs_oracle(prob, Xo, uo, X, u):
 
 def native_block(fsib, torch, prob, dev, flush, steps, warmup, pk, pk_src, fp64_peak, fp32_peak):
     """The FP64 form with its transforms in native FP64 arithmetic (same workload, tuned)."""
-    m = measure(fsib, torch, prob, "fp64", steps, warmup, dev, flush, nufft_reps=5, nprof=5, native=True)
+    m = measure(fsib, torch, prob, "fp64", steps, warmup, dev, flush, nufft_reps=5, nprof=5, native=True,
+                label="native_timed")
     top = max(m["sites"], key=lambda s: s["total_ms"])
     r = roofline_of(top, "f64", pk, pk_src, fp64_peak, fp32_peak, None)
     out = {"value": steps / (m["ms"] * 1e-3), "unit": "steps/s", "ms_per_step": m["ms"] / steps, "steps": steps,
@@ -460,7 +466,7 @@ def native_block(fsib, torch, prob, dev, flush, steps, warmup, pk, pk_src, fp64_
 def mixed_block(fsib, torch, dev, flush, pk, pk_src, fp64_peak, fp32_peak, steps, warmup):
     """FP32-mixed workload (N = 128^3, M = 40322) with its error against an FP64 run of the same seed."""
     prob = wl.config_ns3d_mixed()
-    m = measure(fsib, torch, prob, "mixed", steps, warmup, dev, flush, nufft_reps=10, nprof=10)
+    m = measure(fsib, torch, prob, "mixed", steps, warmup, dev, flush, nufft_reps=10, nprof=10, label="mixed_timed")
     top = max(m["sites"], key=lambda s: s["total_ms"])
     pm = m["pb"]
     p64 = make_problem(fsib, prob, "fp64")
@@ -495,10 +501,10 @@ def mixed_block(fsib, torch, dev, flush, pk, pk_src, fp64_peak, fp32_peak, steps
     return line, detail
 
 
-def batched_block(fsib, torch, dev, flush, steps, warmup, pk):
+def batched_block(fsib, torch, dev, flush, steps, warmup, pk, size=64):
     """64 independent problems (2D/3D, N in {32..128}, M in [128, 20000]), FP32-mixed, autotuned,
-    advanced by one CUDA graph launch per step."""
-    probs = wl.config_batched()
+    advanced by one CUDA graph launch per step (`size` < 64: the first `size` of them)."""
+    probs = wl.config_batched()[:size]
     n = len(probs)
     B = fsib.Batch([p.N for p in probs], [p.d for p in probs], [p.M for p in probs], [p.mu for p in probs],
                    [p.rho for p in probs], [p.dt for p in probs], [p.tol for p in probs], precision="mixed")
@@ -520,11 +526,13 @@ def batched_block(fsib, torch, dev, flush, steps, warmup, pk):
         B.step(X, u, U, nsteps=1)
     torch.cuda.synchronize()
     ev = [_events(torch) for _ in range(steps)]
+    torch.cuda.nvtx.range_push("batched_timed")
     for s in range(steps):
         flush.zero_()
         ev[s][0].record(stream)
         B.step(X, u, U, nsteps=1)
         ev[s][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ok = all(bool(torch.isfinite(x).all()) for x in X)
@@ -747,7 +755,7 @@ def run_ours(args):
         mixed["nufft_pts_per_s"] = {k: v * world for k, v in mixed["nufft_pts_per_s"].items()}
     if not args.no_batched and prec == "fp64" and prob.d == 3:
         batched, detail["batched"] = batched_block(fsib, torch, dev, flush, steps=max(3, min(args.steps, 20)),
-                                                   warmup=max(3, args.warmup), pk=pk)
+                                                   warmup=max(3, args.warmup), pk=pk, size=args.batch_size)
         for k in ("value", "boundary_points_per_s"):
             batched[k] *= world
     if args.adjoint:

@@ -682,7 +682,7 @@ constexpr int kSumPlain = 0, kSumTerm = 1, kSumChunk = 2;
 template <typename T, int COMP> struct SumAcc { using type = T; };
 template <> struct SumAcc<float, kSumTerm> { using type = cf; };
 
-constexpr int kChunk = 32;  // candidates staged per round
+constexpr int kGatherChunk = 128;  // candidates staged per round (2D gather)
 
 // Neighbouring bins whose window starts can reach box (Bx, By, Bz) (defined below).
 __device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int Bx, int By, int Bz, int lane,
@@ -693,10 +693,10 @@ struct KSpreadGather {
   static constexpr int kThreads = 256, kMinBlocks = 0;
   static constexpr bool kAnyGrid = false;
   __device__ static void run(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
-                const T* __restrict__ W, const T* __restrict__ Cw, T* __restrict__ grid) {
-  __shared__ T sW[kChunk * D * kMaxW];
-  __shared__ T sC[kChunk * D];
-  __shared__ int sI[kChunk * 3];
+                             const T* __restrict__ W, const T* __restrict__ Cw, T* __restrict__ grid) {
+  __shared__ __align__(16) T sW[kGatherChunk * D * kMaxW];
+  __shared__ T sC[kGatherChunk * D];
+  __shared__ int sI[kGatherChunk * 3];
   const int w = g.w, nf = g.nf, M = g.M;
   const int bxs = g.b[0], bys = g.b[1], bzs = (D == 3) ? g.b[2] : 1;
   const int nseg = bxs / kSeg;
@@ -704,10 +704,12 @@ struct KSpreadGather {
   const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = (D == 3) ? box / (g.nb[0] * g.nb[1]) : 0;
   if (g.band && !g.band[Bz * g.nb[1] + By]) return;  // a row band that no window reaches: never read
   const int ox = Bx * bxs, oy = By * bys, oz = Bz * bzs;
-  // task: (component, z, y, segment) -> a run of kSeg cells along x
+  // task: (component, z, y, segment) -> a run of kSeg cells along x. The block holds G = blockDim
+  // / ntask groups of ntask threads; group q takes candidates q, q + G, ... of every staged chunk,
+  // and the groups' partial sums are added at the end (dense boxes hold thousands of candidates).
   const int ntask = D * bzs * bys * nseg;
-  const int task = threadIdx.x;
-  const bool active = task < ntask;
+  const int G = blockDim.x / ntask;
+  const int task = threadIdx.x % ntask, group = threadIdx.x / ntask;
   const int seg = task % nseg, ty = (task / nseg) % bys, tz = (task / (nseg * bys)) % bzs;
   const int comp = task / (nseg * bys * bzs);
   const int cx0 = ox + seg * kSeg, cy = oy + ty, cz = oz + tz;
@@ -718,8 +720,8 @@ struct KSpreadGather {
   for (int i = 0; i < kSeg; ++i) { acc[i] = A(0); tot[i] = cf(0.0f); }
   const long long gcells = (long long)nf * nf * (D == 3 ? nf : 1);
   // candidates: the points of the neighbouring bins (B + dlo .. B + dhi per axis, mod nb), as
-  // one list of ranges (first point, prefix of lengths) built by warp 0, staged kChunk at a time
-  __shared__ int sStart[32], sPre[33], sSp[kChunk];
+  // one list of ranges (first point, prefix of lengths) built by warp 0, staged kGatherChunk at a time
+  __shared__ int sStart[32], sPre[33], sSp[kGatherChunk];
   __shared__ int sNr;
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -743,75 +745,97 @@ struct KSpreadGather {
   }
   __syncthreads();
   const int nr = sNr, total = sPre[nr];
-  {
-    for (int c0 = 0; c0 < total; c0 += kChunk) {
-      const int nc = min(kChunk, total - c0);
-      __syncthreads();
-      for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int f = c0 + c;
-        int lo = 0, hi = nr - 1;  // last range with sPre <= f
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (sPre[mid] <= f) lo = mid; else hi = mid - 1;
-        }
-        const int sp = sStart[lo] + (f - sPre[lo]);
-        sSp[c] = sp;
-        for (int a = 0; a < D; ++a) {
-          sI[c * 3 + a] = i0s[(long long)a * M + sp];
-          sC[c * D + a] = Cw[(long long)sp * D + a];
-        }
+  for (int c0 = 0; c0 < total; c0 += kGatherChunk) {
+    const int nc = min(kGatherChunk, total - c0);
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const int f = c0 + c;
+      int lo = 0, hi = nr - 1;  // last range with sPre <= f
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sPre[mid] <= f) lo = mid; else hi = mid - 1;
       }
-      __syncthreads();
-      for (int i = threadIdx.x; i < nc * D * w; i += blockDim.x) {
-        const int c = i / (D * w), r = i % (D * w);
-        sW[c * D * kMaxW + r] = W[(long long)sSp[c] * D * w + r];
-      }
-      __syncthreads();
-      if (!active) continue;
-      for (int c = 0; c < nc; ++c) {
-        // window index of this thread's cells: (cell - i0) mod nf must lie in [0, w). With
-        // cell in [0, nf) and i0 in [-w/2, nf - w/2] one wrap suffices; since w + b <= nf a
-        // window meets the box through one periodic image only.
-        int qy = cy - sI[c * 3 + 1];
-        qy += (qy < 0) ? nf : 0; qy -= (qy >= nf) ? nf : 0;
-        if (qy >= w) continue;
-        int qz = 0;
-        if (D == 3) {
-          qz = cz - sI[c * 3 + 2];
-          qz += (qz < 0) ? nf : 0; qz -= (qz >= nf) ? nf : 0;
-          if (qz >= w) continue;
-        }
-        int qx0 = cx0 - sI[c * 3 + 0];
-        qx0 += (qx0 < 0) ? nf : 0; qx0 -= (qx0 >= nf) ? nf : 0;
-        if (qx0 > nf - kSeg) qx0 -= nf;  // run starts just before the window start
-        if (qx0 >= w) continue;
-        const T* wc = sW + c * D * kMaxW;  // axis a at offset a * w (layout of W)
-        T t = sC[c * D + comp] * wc[w + qy];
-        if (D == 3) t = t * wc[2 * w + qz];
-#pragma unroll
-        for (int i = 0; i < kSeg; ++i) {
-          const int qx = qx0 + i;
-          if (qx >= 0 && qx < w) {
-            if constexpr (COMP == kSumTerm && std::is_same<T, float>::value) fma_acc(acc[i], t, wc[qx]);
-            else acc[i] = acc[i] + t * wc[qx];
-          }
-        }
-      }
-      if constexpr (COMP == kSumChunk && std::is_same<T, float>::value) {
-#pragma unroll
-        for (int i = 0; i < kSeg; ++i) { add_comp(tot[i], acc[i]); acc[i] = A(0); }
+      const int sp = sStart[lo] + (f - sPre[lo]);
+      sSp[c] = sp;
+      for (int a = 0; a < D; ++a) {
+        sI[c * 3 + a] = i0s[(long long)a * M + sp];
+        sC[c * D + a] = Cw[(long long)sp * D + a];
       }
     }
-  }
-  if (active) {
-    T* out = grid + comp * gcells + ((long long)cz * nf + cy) * nf + cx0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc * D * w; i += blockDim.x) {
+      const int c = i / (D * w), r = i % (D * w);
+      sW[c * D * kMaxW + r] = W[(long long)sSp[c] * D * w + r];
+    }
+    __syncthreads();
+    for (int c = group; c < nc; c += G) {
+      // window index of this thread's cells: (cell - i0) mod nf must lie in [0, w). With
+      // cell in [0, nf) and i0 in [-w/2, nf - w/2] one wrap suffices; since w + b <= nf a
+      // window meets the box through one periodic image only.
+      int qy = cy - sI[c * 3 + 1];
+      qy += (qy < 0) ? nf : 0; qy -= (qy >= nf) ? nf : 0;
+      if (qy >= w) continue;
+      int qz = 0;
+      if (D == 3) {
+        qz = cz - sI[c * 3 + 2];
+        qz += (qz < 0) ? nf : 0; qz -= (qz >= nf) ? nf : 0;
+        if (qz >= w) continue;
+      }
+      int qx0 = cx0 - sI[c * 3 + 0];
+      qx0 += (qx0 < 0) ? nf : 0; qx0 -= (qx0 >= nf) ? nf : 0;
+      if (qx0 > nf - kSeg) qx0 -= nf;  // run starts just before the window start
+      if (qx0 >= w) continue;
+      const T* wc = sW + c * D * kMaxW;  // axis a at offset a * w (layout of W)
+      T t = sC[c * D + comp] * wc[w + qy];
+      if (D == 3) t = t * wc[2 * w + qz];
 #pragma unroll
-    for (int i = 0; i < kSeg; ++i) {
-      if constexpr (COMP == kSumChunk && std::is_same<T, float>::value) out[i] = acc_norm(tot[i]);
-      else out[i] = acc_norm(acc[i]);
+      for (int i = 0; i < kSeg; ++i) {
+        const int qx = qx0 + i;
+        if (qx >= 0 && qx < w) {
+          if constexpr (COMP == kSumTerm && std::is_same<T, float>::value) fma_acc(acc[i], t, wc[qx]);
+          else acc[i] = acc[i] + t * wc[qx];
+        }
+      }
+    }
+    if constexpr (COMP == kSumChunk && std::is_same<T, float>::value) {
+#pragma unroll
+      for (int i = 0; i < kSeg; ++i) { add_comp(tot[i], acc[i]); acc[i] = A(0); }
     }
   }
-}
+  // partial sums of the groups: groups 1.. store theirs (in the weight buffer, free now), group 0
+  // adds them (compensated in FP32) and writes the cells
+  T part[kSeg];
+#pragma unroll
+  for (int i = 0; i < kSeg; ++i) {
+    if constexpr (COMP == kSumChunk && std::is_same<T, float>::value) part[i] = acc_norm(tot[i]);
+    else part[i] = acc_norm(acc[i]);
+  }
+  if (G > 1) {
+    T* red = sW;  // [G - 1][ntask][kSeg] <= blockDim.x * kSeg values
+    __syncthreads();
+    if (group > 0) {
+#pragma unroll
+      for (int i = 0; i < kSeg; ++i) red[((group - 1) * ntask + task) * kSeg + i] = part[i];
+    }
+    __syncthreads();
+    if (group > 0) return;
+    if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+      for (int i = 0; i < kSeg; ++i) {
+        cf s(part[i]);
+        for (int q = 1; q < G; ++q) add_comp(s, red[((q - 1) * ntask + task) * kSeg + i]);
+        part[i] = acc_norm(s);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kSeg; ++i)
+        for (int q = 1; q < G; ++q) part[i] = part[i] + red[((q - 1) * ntask + task) * kSeg + i];
+    }
+  }
+  T* out = grid + comp * gcells + ((long long)cz * nf + cy) * nf + cx0;
+#pragma unroll
+  for (int i = 0; i < kSeg; ++i) out[i] = part[i];
+  }
 };
 
 
@@ -1498,9 +1522,11 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
       else run(type_tag<KSpreadBox3<T, kSumPlain>>());
     }
   } else {
-    // one thread per (component, row, run of kSeg cells) of the box
+    // one thread per (component, row, run of kSeg cells) of the box, times the candidate groups
+    // (up to 256 threads; every box side is a multiple of 8, so ntask = b^2/4 divides 256 or is 256)
     const int ntask = 2 * p.bins[1] * (p.bins[0] / kSeg);
-    const int threads = std::min(256, std::max(32, (ntask + 31) / 32 * 32));
+    const int groups = std::max(1, std::min(16, 256 / ntask));
+    const int threads = ntask * groups;
     const int mode = std::is_same<T, float>::value ? p.spread_sum : kSumPlain;
     auto run = [&](auto k) {
       using K = typename decltype(k)::type;
