@@ -239,17 +239,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a site, from one
-# ncu capture of the current kernels per workload (profiles/spread_site_traffic.txt,
-# profiles/kernels_ns3d_N128_M40322_mixed.txt). Set an entry to None when those kernels change.
-SITE_TRAFFIC = {("ns3d_N64_M10082_fp64", "spread"): 3843840.0,
-                ("ns3d_N128_M40322_mixed", "spread"): 9039872.0,
-                ("ns3d_N128_M40322_mixed", "nl.rows_product"): 112303360.0}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the site's dominant
+# kernel, from one ncu --set full capture of the current kernels per workload
+# (profiles/kernel_spread_df64_ns3d_N64_M10082.txt, profiles/kernel_product_pass_mixed_ns3d_N128_M40322.txt).
+# Set an entry to None when those kernels change.
+SITE_TRAFFIC = {("ns3d_N64_M10082_fp64", "spread"): 6672128.0,
+                ("ns3d_N128_M40322_mixed", "nl.rows_product"): 112418560.0}
 # What limits a site when it is not its roofline, from the same captures.
 SITE_LIMITER = {("ns3d_N128_M40322_mixed", "nl.rows_product"):
                 {"unit": "L1/shared memory", "frac": 0.891, "metric": "l1tex__throughput"},
                 ("ns3d_N64_M10082_fp64", "spread"):
-                {"unit": "instruction issue", "frac": 0.709, "metric": "sm__inst_issued per active cycle"}}
+                {"unit": "instruction issue", "frac": 0.597, "metric": "sm__issue_active"}}
 
 
 def _events(torch):
