@@ -316,7 +316,7 @@ int fsib_measure_peak(int kind, double* gflops);
  * double or float complex per precision) must be device arrays; the work is
  * enqueued on `stream` (a cudaStream_t, NULL = legacy default stream).
  * Returns FSIB_EINVAL, with a message in fsib_static_last_error(), when the
- * problem needs more scratch than the array holds (e.g. 3D FP64 N > 40, or 3D
+ * problem needs more scratch than the array holds (e.g. 3D FP64 N > 48, or 3D
  * mixed N > 64 at moderate M) or an argument is invalid.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before

@@ -162,7 +162,7 @@ def interp_direct_complex(Fu: np.ndarray, X: np.ndarray, N: int, L: float = 1.0,
 
 
 def interp_direct(Fu: np.ndarray, X: np.ndarray, N: int, L: float = 1.0,
-                  chunk: int = 2048, imag_rtol: float = 1e-11) -> np.ndarray:
+                  chunk: int = 2048, imag_rtol: float = 1e-14) -> np.ndarray:
     """Real velocity at the points. The imaginary part is checked, not dropped silently."""
     Uc = interp_direct_complex(Fu, X, N, L, chunk)
     scale = max(float(np.max(np.abs(Uc))) if Uc.size else 0.0, 1e-300)
