@@ -270,17 +270,17 @@ struct KRowsProduct {
 template <typename T, int N>
 __device__ __forceinline__ void wfft_load_packed(C<T> (&v)[wfft_M(N)], const C<T>* __restrict__ A,
                                                  const C<T>* __restrict__ B, int l, int h, bool valid) {
-  constexpr int M = wfft_M(N), L = wfft_L(N);
+  constexpr int M = wfft_M(N), L = wfft_L(N), NN = wfft_n(N);
   if constexpr (sizeof(C<T>) != 8) {
 #pragma unroll
-    for (int i = 0; i < M; ++i) v[i] = valid ? pack_rows<T>(A, B, l + L * i, N, h) : mk<T>(T(0), T(0));
+    for (int i = 0; i < M; ++i) v[i] = valid ? pack_rows<T>(A, B, l + L * i, NN, h) : mk<T>(T(0), T(0));
   } else {
   C<T> a[M], b[M];
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const int k = l + L * i;
-    const bool lo = k < h, hi = k > N - h;
-    const int kk = lo ? k : N - k;
+    const bool lo = k < h, hi = k > NN - h;
+    const int kk = lo ? k : NN - k;
     const bool ok = valid && (lo || hi);
     a[i] = ok ? A[kk] : mk<T>(T(0), T(0));
     b[i] = ok ? B[kk] : mk<T>(T(0), T(0));
@@ -356,7 +356,7 @@ using WRowsC2R = std::conditional_t<sizeof(C<T>) == 8, KWRowsC2R<T, N>, KWRowsC2
 template <typename T, int N>
 __device__ __forceinline__ void wfft_untangle(const C<T> (&v)[wfft_M(N)], C<T>* buf, int l, bool valid, int h,
                                               C<T>* __restrict__ outA, C<T>* __restrict__ outB) {
-  constexpr int M = wfft_M(N), L = wfft_L(N);
+  constexpr int M = wfft_M(N), L = wfft_L(N), NN = wfft_n(N);
 #pragma unroll
   for (int i = 0; i < M; ++i) buf[wfft_out_index<N>(l, i)] = v[i];
   __syncwarp();
@@ -366,7 +366,7 @@ __device__ __forceinline__ void wfft_untangle(const C<T> (&v)[wfft_M(N)], C<T>* 
       const int k = l + L * i;
       if (k < h) {
         const C<T> Z = buf[k];
-        const C<T> Zc = cconj<T>(buf[k == 0 ? 0 : N - k]);
+        const C<T> Zc = cconj<T>(buf[k == 0 ? 0 : NN - k]);
         const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
         outA[k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
         outB[k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
@@ -455,6 +455,13 @@ static __constant__ int kProdSched2[5] = {0 | 0 << 4 | 0 << 8 | 2 << 12,        
 // (exchanging through S2) and give xx, xy, yy (exchanging through S2); u_z then goes to S2,
 // and xz, yz, zz each exchange through the buffer of a component they no longer need (S0,
 // S1, S2), which takes three line buffers per row pair instead of four. Blocks of 128 threads.
+// Warp plan of the product pass: FP32 lines of 96 and 192 points take the one-exchange plans
+// (the pass is bound by its shared-memory exchanges), double-float lines the default ones.
+template <typename T, int N>
+constexpr int prod_plan() {
+  return (std::is_same<T, float>::value && wfft_has(N | kOneExchange)) ? (N | kOneExchange) : N;
+}
+
 template <typename T, int N>
 struct KWRowsProduct {
   static constexpr int kThreads = 128, kMinBlocks = 0;
@@ -462,13 +469,14 @@ struct KWRowsProduct {
   static constexpr bool kMerge = std::is_same<T, float>::value;  // batches merge FP32 transforms only
   __device__ static void run(const C<T>* __restrict__ in, C<T>* __restrict__ out, int d, long long nrows, int Nk,
                 const C<T>* __restrict__ twg) {
-  constexpr int M = wfft_M(N), L = wfft_L(N), LPW = 32 / L, SL = wfft_stride(N, (int)sizeof(C<T>));
+  constexpr int PC = prod_plan<T, N>();
+  constexpr int M = wfft_M(PC), L = wfft_L(PC), LPW = 32 / L, SL = wfft_stride(PC, (int)sizeof(C<T>));
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(N))
+  C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(PC))
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int l = lane % L, sub = lane / L;
-  C<T>* S = tw + wfft_tw_size(N) + (warp * LPW + sub) * 3 * SL;  // S0, S1, S2
-  wfft_build_twiddles<T, N>(tw, twg);
+  C<T>* S = tw + wfft_tw_size(PC) + (warp * LPW + sub) * 3 * SL;  // S0, S1, S2
+  wfft_build_twiddles<T, PC>(tw, twg);
   __syncthreads();
   const int h = Nk / 2;
   const long long npairs = nrows / 2;
@@ -486,7 +494,7 @@ struct KWRowsProduct {
       // the loop holds a single copy of the transform code.
       if (kind == 0) {
         const C<T>* base = in + ((long long)sa * nrows + 2 * pr) * h;
-        wfft_load_packed<T, N>(v, base, base + h, l, h, valid);
+        wfft_load_packed<T, PC>(v, base, base + h, l, h, valid);
 #pragma unroll
         for (int i = 0; i < M; ++i) v[i] = cconj<T>(v[i]);
       } else {
@@ -498,14 +506,14 @@ struct KWRowsProduct {
         }
         __syncwarp();  // the exchange slot may hold a factor
       }
-      wfft<T, false, N>(v, X, l, tw);
+      wfft<T, false, PC>(v, X, l, tw);
       if (kind == 0) {
 #pragma unroll
-        for (int i = 0; i < M; ++i) S[sb * SL + wfft_out_index<N>(l, i)] = cconj<T>(v[i]);
+        for (int i = 0; i < M; ++i) S[sb * SL + wfft_out_index<PC>(l, i)] = cconj<T>(v[i]);
         __syncwarp();
       } else {
         C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
-        wfft_untangle<T, N>(v, X, l, valid, h, ob, ob + h);
+        wfft_untangle<T, PC>(v, X, l, valid, h, ob, ob + h);
       }
     }
   }
@@ -831,10 +839,13 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
   const size_t smem = sizeof(C<T>) * (size_t)(fl.n + 2 * kQrows * lp * (fl.n + 1));
   with_fft_len(fl.n, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
-    constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(NC) : 1;
+    constexpr int PC = wfft_has(NC) ? prod_plan<T, NC>() : NC;
+    constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(PC) : 1;
     if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
+      // (blocks of two warps for the one-exchange plans measured slower: 80.6 against 74.6 us at
+      // length 192, with more bank conflicts)
       constexpr int PT = 128;
-      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(NC) + (PT / 32) * LPW * 3 * wfft_stride(NC, (int)sizeof(C<T>)));
+      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(PC) + (PT / 32) * LPW * 3 * wfft_stride(PC, (int)sizeof(C<T>)));
       using K = KWRowsProduct<T, NC>;
       raise_smem_limit(kernel_ptr<K>());
       launch<K>(wrows_grid(kernel_ptr<K>(), PT, ws, (npairs + LPW - 1) / LPW), PT, ws, st, in, out, d, nrows, Nk,

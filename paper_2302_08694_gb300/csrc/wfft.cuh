@@ -1,4 +1,5 @@
-// Warp-level FFT of one line held in registers (row passes of the lengths below).
+// Warp-level FFT of one line held in registers (row passes of the lengths below). The N of the
+// templates below is a plan code (see wfft_n): the line length for the default plans.
 //
 // A line of length N is owned by L lanes of a warp (32/L lines per warp); lane l holds
 // M = N/L elements. The transform is the self-sorting (Stockham) factorisation of
@@ -15,44 +16,65 @@
 
 namespace fsib {
 
-// Lengths with a warp plan: 64, 128, 256 (M = 8) and 48, 96, 192 (M = 12).
-constexpr bool wfft_has(int n) { return n == 64 || n == 128 || n == 256 || n == 48 || n == 96 || n == 192; }
-constexpr int wfft_M(int n) { return (n == 48 || n == 96 || n == 192) ? 12 : 8; }
-constexpr int wfft_L(int n) { return n / wfft_M(n); }
-constexpr int wfft_radix(int n, int s) {
-  return n == 64    ? (s == 0 ? 8 : s == 1 ? 8 : 0)
-         : n == 128 ? (s == 0 ? 8 : s == 1 ? 4 : s == 2 ? 4 : 0)
-         : n == 256 ? (s == 0 ? 8 : s == 1 ? 8 : s == 2 ? 4 : 0)
-         : n == 48  ? (s == 0 ? 12 : s == 1 ? 4 : 0)
-         : n == 96  ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 2 : 0)
-         : n == 192 ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 4 : 0)
+// A warp plan is named by a code: the line length n, plus kOneExchange for the plans with 24
+// elements per lane (lengths 96 and 192, FP32 lines), whose radix-24 first stage leaves a single
+// exchange (24 x 4 and 24 x 8) instead of two; they double a lane's registers, so the
+// double-float passes keep the default plans.
+constexpr int kOneExchange = 1 << 16;
+constexpr int wfft_n(int c) { return c & 0xFFFF; }
+constexpr bool wfft_one(int c) { return (c & kOneExchange) != 0; }
+// Lengths with a warp plan: 64, 128, 256 (M = 8) and 48, 96, 192 (M = 12); one-exchange plans of
+// 96 and 192 (M = 24).
+constexpr bool wfft_has(int c) {
+  return wfft_one(c) ? (wfft_n(c) == 96 || wfft_n(c) == 192)
+                     : (c == 64 || c == 128 || c == 256 || c == 48 || c == 96 || c == 192);
+}
+constexpr int wfft_M(int c) {
+  return wfft_one(c) ? 24 : (c == 48 || c == 96 || c == 192) ? 12 : 8;
+}
+constexpr int wfft_L(int c) { return wfft_n(c) / wfft_M(c); }
+constexpr int wfft_radix(int c, int s) {
+  return c == 64    ? (s == 0 ? 8 : s == 1 ? 8 : 0)
+         : c == 128 ? (s == 0 ? 8 : s == 1 ? 4 : s == 2 ? 4 : 0)
+         : c == 256 ? (s == 0 ? 8 : s == 1 ? 8 : s == 2 ? 4 : 0)
+         : c == 48  ? (s == 0 ? 12 : s == 1 ? 4 : 0)
+         : c == 96  ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 2 : 0)
+         : c == 192 ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 4 : 0)
+         : c == (96 | kOneExchange)  ? (s == 0 ? 24 : s == 1 ? 4 : 0)
+         : c == (192 | kOneExchange) ? (s == 0 ? 24 : s == 1 ? 8 : 0)
                     : 0;
 }
-constexpr int wfft_nstages(int n) {
+constexpr int wfft_nstages(int c) {
   int s = 0;
-  while (wfft_radix(n, s)) ++s;
+  while (wfft_radix(c, s)) ++s;
   return s;
 }
 // Swizzle of the exchange after stage ex for elements of E bytes: shift (hi 8 bits) and mask.
-constexpr int wfft_swz(int n, int E, int ex) {
-  return E == 8 ? (n == 64    ? (ex == 0 ? (3 << 8 | 7) : 0)
-                   : n == 128 ? (ex == 0 ? (3 << 8 | 15) : ex == 1 ? (2 << 8 | 15) : 0)
-                   : n == 256 ? (ex == 0 ? (3 << 8 | 15) : ex == 1 ? (3 << 8 | 15) : 0)
-                   : n == 48  ? (ex == 0 ? (2 << 8 | 3) : 0)
-                   : n == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
-                   : n == 192 ? (ex == 0 ? (2 << 8 | 15) : ex == 1 ? (2 << 8 | 7) : 0)
+// One-exchange plans (FP32 only): chosen with the same bank model, the 16 addresses of each
+// half-warp access (8-byte elements) in distinct bank pairs for the stores after the radix-24
+// stage and the loads before the last one.
+constexpr int wfft_swz(int c, int E, int ex) {
+  return wfft_one(c) ? (E == 8 && ex == 0 ? (wfft_n(c) == 192 ? (3 << 8 | 7) : (3 << 8 | 3)) : 0)
+         : E == 8 ? (c == 64    ? (ex == 0 ? (3 << 8 | 7) : 0)
+                   : c == 128 ? (ex == 0 ? (3 << 8 | 15) : ex == 1 ? (2 << 8 | 15) : 0)
+                   : c == 256 ? (ex == 0 ? (3 << 8 | 15) : ex == 1 ? (3 << 8 | 15) : 0)
+                   : c == 48  ? (ex == 0 ? (2 << 8 | 3) : 0)
+                   : c == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
+                   : c == 192 ? (ex == 0 ? (2 << 8 | 15) : ex == 1 ? (2 << 8 | 7) : 0)
                               : 0)
-                : (n == 64    ? (ex == 0 ? (3 << 8 | 7) : 0)
-                   : n == 128 ? (ex == 0 ? (3 << 8 | 7) : 0)
-                   : n == 256 ? (ex == 0 ? (3 << 8 | 7) : 0)
-                   : n == 48  ? (ex == 0 ? (2 << 8 | 3) : 0)
-                   : n == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
-                   : n == 192 ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
+                : (c == 64    ? (ex == 0 ? (3 << 8 | 7) : 0)
+                   : c == 128 ? (ex == 0 ? (3 << 8 | 7) : 0)
+                   : c == 256 ? (ex == 0 ? (3 << 8 | 7) : 0)
+                   : c == 48  ? (ex == 0 ? (2 << 8 | 3) : 0)
+                   : c == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
+                   : c == 192 ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
                               : 0);
 }
-// Elements per line buffer (N plus bank padding).
-constexpr int wfft_stride(int n, int E) {
-  return n + (E == 8 ? (n == 64 ? 8 : n == 48 ? 4 : n == 96 ? 8 : 0) : (n == 48 ? 4 : 0));
+// Elements per line buffer (n plus bank padding; the one-exchange plans' line strides are 8 and
+// 4 mod 16 elements, so the lines of a half-warp also fall in distinct bank pairs).
+constexpr int wfft_stride(int c, int E) {
+  return wfft_one(c) ? wfft_n(c) + (wfft_n(c) == 192 ? 8 : 4)
+                     : c + (E == 8 ? (c == 64 ? 8 : c == 48 ? 4 : c == 96 ? 8 : 0) : (c == 48 ? 4 : 0));
 }
 template <int SW>
 __device__ __forceinline__ int wswz(int e) {
@@ -95,6 +117,26 @@ __device__ __forceinline__ void dft12(C<T>* v) {
     dft4<T, INV>(b);
 #pragma unroll
     for (int k2 = 0; k2 < 4; ++k2) v[(4 * k1 + 9 * k2) % 12] = b[k2];
+  }
+}
+
+// 24-point DFT by the prime-factor mapping 24 = 3 x 8 (no twiddles): input index
+// (8 n1 + 3 n2) mod 24, output index (16 k1 + 9 k2) mod 24.
+template <typename T, bool INV>
+__device__ __forceinline__ void dft24(C<T>* v) {
+  C<T> a[8][3];
+#pragma unroll
+  for (int n2 = 0; n2 < 8; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 3; ++n1) a[n2][n1] = v[(8 * n1 + 3 * n2) % 24];
+    dft3<T, INV>(a[n2]);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    C<T> b[8] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1], a[4][k1], a[5][k1], a[6][k1], a[7][k1]};
+    dft8<T, INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) v[(16 * k1 + 9 * k2) % 24] = b[k2];
   }
 }
 
@@ -183,29 +225,30 @@ __device__ __forceinline__ void dft_r(C<T>* v) {
   else if constexpr (R == 9) dft9<T, INV>(v);
   else if constexpr (R == 12) dft12<T, INV>(v);
   else if constexpr (R == 16) dft16<T, INV>(v);
+  else if constexpr (R == 24) dft24<T, INV>(v);
 }
 
 // Twiddles in lane order: for stage s >= 1, butterfly slot b, r = 1..R-1 and lane l, entry
 // wfft_tw_off(N, s) + (b (R-1) + r - 1) L + l holds w^{(j mod NS) r N/(NS R)}, j = l + L b,
 // w = exp(-2 pi i / N), so that the lanes of a warp read consecutive entries.
-constexpr int wfft_tw_off(int n, int s) {
+constexpr int wfft_tw_off(int c, int s) {
   int off = 0;
-  for (int t = 1; t < s; ++t) off += (n / wfft_radix(n, t)) * (wfft_radix(n, t) - 1);
+  for (int t = 1; t < s; ++t) off += (wfft_n(c) / wfft_radix(c, t)) * (wfft_radix(c, t) - 1);
   return off;
 }
-constexpr int wfft_tw_size(int n) { return wfft_tw_off(n, wfft_nstages(n)); }
+constexpr int wfft_tw_size(int c) { return wfft_tw_off(c, wfft_nstages(c)); }
 
 // Build the lane-ordered table from the natural table tw[k] = exp(-2 pi i k / N) (global).
 template <typename T, int N>
 __device__ __forceinline__ void wfft_build_twiddles(C<T>* twl, const C<T>* __restrict__ tw) {
-  constexpr int L = wfft_L(N);
+  constexpr int L = wfft_L(N), NN = wfft_n(N);
   for (int e = threadIdx.x; e < wfft_tw_size(N); e += blockDim.x) {
     int s = 1, NS = wfft_radix(N, 0);
     while (e >= wfft_tw_off(N, s + 1)) { NS *= wfft_radix(N, s); ++s; }
     const int R = wfft_radix(N, s), q = e - wfft_tw_off(N, s);
     const int l = q % L, br = q / L, b = br / (R - 1), r = br % (R - 1) + 1;
     const int j = l + L * b;
-    twl[e] = tw[(j % NS) * r * (N / (NS * R))];
+    twl[e] = tw[(j % NS) * r * (NN / (NS * R))];
   }
 }
 
@@ -213,7 +256,7 @@ __device__ __forceinline__ void wfft_build_twiddles(C<T>* twl, const C<T>* __res
 // exchange buffer; twl: the lane-ordered twiddle table in shared memory.
 template <typename T, bool INV, int N, int S = 0, int NS = 1>
 __device__ __forceinline__ void wfft(C<T> (&v)[wfft_M(N)], C<T>* buf, int l, const C<T>* __restrict__ twl) {
-  constexpr int M = wfft_M(N), L = wfft_L(N), R = wfft_radix(N, S), NB = M / R;
+  constexpr int M = wfft_M(N), L = wfft_L(N), R = wfft_radix(N, S), NB = M / R, NN = wfft_n(N);
   constexpr int E = (int)sizeof(C<T>);
   if constexpr (S > 0) {
     // gather this stage's inputs x[j + r N/R], j = l + L b, from the previous stage's outputs
@@ -221,7 +264,7 @@ __device__ __forceinline__ void wfft(C<T> (&v)[wfft_M(N)], C<T>* buf, int l, con
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b * R + r] = buf[wswz<SW>(l + L * b + r * (N / R))];
+      for (int r = 0; r < R; ++r) v[b * R + r] = buf[wswz<SW>(l + L * b + r * (NN / R))];
     __syncwarp();
   }
 #pragma unroll
@@ -254,7 +297,7 @@ __device__ __forceinline__ void wfft(C<T> (&v)[wfft_M(N)], C<T>* buf, int l, con
 template <int N>
 __device__ __forceinline__ int wfft_out_index(int l, int i) {
   constexpr int RL = wfft_radix(N, wfft_nstages(N) - 1);
-  return l + wfft_L(N) * (i / RL) + (N / RL) * (i % RL);
+  return l + wfft_L(N) * (i / RL) + (wfft_n(N) / RL) * (i % RL);
 }
 
 }  // namespace fsib
