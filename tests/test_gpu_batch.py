@@ -185,3 +185,66 @@ def test_batch_members_match_oracle(lib, torch_mod, prec, merge):
         assert eU <= t and eu <= t, (i, p["d"], p["N"], p["M"], eU, eu)
         assert eX <= 4e-16 + 2e-4 * t * np.max(np.abs(Uo)), (i, eX)
     B.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_with_stokes_members_and_group_splits(lib, torch_mod, prec):
+    """Quasi-static Stokes members (whose step ends with copies of U and u-hat, recorded like
+    the kernels) beside Navier-Stokes members, in groups that group_max splits: every member
+    matches its own handle after three steps, whatever the grouping."""
+    torch = torch_mod
+    specs = [(2, 16, 120, 0.0), (2, 16, 90, 0.0), (2, 16, 70, 0.0), (3, 12, 0, 0.0), (3, 12, 0, 0.0),
+             (2, 16, 100, 1.0), (3, 12, 0, 1.0)]
+    probs = []
+    for i, (d, N, M, rho) in enumerate(specs):
+        if d == 2:
+            X0 = wl.ellipse(M, 0.22 + 0.01 * i, 0.17, (0.45 + 0.02 * i, 0.52))
+            probs.append(dict(d=2, N=N, M=M, X0=X0, force="curve", rho=rho))
+        else:
+            Xref, tri = wl.latlong_sphere(4 + i % 2, 8 + 2 * (i % 2), 0.25, (0.5, 0.48, 0.51))
+            X0 = 0.5 + (Xref - 0.5) * np.array([[1.1], [0.93], [1.0]])
+            probs.append(dict(d=3, N=N, M=X0.shape[1], X0=X0, force="mesh", Xref=Xref, tri=tri, rho=rho))
+    n = len(probs)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    refs = []
+    for p in probs:
+        s = lib.Problem(p["N"], p["d"], p["M"], 0.02, p["rho"], 2e-3, tol, precision=prec)
+        setup(s, p, torch)
+        X = torch.from_numpy(p["X0"].copy()).cuda()
+        u, U = s.new_spec(), torch.zeros_like(X)
+        s.step(X, u, U, nsteps=3)
+        torch.cuda.synchronize()
+        refs.append((X.cpu().numpy(), u.cpu().numpy(), U.cpu().numpy()))
+    t = 1e-12 if prec == "fp64" else 1e-5
+    for gmax in (0, 2, 1):
+        B = lib.Batch([p["N"] for p in probs], [p["d"] for p in probs], [p["M"] for p in probs], [0.02] * n,
+                      [p["rho"] for p in probs], [2e-3] * n, [tol] * n, precision=prec)
+        B.set_option("group_max", gmax)
+        assert B.info("group_max") == gmax
+        Xb, ub, Ub = [], [], []
+        for p, m in zip(probs, B.members):
+            setup(m, p, torch)
+            X = torch.from_numpy(p["X0"].copy()).cuda()
+            Xb.append(X)
+            ub.append(m.new_spec())
+            Ub.append(torch.zeros_like(X))
+        B.step(Xb, ub, Ub, nsteps=3)
+        torch.cuda.synchronize()
+        # 2D Stokes / 3D Stokes / 2D NS / 3D NS classes; group_max splits the three 2D Stokes members
+        expect = {0: 4, 2: 5, 1: n}[gmax]
+        assert B.info("groups") == expect
+        for i, (p, (Xr, ur, Ur)) in enumerate(zip(probs, refs)):
+            x0 = p["X0"]
+            assert rel2(Xb[i].cpu().numpy() - x0, Xr - x0) <= t, (gmax, i)
+            assert rel2(ub[i].cpu().numpy(), ur) <= t, (gmax, i)
+            assert rel2(Ub[i].cpu().numpy(), Ur) <= t, (gmax, i)
+        B.close()
+
+
+def test_batch_options_are_checked(lib, torch_mod):
+    B = lib.Batch([8, 8], [2, 2], [20, 30], [0.1, 0.1], [1.0, 1.0], [1e-3, 1e-3], [1e-6, 1e-6], precision="mixed")
+    assert B.info("merge") == 1 and B.info("group_max") == 0
+    for key, value in (("merge", 2), ("group_max", -1), ("group_max", 1.5), ("no_such_key", 1)):
+        with pytest.raises(lib.FsibError):
+            B.set_option(key, value)
+    B.close()
