@@ -55,12 +55,39 @@ struct KForceMesh {
   __device__ static void run(const double* __restrict__ X, double* __restrict__ c, int M,
                              const int* __restrict__ ptr, const int* __restrict__ col,
                              const double* __restrict__ kv) {
-  const int sl = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3;
+  const int sl = threadIdx.x & 7, sub = (threadIdx.x >> 3) & 3, lane = threadIdx.x & 31;
   // warp-uniform loop over groups of four vertices (the shuffles need the whole warp)
   for (long long w0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; w0 < M;
        w0 += (((long long)gridDim.x * blockDim.x) >> 5) * 4) {
     const int i = (int)(w0 + sub);
     const bool ok = i < M;
+    // A vertex of high degree (a pole of a lat-long mesh joins a whole ring) would keep its
+    // eight lanes for degree/8 rounds: such a warp takes its four vertices one at a time, all
+    // 32 lanes on each.
+    const int deg = ok ? ptr[i + 1] - ptr[i] : 0;
+    if (__reduce_max_sync(0xffffffffu, (unsigned)deg) > 32u) {
+      for (int q = 0; q < 4; ++q) {
+        const int iq = (int)(w0 + q);
+        if (iq >= M) break;  // uniform across the warp
+        const double x0 = X[iq], x1 = X[M + iq], x2 = X[2LL * M + iq];
+        double g0 = 0, g1 = 0, g2 = 0;
+        for (int e = ptr[iq] + lane; e < ptr[iq + 1]; e += 32) {
+          const int j = col[e];
+          const double k = kv[e];
+          g0 += k * (X[j] - x0);
+          g1 += k * (X[M + j] - x1);
+          g2 += k * (X[2LL * M + j] - x2);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          g0 += __shfl_xor_sync(0xffffffffu, g0, off);
+          g1 += __shfl_xor_sync(0xffffffffu, g1, off);
+          g2 += __shfl_xor_sync(0xffffffffu, g2, off);
+        }
+        if (lane == 0) { c[iq] = g0; c[M + iq] = g1; c[2LL * M + iq] = g2; }
+      }
+      continue;
+    }
     double f0 = 0, f1 = 0, f2 = 0;
     if (ok) {
       const double x0 = X[i], x1 = X[M + i], x2 = X[2LL * M + i];
