@@ -842,8 +842,8 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
     constexpr int PC = wfft_has(NC) ? prod_plan<T, NC>() : NC;
     constexpr int LPW = wfft_has(NC) ? 32 / wfft_L(PC) : 1;
     if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
-      // (blocks of two warps for the one-exchange plans measured slower: 80.6 against 74.6 us at
-      // length 192, with more bank conflicts)
+      // Blocks of two warps measured no faster: double-float length 96 (five resident blocks instead
+      // of two) 127.0 against 127.4 us a step, FP32 one-exchange length 192 80.6 against 74.6 us.
       constexpr int PT = 128;
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(PC) + (PT / 32) * LPW * 3 * wfft_stride(PC, (int)sizeof(C<T>)));
       using K = KWRowsProduct<T, NC>;
