@@ -47,8 +47,20 @@ template <class H, class... T> struct PackMaker<H, T...> {
   }
 };
 
+// Programmatic dependent launch: every launch-layer kernel is launched with programmatic stream
+// serialisation and waits, before its body runs, for the previous kernel of its stream to
+// complete with its memory operations visible (griddepcontrol.wait). No kernel triggers early, so
+// the next kernel's blocks become eligible as this kernel's blocks exit: its launch overlaps this
+// kernel's last wave instead of following the whole grid, while every body still sees the memory
+// effects of plain stream order. Triggering at block entry (launch_dependents) was slower: the
+// waiting blocks then held SM slots that the running kernel's later waves needed.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <class K, class... P>
 __global__ void __launch_bounds__(K::kThreads, K::kMinBlocks) k_single(P... p) {
+  pdl_enter();
   K::run(p...);
 }
 // The parameters of up to kMaxMerge problems travel by value in the kernel's parameter space (the
@@ -57,7 +69,24 @@ constexpr int kMaxMerge = 16;
 template <class PK> struct PackTable { PK p[kMaxMerge]; };
 template <class K, class... P>
 __global__ void __launch_bounds__(K::kThreads, K::kMinBlocks) k_multi(const PackTable<Pack<P...>> t) {
+  pdl_enter();
   t.p[blockIdx.y].template call<K>();
+}
+
+// Launch with programmatic stream serialisation (see pdl_enter).
+template <class... P, class... A>
+inline void pdl_launch(void (*kern)(P...), dim3 g, dim3 b, size_t smem, cudaStream_t st, A&&... a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<A>(a)...);
 }
 
 void raise_smem_limit(const void* kernel);
@@ -109,10 +138,11 @@ template <class K, class... P> struct Launcher<K, void (*)(P...)> {
     if (smem > 48 * 1024) raise_smem_limit(multi());
     PackTable<PK> t;
     for (unsigned i = 0; i < g.y && i < (unsigned)kMaxMerge; ++i) std::memcpy(&t.p[i], packs[i], sizeof(PK));
-    k_multi<K, std::decay_t<P>...><<<g, b, smem, st>>>(t);
+    pdl_launch(&k_multi<K, std::decay_t<P>...>, g, b, smem, st, t);
   }
   static void emit_one(dim3 g, dim3 b, size_t smem, cudaStream_t st, const void* pack) {
-    reinterpret_cast<const PK*>(pack)->apply([&](auto... a) { k_single<K, std::decay_t<P>...><<<g, b, smem, st>>>(a...); });
+    reinterpret_cast<const PK*>(pack)->apply(
+        [&](auto... a) { pdl_launch(&k_single<K, std::decay_t<P>...>, g, b, smem, st, a...); });
   }
   template <class... A>
   static void go(dim3 g, dim3 b, size_t smem, cudaStream_t st, A&&... a) {
@@ -139,7 +169,7 @@ template <class K, class... P> struct Launcher<K, void (*)(P...)> {
       r->ops.push_back(std::move(op));
       return;
     }
-    k_single<K, std::decay_t<P>...><<<g, b, smem, st>>>(std::decay_t<P>(std::forward<A>(a))...);
+    pdl_launch(&k_single<K, std::decay_t<P>...>, g, b, smem, st, std::decay_t<P>(std::forward<A>(a))...);
   }
 };
 
