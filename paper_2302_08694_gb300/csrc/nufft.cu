@@ -1028,6 +1028,7 @@ __device__ __forceinline__ void finish_split_box(const PointGeom& g, int box, in
 // warp's plane is skipped by the whole warp.
 constexpr int kBoxChunk = 64;
 __device__ __forceinline__ bool is_zero(float v) { return v == 0.0f; }
+__device__ __forceinline__ bool is_zero(double v) { return v == 0.0; }
 __device__ __forceinline__ bool is_zero(dd v) { return v.hi == 0.0f; }
 
 template <typename T, int COMP>
@@ -1171,7 +1172,8 @@ struct KSpreadBox3 {
 // while staging: a group of eight threads per candidate evaluates the box-relative weights
 // of offset t on each axis, shares them by shuffles, and writes the candidate's 8 x 8 table
 // of w_x w_y products and its d x 8 values C_a w_z (plus w_z for the plane test).
-constexpr int kBoxChunkDD = 32;   // candidates per chunk (eight threads each)
+constexpr int kBoxChunkDD = 32;   // candidates per chunk (eight threads each; one per lane of a warp)
+static_assert(kBoxChunkDD == 32, "the double-float gather keeps a chunk's candidate lists in one ballot word");
 constexpr int kXYStride = 72;     // per-candidate stride of the x-y table (64 + 8: staging stores hit all banks)
 struct KSpreadBox3DD {
   static constexpr int kThreads = 256, kMinBlocks = 0;
@@ -1182,8 +1184,9 @@ struct KSpreadBox3DD {
                  dd* __restrict__ part,
                  dd* __restrict__ grid, int* __restrict__ work, int* __restrict__ done) {
   // dynamic shared memory (above the 48 KB static limit): two buffers of
-  //   [c][y][x] w_x w_y (stride kXYStride), [c][a][z] C_a w_z, [c] mask of the z planes the
-  //   candidate reaches (0 when its window misses the box along x or y)
+  //   [c][y][x] w_x w_y (stride kXYStride), [c][a][z] C_a w_z, [c] mask: bits 0-7 the z planes
+  //   the candidate reaches, bits 8 and 9 the lower and upper y halves (0 when its window misses
+  //   the box along x)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd (*sXY)[kBoxChunkDD * kXYStride] = reinterpret_cast<dd (*)[kBoxChunkDD * kXYStride]>(smem_raw);
   dd (*sCz)[kBoxChunkDD * 24] = reinterpret_cast<dd (*)[kBoxChunkDD * 24]>(sXY + 2);
@@ -1270,8 +1273,15 @@ struct KSpreadBox3DD {
       const unsigned bx = (__ballot_sync(0xffffffffu, on && wa[0].hi != 0.0f) >> gs) & 0xffu;
       const unsigned by = (__ballot_sync(0xffffffffu, on && wa[1].hi != 0.0f) >> gs) & 0xffu;
       const unsigned bz = (__ballot_sync(0xffffffffu, on && wa[2].hi != 0.0f) >> gs) & 0xffu;
-      if (on && t == 0) sMask[bb][c] = (bx && by) ? bz : 0u;
+      if (on && t == 0)
+        sMask[bb][c] = bx ? (bz | ((by & 0x0Fu) ? 0x100u : 0u) | ((by & 0xF0u) ? 0x200u : 0u)) : 0u;
     };
+    // Lane (lx, ly) of warp v owns two cells: (lx, ly, v) in the lower y half and (lx, ly + 4,
+    // 7 - v) in the upper y half. A candidate's work on a half is skipped when its window misses
+    // the plane or the half (both tests uniform across the warp), and pairing plane v with 7 - v
+    // evens out the work of the warps: the windows of a box's candidates cover its middle planes
+    // more often than its outer ones.
+    const int zA = warp, zB = 7 - warp;
     dd acc[2][3];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
@@ -1286,31 +1296,40 @@ struct KSpreadBox3DD {
       const dd* XY = sXY[bb];
       const dd* CZ = sCz[bb];
       const unsigned* MK = sMask[bb];
-      for (int c = 0; c < nc; ++c) {
-        if (!((MK[c] >> warp) & 1u)) continue;  // uniform across the warp
-        const dd t0 = XY[c * kXYStride + ly * 8 + lx], t1 = XY[c * kXYStride + (ly + 4) * 8 + lx];
+      // the chunk's candidates that reach each of this warp's two cell groups, as bit lists
+      // (kBoxChunkDD == 32: one candidate per lane), then only those candidates are visited
+      const unsigned m = lane < nc ? MK[lane] : 0u;
+      unsigned la = __ballot_sync(0xffffffffu, (m >> zA) & (m >> 8) & 1u);
+      unsigned lb = __ballot_sync(0xffffffffu, (m >> zB) & (m >> 9) & 1u);
+      while (la) {
+        const int c = __ffs(la) - 1;
+        la &= la - 1;
+        const dd t0 = XY[c * kXYStride + ly * 8 + lx];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const dd cz = CZ[c * 24 + a * 8 + warp];
-          dd_fma_acc(acc[0][a], cz, t0);
-          dd_fma_acc(acc[1][a], cz, t1);
-        }
+        for (int a = 0; a < 3; ++a) dd_fma_acc(acc[0][a], CZ[c * 24 + a * 8 + zA], t0);
+      }
+      while (lb) {
+        const int c = __ffs(lb) - 1;
+        lb &= lb - 1;
+        const dd t1 = XY[c * kXYStride + (ly + 4) * 8 + lx];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dd_fma_acc(acc[1][a], CZ[c * 24 + a * 8 + zB], t1);
       }
       __syncthreads();
       bb ^= 1;
     }
     const long long gcells = (long long)nf * nf * nf;
-    const int cx = o[0] + lx, cz = o[2] + warp;
+    const int cx = o[0] + lx;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const int yk = ly + 4 * k;
+      const int yk = ly + 4 * k, zk = k ? zB : zA;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const dd v = dd_norm(acc[k][a]);
         if (K == 1) {
-          grid[a * gcells + ((long long)cz * nf + (o[1] + yk)) * nf + cx] = v;
+          grid[a * gcells + ((long long)(o[2] + zk) * nf + (o[1] + yk)) * nf + cx] = v;
         } else {
-          part[((long long)(part_off[box] + ks) * 3 + a) * 512 + (warp * 8 + yk) * 8 + lx] = v;
+          part[((long long)(part_off[box] + ks) * 3 + a) * 512 + (zk * 8 + yk) * 8 + lx] = v;
         }
       }
     }
