@@ -376,6 +376,34 @@ __device__ __forceinline__ void wfft_untangle(const C<T> (&v)[wfft_M(N)], C<T>* 
   __syncwarp();
 }
 
+// The same for Z in strided order (lane l holds Z[l + L i] in v[i], as wfft_fwd_transposed leaves
+// it): only the partners Z[N - k] of the kept modes, Z[j] for j >= N - h, go through buf.
+template <typename T, int PC>
+__device__ __forceinline__ void wfft_untangle_strided(const C<T> (&v)[wfft_M(PC)], C<T>* buf, int l, bool valid,
+                                                      int h, C<T>* __restrict__ outA, C<T>* __restrict__ outB) {
+  constexpr int M = wfft_M(PC), L = wfft_L(PC), NN = wfft_n(PC);
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int j = l + L * i;
+    if (j >= NN - h) buf[j - (NN - h)] = v[i];
+  }
+  __syncwarp();
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int k = l + L * i;
+      if (k < h) {
+        const C<T> Z = v[i];
+        const C<T> Zc = cconj<T>(k == 0 ? Z : buf[h - k]);
+        const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
+        outA[k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
+        outB[k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
+      }
+    }
+  }
+  __syncwarp();
+}
+
 template <typename T, int N>
 __device__ __forceinline__ void wrows_r2c_body(const T* __restrict__ in, C<T>* __restrict__ out, long long npairs,
                                                int Nk, const C<T>* __restrict__ twg, RowBands rb) {
@@ -450,6 +478,16 @@ static __constant__ int kProdSched2[5] = {0 | 0 << 4 | 0 << 8 | 2 << 12,        
                                     1 | 0 << 4 | 0 << 8 | 2 << 12 | 0 << 16,  1 | 0 << 4 | 1 << 8 | 2 << 12 | 1 << 16,
                                     1 | 1 << 4 | 1 << 8 | 2 << 12 | 2 << 16};
 
+// Schedule of the product pass for one-exchange plans (see k_wrows_product): kind 0 = inverse
+// transform of component a into the registers u, stored to slot stash - 1 as well when stash > 0;
+// kind 1 = product of u with slot src - 1 (with u itself when src = 0) into output ab
+// (encoded kind | a << 4 | stash << 8 | src << 12 | ab << 16).
+static __constant__ int kProdSchedT3[9] = {0 | 0 << 4 | 1 << 8, 1 | 0 << 12 | 0 << 16, 0 | 1 << 4 | 2 << 8,
+                                           1 | 1 << 12 | 1 << 16, 1 | 0 << 12 | 3 << 16, 0 | 2 << 4,
+                                           1 | 1 << 12 | 2 << 16, 1 | 2 << 12 | 4 << 16, 1 | 0 << 12 | 5 << 16};
+static __constant__ int kProdSchedT2[5] = {0 | 0 << 4 | 1 << 8, 1 | 0 << 12 | 0 << 16, 0 | 1 << 4,
+                                           1 | 1 << 12 | 1 << 16, 1 | 0 << 12 | 2 << 16};
+
 // Products of the velocity components (three-halves rule), one row pair per L lanes, in
 // three line buffers S0..S2 of shared memory: u_x and u_y are transformed into S0 and S1
 // (exchanging through S2) and give xx, xy, yy (exchanging through S2); u_z then goes to S2,
@@ -475,6 +513,66 @@ struct KWRowsProduct {
   C<T>* tw = reinterpret_cast<C<T>*>(smem_raw);  // lane-ordered twiddles (wfft_tw_size(PC))
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int l = lane % L, sub = lane / L;
+  if constexpr (wfft_one(PC)) {
+    // One-exchange plans: the inverse transforms leave u_a in registers in the plan's output
+    // order; the products are formed there and go forward through wfft_fwd_transposed, which
+    // reads that order, then through the untangle of the strided order. Shared memory carries
+    // the transforms' exchanges (S2) and u_x, u_y for the products that pair them with a later
+    // component (S0, S1), not both factors of every product.
+    C<T>* twt = tw + wfft_tw_size(PC);  // w^{n1 k2} of the transposed transform
+    C<T>* S = twt + wfft_twt_size<PC>() + (warp * LPW + sub) * 3 * SL;
+    C<T>* X = S + 2 * SL;
+    wfft_build_twiddles<T, PC>(tw, twg);
+    wfft_build_twiddles_t<T, PC>(twt, twg);
+    __syncthreads();
+    const int h = Nk / 2;
+    const long long npairs = nrows / 2;
+    for (long long g = (long long)blockIdx.x * nwarp + warp; g * LPW < npairs; g += (long long)gridDim.x * nwarp) {
+      const long long pr = g * LPW + sub;
+      const bool valid = pr < npairs;
+      // u_a of rows 2p (real part) and 2p + 1 (imaginary part), inverse = conj F conj
+      auto inverse = [&](int a, C<T> (&u)[M]) {
+        const C<T>* base = in + ((long long)a * nrows + 2 * pr) * h;
+        wfft_load_packed<T, PC>(u, base, base + h, l, h, valid);
+#pragma unroll
+        for (int i = 0; i < M; ++i) u[i] = cconj<T>(u[i]);
+        wfft<T, false, PC>(u, X, l, tw);
+#pragma unroll
+        for (int i = 0; i < M; ++i) u[i] = cconj<T>(u[i]);
+      };
+      auto forward = [&](C<T> (&v)[M], int ab) {
+        wfft_fwd_transposed<T, PC>(v, X, l, twt);
+        C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
+        wfft_untangle_strided<T, PC>(v, X, l, valid, h, ob, ob + h);
+      };
+      // one component in registers at a time (u); u_x and u_y also go to this lane's slots of S0
+      // and S1, from which the products that pair them with a later component read them. A loop
+      // over the schedule holds one copy of each transform's code (the pass is short enough that
+      // unrolled copies overflow the instruction cache).
+      C<T> u[M], v[M];
+      const int nst = (d == 3) ? 9 : 5;
+#pragma unroll 1
+      for (int q = 0; q < nst; ++q) {
+        const int e = (d == 3) ? kProdSchedT3[q] : kProdSchedT2[q];
+        const int kind = e & 15, a = (e >> 4) & 15, stash = ((e >> 8) & 15) - 1, src = ((e >> 12) & 15) - 1;
+        if (kind == 0) {
+          inverse(a, u);
+          if (stash >= 0) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) S[stash * SL + i * L + l] = u[i];
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            const C<T> f = src < 0 ? u[i] : S[src * SL + i * L + l];
+            v[i] = mk<T>(f.x * u[i].x, f.y * u[i].y);
+          }
+          forward(v, e >> 16);
+        }
+      }
+    }
+    return;
+  }
   C<T>* S = tw + wfft_tw_size(PC) + (warp * LPW + sub) * 3 * SL;  // S0, S1, S2
   wfft_build_twiddles<T, PC>(tw, twg);
   __syncthreads();
@@ -845,7 +943,8 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
       // Blocks of two warps measured no faster: double-float length 96 (five resident blocks instead
       // of two) 127.0 against 127.4 us a step, FP32 one-exchange length 192 80.6 against 74.6 us.
       constexpr int PT = 128;
-      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(PC) + (PT / 32) * LPW * 3 * wfft_stride(PC, (int)sizeof(C<T>)));
+      const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(PC) + wfft_twt_size<PC>() +
+                                                (PT / 32) * LPW * 3 * wfft_stride(PC, (int)sizeof(C<T>)));
       using K = KWRowsProduct<T, NC>;
       raise_smem_limit(kernel_ptr<K>());
       launch<K>(wrows_grid(kernel_ptr<K>(), PT, ws, (npairs + LPW - 1) / LPW), PT, ws, st, in, out, d, nrows, Nk,

@@ -300,4 +300,49 @@ __device__ __forceinline__ int wfft_out_index(int l, int i) {
   return l + wfft_L(N) * (i / RL) + (wfft_n(N) / RL) * (i % RL);
 }
 
+// Forward transform of a one-exchange plan (N = 24 L) that takes its input in the order the
+// plan leaves its output: lane l holds x[n1 + 24 n2] in v[b L + n2], n1 = l + L b (b < 24/L,
+// n2 < L), and leaves X[l + L k1] in v[k1] (k1 < 24), the order in which the plan's own
+// transform reads its input. It is the plan's factorisation taken the other way round:
+// with n = n1 + 24 n2 and k = k2 + L k1,
+//   X[k2 + L k1] = sum_n1 w24^{n1 k1} w^{n1 k2} sum_n2 wL^{n2 k2} x[n1 + 24 n2],
+// so every lane first runs its 24/L DFTs of length L (over n2, in registers), multiplies by
+// w^{n1 k2}, and after one exchange (lane k2 gathers all n1 of column k2) runs a DFT of length
+// 24. twt: the lane-ordered table of w^{n1 k2} (wfft_twt_size entries, see
+// wfft_build_twiddles_t); buf: the line's exchange buffer (L rows of 25 elements: the rows of
+// a half-warp's lines fall in distinct bank pairs).
+constexpr int kTRow = 25;
+template <int PC>
+constexpr int wfft_twt_size() {
+  return wfft_one(PC) ? (24 / wfft_L(PC)) * (wfft_L(PC) - 1) * wfft_L(PC) : 0;
+}
+template <typename T, int PC>
+__device__ __forceinline__ void wfft_build_twiddles_t(C<T>* twt, const C<T>* __restrict__ tw) {
+  constexpr int L = wfft_L(PC), NN = wfft_n(PC);
+  for (int e = threadIdx.x; e < wfft_twt_size<PC>(); e += blockDim.x) {
+    const int l = e % L, q = e / L, b = q / (L - 1), k2 = q % (L - 1) + 1;
+    twt[e] = tw[((l + L * b) * k2) % NN];
+  }
+}
+template <typename T, int PC>
+__device__ __forceinline__ void wfft_fwd_transposed(C<T> (&v)[24], C<T>* buf, int l, const C<T>* __restrict__ twt) {
+  static_assert(wfft_one(PC) && wfft_M(PC) == 24, "one-exchange plans only");
+  constexpr int L = wfft_L(PC), NB = 24 / L;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    dft_r<T, false, L>(&v[b * L]);
+#pragma unroll
+    for (int k2 = 1; k2 < L; ++k2) v[b * L + k2] = cmul<T>(v[b * L + k2], twt[(b * (L - 1) + k2 - 1) * L + l]);
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int k2 = 0; k2 < L; ++k2) buf[k2 * kTRow + l + L * b] = v[b * L + k2];
+  __syncwarp();
+#pragma unroll
+  for (int n1 = 0; n1 < 24; ++n1) v[n1] = buf[l * kTRow + n1];
+  __syncwarp();
+  dft24<T, false>(v);
+}
+
 }  // namespace fsib
