@@ -391,7 +391,9 @@ static int alloc_ws(fsib_plan* h) {
   // partial slots: boxes with K > 1 hold K slots, K <= 2 cand/256; sum cand <= 27 M
   // (and at most 16 per box: dense point sets get larger slices)
   ws.part_slots = (d == 3) ? (size_t)std::min<long long>(2 * 27 * (long long)p.M / kMinSlice + 64, 16LL * p.nbins) : 1;
-  rc |= dmalloc(&ws.part, sizeof(double) * 3 * 512 * ws.part_slots, tot);
+  rc |= dmalloc(&ws.part, (d == 3) ? sizeof(double) * 3 * 512 * ws.part_slots : gather2d_part_bytes(p), tot);
+  // the 2D gather's completion counters return to zero after each use; they start at zero
+  if (ws.box_done && cudaMemset(ws.box_done, 0, sizeof(int) * (size_t)p.nbins) != cudaSuccess) rc |= FSIB_ECUDA;
   if (cudaHostAlloc((void**)&ws.miss_host, sizeof(unsigned int), cudaHostAllocMapped) != cudaSuccess) {
     cudaGetLastError();
     ws.miss_host = nullptr;

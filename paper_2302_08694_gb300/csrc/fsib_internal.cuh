@@ -265,6 +265,9 @@ void launch_vjp_combine(int d, int M, double s, double sigma, const double* Gu, 
 
 int check_last(const char* where);
 void raise_smem_limit(const void* kernel);
+// Blocks per box of the 2D gather and the bytes of its partial boxes.
+int gather2d_slices(const Plan& p);
+size_t gather2d_part_bytes(const Plan& p);
 // Dynamic shared memory a block of a kernel without static shared memory may request
 // (the device's opt-in limit per block).
 size_t smem_optin();

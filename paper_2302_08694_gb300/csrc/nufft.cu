@@ -683,6 +683,15 @@ template <typename T, int COMP> struct SumAcc { using type = T; };
 template <> struct SumAcc<float, kSumTerm> { using type = cf; };
 
 constexpr int kGatherChunk = 128;  // candidates staged per round (2D gather)
+constexpr int kGatherSliceMin = 256;  // fewest candidates a block takes when blocks share a 2D box
+
+// Loads that bypass L1 (other blocks wrote the data during this kernel).
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ dd ld_cg(const dd* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return dd(v.x, v.y);
+}
+
 
 // Neighbouring bins whose window starts can reach box (Bx, By, Bz) (defined below).
 __device__ __forceinline__ int nb_list(const PointGeom& g, int dlo, int dhi, int Bx, int By, int Bz, int lane,
@@ -693,14 +702,20 @@ struct KSpreadGather {
   static constexpr int kThreads = 256, kMinBlocks = 0;
   static constexpr bool kAnyGrid = false;
   __device__ static void run(PointGeom g, int dlo, int dhi, const int* __restrict__ offsets, const int* __restrict__ i0s,
-                             const T* __restrict__ W, const T* __restrict__ Cw, T* __restrict__ grid) {
+                             const T* __restrict__ W, const T* __restrict__ Cw, T* __restrict__ grid, int KS,
+                             T* __restrict__ partials, int* __restrict__ done) {
+  // KS > 1: blocks ks = 0 .. KS - 1 of each box (block index box + ks * nbox) share its candidates
+  // when there are enough of them (kGatherSliceMin a block), store partial boxes, and the block
+  // that finishes the box's last slice adds them in slice order (done: a counter per box, back
+  // to zero when the box is stored).
   __shared__ __align__(16) T sW[kGatherChunk * D * kMaxW];
   __shared__ T sC[kGatherChunk * D];
   __shared__ int sI[kGatherChunk * 3];
   const int w = g.w, nf = g.nf, M = g.M;
   const int bxs = g.b[0], bys = g.b[1], bzs = (D == 3) ? g.b[2] : 1;
   const int nseg = bxs / kSeg;
-  const int box = blockIdx.x;
+  const int nbox = g.nb[0] * g.nb[1] * (D == 3 ? g.nb[2] : 1);
+  const int box = blockIdx.x % nbox, ks = blockIdx.x / nbox;
   const int Bx = box % g.nb[0], By = (box / g.nb[0]) % g.nb[1], Bz = (D == 3) ? box / (g.nb[0] * g.nb[1]) : 0;
   if (g.band && !g.band[Bz * g.nb[1] + By]) return;  // a row band that no window reaches: never read
   const int ox = Bx * bxs, oy = By * bys, oz = Bz * bzs;
@@ -745,8 +760,11 @@ struct KSpreadGather {
   }
   __syncthreads();
   const int nr = sNr, total = sPre[nr];
-  for (int c0 = 0; c0 < total; c0 += kGatherChunk) {
-    const int nc = min(kGatherChunk, total - c0);
+  const int slices = (KS > 1) ? min(KS, max(1, (total + kGatherSliceMin - 1) / kGatherSliceMin)) : 1;
+  if (ks >= slices) return;  // uniform across the block
+  const int fb = (int)((long long)total * ks / slices), fe = (int)((long long)total * (ks + 1) / slices);
+  for (int c0 = fb; c0 < fe; c0 += kGatherChunk) {
+    const int nc = min(kGatherChunk, fe - c0);
     __syncthreads();
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       const int f = c0 + c;
@@ -818,23 +836,58 @@ struct KSpreadGather {
       for (int i = 0; i < kSeg; ++i) red[((group - 1) * ntask + task) * kSeg + i] = part[i];
     }
     __syncthreads();
-    if (group > 0) return;
-    if constexpr (std::is_same<T, float>::value) {
+    if (group == 0) {
+      if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
-      for (int i = 0; i < kSeg; ++i) {
-        cf s(part[i]);
-        for (int q = 1; q < G; ++q) add_comp(s, red[((q - 1) * ntask + task) * kSeg + i]);
-        part[i] = acc_norm(s);
+        for (int i = 0; i < kSeg; ++i) {
+          cf s(part[i]);
+          for (int q = 1; q < G; ++q) add_comp(s, red[((q - 1) * ntask + task) * kSeg + i]);
+          part[i] = acc_norm(s);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kSeg; ++i)
+          for (int q = 1; q < G; ++q) part[i] = part[i] + red[((q - 1) * ntask + task) * kSeg + i];
       }
-    } else {
-#pragma unroll
-      for (int i = 0; i < kSeg; ++i)
-        for (int q = 1; q < G; ++q) part[i] = part[i] + red[((q - 1) * ntask + task) * kSeg + i];
     }
   }
   T* out = grid + comp * gcells + ((long long)cz * nf + cy) * nf + cx0;
+  if (slices == 1) {
+    if (group == 0) {
 #pragma unroll
-  for (int i = 0; i < kSeg; ++i) out[i] = part[i];
+      for (int i = 0; i < kSeg; ++i) out[i] = part[i];
+    }
+    return;
+  }
+  // a slice of a shared box: its partial box, then the last block adds the slices in order
+  T* pp = partials + (((long long)box * KS + ks) * ntask + task) * kSeg;
+  if (group == 0) {
+#pragma unroll
+    for (int i = 0; i < kSeg; ++i) pp[i] = part[i];
+  }
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&done[box], 1) == slices - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (group == 0) {
+    const T* p0 = partials + ((long long)box * KS * ntask + task) * kSeg;
+#pragma unroll
+    for (int i = 0; i < kSeg; ++i) {
+      if constexpr (std::is_same<T, float>::value) {
+        cf s(0.0f);
+        for (int k = 0; k < slices; ++k) add_comp(s, ld_cg(p0 + (long long)k * ntask * kSeg + i));
+        out[i] = acc_norm(s);
+      } else {
+        T v = T(0);
+        for (int k = 0; k < slices; ++k) v = v + ld_cg(p0 + (long long)k * ntask * kSeg + i);
+        out[i] = v;
+      }
+    }
+  }
+  if (threadIdx.x == 0) done[box] = 0;
   }
 };
 
@@ -984,13 +1037,6 @@ __device__ __forceinline__ void zero_empty_boxes(const PointGeom& g, const int* 
       zero_box<T>(g, box, grid, lane);
     }
   }
-}
-
-// Loads that bypass L1 (other blocks wrote the data during this kernel).
-__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
-__device__ __forceinline__ dd ld_cg(const dd* p) {
-  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-  return dd(v.x, v.y);
 }
 
 // After a block has stored the partial box of slice ks of a split box (K > 1 slices): the
@@ -1496,6 +1542,20 @@ void launch_point_prep(const Plan& p, Workspace& ws, const double* cw, const dou
                                                       dd(2.0 / p.w), dd(p.beta));
 }
 
+// Blocks per box of the 2D gather: with dense points (16 or more per box on average; a curve
+// puts thousands in the boxes it crosses) enough to give about four blocks per SM, at most 16;
+// one block per box otherwise. A block takes at least kGatherSliceMin of its box's candidates.
+int gather2d_slices(const Plan& p) {
+  const long long nbox = p.nbins;
+  if (p.d != 2 || (long long)p.M < 16 * nbox) return 1;
+  const long long ks = (4LL * num_sms() + nbox - 1) / nbox;
+  return (int)std::max(1LL, std::min(16LL, ks));
+}
+// Bytes of the partial boxes of the 2D gather (8-byte elements cover both precisions).
+size_t gather2d_part_bytes(const Plan& p) {
+  return sizeof(double) * (size_t)p.nbins * (size_t)gather2d_slices(p) * 2 * (size_t)p.bins[0] * p.bins[1];
+}
+
 template <typename T>
 void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st) {
   PointGeom g = geom(p);
@@ -1547,9 +1607,11 @@ void launch_spread_gather(const Plan& p, Workspace& ws, T* grid, cudaStream_t st
     const int groups = std::max(1, std::min(16, 256 / ntask));
     const int threads = ntask * groups;
     const int mode = std::is_same<T, float>::value ? p.spread_sum : kSumPlain;
+    const int KS = gather2d_slices(p);
     auto run = [&](auto k) {
       using K = typename decltype(k)::type;
-      launch<K>(nbox, threads, 0, st, g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid);
+      launch<K>(nbox * KS, threads, 0, st, g, dlo, dhi, ws.offsets, ws.i0, (const T*)ws.wts, (const T*)ws.cwp, grid,
+                KS, (T*)ws.part, ws.box_done);
     };
     if (mode == kSumTerm) run(type_tag<KSpreadGather<T, 2, kSumTerm>>());
     else if (mode == kSumChunk) run(type_tag<KSpreadGather<T, 2, kSumChunk>>());

@@ -97,6 +97,26 @@ def test_spread_dense_points_many_slices(lib, torch_mod, prec):
         assert relmax(got, ref) <= 10 * TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_spread_dense_curve_2d_shared_boxes(lib, torch_mod, prec):
+    """A dense closed curve in 2D (about 300 points per fine cell along it): several blocks share
+    each box's candidates and the last one adds their partial boxes in slice order."""
+    torch = torch_mod
+    rng = np.random.default_rng(654)
+    d, N, M = 2, 32, 20000
+    th = np.sort(rng.uniform(0.0, 2 * np.pi, M))
+    X = np.stack([0.5 + 0.2 * np.cos(th), 0.45 + 0.15 * np.sin(th)])
+    F = rng.standard_normal((d, M))
+    pb = make(lib, N, d, M, prec)
+    ref = sp.full_to_half(sp.spread_direct(X, F, N), N)
+    for _ in range(2):  # twice: the per-box counters return to zero
+        fh = pb.spread(cuda(X, torch), cuda(F, torch))
+        torch.cuda.synchronize()
+        got = to_np(fh)
+        assert rel2(got, ref) <= TOL[prec]
+        assert relmax(got, ref) <= 10 * TOL[prec]
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("d,N,M", [(2, 32, 3000), (3, 16, 20000), (3, 24, 997)])
 def test_mixed_spread_summation_modes(lib, torch_mod, mode, d, N, M):
