@@ -677,6 +677,8 @@ __device__ __forceinline__ void fft_s2_body(const C<Tin>* __restrict__ in, C<Tou
       raw[k] = (qok && si >= 0) ? src[(long long)si * inner + q] : C<Tin>{};
     }
 #pragma unroll
+    constexpr bool kHoist = std::is_same<T, float>::value;  // FP32 lines: the plane factor once a thread
+    const T dpq = (kHoist && INV && qok && mult.dplane) ? mult.dplane[q] : T(1);
     for (int k = 0; k < NL; ++k) {
       const int t = threadIdx.x + k * NT, i = t / P;
       if (t >= N * P) break;
@@ -684,9 +686,8 @@ __device__ __forceinline__ void fft_s2_body(const C<Tin>* __restrict__ in, C<Tou
       if (INV) {
         const int si = (i < h) ? i : ((i > N - h) ? i - (N - Nk) : -1);
         if (qok && si >= 0) {
-          T sc = mult.scale;
-          if (mult.dline) sc *= mult.dline[si];
-          if (mult.dplane) sc *= mult.dplane[q];
+          T sc = mult.dline ? mult.scale * mult.dline[si] : mult.scale;
+          if (mult.dplane) sc = sc * (kHoist ? dpq : mult.dplane[q]);
           v = cscale<T>(v, sc);
         } else {
           v = mk<T>(T(0), T(0));
@@ -723,24 +724,49 @@ __device__ __forceinline__ void fft_s2_body(const C<Tin>* __restrict__ in, C<Tou
     for (int r = 0; r < R2; ++r) tile[(j + r * R1) * P + p] = v[r];
   }
   __syncthreads();
-  if (!INV) {
-    for (int t = threadIdx.x; t < Nk * P; t += NT) {
-      const int pp = t % P, io = t / P, q = q0 + pp;
-      if (q >= inner) continue;
-      C<T> v = mk<T>(T(0), T(0));
-      if (io != h) {
-        const int fi = (io < h) ? io : io + (N - Nk);
-        T sc = mult.scale;
-        if (mult.dline) sc *= mult.dline[io];
-        if (mult.dplane) sc *= mult.dplane[q];
-        v = cscale<T>(tile[fi * P + pp], sc);
+  if constexpr (std::is_same<T, float>::value) {
+    // a thread keeps its line (t mod P is fixed, NT being a multiple of P) and steps 16 rows
+    {
+      const int pp = threadIdx.x % P, q = q0 + pp;
+      if (q < inner) {
+        C<Tout>* dq = dst + q;
+        if (!INV) {
+          const T dpq = mult.dplane ? mult.dplane[q] : T(1);  // (scale dline) dplane, as in the inverse
+          for (int io = threadIdx.x / P; io < Nk; io += NT / P) {
+            C<T> v = mk<T>(T(0), T(0));
+            if (io != h) {
+              const int fi = (io < h) ? io : io + (N - Nk);
+              T sc = mult.dline ? mult.scale * mult.dline[io] : mult.scale;
+              if (mult.dplane) sc = sc * dpq;
+              v = cscale<T>(tile[fi * P + pp], sc);
+            }
+            dq[(long long)io * inner] = ccvt<Tout, T>(v);
+          }
+        } else {
+          for (int i = threadIdx.x / P; i < N; i += NT / P) dq[(long long)i * inner] = ccvt<Tout, T>(tile[i * P + pp]);
+        }
       }
-      dst[(long long)io * inner + q] = ccvt<Tout, T>(v);
     }
-  } else {
-    for (int t = threadIdx.x; t < N * P; t += NT) {
-      const int pp = t % P, i = t / P, q = q0 + pp;
-      if (q < inner) dst[(long long)i * inner + q] = ccvt<Tout, T>(tile[t]);
+  } else {  // double-float and double lines measured faster with the per-element form
+    if (!INV) {
+      for (int t = threadIdx.x; t < Nk * P; t += NT) {
+        const int pp = t % P, io = t / P, q = q0 + pp;
+        if (q >= inner) continue;
+        C<T> v = mk<T>(T(0), T(0));
+        if (io != h) {
+          const int fi = (io < h) ? io : io + (N - Nk);
+          T sc = mult.scale;
+          if (mult.dline) sc *= mult.dline[io];
+          if (mult.dplane) sc *= mult.dplane[q];
+          v = cscale<T>(tile[fi * P + pp], sc);
+        }
+        dst[(long long)io * inner + q] = ccvt<Tout, T>(v);
+      }
+    } else {
+      for (int t = threadIdx.x; t < N * P; t += NT) {
+        const int pp = t % P, i = t / P, q = q0 + pp;
+        if (q < inner) dst[(long long)i * inner + q] = ccvt<Tout, T>(tile[t]);
+      }
     }
   }
 }
