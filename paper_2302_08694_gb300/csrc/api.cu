@@ -271,7 +271,7 @@ static double fft_flops(double lines, int n) { return lines * 5.0 * n * std::log
 static void free_ws(Workspace& ws) {
   void* ptrs[] = {ws.tw, ws.dline, ws.dplane, ws.grid, ws.grid2, ws.s1, ws.s2, ws.s3, ws.s4, ws.fhat, ws.uhalf, ws.bin_of,
                   ws.rank, ws.counts, ws.offsets, ws.occ, ws.nocc, ws.perm, ws.i0, ws.delta, ws.Xh,
-                  ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.wts, ws.cwp,
+                  ws.cw, ws.Uh, ws.omega_ones, ws.red, ws.flag, ws.wts, ws.cwp, ws.ktab,
                   ws.box_ns, ws.box_np, ws.box_so, ws.box_po, ws.box_item, ws.box_sched, ws.box_work, ws.box_done,
                   ws.part, ws.band, ws.band_dil};
   for (void* q : ptrs)
@@ -281,7 +281,7 @@ static void free_ws(Workspace& ws) {
   ws.delta = nullptr;
   ws.Xh = ws.cw = ws.Uh = ws.omega_ones = ws.red = nullptr;
   ws.flag = nullptr;
-  ws.wts = ws.cwp = nullptr;
+  ws.wts = ws.cwp = ws.ktab = nullptr;
   ws.box_ns = ws.box_np = ws.box_so = ws.box_po = ws.box_item = ws.box_sched = ws.box_work = ws.box_done = nullptr;
   ws.part = nullptr;
   ws.band = ws.band_dil = nullptr;
@@ -376,6 +376,21 @@ static int alloc_ws(fsib_plan* h) {
   rc |= dmalloc(&ws.flag, sizeof(int) * 4, tot);
   rc |= dmalloc(&ws.wts, sizeof(double) * (size_t)p.M * d * p.w, tot);
   rc |= dmalloc(&ws.cwp, sizeof(double) * (size_t)p.M * d, tot);
+  rc |= dmalloc(&ws.ktab, sizeof(double) * (size_t)p.N, tot);
+  if (ws.ktab) {  // the same product the device formed per mode: (T)(kunit * m)
+    const double kunit = 2.0 * 3.14159265358979323846 / p.L;
+    std::vector<double> kd(p.N);
+    std::vector<float> kf(p.N);
+    for (int i = 0; i < p.N; ++i) {
+      const int m = (i < p.N / 2) ? i : i - p.N;
+      kd[i] = kunit * m;
+      kf[i] = (float)(kunit * m);
+    }
+    const bool f32 = p.prec == FSIB_MIXED;
+    if (cudaMemcpy(ws.ktab, f32 ? (const void*)kf.data() : (const void*)kd.data(),
+                   (f32 ? sizeof(float) : sizeof(double)) * (size_t)p.N, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc |= FSIB_ECUDA;
+  }
   rc |= dmalloc(&ws.box_ns, sizeof(int) * (size_t)p.nbins, tot);
   rc |= dmalloc(&ws.box_np, sizeof(int) * (size_t)p.nbins, tot);
   rc |= dmalloc(&ws.box_so, sizeof(int) * (size_t)(p.nbins + 1), tot);
@@ -690,10 +705,10 @@ static void do_fluid(fsib_plan* h, const C<TA>* fhat, C<TA>* u, C<TA>* uhalf, cu
   const double ub = (double)h->ws.spec_bytes / d * (np + 3 * d);
   const C<TA>* P = P0 ? P0 : products<TI, TA>(h, u, st, h->ws.s1, h->ws.s2);
   { Prof pr(h, "ns_update", ub, 0.0, st);
-    launch_ns_update<TA>(h->p, P, fhat, u, uhalf, true, st); }
+    launch_ns_update<TA>(h->p, h->ws.ktab, P, fhat, u, uhalf, true, st); }
   P = products<TI, TA>(h, uhalf, st, h->ws.s1, h->ws.s2);
   { Prof pr(h, "ns_update", ub, 0.0, st);
-    launch_ns_update<TA>(h->p, P, fhat, u, u, false, st); }
+    launch_ns_update<TA>(h->p, h->ws.ktab, P, fhat, u, u, false, st); }
 }
 
 template <typename TI, typename TA>
@@ -749,7 +764,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     // U^{m+1/2} interp and the re-sort.
     const double ub = (double)ws.spec_bytes / p.d * (p.d * (p.d + 1) / 2 + 3 * p.d);
     { Prof pr(h, "ns_update", ub, 0.0, st);
-      launch_ns_update<TA>(p, P0, fhat, uhat, uh, true, st); }
+      launch_ns_update<TA>(p, ws.ktab, P0, fhat, uhat, uh, true, st); }
     if (fork) {
       cudaEventRecord(h->ev_fork3, st);
       cudaStreamWaitEvent(h->side, h->ev_fork3, 0);
@@ -758,7 +773,7 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     if (fork) cudaEventRecord(h->ev_join3, h->side);
     const C<TA>* P1 = products<TI, TA>(h, uh, st, ws.s1, ws.s2);
     { Prof pr(h, "ns_update", ub, 0.0, st);
-      launch_ns_update<TA>(p, P1, fhat, uhat, uhat, false, st); }
+      launch_ns_update<TA>(p, ws.ktab, P1, fhat, uhat, uhat, false, st); }
     if (fork) {
       cudaEventRecord(h->ev_fork2, st);
       cudaStreamWaitEvent(h->side, h->ev_fork2, 0);

@@ -71,25 +71,30 @@ struct KStokeslet {
 // A uniform body force density fb (Sec. 5.2.2) is the coefficient at k = 0 and is added there.
 struct Body { double f[3]; };
 
-template <typename T>
+template <typename T, int D>
 struct KNsUpdate {
   static constexpr int kThreads = 256, kMinBlocks = 0;
   static constexpr bool kAnyGrid = true;
-  __device__ static void run(SpecGeom g, T inv_rho, T mu_dt_over_rho, T dt, bool half, Body fb,
-                             const C<T>* __restrict__ prod, const C<T>* __restrict__ f,
+  // ktab: (T)(kunit m(i)) for i < N (the same value decode_mode forms); mode indices are 32-bit
+  // (fewer than 2^31 modes at every supported size)
+  __device__ static void run(SpecGeom g, const T* __restrict__ ktab, T inv_rho, T mu_dt_over_rho, T dt, bool half,
+                             Body fb, const C<T>* __restrict__ prod, const C<T>* __restrict__ f,
                              const C<T>* __restrict__ base, C<T>* __restrict__ out) {
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
-       idx += (long long)gridDim.x * blockDim.x) {
-    T k[3];
-    const bool ok = decode_mode<T>(g, idx, k);
-    const int d = g.d;
-    const T k2 = k[0] * k[0] + k[1] * k[1] + (d == 3 ? k[2] * k[2] : T(0));
+  const unsigned nspec = (unsigned)g.nspec, h = (unsigned)g.h, N = (unsigned)g.N;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nspec; idx += gridDim.x * blockDim.x) {
+    const unsigned ix = idx % h, r = idx / h;
+    const unsigned iy = (D == 3) ? r % N : r, iz = (D == 3) ? r / N : 0u;
+    const bool ok = iy != N / 2 && (D != 3 || iz != N / 2);  // not a Nyquist mode
+    const T k[3] = {ktab[ix], ktab[iy], (D == 3) ? ktab[iz] : T(0)};
+    const T k2 = k[0] * k[0] + k[1] * k[1] + (D == 3 ? k[2] * k[2] : T(0));
     C<T> P[3];
-    for (int a = 0; a < d; ++a) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
       C<T> s = mk<T>(T(0), T(0));
-      for (int b = 0; b < d; ++b) {
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
         const int lo = a < b ? a : b, hi = a < b ? b : a;
-        const int ab = (d == 3) ? (lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)) : (lo + hi);
+        const int ab = (D == 3) ? (lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)) : (lo + hi);
         s = cadd<T>(s, cscale<T>(prod[ab * g.nspec + idx], k[b]));
       }
       s = cmul_i<T>(s);
@@ -98,11 +103,13 @@ struct KNsUpdate {
       P[a] = csub<T>(cscale<T>(fa, inv_rho), s);
     }
     C<T> kP = mk<T>(T(0), T(0));
-    for (int a = 0; a < d; ++a) kP = cadd<T>(kP, cscale<T>(P[a], k[a]));
+#pragma unroll
+    for (int a = 0; a < D; ++a) kP = cadd<T>(kP, cscale<T>(P[a], k[a]));
     const T ik2 = (k2 > T(0)) ? T(1) / k2 : T(1);
     const T lam = mu_dt_over_rho * k2;
     const T den = T(1) / (T(1) + T(0.5) * lam);
-    for (int a = 0; a < d; ++a) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
       C<T> v = mk<T>(T(0), T(0));
       if (ok) {
         const C<T> Q = csub<T>(P[a], cscale<T>(kP, k[a] * ik2));
@@ -281,7 +288,7 @@ void launch_pressure(const Plan& p, const C<T>* prod, const C<T>* fhat, C<T>* ph
 }
 
 template <typename T>
-void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
+void launch_ns_update(const Plan& p, const void* ktab, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
                       C<T>* out, bool half, cudaStream_t st) {
   const SpecGeom g = sgeom(p);
   const Body fb = {{p.fbody[0], p.fbody[1], p.fbody[2]}};
@@ -292,8 +299,13 @@ void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C
       return;
     }
   }
-  launch<KNsUpdate<T>>(grid_for(g.nspec), 256, 0, st, g, (T)(1.0 / p.rho), (T)(p.mu * p.dt / p.rho), (T)p.dt, half,
-                       fb, prod, fhat, ubase, out);
+  auto run = [&](auto k) {
+    using K = typename decltype(k)::type;
+    launch<K>(grid_for(g.nspec), 256, 0, st, g, (const T*)ktab, (T)(1.0 / p.rho), (T)(p.mu * p.dt / p.rho), (T)p.dt,
+              half, fb, prod, fhat, ubase, out);
+  };
+  if (p.d == 3) run(type_tag<KNsUpdate<T, 3>>());
+  else run(type_tag<KNsUpdate<T, 2>>());
 }
 
 template <typename T>
@@ -308,9 +320,9 @@ template void launch_stokeslet<float>(const Plan&, const C<float>*, C<float>*, c
 template void launch_stokeslet<double>(const Plan&, const C<double>*, C<double>*, cudaStream_t);
 template void launch_pressure<float>(const Plan&, const C<float>*, const C<float>*, C<float>*, cudaStream_t);
 template void launch_pressure<double>(const Plan&, const C<double>*, const C<double>*, C<double>*, cudaStream_t);
-template void launch_ns_update<float>(const Plan&, const C<float>*, const C<float>*, const C<float>*,
+template void launch_ns_update<float>(const Plan&, const void*, const C<float>*, const C<float>*, const C<float>*,
                                       C<float>*, bool, cudaStream_t);
-template void launch_ns_update<double>(const Plan&, const C<double>*, const C<double>*, const C<double>*,
+template void launch_ns_update<double>(const Plan&, const void*, const C<double>*, const C<double>*, const C<double>*,
                                        C<double>*, bool, cudaStream_t);
 
 }  // namespace fsib

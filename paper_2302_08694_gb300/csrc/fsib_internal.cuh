@@ -150,6 +150,8 @@ struct Workspace {
   int* flag = nullptr;
   void* wts = nullptr;               // T[M][d][w] kernel weights per sorted point
   void* cwp = nullptr;               // T[M][d] weighted forces per sorted point
+  void* ktab = nullptr;              // T[N] wave numbers (2 pi / L) m(i), m(i) = i or i - N, in the
+                                     // spectral precision (float for FSIB_MIXED, double otherwise)
   int* box_ns = nullptr;             // [nbins] slices per gather box (3D)
   int* box_np = nullptr;             // [nbins] partial slots per box
   int* box_so = nullptr;             // [nbins + 1] slice offsets
@@ -243,7 +245,7 @@ void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t 
 template <typename T>
 void launch_pressure(const Plan& p, const C<T>* prod, const C<T>* fhat, C<T>* phat, cudaStream_t st);
 template <typename T>
-void launch_ns_update(const Plan& p, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
+void launch_ns_update(const Plan& p, const void* ktab, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
                       C<T>* out, bool half, cudaStream_t st);
 
 void launch_axpy(double* y, const double* x, const double* v, double a, long long n, cudaStream_t st);
