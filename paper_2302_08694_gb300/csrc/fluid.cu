@@ -22,10 +22,11 @@ static SpecGeom sgeom(const Plan& p) {
 // Decode a half-spectrum index into wavevector components; false on a Nyquist mode.
 template <typename T>
 __device__ __forceinline__ bool decode_mode(const SpecGeom& g, long long idx, T* k) {
-  const int ix = (int)(idx % g.h);
-  const long long r = idx / g.h;
-  const int iy = (int)(r % g.N);
-  const int iz = (g.d == 3) ? (int)(r / g.N) : 0;
+  // 32-bit arithmetic: fewer than 2^31 modes at every supported size
+  const unsigned u = (unsigned)idx, r = u / (unsigned)g.h;
+  const int ix = (int)(u - r * (unsigned)g.h);
+  const int iy = (int)(r % (unsigned)g.N);
+  const int iz = (g.d == 3) ? (int)(r / (unsigned)g.N) : 0;
   if (iy == g.N / 2 || (g.d == 3 && iz == g.N / 2)) return false;
   const int my = iy < g.N / 2 ? iy : iy - g.N;
   const int mz = iz < g.N / 2 ? iz : iz - g.N;
@@ -198,20 +199,22 @@ __device__ __forceinline__ double join_dd(dd a) { return widen_float(a.hi) + wid
 struct DDc { dd x, y; };
 __device__ __forceinline__ DDc ddc(double2 v) { return {split_double(v.x), split_double(v.y)}; }
 
+template <int D>
 struct KNsUpdateDD {
   static constexpr int kThreads = 256, kMinBlocks = 0;
   static constexpr bool kAnyGrid = true;
   __device__ static void run(SpecGeom g, dd kunit, dd inv_rho, dd mu_dt_over_rho, dd dt, bool half, Body fb,
                              const double2* __restrict__ prod, const double2* __restrict__ f,
                              const double2* __restrict__ base, double2* __restrict__ out) {
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nspec;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(idx % g.h);
-    const long long r = idx / g.h;
-    const int iy = (int)(r % g.N), iz = (g.d == 3) ? (int)(r / g.N) : 0;
-    const bool ok = !(iy == g.N / 2 || (g.d == 3 && iz == g.N / 2));
+  // 32-bit mode indices (fewer than 2^31 modes at every supported size)
+  const unsigned nspec = (unsigned)g.nspec, hh = (unsigned)g.h, NN = (unsigned)g.N;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nspec; idx += gridDim.x * blockDim.x) {
+    const unsigned r = idx / hh;
+    const int ix = (int)(idx - r * hh);
+    const int iy = (D == 3) ? (int)(r % NN) : (int)r, iz = (D == 3) ? (int)(r / NN) : 0;
+    const bool ok = !(iy == g.N / 2 || (D == 3 && iz == g.N / 2));
     const int my = iy < g.N / 2 ? iy : iy - g.N, mz = iz < g.N / 2 ? iz : iz - g.N;
-    const int d = g.d;
+    constexpr int d = D;
     const dd k[3] = {kunit * dd((float)ix), kunit * dd((float)my), kunit * dd((float)mz)};
     dd k2 = k[0] * k[0] + k[1] * k[1];
     if (d == 3) k2 = k2 + k[2] * k[2];
@@ -294,8 +297,13 @@ void launch_ns_update(const Plan& p, const void* ktab, const C<T>* prod, const C
   const Body fb = {{p.fbody[0], p.fbody[1], p.fbody[2]}};
   if constexpr (std::is_same<T, double>::value) {
     if (!p.native_fp64) {
-      launch<KNsUpdateDD>(grid_for(g.nspec), 256, 0, st, g, dd(g.kunit), dd(1.0 / p.rho), dd(p.mu * p.dt / p.rho),
-                          dd(p.dt), half, fb, prod, fhat, ubase, out);
+      auto run = [&](auto k) {
+        using K = typename decltype(k)::type;
+        launch<K>(grid_for(g.nspec), 256, 0, st, g, dd(g.kunit), dd(1.0 / p.rho), dd(p.mu * p.dt / p.rho), dd(p.dt),
+                  half, fb, (const double2*)prod, (const double2*)fhat, (const double2*)ubase, (double2*)out);
+      };
+      if (p.d == 3) run(type_tag<KNsUpdateDD<3>>());
+      else run(type_tag<KNsUpdateDD<2>>());
       return;
     }
   }

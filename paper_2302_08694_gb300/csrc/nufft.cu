@@ -639,14 +639,25 @@ struct KPointPrep {
                              const double* __restrict__ omega, T* __restrict__ W, T* __restrict__ Cw, dd s2w, dd bdd) {
   const int w = g.w, M = g.M;
   const long long nw = (long long)M * D * w;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nw; t += (long long)gridDim.x * blockDim.x) {
-    const long long s = t / (D * w);
-    const int r = (int)(t % (D * w)), a = r / w, q = r % w;
-    W[t] = weight_of<T>(delta[(long long)a * M + s], q, w, beta, s2w, bdd);
+  auto entry = [&](long long s, int r) {
+    const int a = r / w, q = r - a * w;
+    W[s * D * w + r] = weight_of<T>(delta[(long long)a * M + s], q, w, beta, s2w, bdd);
     if (Cw && q == 0) {
       const int j = perm[s];
       const double om = omega ? omega[j] : 1.0;
       Cw[s * D + a] = T(om * cw[(long long)a * M + j]);
+    }
+  };
+  if (nw < (1LL << 31)) {  // 32-bit index arithmetic (the usual case)
+    const unsigned per = (unsigned)(D * w);
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (unsigned)nw; t += gridDim.x * blockDim.x) {
+      const unsigned s = t / per;
+      entry((long long)s, (int)(t - s * per));
+    }
+  } else {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nw; t += (long long)gridDim.x * blockDim.x) {
+      const long long s = t / (D * w);
+      entry(s, (int)(t - s * (D * w)));
     }
   }
 }
