@@ -162,7 +162,7 @@ __device__ __forceinline__ void block_prefix(int (&v)[NV], int (&tot)[NV], int (
 
 // Bin offsets (exclusive scan of the counts, total at [nbins]) and the list of occupied bins.
 // OCC: also list the occupied bins (the scatter spread walks them; the gather does not).
-// It also clears the row-band flags (nband bytes) that k_band_mark then marks, and, without
+// It also clears the row-band flags (nband bytes) that the scatter then marks, and, without
 // them, leaves the counts at zero for the next binning (no memset node in the step graph).
 template <bool OCC>
 struct KBinScan {
@@ -182,7 +182,7 @@ struct KBinScan {
     const long long i0 = base + (long long)threadIdx.x * kScanPer;
     int c[kScanPer];
     scan_load(counts, i0, nbins, c);
-    if (!band) {  // with row bands, k_band_mark clears the counts (a parallel pass over the bins)
+    if (!band) {  // with row bands, the scatter clears the counts of the occupied bins
       int z[kScanPer];
 #pragma unroll
       for (int k = 0; k < kScanPer; ++k) z[k] = 0;
@@ -246,16 +246,48 @@ struct KScan2 {
 }
 };
 
+// Row bands (boxes along y and z) that the windows of an occupied bin reach: windows starting in
+// bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach per axis; band_dil one box more
+// each way (the bands still hold the windows after a move of under a box). The scan has cleared
+// the flags; a flag already set is not stored again.
+__device__ __forceinline__ void band_mark(const PointGeom& g, int bin, unsigned char* __restrict__ band,
+                                          unsigned char* __restrict__ band_dil, int reach) {
+  const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
+  const int rz = (g.d == 3) ? reach : 0, z0 = (g.d == 3) ? -1 : 0;
+  const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
+  for (int dz = 0; dz <= rz; ++dz)
+    for (int dy = 0; dy <= reach; ++dy) {
+      unsigned char* f = &band[((bz + dz) % nbz) * nby + (by + dy) % nby];
+      if (!*f) *f = 1;
+    }
+  if (band_dil)
+    for (int dz = z0; dz <= rz - z0; ++dz)
+      for (int dy = -1; dy <= reach + 1; ++dy) {
+        unsigned char* f = &band_dil[((bz + dz + nbz) % nbz) * nby + (by + dy + nby) % nby];
+        if (!*f) *f = 1;
+      }
+}
+
 template <typename T>
 struct KBinScatter {
   static constexpr int kThreads = 256, kMinBlocks = 0;
   static constexpr bool kAnyGrid = true;
+  // With row bands (band != nullptr): the first point of each occupied bin (rank 0) also marks
+  // the bands its bin's windows reach (band_mark) and returns the bin's count to zero for the
+  // next binning (empty bins were never counted).
   __device__ static void run(PointGeom g, const double* __restrict__ X, const int* __restrict__ bin_of,
                               const int* __restrict__ rank, const int* __restrict__ offsets,
-                              int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta) {
+                              int* __restrict__ perm, int* __restrict__ i0, T* __restrict__ delta,
+                              int* __restrict__ counts, unsigned char* __restrict__ band,
+                              unsigned char* __restrict__ band_dil, int reach) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.M; j += gridDim.x * blockDim.x) {
-    const int s = offsets[bin_of[j]] + rank[j];
+    const int bin = bin_of[j], rk = rank[j];
+    const int s = offsets[bin] + rk;
     perm[s] = j;
+    if (band && rk == 0) {
+      counts[bin] = 0;
+      band_mark(g, bin, band, band_dil, reach);
+    }
     for (int a = 0; a < g.d; ++a) {
       const double t = grid_coord(X[(long long)a * g.M + j], g);
       const int c0 = window_start(t, g.w);
@@ -267,38 +299,6 @@ struct KBinScatter {
 };
 
 static int num_sms();
-
-// Row bands (boxes along y and z) that the windows of each occupied bin reach: windows
-// starting in bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach per axis; band_dil
-// one box more each way (the bands still hold the windows after a move of under a box). One
-// thread per bin, after the scan has cleared the flags; a flag already set is not stored again.
-// It also returns the bin counts to zero.
-struct KBandMark {
-  static constexpr int kThreads = 256, kMinBlocks = 0;
-  static constexpr bool kAnyGrid = true;
-  __device__ static void run(PointGeom g, const int* __restrict__ offsets, int* __restrict__ counts,
-                            unsigned char* __restrict__ band, unsigned char* __restrict__ band_dil, int reach) {
-  const int nbins = g.nb[0] * g.nb[1] * (g.d == 3 ? g.nb[2] : 1);
-  const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
-  const int rz = (g.d == 3) ? reach : 0, z0 = (g.d == 3) ? -1 : 0;
-  for (int bin = blockIdx.x * blockDim.x + threadIdx.x; bin < nbins; bin += gridDim.x * blockDim.x) {
-    counts[bin] = 0;  // zero again for the next binning (the scan has consumed them)
-    if (offsets[bin + 1] == offsets[bin]) continue;
-    const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
-    for (int dz = 0; dz <= rz; ++dz)
-      for (int dy = 0; dy <= reach; ++dy) {
-        unsigned char* f = &band[((bz + dz) % nbz) * nby + (by + dy) % nby];
-        if (!*f) *f = 1;
-      }
-    if (band_dil)
-      for (int dz = z0; dz <= rz - z0; ++dz)
-        for (int dy = -1; dy <= reach + 1; ++dy) {
-          unsigned char* f = &band_dil[((bz + dz + nbz) % nbz) * nby + (by + dy + nby) % nby];
-          if (!*f) *f = 1;
-        }
-  }
-}
-};
 
 // The whole binning of a small problem in one block (one launch instead of four): bins and
 // ranks with shared-memory atomics, the exclusive scan of the bin counts in shared memory, the
@@ -351,7 +351,7 @@ struct KBinSmall {
     sc[bin] = run;
     offsets[bin] = run;
     run += c;
-    if (c > 0 && band) {  // row bands of this bin's windows (see k_band_mark)
+    if (c > 0 && band) {  // row bands of this bin's windows (see band_mark)
       const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
       for (int dz = 0; dz <= rz; ++dz)
         for (int dy = 0; dy <= reach; ++dy) band[((bz + dz) % nbz) * nby + (by + dy) % nby] = 1;
@@ -396,17 +396,12 @@ void launch_bin_points(const Plan& p, Workspace& ws, const double* X, cudaStream
   launch<KBinCount>(nb, 256, 0, st, g, X, ws.bin_of, ws.rank, ws.counts);
   if (occupied) launch<KBinScan<true>>(1, kScanThreads, 0, st, ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
   else launch<KBinScan<false>>(1, kScanThreads, 0, st, ws.counts, p.nbins, ws.offsets, ws.occ, ws.nocc, band, band_dil, nband);
-  if (band) {
-    const long long nbb = std::min<long long>((p.nbins + 255) / 256, 4LL * num_sms());
-    launch<KBandMark>((unsigned)std::max<long long>(1, nbb), 256, 0, st, g, ws.offsets, ws.counts, band, band_dil,
-                                                                         reach);
-  }
   if (p.prec == FSIB_FP64)
     launch<KBinScatter<double>>(nb, 256, 0, st, g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
-                                              (double*)ws.delta);
+                                (double*)ws.delta, ws.counts, band, band_dil, reach);
   else
     launch<KBinScatter<float>>(nb, 256, 0, st, g, X, ws.bin_of, ws.rank, ws.offsets, ws.perm, ws.i0,
-                                             (float*)ws.delta);
+                               (float*)ws.delta, ws.counts, band, band_dil, reach);
 }
 
 // ---------------------------------------------------------------------------
