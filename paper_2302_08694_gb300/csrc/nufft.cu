@@ -1092,7 +1092,7 @@ struct KSpreadBox3 {
               const int* __restrict__ box_item, const int* __restrict__ sched, const int* __restrict__ part_off,
               T* __restrict__ part,
               T* __restrict__ grid, int* __restrict__ work, int* __restrict__ done) {
-  __shared__ T sB[2][kBoxChunk * 24];  // [c][axis][8] box-relative weights
+  __shared__ __align__(16) T sB[2][kBoxChunk * 24];  // [c][axis][8] box-relative weights
   __shared__ T sC[2][kBoxChunk * 3];
   __shared__ int sStart[32], sPre[33];  // non-empty neighbour ranges: first point, prefix of lengths
   __shared__ int sNr;
@@ -1150,11 +1150,19 @@ struct KSpreadBox3 {
         q0 += (q0 < 0) ? nf : 0; q0 -= (q0 >= nf) ? nf : 0;
         const T* wsrc = W + sp * 3 * w + a * w;
         T* dst = &sB[bb][(c * 3 + a) * 8];
+        T wv[8];
 #pragma unroll
         for (int l = 0; l < 8; ++l) {
           int q = q0 + l;
           q -= (q >= nf) ? nf : 0;
-          dst[l] = (q < w) ? wsrc[q] : T(0);
+          wv[l] = (q < w) ? wsrc[q] : T(0);
+        }
+        if constexpr (sizeof(T) == 4) {  // two 16-byte stores: the threads' rows are 32 bytes apart
+          reinterpret_cast<float4*>(dst)[0] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+          reinterpret_cast<float4*>(dst)[1] = make_float4(wv[4], wv[5], wv[6], wv[7]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < 8; ++l) dst[l] = wv[l];
         }
         sC[bb][c * 3 + a] = Cw[sp * 3 + a];
       }
