@@ -249,7 +249,8 @@ struct KScan2 {
 // Row bands (boxes along y and z) that the windows of an occupied bin reach: windows starting in
 // bin B cover cells [B b, B b + b + w - 1), boxes B .. B + reach per axis; band_dil one box more
 // each way (the bands still hold the windows after a move of under a box). The scan has cleared
-// the flags; a flag already set is not stored again.
+// the flags; the stores are unconditional (one lane of a warp marks its bin: a read before each
+// store would wait on memory 34 times in a row).
 __device__ __forceinline__ void band_mark(const PointGeom& g, int bin, unsigned char* __restrict__ band,
                                           unsigned char* __restrict__ band_dil, int reach) {
   const int nby = g.nb[1], nbz = (g.d == 3) ? g.nb[2] : 1;
@@ -257,14 +258,12 @@ __device__ __forceinline__ void band_mark(const PointGeom& g, int bin, unsigned 
   const int by = (bin / g.nb[0]) % nby, bz = bin / (g.nb[0] * nby);
   for (int dz = 0; dz <= rz; ++dz)
     for (int dy = 0; dy <= reach; ++dy) {
-      unsigned char* f = &band[((bz + dz) % nbz) * nby + (by + dy) % nby];
-      if (!*f) *f = 1;
+      band[((bz + dz) % nbz) * nby + (by + dy) % nby] = 1;
     }
   if (band_dil)
     for (int dz = z0; dz <= rz - z0; ++dz)
       for (int dy = -1; dy <= reach + 1; ++dy) {
-        unsigned char* f = &band_dil[((bz + dz + nbz) % nbz) * nby + (by + dy + nby) % nby];
-        if (!*f) *f = 1;
+        band_dil[((bz + dz + nbz) % nbz) * nby + (by + dy + nby) % nby] = 1;
       }
 }
 
