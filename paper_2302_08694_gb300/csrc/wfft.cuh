@@ -23,14 +23,14 @@ namespace fsib {
 constexpr int kOneExchange = 1 << 16;
 constexpr int wfft_n(int c) { return c & 0xFFFF; }
 constexpr bool wfft_one(int c) { return (c & kOneExchange) != 0; }
-// Lengths with a warp plan: 64, 128, 256 (M = 8) and 48, 96, 192 (M = 12); one-exchange plans of
-// 96 and 192 (M = 24).
+// Lengths with a warp plan: 64, 128, 256 (M = 8), 48, 96, 192 (M = 12) and 144 (M = 18: 8 lanes a
+// line, radices 18 x 2 x 2 x 2); one-exchange plans of 96 and 192 (M = 24).
 constexpr bool wfft_has(int c) {
   return wfft_one(c) ? (wfft_n(c) == 96 || wfft_n(c) == 192)
-                     : (c == 64 || c == 128 || c == 256 || c == 48 || c == 96 || c == 192);
+                     : (c == 64 || c == 128 || c == 256 || c == 48 || c == 96 || c == 192 || c == 144);
 }
 constexpr int wfft_M(int c) {
-  return wfft_one(c) ? 24 : (c == 48 || c == 96 || c == 192) ? 12 : 8;
+  return wfft_one(c) ? 24 : (c == 48 || c == 96 || c == 192) ? 12 : c == 144 ? 18 : 8;
 }
 constexpr int wfft_L(int c) { return wfft_n(c) / wfft_M(c); }
 constexpr int wfft_radix(int c, int s) {
@@ -40,6 +40,7 @@ constexpr int wfft_radix(int c, int s) {
          : c == 48  ? (s == 0 ? 12 : s == 1 ? 4 : 0)
          : c == 96  ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 2 : 0)
          : c == 192 ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 4 : 0)
+         : c == 144 ? (s == 0 ? 18 : s <= 3 ? 2 : 0)
          : c == (96 | kOneExchange)  ? (s == 0 ? 24 : s == 1 ? 4 : 0)
          : c == (192 | kOneExchange) ? (s == 0 ? 24 : s == 1 ? 8 : 0)
                     : 0;
@@ -61,6 +62,7 @@ constexpr int wfft_swz(int c, int E, int ex) {
                    : c == 48  ? (ex == 0 ? (2 << 8 | 3) : 0)
                    : c == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
                    : c == 192 ? (ex == 0 ? (2 << 8 | 15) : ex == 1 ? (2 << 8 | 7) : 0)
+                   : c == 144 ? (ex == 0 ? (3 << 8 | 1) : 0)
                               : 0)
                 : (c == 64    ? (ex == 0 ? (3 << 8 | 7) : 0)
                    : c == 128 ? (ex == 0 ? (3 << 8 | 7) : 0)
@@ -68,13 +70,14 @@ constexpr int wfft_swz(int c, int E, int ex) {
                    : c == 48  ? (ex == 0 ? (2 << 8 | 3) : 0)
                    : c == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
                    : c == 192 ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
+                   : c == 144 ? (ex == 0 ? (3 << 8 | 1) : 0)
                               : 0);
 }
 // Elements per line buffer (n plus bank padding; the one-exchange plans' line strides are 8 and
 // 4 mod 16 elements, so the lines of a half-warp also fall in distinct bank pairs).
 constexpr int wfft_stride(int c, int E) {
   return wfft_one(c) ? wfft_n(c) + (wfft_n(c) == 192 ? 8 : 4)
-                     : c + (E == 8 ? (c == 64 ? 8 : c == 48 ? 4 : c == 96 ? 8 : 0) : (c == 48 ? 4 : 0));
+                     : c + (E == 8 ? (c == 64 ? 8 : c == 48 ? 4 : c == 96 ? 8 : c == 144 ? 8 : 0) : (c == 48 ? 4 : 0));
 }
 template <int SW>
 __device__ __forceinline__ int wswz(int e) {
@@ -119,6 +122,11 @@ __device__ __forceinline__ void dft12(C<T>* v) {
     for (int k2 = 0; k2 < 4; ++k2) v[(4 * k1 + 9 * k2) % 12] = b[k2];
   }
 }
+
+// 18-point DFT by the prime-factor mapping 18 = 2 x 9 (no twiddles): input index
+// (9 n1 + 2 n2) mod 18, output index (9 k1 + 10 k2) mod 18.
+template <typename T, bool INV>
+__device__ __forceinline__ void dft18(C<T>* v);
 
 // 24-point DFT by the prime-factor mapping 24 = 3 x 8 (no twiddles): input index
 // (8 n1 + 3 n2) mod 24, output index (16 k1 + 9 k2) mod 24.
@@ -216,6 +224,24 @@ __device__ __forceinline__ void dft9(C<T>* v) {
   }
 }
 
+template <typename T, bool INV>
+__device__ __forceinline__ void dft18(C<T>* v) {
+  C<T> a[9][2];
+#pragma unroll
+  for (int n2 = 0; n2 < 9; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 2; ++n1) a[n2][n1] = v[(9 * n1 + 2 * n2) % 18];
+    dft2<T, INV>(a[n2]);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 2; ++k1) {
+    C<T> b[9] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1], a[4][k1], a[5][k1], a[6][k1], a[7][k1], a[8][k1]};
+    dft9<T, INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 9; ++k2) v[(9 * k1 + 10 * k2) % 18] = b[k2];
+  }
+}
+
 template <typename T, bool INV, int R>
 __device__ __forceinline__ void dft_r(C<T>* v) {
   if constexpr (R == 2) dft2<T, INV>(v);
@@ -225,6 +251,7 @@ __device__ __forceinline__ void dft_r(C<T>* v) {
   else if constexpr (R == 9) dft9<T, INV>(v);
   else if constexpr (R == 12) dft12<T, INV>(v);
   else if constexpr (R == 16) dft16<T, INV>(v);
+  else if constexpr (R == 18) dft18<T, INV>(v);
   else if constexpr (R == 24) dft24<T, INV>(v);
 }
 
