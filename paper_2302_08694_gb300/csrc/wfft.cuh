@@ -23,14 +23,15 @@ namespace fsib {
 constexpr int kOneExchange = 1 << 16;
 constexpr int wfft_n(int c) { return c & 0xFFFF; }
 constexpr bool wfft_one(int c) { return (c & kOneExchange) != 0; }
-// Lengths with a warp plan: 64, 128, 256 (M = 8), 48, 96, 192 (M = 12) and 144 (M = 18: 8 lanes a
-// line, radices 18 x 2 x 2 x 2); one-exchange plans of 96 and 192 (M = 24).
+// Lengths with a warp plan: 64, 128, 256 (M = 8), 48, 96, 192 (M = 12), 72 and 144 (M = 18: 4 and 8
+// lanes a line, radices 18 x 2 x 2 and 18 x 2 x 2 x 2); one-exchange plans of 96 and 192 (M = 24).
 constexpr bool wfft_has(int c) {
   return wfft_one(c) ? (wfft_n(c) == 96 || wfft_n(c) == 192)
-                     : (c == 64 || c == 128 || c == 256 || c == 48 || c == 96 || c == 192 || c == 144);
+                     : (c == 64 || c == 128 || c == 256 || c == 48 || c == 96 || c == 192 || c == 144 ||
+                        c == 72);
 }
 constexpr int wfft_M(int c) {
-  return wfft_one(c) ? 24 : (c == 48 || c == 96 || c == 192) ? 12 : c == 144 ? 18 : 8;
+  return wfft_one(c) ? 24 : (c == 48 || c == 96 || c == 192) ? 12 : (c == 144 || c == 72) ? 18 : 8;
 }
 constexpr int wfft_L(int c) { return wfft_n(c) / wfft_M(c); }
 constexpr int wfft_radix(int c, int s) {
@@ -41,6 +42,7 @@ constexpr int wfft_radix(int c, int s) {
          : c == 96  ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 2 : 0)
          : c == 192 ? (s == 0 ? 12 : s == 1 ? 4 : s == 2 ? 4 : 0)
          : c == 144 ? (s == 0 ? 18 : s <= 3 ? 2 : 0)
+         : c == 72  ? (s == 0 ? 18 : s <= 2 ? 2 : 0)
          : c == (96 | kOneExchange)  ? (s == 0 ? 24 : s == 1 ? 4 : 0)
          : c == (192 | kOneExchange) ? (s == 0 ? 24 : s == 1 ? 8 : 0)
                     : 0;
@@ -63,6 +65,7 @@ constexpr int wfft_swz(int c, int E, int ex) {
                    : c == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
                    : c == 192 ? (ex == 0 ? (2 << 8 | 15) : ex == 1 ? (2 << 8 | 7) : 0)
                    : c == 144 ? (ex == 0 ? (3 << 8 | 1) : 0)
+                   : c == 72  ? (ex == 0 ? (2 << 8 | 1) : 0)
                               : 0)
                 : (c == 64    ? (ex == 0 ? (3 << 8 | 7) : 0)
                    : c == 128 ? (ex == 0 ? (3 << 8 | 7) : 0)
@@ -71,13 +74,15 @@ constexpr int wfft_swz(int c, int E, int ex) {
                    : c == 96  ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
                    : c == 192 ? (ex == 0 ? (2 << 8 | 7) : ex == 1 ? (3 << 8 | 7) : 0)
                    : c == 144 ? (ex == 0 ? (3 << 8 | 1) : 0)
+                   : c == 72  ? (ex == 0 ? (2 << 8 | 1) : 0)
                               : 0);
 }
 // Elements per line buffer (n plus bank padding; the one-exchange plans' line strides are 8 and
 // 4 mod 16 elements, so the lines of a half-warp also fall in distinct bank pairs).
 constexpr int wfft_stride(int c, int E) {
   return wfft_one(c) ? wfft_n(c) + (wfft_n(c) == 192 ? 8 : 4)
-                     : c + (E == 8 ? (c == 64 ? 8 : c == 48 ? 4 : c == 96 ? 8 : c == 144 ? 8 : 0) : (c == 48 ? 4 : 0));
+                     : c + (E == 8 ? (c == 64 ? 8 : c == 48 ? 4 : c == 96 ? 8 : c == 144 ? 8 : c == 72 ? 4 : 0)
+                                   : (c == 48 ? 4 : c == 72 ? 4 : 0));
 }
 template <int SW>
 __device__ __forceinline__ int wswz(int e) {
