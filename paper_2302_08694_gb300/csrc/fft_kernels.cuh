@@ -968,6 +968,8 @@ void launch_rows_product(const C<T>* in, C<T>* out, int d, long long nrows, int 
     if constexpr (wfft_has(NC)) if ((npairs + LPW - 1) / LPW >= kWarpRowsMin) {
       // Blocks of two warps measured no faster: double-float length 96 (five resident blocks instead
       // of two) 127.0 against 127.4 us a step, FP32 one-exchange length 192 80.6 against 74.6 us.
+      // Blocks of three warps for the one-exchange plans (three resident blocks, nine warps an SM
+      // instead of eight) measured slower too: 191.8 against 143.3 us a step at length 192.
       constexpr int PT = 128;
       const size_t ws = sizeof(C<T>) * (size_t)(wfft_tw_size(PC) + wfft_twt_size<PC>() +
                                                 (PT / 32) * LPW * 3 * wfft_stride(PC, (int)sizeof(C<T>)));
