@@ -67,6 +67,39 @@ __device__ __forceinline__ dd operator*(dd a, dd b) {
 }
 __device__ __forceinline__ dd& operator+=(dd& a, dd b) { a = a + b; return a; }
 
+// Sum without the final renormalisation (8 instructions instead of 11): hi is the rounded sum
+// of the high parts, lo the TwoSum error plus the low parts, so hi + lo is the same value as
+// a + b above but |lo| may exceed ulp(hi)/2 by a few units. Chains of such sums (the butterflies
+// of one DFT) keep their norm-wise error bound, which is what FFT error analysis needs; a
+// later product or renormalising sum restores the canonical form.
+__device__ __forceinline__ dd dd_add_nr(dd a, dd b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return dd(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+// a b + c d with one TwoSum: each product formed by TwoProd plus its two cross terms, the
+// high parts added by TwoSum, every error term by plain adds, one renormalisation at the end
+// (19 instructions instead of 25 for two rounded products and a sum).
+__device__ __forceinline__ dd dd_dot2(dd a, dd b, dd c, dd d) {
+  float p, e, q, f;
+  two_prod(a.hi, b.hi, p, e);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  two_prod(c.hi, d.hi, q, f);
+  f = __fmaf_rn(c.hi, d.lo, f);
+  f = __fmaf_rn(c.lo, d.hi, f);
+  float s, r;
+  two_sum(p, q, s, r);
+  r = __fadd_rn(r, __fadd_rn(e, f));
+  float h, l;
+  quick_two_sum(s, r, h, l);
+  return dd(h, l);
+}
+
+// Exact halving (a power-of-two scale of both parts).
+__device__ __forceinline__ dd dd_half(dd a) { return dd(__fmul_rn(0.5f, a.hi), __fmul_rn(0.5f, a.lo)); }
+
 // Accumulator for long sums of products: acc.hi collects the rounded sum, acc.lo the
 // exact rounding errors (TwoSum) plus the low parts; renormalised only when read.
 // The product a*b is formed without the final renormalisation (TwoProd plus the two

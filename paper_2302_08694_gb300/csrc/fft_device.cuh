@@ -8,9 +8,27 @@
 // Lines live in shared memory; element i of line l is at base[l*ls + i*es].
 // Two buffers alternate between stages.
 #pragma once
+#include <type_traits>
 #include "fsib_internal.cuh"
 
 namespace fsib {
+
+// Butterfly sums: double-float sums inside a DFT skip their renormalisation (dd_add_nr); the
+// twiddle and constant products between the DFTs renormalise. Other types: plain sums.
+template <typename T> __device__ __forceinline__ T sadd(T a, T b) {
+  if constexpr (std::is_same<T, dd>::value) return dd_add_nr(a, b);
+  else return a + b;
+}
+template <typename T> __device__ __forceinline__ T ssub(T a, T b) {
+  if constexpr (std::is_same<T, dd>::value) return dd_add_nr(a, -b);
+  else return a - b;
+}
+template <typename T> __device__ __forceinline__ C<T> badd(C<T> a, C<T> b) {
+  return mk<T>(sadd<T>(a.x, b.x), sadd<T>(a.y, b.y));
+}
+template <typename T> __device__ __forceinline__ C<T> bsub(C<T> a, C<T> b) {
+  return mk<T>(ssub<T>(a.x, b.x), ssub<T>(a.y, b.y));
+}
 
 // sqrt(3)/2 in each arithmetic type
 template <typename T> __device__ __forceinline__ T sqrt3_2();
@@ -33,32 +51,34 @@ template <> __device__ __forceinline__ dd rsqrt2<dd>() {
 template <typename T, bool INV>
 __device__ __forceinline__ void dft2(C<T>* v) {
   C<T> a = v[0], b = v[1];
-  v[0] = cadd<T>(a, b);
-  v[1] = csub<T>(a, b);
+  v[0] = badd<T>(a, b);
+  v[1] = bsub<T>(a, b);
 }
 
 template <typename T, bool INV>
 __device__ __forceinline__ void dft3(C<T>* v) {
   // forward: y1 = v0 - (v1+v2)/2 - i s3 (v1 - v2), y2 = v0 - (v1+v2)/2 + i s3 (v1 - v2)
-  C<T> s = cadd<T>(v[1], v[2]);
-  C<T> d = csub<T>(v[1], v[2]);
-  C<T> m = mk<T>(v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y);
+  C<T> s = badd<T>(v[1], v[2]);
+  C<T> d = bsub<T>(v[1], v[2]);
+  C<T> m;
+  if constexpr (std::is_same<T, dd>::value) m = bsub<T>(v[0], mk<T>(dd_half(s.x), dd_half(s.y)));
+  else m = mk<T>(v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y);
   C<T> t = cscale<T>(d, sqrt3_2<T>());
   C<T> it = INV ? cmul_i<T>(t) : cmul_mi<T>(t);
-  v[0] = cadd<T>(v[0], s);
-  v[1] = cadd<T>(m, it);
-  v[2] = csub<T>(m, it);
+  v[0] = badd<T>(v[0], s);
+  v[1] = badd<T>(m, it);
+  v[2] = bsub<T>(m, it);
 }
 
 template <typename T, bool INV>
 __device__ __forceinline__ void dft4(C<T>* v) {
-  C<T> s02 = cadd<T>(v[0], v[2]), d02 = csub<T>(v[0], v[2]);
-  C<T> s13 = cadd<T>(v[1], v[3]), d13 = csub<T>(v[1], v[3]);
+  C<T> s02 = badd<T>(v[0], v[2]), d02 = bsub<T>(v[0], v[2]);
+  C<T> s13 = badd<T>(v[1], v[3]), d13 = bsub<T>(v[1], v[3]);
   C<T> id = INV ? cmul_i<T>(d13) : cmul_mi<T>(d13);
-  v[0] = cadd<T>(s02, s13);
-  v[2] = csub<T>(s02, s13);
-  v[1] = cadd<T>(d02, id);
-  v[3] = csub<T>(d02, id);
+  v[0] = badd<T>(s02, s13);
+  v[2] = bsub<T>(s02, s13);
+  v[1] = badd<T>(d02, id);
+  v[3] = bsub<T>(d02, id);
 }
 
 template <typename T, bool INV, int R>

@@ -97,15 +97,15 @@ __device__ __forceinline__ void dft8(C<T>* v) {
   dft4<T, INV>(o);
   const T h = rsqrt2<T>();
   // w^k o[k], w = exp(-+ 2 pi i / 8)
-  const C<T> o1 = INV ? mk<T>((o[1].x - o[1].y) * h, (o[1].x + o[1].y) * h)
-                      : mk<T>((o[1].x + o[1].y) * h, (o[1].y - o[1].x) * h);
+  const C<T> o1 = INV ? mk<T>(ssub<T>(o[1].x, o[1].y) * h, sadd<T>(o[1].x, o[1].y) * h)
+                      : mk<T>(sadd<T>(o[1].x, o[1].y) * h, ssub<T>(o[1].y, o[1].x) * h);
   const C<T> o2 = INV ? cmul_i<T>(o[2]) : cmul_mi<T>(o[2]);
-  const C<T> o3 = INV ? mk<T>(-(o[3].x + o[3].y) * h, (o[3].x - o[3].y) * h)
-                      : mk<T>((o[3].y - o[3].x) * h, -(o[3].x + o[3].y) * h);
-  v[0] = cadd<T>(e[0], o[0]); v[4] = csub<T>(e[0], o[0]);
-  v[1] = cadd<T>(e[1], o1);   v[5] = csub<T>(e[1], o1);
-  v[2] = cadd<T>(e[2], o2);   v[6] = csub<T>(e[2], o2);
-  v[3] = cadd<T>(e[3], o3);   v[7] = csub<T>(e[3], o3);
+  const C<T> o3 = INV ? mk<T>(-sadd<T>(o[3].x, o[3].y) * h, ssub<T>(o[3].x, o[3].y) * h)
+                      : mk<T>(ssub<T>(o[3].y, o[3].x) * h, -sadd<T>(o[3].x, o[3].y) * h);
+  v[0] = badd<T>(e[0], o[0]); v[4] = bsub<T>(e[0], o[0]);
+  v[1] = badd<T>(e[1], o1);   v[5] = bsub<T>(e[1], o1);
+  v[2] = badd<T>(e[2], o2);   v[6] = bsub<T>(e[2], o2);
+  v[3] = badd<T>(e[3], o3);   v[7] = bsub<T>(e[3], o3);
 }
 
 // 12-point DFT by the prime-factor mapping 12 = 3 x 4 (no twiddles): input index
@@ -176,7 +176,8 @@ FSIB_TRIG_CONST(sin_8pi9, 0.34202014332566873304409961468225958)
 template <typename T, bool INV>
 __device__ __forceinline__ C<T> crot(C<T> v, T cr, T si) {
   const T ci = INV ? si : -si;
-  return mk<T>(v.x * cr - v.y * ci, v.x * ci + v.y * cr);
+  if constexpr (std::is_same<T, dd>::value) return mk<T>(dd_dot2(v.x, cr, -v.y, ci), dd_dot2(v.x, ci, v.y, cr));
+  else return mk<T>(v.x * cr - v.y * ci, v.x * ci + v.y * cr);
 }
 
 // 16-point DFT: 4 x 4 Cooley-Tukey (inner twiddles w^{n2 k1}, w = exp(-+ 2 pi i / 16)).
