@@ -10,6 +10,7 @@
 // contracted into an FMA behind our back.
 #pragma once
 #include <cuda_runtime.h>
+#include "ddconv.cuh"
 
 namespace fsib {
 
@@ -28,6 +29,19 @@ struct __align__(8) dd {
 struct __align__(16) dd2 {  // 16-byte aligned so that a complex value moves as one vector
   dd x, y;
 };
+
+// double -> double-float on the integer and FP32 pipes (ddconv.cuh); magnitudes of 2^128 and
+// above, infinities and NaN go through FP64.
+__device__ __forceinline__ dd dd_from_double(double x) {
+  float h, l;
+  if (ddconv::split_double(x, h, l)) return dd(h, l);
+  return dd(x);
+}
+// double-float -> double: both parts widened exactly by integer operations, then one FP64
+// addition (a join of the pair by integer arithmetic alone measured slower than this form).
+__device__ __forceinline__ double dd_to_double(dd v) {
+  return ddconv::widen_float(v.hi) + ddconv::widen_float(v.lo);
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);

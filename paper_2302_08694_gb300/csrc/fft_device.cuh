@@ -30,6 +30,20 @@ template <typename T> __device__ __forceinline__ C<T> bsub(C<T> a, C<T> b) {
   return mk<T>(ssub<T>(a.x, b.x), ssub<T>(a.y, b.y));
 }
 
+// Spectra A, B of the two real rows packed as z = a + i b, from Z[k] and Zc = conj Z[N - k]:
+// A[k] = (Z[k] + Zc) / 2, B[k] = (Z[k] - Zc) / 2i. Double-float: non-renormalising sums and
+// exact halving; other types: the plain expressions.
+template <typename T> struct CPair { C<T> a, b; };
+template <typename T> __device__ __forceinline__ CPair<T> untangle_pair(C<T> Z, C<T> Zc) {
+  if constexpr (std::is_same<T, dd>::value) {
+    const C<T> s = badd<T>(Z, Zc), df = bsub<T>(Z, Zc);
+    return {mk<T>(dd_half(s.x), dd_half(s.y)), mk<T>(dd_half(df.y), -dd_half(df.x))};
+  } else {
+    const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
+    return {mk<T>(T(0.5) * s.x, T(0.5) * s.y), mk<T>(T(0.5) * df.y, T(-0.5) * df.x)};
+  }
+}
+
 // sqrt(3)/2 in each arithmetic type
 template <typename T> __device__ __forceinline__ T sqrt3_2();
 template <> __device__ __forceinline__ float sqrt3_2<float>() { return 0.866025403784438646763723170752936183f; }

@@ -136,9 +136,9 @@ struct KRowsR2C {
     if (pr >= npairs) continue;
     const C<T> Z = r[p * ls + k];
     const C<T> Zc = cconj<T>(r[p * ls + (k == 0 ? 0 : n - k)]);
-    const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
-    out[(2 * pr) * h + k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
-    out[(2 * pr + 1) * h + k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
+    const CPair<T> ab = untangle_pair<T>(Z, Zc);
+    out[(2 * pr) * h + k] = ab.a;
+    out[(2 * pr + 1) * h + k] = ab.b;
   }
 }
 };
@@ -150,11 +150,11 @@ __device__ __forceinline__ C<T> pack_rows(const C<T>* __restrict__ A, const C<T>
   if (k == 0) return mk<T>(A[0].x, B[0].x);  // Hermitian part of the m_x = 0 column
   if (k < h) {
     const C<T> a = A[k], bb = B[k];
-    return mk<T>(a.x - bb.y, a.y + bb.x);
+    return mk<T>(ssub<T>(a.x, bb.y), sadd<T>(a.y, bb.x));
   }
   if (k > n - h) {
     const C<T> a = A[n - k], bb = B[n - k];  // conj(A) + i conj(B)
-    return mk<T>(a.x + bb.y, -a.y + bb.x);
+    return mk<T>(sadd<T>(a.x, bb.y), sadd<T>(-a.y, bb.x));
   }
   return mk<T>(T(0), T(0));
 }
@@ -250,10 +250,10 @@ struct KRowsProduct {
     if (pr >= npairs) continue;
     const C<T> Z = f[line * ls + k];
     const C<T> Zc = cconj<T>(f[line * ls + (k == 0 ? 0 : n - k)]);
-    const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
     C<T>* ob = out + ((long long)ab * nrows + 2 * pr) * h;
-    ob[k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
-    ob[h + k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
+    const CPair<T> u = untangle_pair<T>(Z, Zc);
+    ob[k] = u.a;
+    ob[h + k] = u.b;
   }
 }
 };
@@ -367,9 +367,9 @@ __device__ __forceinline__ void wfft_untangle(const C<T> (&v)[wfft_M(N)], C<T>* 
       if (k < h) {
         const C<T> Z = buf[k];
         const C<T> Zc = cconj<T>(buf[k == 0 ? 0 : NN - k]);
-        const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
-        outA[k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
-        outB[k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
+        const CPair<T> u = untangle_pair<T>(Z, Zc);
+        outA[k] = u.a;
+        outB[k] = u.b;
       }
     }
   }
@@ -395,9 +395,9 @@ __device__ __forceinline__ void wfft_untangle_strided(const C<T> (&v)[wfft_M(PC)
       if (k < h) {
         const C<T> Z = v[i];
         const C<T> Zc = cconj<T>(k == 0 ? Z : buf[h - k]);
-        const C<T> s = cadd<T>(Z, Zc), df = csub<T>(Z, Zc);
-        outA[k] = mk<T>(T(0.5) * s.x, T(0.5) * s.y);
-        outB[k] = mk<T>(T(0.5) * df.y, T(-0.5) * df.x);
+        const CPair<T> u = untangle_pair<T>(Z, Zc);
+        outA[k] = u.a;
+        outB[k] = u.b;
       }
     }
   }

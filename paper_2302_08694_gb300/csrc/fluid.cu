@@ -165,39 +165,12 @@ __device__ __forceinline__ dd dd_rcp(dd a) {
   const dd r(__frcp_rn(a.hi));
   return r + r * (dd(1.0f) - a * r);
 }
-// Exact-enough split of a double into hi + lo floats with integer operations (the FP64
-// conversions run at the FP64 rate): hi keeps the top 24 significant bits (truncated), lo is
-// the remaining 29 bits rounded to a float and scaled by 2^(E - 52). Values below 2^-100
-// (far under any tolerance here) become zero; Inf, NaN and values beyond the float range
-// take the slow conversion so that they stay visible.
-__device__ __forceinline__ dd split_double(double v) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((u >> 52) & 0x7ffULL) - 1023;
-  if (e < -100) return dd(0.0f, 0.0f);
-  if (e > 127) return dd(__double2float_rn(v), 0.0f);  // Inf, NaN or out of float range: keep it visible
-  const unsigned sgn = (unsigned)(u >> 32) & 0x80000000u;
-  const unsigned long long m = u & 0xfffffffffffffULL;
-  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
-  float lo = __uint2float_rn((unsigned)(m & 0x1fffffffULL));          // low 29 bits, exact up to 2^24 rounding
-  lo *= __uint_as_float((unsigned)(e - 52 + 127) << 23);               // 2^(e - 52), a normal float for e >= -74
-  if (e < -74) lo = 0.0f;
-  return dd(hi, sgn ? -lo : lo);
-}
-// hi + lo as a double: both floats widened by integer operations, one FP64 addition.
-__device__ __forceinline__ double widen_float(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned ex = (b >> 23) & 0xffu;
-  if (ex == 0) return 0.0;  // zero (float subnormals do not occur in these values)
-  if (ex == 255) return (double)f;  // Inf or NaN
-  const unsigned long long r = ((unsigned long long)(b & 0x80000000u) << 32) |
-                               ((unsigned long long)(ex - 127 + 1023) << 52) |
-                               ((unsigned long long)(b & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)r);
-}
-__device__ __forceinline__ double join_dd(dd a) { return widen_float(a.hi) + widen_float(a.lo); }
+// Spectra are split into double-float pairs on load and joined on store with integer and FP32
+// operations (dd_from_double, dd_to_double).
+__device__ __forceinline__ double join_dd(dd a) { return dd_to_double(a); }
 
 struct DDc { dd x, y; };
-__device__ __forceinline__ DDc ddc(double2 v) { return {split_double(v.x), split_double(v.y)}; }
+__device__ __forceinline__ DDc ddc(double2 v) { return {dd_from_double(v.x), dd_from_double(v.y)}; }
 
 template <int D>
 struct KNsUpdateDD {

@@ -44,8 +44,8 @@ template <typename T> __device__ __forceinline__ C<T> cmul_mi(C<T> a) { return m
 __device__ __forceinline__ void cvt(float& o, float i) { o = i; }
 __device__ __forceinline__ void cvt(double& o, double i) { o = i; }
 __device__ __forceinline__ void cvt(dd& o, dd i) { o = i; }
-__device__ __forceinline__ void cvt(dd& o, double i) { o = dd(i); }
-__device__ __forceinline__ void cvt(double& o, dd i) { o = i.to_double(); }
+__device__ __forceinline__ void cvt(dd& o, double i) { o = dd_from_double(i); }
+__device__ __forceinline__ void cvt(double& o, dd i) { o = dd_to_double(i); }
 template <typename To, typename From>
 __device__ __forceinline__ C<To> ccvt(const C<From>& i) {
   C<To> o;

@@ -422,7 +422,7 @@ __device__ __forceinline__ dd warp_sum(dd v) {
   return v;
 }
 __device__ __forceinline__ double to_double_val(float v) { return (double)v; }
-__device__ __forceinline__ double to_double_val(dd v) { return v.to_double(); }
+__device__ __forceinline__ double to_double_val(dd v) { return dd_to_double(v); }
 
 template <typename T, int D>
 __device__ __forceinline__ void point_weights(T* wts /*[D][kMaxW]*/, const T* __restrict__ delta,
@@ -597,8 +597,8 @@ __device__ __forceinline__ float weight_of<float>(float delta, int q, int w, dou
 template <>
 __device__ __forceinline__ dd weight_of<dd>(double delta, int q, int, double, dd s2w, dd bdd) {
   // phi(z) = exp(beta (sqrt(1 - z^2) - 1)), z = (2/w)(q + delta), in double-float on the FP32
-  // pipes (the FP64 pipe of this GPU is the slow one); q + delta is exact in FP64.
-  const dd z = dd((double)q + delta) * s2w;
+  // pipes (the FP64 pipe of this GPU is the slow one): delta split into a pair, q added to it.
+  const dd z = (dd((float)q) + dd_from_double(delta)) * s2w;
   const dd s = dd(1.0f) - z * z;
   if (!(s.hi > 0.0f)) return dd(0.0f);
   return dd_exp_nonpos((dd_sqrt(s) - dd(1.0f)) * bdd);
@@ -639,7 +639,9 @@ struct KPointPrep {
     if (Cw && q == 0) {
       const int j = perm[s];
       const double om = omega ? omega[j] : 1.0;
-      Cw[s * D + a] = T(om * cw[(long long)a * M + j]);
+      const double c = om * cw[(long long)a * M + j];
+      if constexpr (std::is_same<T, dd>::value) Cw[s * D + a] = dd_from_double(c);
+      else Cw[s * D + a] = T(c);
     }
   };
   if (nw < (1LL << 31)) {  // 32-bit index arithmetic (the usual case)
