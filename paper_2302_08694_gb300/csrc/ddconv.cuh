@@ -118,37 +118,5 @@ __host__ __device__ inline double widen_float(float f) {
   return u2d(sign | ((uint64_t)(ex - 127 + 1023) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29));
 }
 
-// hi + lo as a double, truncated to 53 bits (error below 2^-52 of the value, under the
-// pair's own 2^-48), when hi is normal and |lo| < |hi| / 2 (exponent of lo at least two below
-// that of hi; lo zero or denormal counts as zero). Returns false otherwise.
-__host__ __device__ inline bool join_pair(float hi, float lo, double& out) {
-  const uint32_t hb = f2u(hi), lb = f2u(lo);
-  const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
-  if (eh == 0 || eh == 255 || el == 255) return false;
-  const uint64_t dsign = (uint64_t)(hb & 0x80000000u) << 32;
-  const uint64_t hm = (uint64_t)(hb & 0x7FFFFFu);
-  if (el == 0) {  // lo is zero (or a denormal, below 2^-126): hi exactly
-    out = u2d(dsign | ((uint64_t)(eh - 127 + 1023) << 52) | (hm << 29));
-    return true;
-  }
-  const int d = eh - el;
-  if (d < 2) return false;
-  // both significands on the scale 2^(eh - 179): hi's occupies bits 52..29
-  const int64_t H = (int64_t)((hm | 0x800000u)) << 29;
-  const uint64_t lmag = (uint64_t)((lb & 0x7FFFFFu) | 0x800000u);
-  int64_t L = 0;
-  if (d <= 29) L = (int64_t)(lmag << (29 - d));
-  else if (d - 29 < 24) L = (int64_t)(lmag >> (d - 29));
-  const bool same = ((hb ^ lb) & 0x80000000u) == 0;
-  const uint64_t S = (uint64_t)(same ? H + L : H - L);  // magnitude, in (2^51, 2^54)
-  // leading bit at 51, 52 or 53: shift it to bit 52 (truncating), adjust the exponent
-  int p = 52;
-  if (S >> 53) p = 53;
-  else if (!(S >> 52)) p = 51;
-  const uint64_t m = (p == 53) ? (S >> 1) : (p == 51 ? (S << 1) : S);
-  out = u2d(dsign | ((uint64_t)(eh - 127 + 1023 + (p - 52)) << 52) | (m & 0xFFFFFFFFFFFFFull));
-  return true;
-}
-
 }  // namespace ddconv
 }  // namespace fsib
