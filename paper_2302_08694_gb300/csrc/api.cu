@@ -8,6 +8,7 @@
 #include <mutex>
 #include <unordered_set>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fsib_internal.cuh"
@@ -579,9 +580,13 @@ static void inverse_fine(fsib_plan* h, const C<TA>* in, TI* grid, cudaStream_t s
   }
 }
 
-// Fourier coefficients on K_N of the products u_a u_b (three-halves rule), as TA; returns the buffer.
+// Fourier coefficients on K_N of the products u_a u_b (three-halves rule); returns the buffer. It
+// holds C<TA> values, or with pairs and double-float transforms the double-float pairs themselves
+// (the Navier-Stokes update reads those without a join and a split per value).
 template <typename TI, typename TA>
-static const C<TA>* products(fsib_plan* h, const C<TA>* u, cudaStream_t st, void* scratch1, void* scratch2) {
+static const void* products(fsib_plan* h, const C<TA>* u, cudaStream_t st, void* scratch1, void* scratch2,
+                            bool pairs = false) {
+  const bool keep = pairs && std::is_same<TI, dd>::value;
   const Plan& p = h->p;
   Workspace& ws = h->ws;
   const int N = p.N, hh = N / 2, nt = p.Nt, d = p.d;
@@ -602,8 +607,9 @@ static const C<TA>* products(fsib_plan* h, const C<TA>* u, cudaStream_t st, void
     { Prof pr(h, "nl.fy_strided", 6.0 * nt * hh * (N + nt) * cs, fft_flops(6.0 * nt * hh, nt), st);
       launch_fft_strided<TI>(s1, s2, 6, nt, hh, N, p.fl_nt, false, none, tw, st); }
     { Prof pr(h, "nl.fz_strided", 6.0 * N * hh * (N + nt) * cs, fft_flops(6.0 * N * hh, nt), st);
-      launch_fft_strided<TI, TI, TA>(s2, (C<TA>*)s1, 6, 1, N * hh, N, p.fl_nt, false, sc, tw, st); }
-    return (const C<TA>*)s1;
+      if (keep) launch_fft_strided<TI>(s2, s1, 6, 1, N * hh, N, p.fl_nt, false, sc, tw, st);
+      else launch_fft_strided<TI, TI, TA>(s2, (C<TA>*)s1, 6, 1, N * hh, N, p.fl_nt, false, sc, tw, st); }
+    return s1;
   } else {
     sc.scale = (TI)(1.0 / ((double)nt * nt));
     { Prof pr(h, "nl.iy_strided", 2.0 * hh * (N + nt) * cs, fft_flops(2.0 * hh, nt), st);
@@ -611,8 +617,9 @@ static const C<TA>* products(fsib_plan* h, const C<TA>* u, cudaStream_t st, void
     { Prof pr(h, "nl.rows_product", 5.0 * nt * hh * cs, fft_flops(0.5 * nt * 5.0, nt), st);
       launch_rows_product<TI>(s2, s1, 2, (long long)nt, N, p.fl_nt, tw, st); }
     { Prof pr(h, "nl.fy_strided", 3.0 * hh * (N + nt) * cs, fft_flops(3.0 * hh, nt), st);
-      launch_fft_strided<TI, TI, TA>(s1, (C<TA>*)s2, 3, 1, hh, N, p.fl_nt, false, sc, tw, st); }
-    return (const C<TA>*)s2;
+      if (keep) launch_fft_strided<TI>(s1, s2, 3, 1, hh, N, p.fl_nt, false, sc, tw, st);
+      else launch_fft_strided<TI, TI, TA>(s1, (C<TA>*)s2, 3, 1, hh, N, p.fl_nt, false, sc, tw, st); }
+    return s2;
   }
 }
 
@@ -694,26 +701,28 @@ static void do_stokeslet(fsib_plan* h, const C<TA>* fhat, C<TA>* u, cudaStream_t
 }
 
 template <typename TI, typename TA>
-// P0: the product coefficients of u^m when they were computed beforehand (see do_step).
+// P0: the product coefficients of u^m when they were computed beforehand (see do_step), as
+// products() returns them with pairs = true.
 static void do_fluid(fsib_plan* h, const C<TA>* fhat, C<TA>* u, C<TA>* uhalf, cudaStream_t st,
-                     const C<TA>* P0 = nullptr) {
+                     const void* P0 = nullptr) {
+  constexpr bool kPairs = std::is_same<TI, dd>::value;  // products kept as double-float pairs
   if (h->p.stokes) {
     do_stokeslet<TA>(h, fhat, u, st);
     return;
   }
   const int d = h->p.d, np = d * (d + 1) / 2;
   const double ub = (double)h->ws.spec_bytes / d * (np + 3 * d);
-  const C<TA>* P = P0 ? P0 : products<TI, TA>(h, u, st, h->ws.s1, h->ws.s2);
+  const void* P = P0 ? P0 : products<TI, TA>(h, u, st, h->ws.s1, h->ws.s2, true);
   { Prof pr(h, "ns_update", ub, 0.0, st);
-    launch_ns_update<TA>(h->p, h->ws.ktab, P, fhat, u, uhalf, true, st); }
-  P = products<TI, TA>(h, uhalf, st, h->ws.s1, h->ws.s2);
+    launch_ns_update<TA>(h->p, h->ws.ktab, P, kPairs, fhat, u, uhalf, true, st); }
+  P = products<TI, TA>(h, uhalf, st, h->ws.s1, h->ws.s2, true);
   { Prof pr(h, "ns_update", ub, 0.0, st);
-    launch_ns_update<TA>(h->p, h->ws.ktab, P, fhat, u, u, false, st); }
+    launch_ns_update<TA>(h->p, h->ws.ktab, P, kPairs, fhat, u, u, false, st); }
 }
 
 template <typename TI, typename TA>
 static void do_pressure(fsib_plan* h, const C<TA>* fhat, const C<TA>* u, C<TA>* phat, cudaStream_t st) {
-  const C<TA>* P = (!h->p.stokes && u) ? products<TI, TA>(h, u, st, h->ws.s1, h->ws.s2) : nullptr;
+  const C<TA>* P = (!h->p.stokes && u) ? (const C<TA>*)products<TI, TA>(h, u, st, h->ws.s1, h->ws.s2) : nullptr;
   launch_pressure<TA>(h->p, P, fhat, phat, st);
 }
 
@@ -752,7 +761,8 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
       cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     }
     if (u_in) cudaMemcpyAsync(uhat, u_in, ws.spec_bytes, cudaMemcpyHostToDevice, sb);
-    const C<TA>* P0 = products<TI, TA>(h, uhat, sb, ws.s3, ws.s4);
+    constexpr bool kPairs = std::is_same<TI, dd>::value;  // products kept as double-float pairs
+    const void* P0 = products<TI, TA>(h, uhat, sb, ws.s3, ws.s4, true);
     if (fork) cudaEventRecord(h->ev_join, h->side);
     do_axpy(h, ws.Xh, X, U, 0.5 * p.dt, st);                    // Eq. spatial_1
     do_force(h, ws.Xh, ws.cw, st);                               // F^{m+1/2}
@@ -764,16 +774,16 @@ static void do_step(fsib_plan* h, double* X, C<TA>* uhat, double* U, cudaStream_
     // U^{m+1/2} interp and the re-sort.
     const double ub = (double)ws.spec_bytes / p.d * (p.d * (p.d + 1) / 2 + 3 * p.d);
     { Prof pr(h, "ns_update", ub, 0.0, st);
-      launch_ns_update<TA>(p, ws.ktab, P0, fhat, uhat, uh, true, st); }
+      launch_ns_update<TA>(p, ws.ktab, P0, kPairs, fhat, uhat, uh, true, st); }
     if (fork) {
       cudaEventRecord(h->ev_fork3, st);
       cudaStreamWaitEvent(h->side, h->ev_fork3, 0);
     }
     inverse_fine<TI, TA>(h, uh, (TI*)ws.grid, sb, ws.s3, ws.s4, 1);  // binning of X^{m+1/2}
     if (fork) cudaEventRecord(h->ev_join3, h->side);
-    const C<TA>* P1 = products<TI, TA>(h, uh, st, ws.s1, ws.s2);
+    const void* P1 = products<TI, TA>(h, uh, st, ws.s1, ws.s2, true);
     { Prof pr(h, "ns_update", ub, 0.0, st);
-      launch_ns_update<TA>(p, ws.ktab, P1, fhat, uhat, uhat, false, st); }
+      launch_ns_update<TA>(p, ws.ktab, P1, kPairs, fhat, uhat, uhat, false, st); }
     if (fork) {
       cudaEventRecord(h->ev_fork2, st);
       cudaStreamWaitEvent(h->side, h->ev_fork2, 0);

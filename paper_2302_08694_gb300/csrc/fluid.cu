@@ -1,4 +1,6 @@
 // Fourier-space fluid solves on the half spectrum (Secs. 3.1-3.3, 6.1).
+#include <cstdio>
+#include <cstdlib>
 #include <type_traits>
 
 #include "fsib_internal.cuh"
@@ -172,12 +174,13 @@ __device__ __forceinline__ double join_dd(dd a) { return dd_to_double(a); }
 struct DDc { dd x, y; };
 __device__ __forceinline__ DDc ddc(double2 v) { return {dd_from_double(v.x), dd_from_double(v.y)}; }
 
-template <int D>
+template <int D, bool PAIRS>
 struct KNsUpdateDD {
   static constexpr int kThreads = 256, kMinBlocks = 0;
   static constexpr bool kAnyGrid = true;
+  // prod_: the product coefficients as double2, or as double-float pairs (dd2) when PAIRS
   __device__ static void run(SpecGeom g, dd kunit, dd inv_rho, dd mu_dt_over_rho, dd dt, bool half, Body fb,
-                             const double2* __restrict__ prod, const double2* __restrict__ f,
+                             const void* __restrict__ prod_, const double2* __restrict__ f,
                              const double2* __restrict__ base, double2* __restrict__ out) {
   // 32-bit mode indices (fewer than 2^31 modes at every supported size)
   const unsigned nspec = (unsigned)g.nspec, hh = (unsigned)g.h, NN = (unsigned)g.N;
@@ -197,7 +200,13 @@ struct KNsUpdateDD {
       for (int b = 0; b < d; ++b) {
         const int lo = a < b ? a : b, hi = a < b ? b : a;
         const int ab = (d == 3) ? (lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)) : (lo + hi);
-        const DDc pv = ddc(prod[ab * g.nspec + idx]);
+        DDc pv;
+        if constexpr (PAIRS) {
+          const dd2 q = static_cast<const dd2*>(prod_)[ab * g.nspec + idx];
+          pv = {q.x, q.y};
+        } else {
+          pv = ddc(static_cast<const double2*>(prod_)[ab * g.nspec + idx]);
+        }
         sx = sx + pv.x * k[b];
         sy = sy + pv.y * k[b];
       }
@@ -264,8 +273,8 @@ void launch_pressure(const Plan& p, const C<T>* prod, const C<T>* fhat, C<T>* ph
 }
 
 template <typename T>
-void launch_ns_update(const Plan& p, const void* ktab, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
-                      C<T>* out, bool half, cudaStream_t st) {
+void launch_ns_update(const Plan& p, const void* ktab, const void* prod, bool prod_pairs, const C<T>* fhat,
+                      const C<T>* ubase, C<T>* out, bool half, cudaStream_t st) {
   const SpecGeom g = sgeom(p);
   const Body fb = {{p.fbody[0], p.fbody[1], p.fbody[2]}};
   if constexpr (std::is_same<T, double>::value) {
@@ -273,17 +282,26 @@ void launch_ns_update(const Plan& p, const void* ktab, const C<T>* prod, const C
       auto run = [&](auto k) {
         using K = typename decltype(k)::type;
         launch<K>(grid_for(g.nspec), 256, 0, st, g, dd(g.kunit), dd(1.0 / p.rho), dd(p.mu * p.dt / p.rho), dd(p.dt),
-                  half, fb, (const double2*)prod, (const double2*)fhat, (const double2*)ubase, (double2*)out);
+                  half, fb, prod, (const double2*)fhat, (const double2*)ubase, (double2*)out);
       };
-      if (p.d == 3) run(type_tag<KNsUpdateDD<3>>());
-      else run(type_tag<KNsUpdateDD<2>>());
+      if (p.d == 3) {
+        if (prod_pairs) run(type_tag<KNsUpdateDD<3, true>>());
+        else run(type_tag<KNsUpdateDD<3, false>>());
+      } else {
+        if (prod_pairs) run(type_tag<KNsUpdateDD<2, true>>());
+        else run(type_tag<KNsUpdateDD<2, false>>());
+      }
       return;
     }
+  }
+  if (prod_pairs) {
+    std::fprintf(stderr, "fsib: double-float product pairs reach a non double-float update\n");
+    std::abort();
   }
   auto run = [&](auto k) {
     using K = typename decltype(k)::type;
     launch<K>(grid_for(g.nspec), 256, 0, st, g, (const T*)ktab, (T)(1.0 / p.rho), (T)(p.mu * p.dt / p.rho), (T)p.dt,
-              half, fb, prod, fhat, ubase, out);
+              half, fb, (const C<T>*)prod, fhat, ubase, out);
   };
   if (p.d == 3) run(type_tag<KNsUpdate<T, 3>>());
   else run(type_tag<KNsUpdate<T, 2>>());
@@ -301,9 +319,9 @@ template void launch_stokeslet<float>(const Plan&, const C<float>*, C<float>*, c
 template void launch_stokeslet<double>(const Plan&, const C<double>*, C<double>*, cudaStream_t);
 template void launch_pressure<float>(const Plan&, const C<float>*, const C<float>*, C<float>*, cudaStream_t);
 template void launch_pressure<double>(const Plan&, const C<double>*, const C<double>*, C<double>*, cudaStream_t);
-template void launch_ns_update<float>(const Plan&, const void*, const C<float>*, const C<float>*, const C<float>*,
+template void launch_ns_update<float>(const Plan&, const void*, const void*, bool, const C<float>*, const C<float>*,
                                       C<float>*, bool, cudaStream_t);
-template void launch_ns_update<double>(const Plan&, const void*, const C<double>*, const C<double>*, const C<double>*,
-                                       C<double>*, bool, cudaStream_t);
+template void launch_ns_update<double>(const Plan&, const void*, const void*, bool, const C<double>*,
+                                       const C<double>*, C<double>*, bool, cudaStream_t);
 
 }  // namespace fsib

@@ -248,9 +248,11 @@ template <typename T>
 void launch_stokeslet(const Plan& p, const C<T>* fhat, C<T>* uhat, cudaStream_t st);
 template <typename T>
 void launch_pressure(const Plan& p, const C<T>* prod, const C<T>* fhat, C<T>* phat, cudaStream_t st);
+// prod: the product coefficients, C<T> values, or double-float pairs (dd2) when prod_pairs (FP64
+// mode with double-float transforms only).
 template <typename T>
-void launch_ns_update(const Plan& p, const void* ktab, const C<T>* prod, const C<T>* fhat, const C<T>* ubase,
-                      C<T>* out, bool half, cudaStream_t st);
+void launch_ns_update(const Plan& p, const void* ktab, const void* prod, bool prod_pairs, const C<T>* fhat,
+                      const C<T>* ubase, C<T>* out, bool half, cudaStream_t st);
 
 void launch_axpy(double* y, const double* x, const double* v, double a, long long n, cudaStream_t st);
 void launch_force(const Plan& p, const Workspace& ws, const double* X, double* c, cudaStream_t st);
